@@ -1,0 +1,64 @@
+"""Workload recipes: a mesh, its rig, its material constants and seeded poses.
+
+Each recipe returns a plain dict of arrays.  Rigs name handles by joint index;
+``cluster_rule`` says how tets pick a handle rotation ("bone": nearest bone
+segment, "joint": nearest joint) and pins are either explicit (``pin_verts``,
+``pin_handle``) or chosen by radius around joints and bone midpoints.
+"""
+from __future__ import annotations
+
+import functools
+
+import numpy as np
+
+from .meshes import bar_mesh, figure_mesh_for_tets
+from .poses import bar_twist_pose, figure_pose
+
+# Stable neo-Hookean figure material: Young's modulus (Pa) and Poisson ratio.
+SNH_E = 1.0e5
+SNH_NU = 0.45
+
+
+def lame_from_young(E, nu):
+    """Lame constants (mu, lambda) of an isotropic material."""
+    mu = E / (2.0 * (1.0 + nu))
+    lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu))
+    return mu, lam
+
+
+def bar_twist_config(nx=4, ny=4, nz=16):
+    """The 4x4x16 bar: ARAP, handle 0 fixed at z=0, handle 1 at z=nz turned
+    90 deg about the long axis and shifted 0.5 along it; every vertex of an end
+    face is pinned to that face's handle; tets take the nearest handle."""
+    X, T = bar_mesh(nx, ny, nz)
+    joints = np.array([[nx / 2, ny / 2, 0.0], [nx / 2, ny / 2, float(nz)]])
+    parent = np.array([-1, -1], dtype=np.int32)
+    lo = np.where(X[:, 2] == 0.0)[0]
+    hi = np.where(X[:, 2] == float(nz))[0]
+    pin_verts = np.concatenate([lo, hi]).astype(np.int32)
+    pin_handle = np.concatenate([np.zeros(len(lo)), np.ones(len(hi))]).astype(np.int32)
+    return dict(
+        name=f"bar{nx}x{ny}x{nz}", X=X, T=T, joints=joints, parent=parent,
+        cluster_rule="joint", pin_verts=pin_verts, pin_handle=pin_handle, pin_radius=0.0,
+        model="arap", mu=1.0, lam=0.0, xfs=bar_twist_pose(nx, ny, nz)[None],
+    )
+
+
+@functools.lru_cache(maxsize=8)
+def _figure_mesh_cached(target_tets, scale):
+    return figure_mesh_for_tets(target_tets, scale)
+
+
+def figure_config(target_tets=200_000, model="snh", seeds=range(16), scale=1.0,
+                  E=SNH_E, nu=SNH_NU, pin_radius_cells=1.5):
+    """Capsule stick figure voxelised to ~target_tets, 15 joint handles,
+    FK poses seeded by ``seeds`` (+-45 deg turns, +-0.1 root shift)."""
+    X, T, joints, parent, h = _figure_mesh_cached(int(target_tets), float(scale))
+    mu, lam = lame_from_young(E, nu)
+    xfs = np.stack([figure_pose(joints, parent, s) for s in seeds]) if len(seeds) else \
+        np.zeros((0, len(joints), 12))
+    return dict(
+        name=f"figure{len(T)}", X=X.copy(), T=T.copy(), joints=joints, parent=parent,
+        cluster_rule="bone", pin_verts=None, pin_handle=None, pin_radius=pin_radius_cells * h,
+        model=model, mu=mu, lam=lam, xfs=xfs, h=h,
+    )
