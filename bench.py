@@ -1,0 +1,396 @@
+#!/usr/bin/env python3
+"""Pose-solve throughput of the mixed-FEM skinning solver on one GB300.
+
+Workload: the capsule stick figure voxelised to ~200k tets (~40k verts), stable
+neo-Hookean (E = 1e5 Pa, nu = 0.45), 15 joint handles, a batch of seeded FK
+poses (+-45 deg per joint, +-0.1 root shift), each pose solved to a 1e-6
+relative FP64 free-gradient residual.  One step = one batch of poses through
+the whole path (pose update, element step, assembly with pin elimination,
+block-Jacobi PCG, line search, update, output).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl mfem|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs its own replica
+on its own GPU (different pose seeds); value = all poses / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "pose-solve frames/s & p50/p99 latency vs plain FP64 GPU path at 1e-6 residual"
+UNIT = "frames/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="mfem", choices=["mfem", "reference"])
+    p.add_argument("--tets", type=int, default=200000)
+    p.add_argument("--batch", type=int, default=16)
+    p.add_argument("--model", default="snh")
+    p.add_argument("--precision", default="mixed")
+    p.add_argument("--fp64-steps", type=int, default=2)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-newton-steps", type=int, default=2)
+    return p.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group("gloo", rank=self.rank, world_size=self.world)
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, v):
+        if not self.pg:
+            return v
+        import torch
+        t = torch.tensor([float(v)], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, v):
+        if not self.pg:
+            return v
+        import torch
+        t = torch.tensor([float(v)], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.SUM)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples (200 ms) while the timed region runs."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+        self.th = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.th = threading.Thread(target=self._read, daemon=True)
+        self.th.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([c.strip() for c in line.split(",")])
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.th.join(timeout=5)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+                power.append(float(r[3]))
+            except (ValueError, IndexError):
+                continue
+            for i, nm in enumerate(names):
+                if len(r) > 5 + i and r[5 + i].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+def hbm_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def pcg_traffic_record():
+    """DRAM bytes per PCG launch from the committed ncu summary, if it was taken
+    on the current kernel source (hash match); else None."""
+    import hashlib
+    rec = os.path.join(ROOT, "profiles", "pcg_traffic.json")
+    src = os.path.join(ROOT, "paper_2408_04066_gb300", "csrc", "k_rows.cu")
+    try:
+        with open(rec) as f:
+            r = json.load(f)
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return r if r.get("k_rows_sha256_16") == h else None
+    except (OSError, ValueError):
+        return None
+
+
+# ---------------------------------------------------------------- CPU oracle
+def newton_steps_per_frame():
+    path = os.path.join(ROOT, "tests", "golden", "figure200k_newton_steps.txt")
+    try:
+        rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
+        return statistics.mean(float(r[1]) for r in rows), path
+    except (OSError, ValueError, statistics.StatisticsError):
+        return None, path
+
+
+def _oracle_newton_steps(tets, model, seed, nsteps, q):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    sys.path.insert(0, ROOT)
+    from oracle import solve as S
+    from synth import figure_config
+    cfg = figure_config(tets, model=model, seeds=[seed])
+    st = S.Setup.from_config(cfg)
+    times = []
+    for k in range(nsteps):
+        t0 = time.perf_counter()
+        S.solve(st, cfg["xfs"][0], model, newton_max=1, newton_tol=1e-6, linear="cg", cg_tol=1e-3)
+        times.append(time.perf_counter() - t0)
+    q.put(times)
+
+
+def oracle_step_times(tets, model, seed, nsteps):
+    """Time `nsteps` single oracle Newton steps (CG mode) in a spawned process."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_oracle_newton_steps, args=(tets, model, seed, nsteps, q))
+    p.start()
+    times = q.get()
+    p.join()
+    return times
+
+
+def cpu_baseline(args, steps_frame):
+    times = oracle_step_times(args.tets, args.model, 0, args.cpu_newton_steps)
+    t = statistics.mean(times)
+    spf, src = newton_steps_per_frame()
+    if spf is None:
+        spf = steps_frame
+        src = "GPU-measured Newton steps per frame"
+    return {"value": 1.0 / (t * spf), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"{len(times)} oracle Newton steps (FP64, Jacobi-PCG to 1e-3) of pose 0 on the "
+                       f"{args.tets // 1000}k-tet figure, {t:.2f} s each, x {spf:.2f} Newton steps per frame "
+                       f"(oracle counts, {os.path.relpath(src, ROOT) if os.path.isabs(src) else src}); "
+                       f"BLAS/OpenMP threads = 1")}
+
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return
+    from synth import figure_config
+    figure_config(args.tets, model=args.model, seeds=[0])   # mesh generation is setup, not timed
+    total = oracle_step_times(args.tets, args.model, 0, args.warmup + args.steps)
+    times = total[args.warmup:]
+    t = statistics.mean(times)
+    spf, src = newton_steps_per_frame()
+    spf = spf or 1.0
+    value = 1.0 / (t * spf)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"figure{args.tets // 1000}k-{args.model}", "tets": args.tets,
+                   "model": args.model},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step = one oracle Newton step (FP64, Jacobi-PCG 1e-3) of pose 0; "
+                                   f"frames/s = 1 / (mean step time x {spf:.2f} Newton steps per frame)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def run_mfem(args, dist):
+    import numpy as np
+    import torch
+    from paper_2408_04066_gb300 import build as B
+    B.build()
+    from paper_2408_04066_gb300 import mfem
+    from synth import figure_config
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    nb = args.batch
+    cfg = figure_config(args.tets, model=args.model, seeds=range(dist.rank * nb, dist.rank * nb + nb))
+    opts = dict(precision=args.precision, max_batch=nb, newton_tol=1e-6)
+    ctx = mfem.Context.from_config(cfg, **opts)
+    stream = torch.cuda.current_stream(dev)
+    ctx.set_stream(stream.cuda_stream)
+    info = ctx.info()
+    xfs = torch.tensor(cfg["xfs"], dtype=torch.float64, device=dev)
+    out = torch.empty((nb, info["n"], 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)       # > 129 MB L2
+
+    for _ in range(args.warmup):
+        ctx.solve_batch(xfs, out)
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(dist.local)
+    step_ms, prof, stats_all = [], [], []
+    clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = ctx.solve_batch(xfs, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        prof.append(ctx.profile())
+        stats_all.append(st)
+    dist.barrier()
+    clk = clocks.stop()
+    total_ms = sum(step_ms)
+    total_ms_max = dist.max(total_ms)
+    poses = dist.sum(nb * args.steps)
+    value = poses / (total_ms_max / 1e3)
+
+    # roofline of the dominant kernel (persistent PCG)
+    pcg_ms = sum(p["pcg_ms"] for p in prof)
+    pcg_bytes = sum(p["pcg_bytes"] for p in prof)
+    pcg_launches = sum(p["pcg_launches"] for p in prof)
+    peak, peak_kind = hbm_peak()
+    achieved = pcg_bytes / (pcg_ms / 1e3) / 1e9 if pcg_ms > 0 else 0.0
+    tr = pcg_traffic_record()
+    roof = {"kernel": "k_pcg (persistent PCG)", "bound": "hbm", "achieved": achieved, "peak": peak,
+            "peak_source": f"{peak_kind} hbm_gbs", "unit": "GB/s", "frac": achieved / peak,
+            "traffic": (tr["dram_bytes_per_launch"] if tr else None),
+            "algorithmic_bytes_per_launch": pcg_bytes / max(pcg_launches, 1),
+            "avg_launch_ms": pcg_ms / max(pcg_launches, 1), "launches": pcg_launches,
+            "share_of_step": pcg_ms / total_ms if total_ms else None}
+    newton = [s["newton_iters"] for st in stats_all for s in st]
+    pcg_it = [s["pcg_iters"] for st in stats_all for s in st]
+    conv = all(s["converged"] for st in stats_all for s in st)
+    launches = sum(p["kernel_launches"] for p in prof)
+
+    # end to end through the public API with host buffers (copies inside the call)
+    xfs_h = torch.tensor(cfg["xfs"], dtype=torch.float64).pin_memory()
+    out_h = torch.empty((nb, info["n"], 3), dtype=torch.float64).pin_memory()
+    e2e_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        dist.barrier()
+        t0 = time.perf_counter()
+        ctx.solve_batch(xfs_h.numpy(), out_h.numpy())
+        e2e_ms.append(1e3 * (time.perf_counter() - t0))
+    e2e_value = dist.sum(nb * args.steps) / (dist.max(sum(e2e_ms)) / 1e3)
+
+    # plain FP64 GPU path, same workload and tolerance
+    fp64 = None
+    if args.fp64_steps > 0 and args.precision != "fp64":
+        ctx64 = mfem.Context.from_config(cfg, **dict(opts, precision="fp64"))
+        ctx64.set_stream(stream.cuda_stream)
+        ctx64.solve_batch(xfs, out)
+        ms64, st64 = [], []
+        for _ in range(args.fp64_steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            x64, s64 = ctx64.solve_batch(xfs, out)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms64.append(e0.elapsed_time(e1))
+            st64 += s64
+        p64 = ctx64.profile()
+        fp64 = {"value": dist.sum(nb * args.fp64_steps) / (dist.max(sum(ms64)) / 1e3), "unit": UNIT,
+                "ms_per_step": statistics.mean(ms64),
+                "newton_iters_mean": statistics.mean(s["newton_iters"] for s in st64),
+                "pcg_iters_mean": statistics.mean(s["pcg_iters"] for s in st64),
+                "pcg_GBps": p64["pcg_bytes"] / (p64["pcg_ms"] / 1e3) / 1e9 if p64["pcg_ms"] else None}
+        # mixed vs FP64 agreement at the timed tolerance, per pose
+        xm, _ = ctx.solve_batch(xfs)
+        x64, _ = ctx64.solve_batch(xfs)
+        bbox = float(np.linalg.norm(cfg["X"].max(0) - cfg["X"].min(0)))
+        fp64["mixed_vs_fp64_max_err_over_bbox"] = float((xm - x64).abs().max().item() / bbox)
+        ctx64.close()
+
+    cpu = None
+    if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args, statistics.mean(newton))
+
+    if dist.rank == 0:
+        lat = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": {"workload": f"figure{info['m'] // 1000}k-{args.model}-batch{nb}", "tets": info["m"],
+                       "verts": info["n"], "handles": info["n_handles"], "pins": info["n_pins"],
+                       "batch_poses": nb, "precision": args.precision, "newton_tol": 1e-6,
+                       "l2": "256 MiB buffer written between timed steps; per-step working set > L2",
+                       "parallelism": f"replicas x{dist.world}"},
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "note": "per batch step; every pose of a batch completes with the step"},
+            "plain_fp64": fp64,
+            "newton_iters_mean": statistics.mean(newton), "pcg_iters_mean": statistics.mean(pcg_it),
+            "all_converged": conv,
+            "roofline": roof, "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xfs_h.numel() * 8),
+                    "d2h_bytes_per_step": int(out_h.numel() * 8)},
+            "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_mfem(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

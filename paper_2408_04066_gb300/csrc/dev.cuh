@@ -1,0 +1,169 @@
+// Device-side structures and helpers shared by the kernels of the pose solver.
+//
+// Reductions are deterministic: every per-problem sum is formed per fixed tile
+// of rows (or tets), tile partials are written to global memory, and the last
+// tile to finish (a ticket counter) adds the partials in tile order.  The result
+// therefore does not depend on the grid, on scheduling, or on which other
+// problems share the launch.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace mfem {
+
+constexpr int kWarp = 32;
+constexpr int kSliceRows = 32;       // rows per SELL slice (one warp)
+constexpr int kTetTile = 128;        // tets per element-kernel block
+constexpr int kRowTile = 256;        // rows per block in row kernels other than PCG
+constexpr int kKe = 90;              // 10 upper 3x3 blocks of a symmetric 12x12
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
+
+// Problem states (PCG)
+enum : int { kIdle = 0, kActive = 1, kConverged = 2, kMaxIter = 3 };
+
+// Per-problem scalars.  Tickets are reset to 0 by the tile that completes them.
+struct ProbScal {
+    double rho, alpha, beta, rr0, rr, tol2;
+    double gnorm2, energy, slope, energy_trial;
+    double alpha_ls, pad0;
+    int iter, state, maxit, active;
+    unsigned tk_a, tk_b, tk_g, tk_e, tk_s, tk_init, tk_pad0, tk_pad1;
+};
+
+// Grid barrier state of one persistent launch.
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+    int err;
+    int pad;
+};
+
+// One PCG problem (a pose of a mesh) inside a persistent launch.
+template <typename T>
+struct PcgDesc {
+    const int* slice_ptr;  // [n_slices+1] first slot of each slice
+    const int* col;        // [slots] column block or -1
+    const T* val;          // [slots/32][9][32]
+    const T* dinv;         // [n][9] inverse diagonal blocks
+    T* dx;
+    T* r;
+    T* z;
+    T* p0;
+    T* p1;
+    T* q;                  // [n][3] each
+    double* part;          // [tiles][4] tile partials
+    ProbScal* sc;
+    int n_rows, n_tiles, unit_begin, pad;
+};
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(volatile const int*)p; }
+
+// Sum NV doubles over the block with a fixed shuffle/shared-memory tree.  The
+// result is valid in thread 0.  All threads of the block must call it.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+    __shared__ double sm[32][NV];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int nwarps = (blockDim.x + 31) >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    __syncthreads();
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) sm[warp][i] = v[i];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) v[i] = lane < nwarps ? sm[lane][i] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
+    __syncthreads();
+}
+
+// Commit this block's NV partial sums for `tile` of a problem; the block that
+// completes the ticket adds all tiles in order and returns true with the totals
+// in `tot` (valid in thread 0 only).  part layout: [n_tiles][4], NV <= 4.
+template <int NV>
+__device__ __forceinline__ bool tile_commit(double (&v)[NV], double* part, int tile, int n_tiles,
+                                            unsigned* ticket, int slot0, double (&tot)[NV]) {
+    __shared__ int s_last;
+    block_sum<NV>(v);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) part[4 * tile + slot0 + i] = v[i];
+        __threadfence();
+        unsigned prev = atomicAdd(ticket, 1u);
+        s_last = (prev == (unsigned)(n_tiles - 1));
+    }
+    __syncthreads();
+    if (!s_last) return false;
+    __threadfence();
+    double acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) acc[i] = 0.0;
+    for (int t = threadIdx.x; t < n_tiles; t += blockDim.x)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) acc[i] += *(volatile double*)&part[4 * t + slot0 + i];
+    block_sum<NV>(acc);
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) tot[i] = acc[i];
+        *ticket = 0u;
+    }
+    return true;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The wait
+// is bounded: after kBarrierTimeoutNs the block records bar->err = 1 and leaves;
+// callers check grid_failed() after every barrier and stop.
+__device__ __forceinline__ void grid_sync(GridBar* bar) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
+        unsigned g = ld_acquire_u32(&bar->gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(&bar->count, 1u);
+        if (arrived == nb - 1) {
+            bar->count = 0u;
+            __threadfence();
+            st_release_u32(&bar->gen, g + 1u);
+        } else {
+            unsigned long long t0 = globaltimer_ns();
+            while (ld_acquire_u32(&bar->gen) == g) {
+                __nanosleep(40);
+                if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
+                    atomicExch(&bar->err, 1);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ bool grid_failed(const GridBar* bar) { return ld_volatile_i32(&bar->err) != 0; }
+
+}  // namespace mfem

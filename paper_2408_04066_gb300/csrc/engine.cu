@@ -1,0 +1,998 @@
+// Solver engine: context creation (device upload of the planned mesh), the
+// Newton driver (paper Algorithm 1 and the Newton form of Eq. 12), and the C ABI.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "engine.h"
+
+namespace {
+thread_local std::string g_thread_err = "no error";
+
+constexpr double kLsC = 1.0e-4;      // Armijo constant
+constexpr int kLsMax = 20;           // halvings
+constexpr double kLsNoise = 1.0e-10; // predicted decrease below this * |E|: take the step
+constexpr int kPcgTiles[3] = {64, 128, 256};
+}  // namespace
+
+namespace mfem {
+
+mfem_status ctx_fail(mfem_ctx* c, mfem_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    g_thread_err = msg;
+    return s;
+}
+
+mfem_status cuda_check(mfem_ctx* c, cudaError_t e, const char* what) {
+    if (e == cudaSuccess) return MFEM_OK;
+    std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+    return ctx_fail(c, e == cudaErrorMemoryAllocation ? MFEM_ENOMEM : MFEM_ECUDA, msg);
+}
+
+#define CK(expr)                                                       \
+    do {                                                               \
+        mfem_status _s = cuda_check(c, (expr), #expr);                 \
+        if (_s != MFEM_OK) return _s;                                  \
+    } while (0)
+
+int Profiler::begin(int k, cudaStream_t s) {
+    if (used + 1 >= (int)ev.size() / 2) return -1;
+    int idx = used++;
+    kind.push_back(k);
+    cudaEventRecord(ev[2 * idx], s);
+    return idx;
+}
+
+void Profiler::end(int idx, cudaStream_t s) {
+    if (idx >= 0) cudaEventRecord(ev[2 * idx + 1], s);
+}
+
+ElemArgs elem_args(const mfem_ctx* c) {
+    ElemArgs a;
+    a.mesh = c->mesh;
+    a.slot = c->slot;
+    a.model = c->model;
+    a.constraint = c->opt.constraint;
+    a.ks = c->opt.k_s;
+    return a;
+}
+
+namespace {
+
+template <typename U>
+mfem_status upload(mfem_ctx* c, U** dst, const U* src, size_t count) {
+    *dst = nullptr;
+    if (count == 0) return MFEM_OK;
+    CK(cudaMalloc((void**)dst, count * sizeof(U)));
+    c->mesh_bytes += count * sizeof(U);
+    CK(cudaMemcpy(*dst, src, count * sizeof(U), cudaMemcpyHostToDevice));
+    return MFEM_OK;
+}
+
+void free_slots(mfem_ctx* c) {
+    SlotDev& S = c->slot;
+    void* ptrs[] = {S.xf, S.x, S.xp, S.g, S.ge, S.Ke, S.val, S.dinv, S.vec, S.part, S.sc, S.active, S.alpha, S.outbuf};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    int prec = S.prec;
+    S = SlotDev();
+    S.prec = prec;
+    c->slot_bytes = 0;
+}
+
+int part_tiles_for(const mfem_ctx* c) {
+    int a = (c->plan.n + 63) / 64, b = (c->plan.m + kTetTile - 1) / kTetTile;
+    return std::max(std::max(a, b), 1);
+}
+
+size_t bytes_per_slot(const mfem_ctx* c) {
+    const size_t n = c->plan.n, m = c->plan.m, H = c->plan.H;
+    const size_t kt = c->slot.prec == 1 ? 4 : 8;
+    const size_t slots = (size_t)c->plan.slice_ptr.back();
+    return H * 12 * 8 + 4 * n * 3 * 8 + m * 12 * 8 + m * kKe * kt + slots * 9 * kt + n * 9 * kt +
+           6 * n * 3 * kt + (size_t)part_tiles_for(c) * 4 * 8 + sizeof(ProbScal) + 4 + 8;
+}
+
+mfem_status alloc_slots(mfem_ctx* c, int B) {
+    SlotDev& S = c->slot;
+    const size_t n = c->plan.n, m = c->plan.m, H = c->plan.H;
+    const size_t kt = S.prec == 1 ? 4 : 8;
+    const size_t slots = (size_t)c->plan.slice_ptr.back();
+    S.part_tiles = part_tiles_for(c);
+    auto al = [&](void** p, size_t bytes) -> mfem_status {
+        CK(cudaMalloc(p, std::max<size_t>(bytes, 16)));
+        c->slot_bytes += bytes;
+        return MFEM_OK;
+    };
+    mfem_status st;
+#define AL(ptr, bytes) \
+    if ((st = al((void**)&(ptr), (bytes))) != MFEM_OK) return st;
+    AL(S.xf, B * H * 12 * 8);
+    AL(S.x, B * n * 3 * 8);
+    AL(S.xp, B * n * 3 * 8);
+    AL(S.g, B * n * 3 * 8);
+    AL(S.outbuf, B * n * 3 * 8);
+    AL(S.ge, B * m * 12 * 8);
+    AL(S.Ke, B * m * kKe * kt);
+    AL(S.val, B * slots * 9 * kt);
+    AL(S.dinv, B * n * 9 * kt);
+    AL(S.vec, B * 6 * n * 3 * kt);
+    AL(S.part, B * (size_t)S.part_tiles * 4 * 8);
+    AL(S.sc, B * sizeof(ProbScal));
+    AL(S.active, B * sizeof(int));
+    AL(S.alpha, B * sizeof(double));
+#undef AL
+    CK(cudaMemset(S.sc, 0, B * sizeof(ProbScal)));
+    CK(cudaMemset(S.val, 0, B * slots * 9 * kt));   // padding slots stay zero
+    CK(cudaMemset(S.vec, 0, B * 6 * n * 3 * kt));
+    S.cap = B;
+    // every slot starts at the rest shape (the WARM start without history)
+    for (int b = 0; b < B; ++b)
+        CK(cudaMemcpy(S.x + (size_t)b * n * 3, c->mesh.X, n * 3 * 8, cudaMemcpyDeviceToDevice));
+    c->has_state.assign(B, 0);
+    // pinned host staging
+    if (c->sc_host) cudaFreeHost(c->sc_host);
+    if (c->active_host) cudaFreeHost(c->active_host);
+    if (c->alpha_host) cudaFreeHost(c->alpha_host);
+    if (c->alpha_ring) cudaFreeHost(c->alpha_ring);
+    CK(cudaMallocHost((void**)&c->sc_host, B * sizeof(ProbScal)));
+    CK(cudaMallocHost((void**)&c->active_host, (size_t)kStageRing * B * sizeof(int)));
+    CK(cudaMallocHost((void**)&c->alpha_host, B * sizeof(double)));
+    CK(cudaMallocHost((void**)&c->alpha_ring, (size_t)kStageRing * B * sizeof(double)));
+    c->ring_pos = 0;
+    size_t dcap = 2 * B * std::max(sizeof(PcgDesc<float>), sizeof(PcgDesc<double>));
+    if (dcap > c->descs_cap) {
+        if (c->descs_dev) cudaFree(c->descs_dev);
+        if (c->descs_host) cudaFreeHost(c->descs_host);
+        CK(cudaMalloc(&c->descs_dev, dcap));
+        CK(cudaMallocHost(&c->descs_host, dcap));
+        c->descs_cap = dcap;
+    }
+    return MFEM_OK;
+}
+
+}  // namespace
+
+size_t slot_bytes_for(const mfem_ctx* c, int B) { return bytes_per_slot(c) * (size_t)B; }
+
+mfem_status ensure_slots(mfem_ctx* c, int B) {
+    if (B <= c->slot.cap) return MFEM_OK;
+    free_slots(c);
+    return alloc_slots(c, B);
+}
+
+void begin_profile(mfem_ctx* c) {
+    c->prof.reset();
+    cudaEventRecord(c->prof.start, c->stream);
+}
+
+void end_profile(mfem_ctx* c) {
+    cudaEventRecord(c->prof.stop, c->stream);
+    cudaEventSynchronize(c->prof.stop);
+    mfem_profile& P = c->last_profile;
+    P = mfem_profile();
+    P.kernel_launches = c->prof.launches;
+    P.pcg_launches = c->prof.pcg_launches;
+    P.element_launches = c->prof.element_launches;
+    P.pcg_bytes = c->prof.pcg_bytes;
+    P.element_bytes = c->prof.element_bytes;
+    P.pcg_iters = c->prof.pcg_iters;
+    P.tile_rows = c->tile_rows;
+    P.grid_blocks = c->grid_blocks;
+    for (int i = 0; i < c->prof.used; ++i) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, c->prof.ev[2 * i], c->prof.ev[2 * i + 1]) != cudaSuccess) continue;
+        switch (c->prof.kind[i]) {
+            case 0: P.element_ms += ms; break;
+            case 1: P.assemble_ms += ms; break;
+            case 2: P.pcg_ms += ms; break;
+            case 3: P.linesearch_ms += ms; break;
+            default: break;
+        }
+    }
+    float tot = 0.f;
+    cudaEventElapsedTime(&tot, c->prof.start, c->prof.stop);
+    P.total_ms = tot;
+    cudaGetLastError();
+}
+
+namespace {
+
+// Algorithmic bytes of one PCG iteration of one problem (each datum crossing
+// HBM once): matrix values and column ids, the own rows of z and p_old read
+// and p_new, q written (phase A); p_new, q, dx, r, D^-1 read and dx, r, z
+// written (phase B).
+double pcg_bytes_per_iter(const mfem_ctx* c) {
+    const double kt = c->slot.prec == 1 ? 4.0 : 8.0;
+    const double nnzb = (double)c->plan.nnz_blocks, n = c->plan.n;
+    return nnzb * (9.0 * kt + 4.0) + n * (4.0 * 3.0 * kt) + n * (4.0 * 3.0 * kt + 9.0 * kt + 3.0 * 3.0 * kt);
+}
+
+// Element kernel: static tet data (idx 16, D_m^-1 72, W 8, cluster 4, mu/lam 16),
+// vertex positions once (24 n), element forces (96) and blocks (90 kt) written.
+double element_bytes(const mfem_ctx* c) {
+    const double kt = c->slot.prec == 1 ? 4.0 : 8.0;
+    return (double)c->plan.m * (16 + 72 + 8 + 4 + 16 + 96 + kKe * kt) + 24.0 * c->plan.n;
+}
+
+template <typename T>
+void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc<T>>& out, int& units) {
+    units = 0;
+    for (auto& g : gs) {
+        mfem_ctx* c = g.ctx;
+        if (c->slot.prec != prec) continue;
+        const int n = c->plan.n;
+        const size_t slots = (size_t)c->plan.slice_ptr.back();
+        for (int b = 0; b < g.B; ++b) {
+            if (!g.ph[b].active) continue;
+            PcgDesc<T> d;
+            d.slice_ptr = c->mesh.slice_ptr;
+            d.col = c->mesh.col;
+            d.val = (const T*)c->slot.val + (size_t)b * slots * 9;
+            d.dinv = (const T*)c->slot.dinv + (size_t)b * n * 9;
+            T* v = (T*)c->slot.vec + (size_t)b * 6 * n * 3;
+            d.dx = v;
+            d.r = v + 3 * (size_t)n;
+            d.z = v + 6 * (size_t)n;
+            d.p0 = v + 9 * (size_t)n;
+            d.p1 = v + 12 * (size_t)n;
+            d.q = v + 15 * (size_t)n;
+            d.part = c->slot.part + (size_t)b * c->slot.part_tiles * 4;
+            d.sc = c->slot.sc + b;
+            d.n_rows = n;
+            d.n_tiles = (n + tile - 1) / tile;
+            d.unit_begin = units;
+            d.pad = 0;
+            units += d.n_tiles;
+            out.push_back(d);
+        }
+    }
+}
+
+// Next free staging region; waits for the stream only when the ring is used up.
+mfem_status next_stage(mfem_ctx* c, int& pos) {
+    if (c->ring_pos >= kStageRing) {
+        CK(cudaStreamSynchronize(c->stream));
+        c->ring_pos = 0;
+    }
+    pos = c->ring_pos++;
+    return MFEM_OK;
+}
+
+mfem_status upload_active(mfem_ctx* c, int B, const std::vector<int>& flags) {
+    int pos = 0;
+    mfem_status st = next_stage(c, pos);
+    if (st != MFEM_OK) return st;
+    int* h = c->active_host + (size_t)pos * c->slot.cap;
+    for (int b = 0; b < B; ++b) h[b] = flags[b];
+    CK(cudaMemcpyAsync(c->slot.active, h, B * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    return MFEM_OK;
+}
+
+mfem_status upload_alpha(mfem_ctx* c, int B) {
+    int pos = 0;
+    mfem_status st = next_stage(c, pos);
+    if (st != MFEM_OK) return st;
+    double* h = c->alpha_ring + (size_t)pos * c->slot.cap;
+    for (int b = 0; b < B; ++b) h[b] = c->alpha_host[b];
+    CK(cudaMemcpyAsync(c->slot.alpha, h, B * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    return MFEM_OK;
+}
+
+void synced(std::vector<Group>& gs) {
+    for (auto& g : gs) g.ctx->ring_pos = 0;
+}
+
+mfem_status read_scalars(mfem_ctx* c, int B) {
+    CK(cudaMemcpyAsync(c->sc_host, c->slot.sc, B * sizeof(ProbScal), cudaMemcpyDeviceToHost, c->stream));
+    return MFEM_OK;
+}
+
+template <typename T>
+mfem_status launch_pcg_group(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, int max_iters,
+                             bool count) {
+    mfem_ctx* c = c0;
+    std::vector<PcgDesc<T>> d;
+    int units = 0;
+    build_descs<T>(gs, tile, prec, d, units);
+    if (d.empty()) return MFEM_OK;
+    const size_t bytes = d.size() * sizeof(PcgDesc<T>);
+    if (2 * bytes > c->descs_cap) {   // grow: wait until no copy reads the old buffers
+        CK(cudaStreamSynchronize(c->stream));
+        if (c->descs_dev) cudaFree(c->descs_dev);
+        if (c->descs_host) cudaFreeHost(c->descs_host);
+        CK(cudaMalloc(&c->descs_dev, 2 * bytes));
+        CK(cudaMallocHost(&c->descs_host, 2 * bytes));
+        c->descs_cap = 2 * bytes;
+    }
+    // each precision class has its own half, so two launches of one step never
+    // share a staging region; a step starts only after the previous one synced
+    const size_t off = (size_t)prec * (c->descs_cap / 2);
+    char* hst = (char*)c->descs_host + off;
+    char* dst = (char*)c->descs_dev + off;
+    std::memcpy(hst, d.data(), bytes);
+    CK(cudaMemcpyAsync(dst, hst, bytes, cudaMemcpyHostToDevice, c->stream));
+    GridBar* bar = c->bar + prec;
+    CK(cudaMemsetAsync(bar, 0, sizeof(GridBar), c->stream));
+    int grid = std::min(pcg_max_blocks<T>(tile), units);
+    grid = std::max(grid, 1);
+    c->grid_blocks = grid;
+    int pe = count ? c->prof.begin(2, c->stream) : -1;
+    CK(launch_pcg<T>((const PcgDesc<T>*)dst, (int)d.size(), units, bar, max_iters, tile, grid, c->stream));
+    if (count) {
+        c->prof.end(pe, c->stream);
+        c->prof.launches++;
+        c->prof.pcg_launches++;
+    }
+    return MFEM_OK;
+}
+
+// Pick the PCG tile by timing a capped number of iterations of each candidate
+// on the first assembled system (results are discarded; PCG is re-initialised).
+mfem_status autotune_tile(mfem_ctx* c, std::vector<Group>& gs) {
+    const char* cache = std::getenv("MFEM_AUTOTUNE_CACHE");
+    char key[128];
+    snprintf(key, sizeof key, "%d %d %lld %d %d", c->plan.n, c->plan.m, (long long)c->plan.nnz_blocks,
+             c->slot.prec, gs[0].B);
+    if (cache) {
+        if (FILE* f = fopen(cache, "r")) {
+            char line[256];
+            while (fgets(line, sizeof line, f)) {
+                int tile = 0;
+                size_t kl = strlen(key);
+                if (strncmp(line, key, kl) == 0 && sscanf(line + kl, " %d", &tile) == 1 &&
+                    (tile == 64 || tile == 128 || tile == 256)) {
+                    c->tile_rows = tile;
+                }
+            }
+            fclose(f);
+            if (c->tile_rows) return MFEM_OK;
+        }
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_tile = 128;
+    ElemArgs a = elem_args(c);
+    for (int tile : kPcgTiles) {
+        for (int rep = 0; rep < 2; ++rep) {
+            launch_pcg_init(a, gs[0].B, tile, 0.0, 1 << 30, c->stream);
+            CK(cudaEventRecord(e0, c->stream));
+            mfem_status st = c->slot.prec == 1 ? launch_pcg_group<float>(c, gs, 1, tile, 25, false)
+                                               : launch_pcg_group<double>(c, gs, 0, tile, 25, false);
+            if (st != MFEM_OK) return st;
+            CK(cudaEventRecord(e1, c->stream));
+            CK(cudaEventSynchronize(e1));
+            c->ring_pos = 0;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 1 && ms < best) {
+                best = ms;
+                best_tile = tile;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tile_rows = best_tile;
+    if (cache) {
+        if (FILE* f = fopen(cache, "a")) {
+            fprintf(f, "%s %d\n", key, best_tile);
+            fclose(f);
+        }
+    }
+    return MFEM_OK;
+}
+
+}  // namespace
+
+mfem_status newton_step(std::vector<Group>& gs) {
+    mfem_ctx* c = gs[0].ctx;
+    cudaStream_t s = c->stream;
+    // a0: apply poses of newly admitted problems
+    for (auto& g : gs) {
+        std::vector<int> f(g.B, 0);
+        bool any = false;
+        for (int b = 0; b < g.B; ++b)
+            if (g.ph[b].need_init) { f[b] = 1; any = true; }
+        if (!any) continue;
+        mfem_ctx* gc = g.ctx;
+        mfem_status st = upload_active(gc, g.B, f);
+        if (st != MFEM_OK) return st;
+        launch_pose_init(elem_args(gc), g.B, gc->opt.init == MFEM_INIT_RIGID ? 0 : (gc->opt.init == MFEM_INIT_REST ? 1 : 2), s);
+        gc->prof.launches++;
+        for (int b = 0; b < g.B; ++b)
+            if (g.ph[b].need_init) {
+                g.ph[b].need_init = 0;
+                g.ph[b].active = 1;
+                g.ph[b].it = 0;
+                g.ph[b].g0 = -1.0;
+                g.ph[b].pcg_iters = 0;
+                g.ph[b].ran_pcg = 0;
+                g.ph[b].status = MFEM_OK;
+                g.ph[b].converged = 0;
+            }
+    }
+    // a1-a4: element step, assembly, gradient for active problems
+    for (auto& g : gs) {
+        std::vector<int> f(g.B, 0);
+        bool any = false;
+        for (int b = 0; b < g.B; ++b)
+            if (g.ph[b].active) { f[b] = 1; any = true; }
+        if (!any) continue;
+        mfem_ctx* gc = g.ctx;
+        mfem_status st = upload_active(gc, g.B, f);
+        if (st != MFEM_OK) return st;
+        ElemArgs a = elem_args(gc);
+        int pe = gc->prof.begin(0, s);
+        launch_element(a, g.B, s);
+        gc->prof.end(pe, s);
+        int pa = gc->prof.begin(1, s);
+        launch_assemble(a, g.B, s);
+        gc->prof.end(pa, s);
+        gc->prof.launches += 2;
+        gc->prof.element_launches++;
+        int na = 0;
+        for (int b = 0; b < g.B; ++b) na += f[b];
+        gc->prof.element_bytes += na * element_bytes(gc);
+        st = read_scalars(gc, g.B);
+        if (st != MFEM_OK) return st;
+    }
+    CK(cudaStreamSynchronize(s));
+    synced(gs);
+    // convergence test on the FP64 free gradient
+    bool any_active = false;
+    for (auto& g : gs) {
+        mfem_ctx* gc = g.ctx;
+        for (int b = 0; b < g.B; ++b) {
+            ProbHost& p = g.ph[b];
+            if (!p.active) continue;
+            const ProbScal& sc = gc->sc_host[b];
+            p.gn = std::sqrt(sc.gnorm2);
+            p.energy = sc.energy;
+            if (p.g0 < 0.0) p.g0 = p.gn;
+            if (!std::isfinite(p.gn)) {
+                p.active = 0;
+                p.status = MFEM_ENOTCONV;
+            } else if (p.gn == 0.0 || p.gn <= gc->opt.newton_tol * p.g0) {
+                p.active = 0;
+                p.converged = 1;
+                p.status = MFEM_OK;
+            } else if (p.it >= gc->opt.newton_max) {
+                p.active = 0;
+                p.status = MFEM_ENOTCONV;
+            } else {
+                any_active = true;
+            }
+        }
+    }
+    if (!any_active) return MFEM_OK;
+    // a5: PCG for every active problem of every group, one persistent launch per precision
+    for (auto& g : gs) {
+        std::vector<int> f(g.B, 0);
+        bool any = false;
+        for (int b = 0; b < g.B; ++b)
+            if (g.ph[b].active) { f[b] = 1; any = true; }
+        if (!any) continue;
+        mfem_ctx* gc = g.ctx;
+        mfem_status st = upload_active(gc, g.B, f);
+        if (st != MFEM_OK) return st;
+    }
+    if (c->tile_rows == 0) {
+        mfem_status st = autotune_tile(c, gs);
+        if (st != MFEM_OK) return st;
+    }
+    const int tile = c->tile_rows;
+    for (auto& g : gs) {
+        bool any = false;
+        for (int b = 0; b < g.B; ++b) any |= g.ph[b].active != 0;
+        if (!any) continue;
+        mfem_ctx* gc = g.ctx;
+        const double tol2 = gc->opt.cg_tol * gc->opt.cg_tol;
+        launch_pcg_init(elem_args(gc), g.B, tile, tol2, gc->opt.cg_max, s);
+        gc->prof.launches++;
+    }
+    for (int prec = 0; prec < 2; ++prec) {
+        bool any = false;
+        for (auto& g : gs)
+            if (g.ctx->slot.prec == prec)
+                for (int b = 0; b < g.B; ++b) any |= g.ph[b].active != 0;
+        if (!any) continue;
+        mfem_status st = prec == 1 ? launch_pcg_group<float>(c, gs, 1, tile, 1 << 30, true)
+                                   : launch_pcg_group<double>(c, gs, 0, tile, 1 << 30, true);
+        if (st != MFEM_OK) return st;
+    }
+    // a6: slope for line search (SNH) and PCG statistics
+    for (auto& g : gs) {
+        mfem_ctx* gc = g.ctx;
+        bool any = false;
+        for (int b = 0; b < g.B; ++b) any |= g.ph[b].active != 0;
+        if (!any) continue;
+        if (gc->model == MFEM_SNH) {
+            int pl = gc->prof.begin(3, s);
+            launch_slope(elem_args(gc), g.B, s);
+            gc->prof.end(pl, s);
+            gc->prof.launches++;
+        }
+        mfem_status st = read_scalars(gc, g.B);
+        if (st != MFEM_OK) return st;
+    }
+    CK(cudaMemcpyAsync(c->bar_host, c->bar, 2 * sizeof(GridBar), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    synced(gs);
+    CK(cudaGetLastError());
+    if (c->bar_host[0].err || c->bar_host[1].err) {
+        cudaMemsetAsync(c->bar, 0, 2 * sizeof(GridBar), s);
+        return ctx_fail(c, MFEM_ETIMEOUT, "PCG grid barrier wait timed out");
+    }
+    for (auto& g : gs) {
+        mfem_ctx* gc = g.ctx;
+        for (int b = 0; b < g.B; ++b) {
+            ProbHost& p = g.ph[b];
+            if (!p.active) continue;
+            p.pcg_iters += gc->sc_host[b].iter;
+            gc->prof.pcg_iters += gc->sc_host[b].iter;
+            gc->prof.pcg_bytes += gc->sc_host[b].iter * pcg_bytes_per_iter(gc);
+            gc->alpha_host[b] = 1.0;
+        }
+    }
+    // backtracking line search on E (SNH); quadratic models take alpha = 1
+    for (auto& g : gs) {
+        mfem_ctx* gc = g.ctx;
+        if (gc->model != MFEM_SNH) continue;
+        std::vector<int> testing(g.B, 0);
+        std::vector<double> e0(g.B, 0.0), slope(g.B, 0.0);
+        bool any = false;
+        for (int b = 0; b < g.B; ++b) {
+            if (!g.ph[b].active) continue;
+            e0[b] = g.ph[b].energy;
+            slope[b] = gc->sc_host[b].slope;
+            if (-slope[b] > kLsNoise * std::fabs(e0[b])) { testing[b] = 1; any = true; }
+        }
+        for (int k = 0; any && k <= kLsMax; ++k) {
+            mfem_status st = upload_active(gc, g.B, testing);
+            if (st != MFEM_OK) return st;
+            st = upload_alpha(gc, g.B);
+            if (st != MFEM_OK) return st;
+            int pl = gc->prof.begin(3, s);
+            launch_energy_trial(elem_args(gc), g.B, s);
+            gc->prof.end(pl, s);
+            gc->prof.launches++;
+            st = read_scalars(gc, g.B);
+            if (st != MFEM_OK) return st;
+            CK(cudaStreamSynchronize(s));
+            synced(gs);
+            any = false;
+            for (int b = 0; b < g.B; ++b) {
+                if (!testing[b]) continue;
+                const double a = gc->alpha_host[b];
+                const double et = gc->sc_host[b].energy_trial;
+                if (et <= e0[b] + kLsC * a * slope[b] || k == kLsMax) {
+                    testing[b] = 0;
+                } else {
+                    gc->alpha_host[b] = 0.5 * a;
+                    any = true;
+                }
+            }
+        }
+    }
+    // x <- x + alpha dx
+    for (auto& g : gs) {
+        std::vector<int> f(g.B, 0);
+        bool any = false;
+        for (int b = 0; b < g.B; ++b)
+            if (g.ph[b].active) { f[b] = 1; any = true; }
+        if (!any) continue;
+        mfem_ctx* gc = g.ctx;
+        mfem_status st = upload_active(gc, g.B, f);
+        if (st != MFEM_OK) return st;
+        st = upload_alpha(gc, g.B);
+        if (st != MFEM_OK) return st;
+        launch_update(elem_args(gc), g.B, s);
+        gc->prof.launches++;
+        for (int b = 0; b < g.B; ++b)
+            if (g.ph[b].active) {
+                g.ph[b].it++;
+                g.ph[b].ran_pcg = 1;
+            }
+    }
+    CK(cudaGetLastError());
+    return MFEM_OK;
+}
+
+mfem_status run_batch(mfem_ctx* c, int B, std::vector<ProbHost>& ph) {
+    ph.assign(B, ProbHost());
+    for (int b = 0; b < B; ++b) ph[b].need_init = 1;
+    std::vector<Group> gs{Group{c, B, ph.data()}};
+    for (int guard = 0; guard < 100000; ++guard) {
+        mfem_status st = newton_step(gs);
+        if (st != MFEM_OK) return st;
+        bool any = false;
+        for (int b = 0; b < B; ++b) any |= ph[b].active || ph[b].need_init;
+        if (!any) break;
+    }
+    for (int b = 0; b < B; ++b) c->has_state[b] = 1;
+    return MFEM_OK;
+}
+
+void fill_stats(const mfem_ctx* c, const ProbHost& p, mfem_stats* st) {
+    if (!st) return;
+    (void)c;
+    st->status = p.status;
+    st->newton_iters = p.it;
+    st->pcg_iters = p.pcg_iters;
+    st->converged = p.converged;
+    st->grad0 = p.g0 < 0 ? 0.0 : p.g0;
+    st->rel_grad = p.g0 > 0 ? p.gn / p.g0 : 0.0;
+    st->energy = p.energy;
+    st->inverted = -1;
+    st->max_rel_skew = -1.0;
+    st->max_angle = -1.0;
+}
+
+}  // namespace mfem
+
+using namespace mfem;
+
+// ============================================================================
+// C ABI
+// ============================================================================
+extern "C" {
+
+int32_t mfem_abi_version(void) { return MFEM_ABI_VERSION; }
+
+void mfem_default_options(mfem_options* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = MFEM_MIXED;
+    o->constraint = MFEM_ELIMINATE;
+    o->k_s = 0.0;
+    o->newton_tol = 1e-6;
+    o->cg_tol = 1e-3;
+    o->newton_max = 50;
+    o->cg_max = 5000;
+    o->init = MFEM_INIT_RIGID;
+    o->max_batch = 16;
+    o->tile_rows = 0;
+    o->diagnostics = 0;
+}
+
+const char* mfem_status_string(mfem_status s) {
+    switch (s) {
+        case MFEM_OK: return "ok";
+        case MFEM_EINVAL: return "invalid argument";
+        case MFEM_EDEGEN: return "degenerate rest tet";
+        case MFEM_ENOMEM: return "out of memory";
+        case MFEM_ENOTCONV: return "not converged";
+        case MFEM_ETIMEOUT: return "timed out";
+        case MFEM_EBUSY: return "busy";
+        case MFEM_ECUDA: return "CUDA error";
+    }
+    return "unknown status";
+}
+
+const char* mfem_last_error(const mfem_ctx* ctx) {
+    if (ctx) return ctx->err.c_str();
+    return g_thread_err.c_str();
+}
+
+mfem_status mfem_plan(const double* rest_verts, int32_t n, const int32_t* tets, int32_t m,
+                      const mfem_handles* hs, int32_t* tet_cluster, int32_t* pinned, int32_t* pin_handle) {
+    Plan p;
+    std::string err;
+    mfem_status st = plan_rig(rest_verts, n, tets, m, hs, p, err);
+    if (st != MFEM_OK) return ctx_fail(nullptr, st, err);
+    if (tet_cluster) std::memcpy(tet_cluster, p.cluster_orig.data(), sizeof(int32_t) * m);
+    if (pinned) std::memcpy(pinned, p.pinned_orig.data(), sizeof(int32_t) * n);
+    if (pin_handle) std::memcpy(pin_handle, p.pin_handle_orig.data(), sizeof(int32_t) * n);
+    return MFEM_OK;
+}
+
+void mfem_destroy(mfem_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    free_slots(c);
+    MeshDev& M = c->mesh;
+    void* ptrs[] = {M.tet, M.Dminv64, M.Dminv32, M.vol, M.cluster, M.mu, M.lam, M.X, M.vhandle, M.pin_handle_v,
+                    M.vperm, M.tperm, M.slice_ptr, M.col, M.contrib_ptr, M.contrib, M.vinc_ptr, M.vinc,
+                    c->bar, c->descs_dev, c->diag_dev};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    void* hp[] = {c->sc_host, c->active_host, c->alpha_host, c->alpha_ring, c->bar_host, c->descs_host,
+                  c->diag_host};
+    for (void* p : hp)
+        if (p) cudaFreeHost(p);
+    for (auto e : c->prof.ev) cudaEventDestroy(e);
+    if (c->prof.start) cudaEventDestroy(c->prof.start);
+    if (c->prof.stop) cudaEventDestroy(c->prof.stop);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+}
+
+mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets, int32_t m,
+                        const mfem_material* mat, const mfem_handles* hs, const mfem_options* opt,
+                        mfem_ctx** out) {
+    if (!out) return ctx_fail(nullptr, MFEM_EINVAL, "null output pointer");
+    *out = nullptr;
+    mfem_ctx* c = new mfem_ctx();
+    if (opt) c->opt = *opt;
+    else mfem_default_options(&c->opt);
+    const mfem_options& o = c->opt;
+    auto fail = [&](mfem_status s, const std::string& msg) {
+        g_thread_err = msg;
+        mfem_destroy(c);
+        return s;
+    };
+    if (o.precision != MFEM_FP64 && o.precision != MFEM_MIXED) return fail(MFEM_EINVAL, "bad precision");
+    if (o.constraint != MFEM_ELIMINATE && o.constraint != MFEM_PENALTY) return fail(MFEM_EINVAL, "bad constraint");
+    if (o.constraint == MFEM_PENALTY && !(o.k_s > 0.0)) return fail(MFEM_EINVAL, "penalty needs k_s > 0");
+    if (!(o.newton_tol >= 0.0) || !(o.cg_tol >= 0.0) || o.newton_max < 0 || o.cg_max < 1)
+        return fail(MFEM_EINVAL, "bad tolerances or iteration caps");
+    if (o.init < MFEM_INIT_RIGID || o.init > MFEM_INIT_WARM) return fail(MFEM_EINVAL, "bad init");
+    if (o.tile_rows != 0 && o.tile_rows != 64 && o.tile_rows != 128 && o.tile_rows != 256)
+        return fail(MFEM_EINVAL, "tile_rows must be 0, 64, 128 or 256");
+    if (!mat) return fail(MFEM_EINVAL, "null material");
+    std::string err;
+    mfem_status st = plan_rig(rest_verts, n, tets, m, hs, c->plan, err);
+    if (st != MFEM_OK) return fail(st, err);
+    st = plan_layout(mat, rest_verts, tets, c->plan, err);
+    if (st != MFEM_OK) return fail(st, err);
+    c->model = mat->model;
+    c->slot.prec = o.precision == MFEM_MIXED ? 1 : 0;
+    c->tile_rows = o.tile_rows;
+    const Plan& P = c->plan;
+    if (cudaGetDevice(&c->device) != cudaSuccess) return fail(MFEM_ECUDA, "no CUDA device");
+    if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(MFEM_ECUDA, "cudaStreamCreate failed");
+    c->stream = c->own_stream;
+    // device mesh (SoA per tet)
+    MeshDev& M = c->mesh;
+    M.n = P.n;
+    M.m = P.m;
+    M.H = P.H;
+    M.n_slices = P.n_slices;
+    M.n_pins = (int)P.pin_vert.size();
+    M.slots = P.slice_ptr.back();
+    std::vector<double> Dm64((size_t)9 * P.m);
+    std::vector<float> Dm32((size_t)9 * P.m);
+    for (int k = 0; k < P.m; ++k)
+        for (int e = 0; e < 9; ++e) {
+            Dm64[(size_t)e * P.m + k] = P.Dminv[9 * (size_t)k + e];
+            Dm32[(size_t)e * P.m + k] = (float)P.Dminv[9 * (size_t)k + e];
+        }
+    std::vector<int32_t> pin_h(P.n, -1);
+    for (size_t i = 0; i < P.pin_vert.size(); ++i) pin_h[P.pin_vert[i]] = P.pin_handle[i];
+    std::vector<int32_t> sp(P.slice_ptr.begin(), P.slice_ptr.end());
+#define UP(dst, src, cnt)                                   \
+    if ((st = upload(c, &(dst), (src), (cnt))) != MFEM_OK) { \
+        std::string e2 = c->err;                            \
+        return fail(st, e2);                                \
+    }
+    UP(M.tet, (const int4*)P.tet.data(), (size_t)P.m);
+    UP(M.Dminv64, Dm64.data(), Dm64.size());
+    UP(M.Dminv32, Dm32.data(), Dm32.size());
+    UP(M.vol, P.vol.data(), P.vol.size());
+    UP(M.cluster, P.cluster.data(), P.cluster.size());
+    UP(M.mu, P.mu.data(), P.mu.size());
+    UP(M.lam, P.lam.data(), P.lam.size());
+    UP(M.X, P.X.data(), P.X.size());
+    UP(M.vhandle, P.vhandle.data(), P.vhandle.size());
+    UP(M.pin_handle_v, pin_h.data(), pin_h.size());
+    UP(M.vperm, P.vperm.data(), P.vperm.size());
+    UP(M.tperm, P.tperm.data(), P.tperm.size());
+    UP(M.slice_ptr, sp.data(), sp.size());
+    UP(M.col, P.sell_col.data(), P.sell_col.size());
+    UP(M.contrib_ptr, P.contrib_ptr.data(), P.contrib_ptr.size());
+    UP(M.contrib, P.contrib.data(), P.contrib.size());
+    UP(M.vinc_ptr, P.vinc_ptr.data(), P.vinc_ptr.size());
+    UP(M.vinc, P.vinc.data(), P.vinc.size());
+#undef UP
+    if (cudaMalloc((void**)&c->bar, 2 * sizeof(GridBar)) != cudaSuccess ||
+        cudaMemset(c->bar, 0, 2 * sizeof(GridBar)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->bar_host, 2 * sizeof(GridBar)) != cudaSuccess ||
+        cudaMalloc((void**)&c->diag_dev, 4 * sizeof(unsigned)) != cudaSuccess ||
+        cudaMallocHost((void**)&c->diag_host, 4 * sizeof(unsigned)) != cudaSuccess)
+        return fail(MFEM_ENOMEM, "small device/host buffers");
+    c->prof.ev.resize(2 * 4096);
+    for (auto& e : c->prof.ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return fail(MFEM_ECUDA, "cudaEventCreate failed");
+    if (cudaEventCreate(&c->prof.start) != cudaSuccess || cudaEventCreate(&c->prof.stop) != cudaSuccess)
+        return fail(MFEM_ECUDA, "cudaEventCreate failed");
+    st = ensure_slots(c, std::max(1, o.max_batch));
+    if (st != MFEM_OK) {
+        std::string e2 = c->err;
+        return fail(st, e2);
+    }
+    *out = c;
+    return MFEM_OK;
+}
+
+mfem_status mfem_set_stream(mfem_ctx* c, void* stream) {
+    if (!c) return ctx_fail(nullptr, MFEM_EINVAL, "null context");
+    if (c->owned_by_server) return ctx_fail(c, MFEM_EINVAL, "context belongs to a server");
+    cudaStreamSynchronize(c->stream);
+    c->stream = stream ? (cudaStream_t)stream : c->own_stream;
+    return MFEM_OK;
+}
+
+static mfem_status validate_pose(mfem_ctx* c, const double* xf, int H) {
+    for (int h = 0; h < H; ++h) {
+        const double* T = xf + 12 * h;
+        for (int i = 0; i < 12; ++i)
+            if (!std::isfinite(T[i])) return ctx_fail(c, MFEM_EINVAL, "non-finite handle transform");
+        double err = 0.0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                double s = 0.0;
+                for (int k = 0; k < 3; ++k) s += T[4 * k + i] * T[4 * k + j];
+                err = std::max(err, std::fabs(s - (i == j ? 1.0 : 0.0)));
+            }
+        double det = T[0] * (T[5] * T[10] - T[6] * T[9]) - T[1] * (T[4] * T[10] - T[6] * T[8]) +
+                     T[2] * (T[4] * T[9] - T[5] * T[8]);
+        if (err > 1e-6 || det <= 0.0) {
+            char buf[128];
+            snprintf(buf, sizeof buf, "handle %d: Q is not a rotation (|Q^T Q - I| = %.2e, det = %.3f)", h, err, det);
+            return ctx_fail(c, MFEM_EINVAL, buf);
+        }
+    }
+    return MFEM_OK;
+}
+
+mfem_status mfem_set_pose(mfem_ctx* c, const double* xf, int32_t H) {
+    if (!c || !xf) return ctx_fail(c, MFEM_EINVAL, "null argument");
+    if (c->owned_by_server) return ctx_fail(c, MFEM_EINVAL, "context belongs to a server");
+    if (H != c->plan.H) return ctx_fail(c, MFEM_EINVAL, "pose has the wrong number of handles");
+    mfem_status st = validate_pose(c, xf, H);
+    if (st != MFEM_OK) return st;
+    CK(cudaMemcpyAsync(c->slot.xf, xf, sizeof(double) * 12 * H, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    c->pose_set = true;
+    return MFEM_OK;
+}
+
+static mfem_status finish_stats(mfem_ctx* c, const std::vector<ProbHost>& ph, int B, mfem_stats* stats) {
+    mfem_status worst = MFEM_OK;
+    for (int b = 0; b < B; ++b) {
+        if (ph[b].status != MFEM_OK) worst = (mfem_status)ph[b].status;
+        if (!stats) continue;
+        fill_stats(c, ph[b], &stats[b]);
+        if (c->opt.diagnostics) {
+            CK(cudaMemsetAsync(c->diag_dev, 0, 4 * sizeof(unsigned), c->stream));
+            launch_diag(elem_args(c), b, c->diag_dev, c->stream);
+            CK(cudaMemcpyAsync(c->diag_host, c->diag_dev, 4 * sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
+            CK(cudaStreamSynchronize(c->stream));
+            float f1, f2;
+            std::memcpy(&f1, &c->diag_host[1], 4);
+            std::memcpy(&f2, &c->diag_host[2], 4);
+            stats[b].inverted = (int32_t)c->diag_host[0];
+            stats[b].max_rel_skew = f1;
+            stats[b].max_angle = f2;
+        }
+    }
+    if (worst == MFEM_ENOTCONV) ctx_fail(c, worst, "Newton iteration cap reached before newton_tol");
+    return worst;
+}
+
+mfem_status mfem_solve(mfem_ctx* c, double* out, mfem_stats* stats) {
+    if (!c || !out) return ctx_fail(c, MFEM_EINVAL, "null argument");
+    if (c->owned_by_server) return ctx_fail(c, MFEM_EINVAL, "context belongs to a server");
+    if (!c->pose_set) return ctx_fail(c, MFEM_EINVAL, "mfem_set_pose must come first");
+    begin_profile(c);
+    std::vector<ProbHost> ph;
+    mfem_status st = run_batch(c, 1, ph);
+    if (st != MFEM_OK) return st;
+    launch_unpermute(elem_args(c), 1, c->slot.outbuf, c->stream);
+    c->prof.launches++;
+    CK(cudaMemcpyAsync(out, c->slot.outbuf, sizeof(double) * 3 * c->plan.n, cudaMemcpyDeviceToHost, c->stream));
+    end_profile(c);
+    return finish_stats(c, ph, 1, stats);
+}
+
+mfem_status mfem_solve_batch(mfem_ctx* c, const double* xf, int32_t B, double* out, int32_t memory,
+                             mfem_stats* stats) {
+    if (!c || !xf || !out) return ctx_fail(c, MFEM_EINVAL, "null argument");
+    if (c->owned_by_server) return ctx_fail(c, MFEM_EINVAL, "context belongs to a server");
+    if (B < 1) return ctx_fail(c, MFEM_EINVAL, "B must be >= 1");
+    if (memory != MFEM_MEM_HOST && memory != MFEM_MEM_DEVICE) return ctx_fail(c, MFEM_EINVAL, "bad memory kind");
+    const int H = c->plan.H, n = c->plan.n;
+    mfem_status st = ensure_slots(c, B);
+    if (st != MFEM_OK) return st;
+    begin_profile(c);
+    const size_t xf_bytes = sizeof(double) * 12 * (size_t)H * B;
+    if (memory == MFEM_MEM_HOST) {
+        st = validate_pose(c, xf, H * B);
+        if (st != MFEM_OK) return st;
+        CK(cudaMemcpyAsync(c->slot.xf, xf, xf_bytes, cudaMemcpyHostToDevice, c->stream));
+    } else {
+        std::vector<double> tmp((size_t)12 * H * B);
+        CK(cudaMemcpyAsync(tmp.data(), xf, xf_bytes, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        st = validate_pose(c, tmp.data(), H * B);
+        if (st != MFEM_OK) return st;
+        CK(cudaMemcpyAsync(c->slot.xf, xf, xf_bytes, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    std::vector<ProbHost> ph;
+    st = run_batch(c, B, ph);
+    if (st != MFEM_OK) return st;
+    if (memory == MFEM_MEM_HOST) {
+        launch_unpermute(elem_args(c), B, c->slot.outbuf, c->stream);
+        CK(cudaMemcpyAsync(out, c->slot.outbuf, sizeof(double) * 3 * (size_t)n * B, cudaMemcpyDeviceToHost,
+                           c->stream));
+    } else {
+        launch_unpermute(elem_args(c), B, out, c->stream);
+    }
+    c->prof.launches++;
+    end_profile(c);
+    return finish_stats(c, ph, B, stats);
+}
+
+mfem_status mfem_get_elem(mfem_ctx* c, double* s, double* lam) {
+    if (!c) return ctx_fail(nullptr, MFEM_EINVAL, "null context");
+    if (!s && !lam) return MFEM_OK;
+    const size_t m = c->plan.m;
+    double* buf = nullptr;
+    CK(cudaMalloc((void**)&buf, sizeof(double) * 15 * m));
+    launch_elem_out(elem_args(c), 0, s ? buf : nullptr, lam ? buf + 6 * m : nullptr, c->stream);
+    mfem_status st = MFEM_OK;
+    if (s && (st = cuda_check(c, cudaMemcpyAsync(s, buf, sizeof(double) * 6 * m, cudaMemcpyDeviceToHost, c->stream),
+                              "copy s")) != MFEM_OK) {
+        cudaFree(buf);
+        return st;
+    }
+    if (lam && (st = cuda_check(c, cudaMemcpyAsync(lam, buf + 6 * m, sizeof(double) * 9 * m,
+                                                   cudaMemcpyDeviceToHost, c->stream), "copy lam")) != MFEM_OK) {
+        cudaFree(buf);
+        return st;
+    }
+    st = cuda_check(c, cudaStreamSynchronize(c->stream), "get_elem");
+    cudaFree(buf);
+    return st;
+}
+
+mfem_status mfem_get_state(const mfem_ctx* cc, double* x) {
+    mfem_ctx* c = const_cast<mfem_ctx*>(cc);
+    if (!c || !x) return ctx_fail(c, MFEM_EINVAL, "null argument");
+    launch_unpermute(elem_args(c), 1, c->slot.outbuf, c->stream);
+    CK(cudaMemcpyAsync(x, c->slot.outbuf, sizeof(double) * 3 * c->plan.n, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return MFEM_OK;
+}
+
+mfem_status mfem_set_state(mfem_ctx* c, const double* x) {
+    if (!c || !x) return ctx_fail(c, MFEM_EINVAL, "null argument");
+    for (size_t i = 0; i < 3 * (size_t)c->plan.n; ++i)
+        if (!std::isfinite(x[i])) return ctx_fail(c, MFEM_EINVAL, "non-finite state");
+    CK(cudaMemcpyAsync(c->slot.outbuf, x, sizeof(double) * 3 * c->plan.n, cudaMemcpyHostToDevice, c->stream));
+    launch_permute_in(elem_args(c), 0, c->slot.outbuf, c->stream);
+    CK(cudaStreamSynchronize(c->stream));
+    c->has_state[0] = 1;
+    return MFEM_OK;
+}
+
+mfem_status mfem_get_profile(const mfem_ctx* c, mfem_profile* p) {
+    if (!c || !p) return ctx_fail(const_cast<mfem_ctx*>(c), MFEM_EINVAL, "null argument");
+    *p = c->last_profile;
+    return MFEM_OK;
+}
+
+mfem_status mfem_get_info(const mfem_ctx* c, int32_t* n, int32_t* m, int32_t* H, int32_t* n_pins,
+                          int64_t* nnz_blocks, int64_t* sell_slots, int64_t* device_bytes) {
+    if (!c) return ctx_fail(nullptr, MFEM_EINVAL, "null context");
+    if (n) *n = c->plan.n;
+    if (m) *m = c->plan.m;
+    if (H) *H = c->plan.H;
+    if (n_pins) *n_pins = (int32_t)c->plan.pin_vert.size();
+    if (nnz_blocks) *nnz_blocks = c->plan.nnz_blocks;
+    if (sell_slots) *sell_slots = c->plan.slice_ptr.back();
+    if (device_bytes) *device_bytes = (int64_t)(c->mesh_bytes + c->slot_bytes);
+    return MFEM_OK;
+}
+
+}  // extern "C"

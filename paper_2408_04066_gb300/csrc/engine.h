@@ -1,0 +1,115 @@
+// Engine internals: the solver context and the Newton driver shared by the
+// batch entry points and the serving loop.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/mfem.h"
+#include "kernels.h"
+#include "plan.h"
+
+namespace mfem {
+
+// Host view of one problem (one pose of one mesh) during a Newton solve.
+struct ProbHost {
+    int active = 0;      // still iterating
+    int need_init = 0;   // pose/initial guess not yet applied
+    int it = 0;          // Newton steps taken
+    int pcg_iters = 0;
+    int ran_pcg = 0;     // PCG ran in the current step
+    int status = MFEM_OK;
+    int converged = 0;
+    double g0 = -1.0, gn = 0.0, energy = 0.0;
+};
+
+// Profile accumulator with a pool of CUDA events on the context stream.
+struct Profiler {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;   // per event pair: 0 element, 1 assemble, 2 pcg, 3 line search, 4 other
+    int used = 0;
+    int launches = 0;
+    int pcg_launches = 0, element_launches = 0;
+    double pcg_bytes = 0.0, element_bytes = 0.0;
+    int64_t pcg_iters = 0;
+    cudaEvent_t start = nullptr, stop = nullptr;
+    void reset() {
+        used = 0;
+        launches = pcg_launches = element_launches = 0;
+        pcg_bytes = element_bytes = 0.0;
+        pcg_iters = 0;
+        kind.clear();
+    }
+    int begin(int k, cudaStream_t s);   // returns pair index or -1
+    void end(int idx, cudaStream_t s);
+};
+
+}  // namespace mfem
+
+struct mfem_ctx {
+    mfem::Plan plan;
+    int model = MFEM_ARAP;
+    mfem_options opt{};
+    int device = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    mfem::MeshDev mesh;
+    mfem::SlotDev slot;
+    size_t mesh_bytes = 0, slot_bytes = 0;
+    mfem::GridBar* bar = nullptr;     // [2]: one per PCG precision class
+    void* descs_dev = nullptr;
+    size_t descs_cap = 0;
+    // pinned host staging.  Async uploads read from a ring of regions so that a
+    // region is never rewritten before its copy has run; the ring restarts after
+    // every stream synchronisation.
+    mfem::ProbScal* sc_host = nullptr;
+    int* active_host = nullptr;      // [kStageRing][cap]
+    double* alpha_host = nullptr;    // current step lengths [cap]
+    double* alpha_ring = nullptr;    // [kStageRing][cap]
+    int ring_pos = 0;
+    mfem::GridBar* bar_host = nullptr;
+    void* descs_host = nullptr;
+    unsigned* diag_dev = nullptr;
+    unsigned* diag_host = nullptr;
+    int tile_rows = 0;
+    int grid_blocks = 0;
+    bool pose_set = false;
+    std::vector<int> has_state;   // per slot: x holds a previous solution
+    mfem::Profiler prof;
+    mfem_profile last_profile{};
+    std::string err;
+    bool owned_by_server = false;
+};
+
+namespace mfem {
+
+constexpr int kStageRing = 64;
+
+// One Newton group: B problems of one context.
+struct Group {
+    mfem_ctx* ctx;
+    int B;
+    ProbHost* ph;
+};
+
+mfem_status ctx_fail(mfem_ctx* c, mfem_status s, const std::string& msg);
+mfem_status cuda_check(mfem_ctx* c, cudaError_t e, const char* what);
+mfem_status ensure_slots(mfem_ctx* c, int B);
+size_t slot_bytes_for(const mfem_ctx* c, int B);
+ElemArgs elem_args(const mfem_ctx* c);
+
+// Advance every active problem of every group by one Newton step.  All groups
+// must share one stream (groups[0].ctx->stream).  Problems with need_init get
+// their pose applied first.  Returns MFEM_OK or a device/timeout error.
+mfem_status newton_step(std::vector<Group>& groups);
+
+// Whole solve of B problems of one context (poses already in slot.xf).
+mfem_status run_batch(mfem_ctx* c, int B, std::vector<ProbHost>& ph);
+
+void fill_stats(const mfem_ctx* c, const ProbHost& p, mfem_stats* st);
+void begin_profile(mfem_ctx* c);
+void end_profile(mfem_ctx* c);
+
+}  // namespace mfem

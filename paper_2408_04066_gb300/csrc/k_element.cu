@@ -1,0 +1,620 @@
+// Per-tetrahedron kernels: pose update (a0), element local step (a1), line-search
+// energy (a6), element outputs and diagnostics.
+//
+// Element step, paper §3: F_k = B_k x (text after Eq. 4), S_k = sym(R_k^T F_k)
+// (the pseudo-inverse of [R] named after Eq. 12), Psi(S_k) and its derivatives
+// (Eq. 6), the multiplier Lambda_k = R_k dPsi/dS (Eq. 10-11), the element
+// forces W_k Lambda_k G_a and the element blocks of the condensed matrix
+// W_k A_k^T H_s A_k of Eq. 12, with A_k = R_k^+ B_k.  R_k is the rotation of the
+// rig handle of the tet's cluster (§3.1).
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace mfem {
+
+namespace {
+
+constexpr double kSqrt2 = 1.4142135623730951;
+constexpr double kInvSqrt2 = 0.7071067811865476;
+constexpr double kSpdEps = 1.0e-6;     // Hessian eigenvalue floor, times mu
+constexpr double kFallbackJ = 0.25;    // mixed path: det S below this -> FP64 Hessian
+
+__device__ __forceinline__ int pair_index(int a, int b) {  // a <= b
+    return a * 4 - (a * (a - 1)) / 2 + (b - a);
+}
+
+// Gather the four vertex positions of tet k of problem b (optionally x + alpha dx).
+template <typename T>
+__device__ __forceinline__ void gather_x(const double* __restrict__ x, const T* __restrict__ dx,
+                                         double alpha, int4 tv, double (&xa)[4][3]) {
+    const int id[4] = {tv.x, tv.y, tv.z, tv.w};
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            double v = x[3 * (size_t)id[a] + i];
+            if (dx) v = fma(alpha, (double)dx[3 * (size_t)id[a] + i], v);
+            xa[a][i] = v;
+        }
+}
+
+// Shape-function gradients G_a (rows of D_m^{-1}, G_0 = -(G_1+G_2+G_3)).
+__device__ __forceinline__ void load_G(const double* __restrict__ Dm, int m, int k, double (&G)[4][3]) {
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) G[r + 1][c] = Dm[(size_t)(3 * r + c) * m + k];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) G[0][c] = -(G[1][c] + G[2][c] + G[3][c]);
+}
+
+__device__ __forceinline__ void load_Q(const double* __restrict__ xf, int h, double (&Q)[3][3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Q[i][j] = xf[12 * h + 4 * i + j];
+}
+
+// S = sym(Q^T F), F = sum_{a=1..3} (x_a - x_0) G_a^T.  S as (S00,S11,S22,S12,S02,S01).
+__device__ __forceinline__ void stretch(const double (&xa)[4][3], const double (&G)[4][3],
+                                        const double (&Q)[3][3], double (&F)[3][3], double (&S)[6]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            double f = 0.0;
+#pragma unroll
+            for (int a = 1; a < 4; ++a) f = fma(xa[a][i] - xa[0][i], G[a][j], f);
+            F[i][j] = f;
+        }
+    double A[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) A[i][j] = Q[0][i] * F[0][j] + Q[1][i] * F[1][j] + Q[2][i] * F[2][j];
+    S[0] = A[0][0];
+    S[1] = A[1][1];
+    S[2] = A[2][2];
+    S[3] = 0.5 * (A[1][2] + A[2][1]);
+    S[4] = 0.5 * (A[0][2] + A[2][0]);
+    S[5] = 0.5 * (A[0][1] + A[1][0]);
+}
+
+// Energy density and stress sigma = dPsi/dS (plain symmetric components).
+template <int MODEL>
+__device__ __forceinline__ double psi_sigma(const double (&S)[6], double mu, double lam, double (&sig)[6]) {
+    const double d0 = S[0] - 1.0, d1 = S[1] - 1.0, d2 = S[2] - 1.0;
+    if (MODEL == 0 || MODEL == 1) {
+        double psi = mu * (d0 * d0 + d1 * d1 + d2 * d2 + 2.0 * (S[3] * S[3] + S[4] * S[4] + S[5] * S[5]));
+        sig[0] = 2.0 * mu * d0;
+        sig[1] = 2.0 * mu * d1;
+        sig[2] = 2.0 * mu * d2;
+        sig[3] = 2.0 * mu * S[3];
+        sig[4] = 2.0 * mu * S[4];
+        sig[5] = 2.0 * mu * S[5];
+        if (MODEL == 1) {
+            double tr = d0 + d1 + d2;
+            psi += 0.5 * lam * tr * tr;
+            sig[0] += lam * tr;
+            sig[1] += lam * tr;
+            sig[2] += lam * tr;
+        }
+        return psi;
+    } else {
+        // adjugate (cofactor) of symmetric S and J = det S
+        const double a = S[0], b = S[1], c = S[2], s12 = S[3], s02 = S[4], s01 = S[5];
+        const double c00 = b * c - s12 * s12, c11 = a * c - s02 * s02, c22 = a * b - s01 * s01;
+        const double c12 = s01 * s02 - a * s12, c02 = s01 * s12 - b * s02, c01 = s02 * s12 - c * s01;
+        const double J = a * c00 + s01 * c01 + s02 * c02;
+        const double ls = lam + mu;
+        const double nS2 = a * a + b * b + c * c + 2.0 * (s12 * s12 + s02 * s02 + s01 * s01);
+        const double psi = 0.5 * mu * (nS2 - 3.0) - mu * (J - 1.0) + 0.5 * ls * (J - 1.0) * (J - 1.0);
+        const double k = ls * (J - 1.0) - mu;
+        sig[0] = mu * a + k * c00;
+        sig[1] = mu * b + k * c11;
+        sig[2] = mu * c + k * c22;
+        sig[3] = mu * s12 + k * c12;
+        sig[4] = mu * s02 + k * c02;
+        sig[5] = mu * s01 + k * c01;
+        return psi;
+    }
+}
+
+// ---- SNH Hessian in Mandel coordinates, SPD filtering ----------------------
+// s = (a, b, c, d, e, f) = (S00, S11, S22, sqrt2 S12, sqrt2 S02, sqrt2 S01).
+template <typename RT>
+__device__ void snh_hessian(const double (&S)[6], double mu_d, double lam_d, RT (&C)[6][6]) {
+    const RT a = (RT)S[0], b = (RT)S[1], c = (RT)S[2];
+    const RT d = (RT)(kSqrt2 * S[3]), e = (RT)(kSqrt2 * S[4]), f = (RT)(kSqrt2 * S[5]);
+    const RT is2 = (RT)kInvSqrt2;
+    const RT mu = (RT)mu_d, ls = (RT)(lam_d + mu_d);
+    const RT J = a * b * c + d * e * f * is2 - (RT)0.5 * (a * d * d + b * e * e + c * f * f);
+    const RT j[6] = {b * c - (RT)0.5 * d * d, a * c - (RT)0.5 * e * e, a * b - (RT)0.5 * f * f,
+                     e * f * is2 - a * d,    d * f * is2 - b * e,    d * e * is2 - c * f};
+    RT HJ[6][6];
+#pragma unroll
+    for (int p = 0; p < 6; ++p)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) HJ[p][q] = (RT)0;
+    HJ[0][1] = HJ[1][0] = c;
+    HJ[0][2] = HJ[2][0] = b;
+    HJ[1][2] = HJ[2][1] = a;
+    HJ[0][3] = HJ[3][0] = -d;
+    HJ[1][4] = HJ[4][1] = -e;
+    HJ[2][5] = HJ[5][2] = -f;
+    HJ[3][3] = -a;
+    HJ[4][4] = -b;
+    HJ[5][5] = -c;
+    HJ[3][4] = HJ[4][3] = f * is2;
+    HJ[3][5] = HJ[5][3] = e * is2;
+    HJ[4][5] = HJ[5][4] = d * is2;
+    const RT k = ls * (J - (RT)1) - mu;
+#pragma unroll
+    for (int p = 0; p < 6; ++p)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) C[p][q] = k * HJ[p][q] + ls * j[p] * j[q] + (p == q ? mu : (RT)0);
+}
+
+// true if every eigenvalue of C exceeds `floor` (Cholesky of C - floor I)
+template <typename RT>
+__device__ bool chol_shifted_ok(const RT (&C)[6][6], RT floor) {
+    RT L[6][6];
+#pragma unroll
+    for (int j = 0; j < 6; ++j) {
+        RT dsum = C[j][j] - floor;
+#pragma unroll
+        for (int k = 0; k < j; ++k) dsum -= L[j][k] * L[j][k];
+        if (!(dsum > (RT)0)) return false;
+        RT ljj = sqrt(dsum);
+        L[j][j] = ljj;
+        RT inv = (RT)1 / ljj;
+#pragma unroll
+        for (int i = j + 1; i < 6; ++i) {
+            RT s = C[i][j];
+#pragma unroll
+            for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+            L[i][j] = s * inv;
+        }
+    }
+    return true;
+}
+
+// Cyclic Jacobi eigen-decomposition of a symmetric 6x6 (Golub & Van Loan,
+// "Matrix Computations", symmetric Jacobi method), then every eigenvalue is
+// replaced by max(|eigenvalue|, floor) (absolute-value eigenvalue filtering).
+template <typename RT>
+__device__ __noinline__ void filter_spd(RT (&C)[6][6], RT floor) {
+    RT V[6][6];
+    for (int p = 0; p < 6; ++p)
+        for (int q = 0; q < 6; ++q) V[p][q] = (p == q) ? (RT)1 : (RT)0;
+    const RT eps = sizeof(RT) == 8 ? (RT)1e-15 : (RT)1e-7;
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        RT off = 0, dia = 0;
+        for (int p = 0; p < 6; ++p) {
+            dia += C[p][p] * C[p][p];
+            for (int q = p + 1; q < 6; ++q) off += C[p][q] * C[p][q];
+        }
+        if (off <= eps * eps * dia) break;
+        for (int p = 0; p < 5; ++p)
+            for (int q = p + 1; q < 6; ++q) {
+                RT apq = C[p][q];
+                if (apq == (RT)0) continue;
+                RT theta = (C[q][q] - C[p][p]) / ((RT)2 * apq);
+                RT t = (theta >= (RT)0 ? (RT)1 : (RT)-1) / (fabs(theta) + sqrt(theta * theta + (RT)1));
+                RT cs = (RT)1 / sqrt(t * t + (RT)1);
+                RT sn = t * cs;
+                for (int r = 0; r < 6; ++r) {  // columns p, q
+                    RT crp = C[r][p], crq = C[r][q];
+                    C[r][p] = cs * crp - sn * crq;
+                    C[r][q] = sn * crp + cs * crq;
+                }
+                for (int r = 0; r < 6; ++r) {  // rows p, q
+                    RT cpr = C[p][r], cqr = C[q][r];
+                    C[p][r] = cs * cpr - sn * cqr;
+                    C[q][r] = sn * cpr + cs * cqr;
+                }
+                for (int r = 0; r < 6; ++r) {
+                    RT vrp = V[r][p], vrq = V[r][q];
+                    V[r][p] = cs * vrp - sn * vrq;
+                    V[r][q] = sn * vrp + cs * vrq;
+                }
+            }
+    }
+    RT lam[6];
+    for (int p = 0; p < 6; ++p) {
+        RT l = fabs(C[p][p]);
+        lam[p] = l > floor ? l : floor;
+    }
+    for (int p = 0; p < 6; ++p)
+        for (int q = p; q < 6; ++q) {
+            RT s = 0;
+            for (int r = 0; r < 6; ++r) s += V[p][r] * lam[r] * V[q][r];
+            C[p][q] = s;
+            C[q][p] = s;
+        }
+}
+
+// Column j of E_a = M_a(row j of Q): the Mandel stretch from a unit move of
+// vertex a along axis j (rotated into the cluster frame).
+template <typename KT>
+__device__ __forceinline__ void Ecol(const KT (&g)[3], const KT (&u)[3], KT (&e)[6]) {
+    const KT is2 = (KT)kInvSqrt2;
+    e[0] = u[0] * g[0];
+    e[1] = u[1] * g[1];
+    e[2] = u[2] * g[2];
+    e[3] = (u[1] * g[2] + u[2] * g[1]) * is2;
+    e[4] = (u[0] * g[2] + u[2] * g[0]) * is2;
+    e[5] = (u[0] * g[1] + u[1] * g[0]) * is2;
+}
+
+// Element blocks K_ab = W E_a^T C E_b for a <= b, generic 6x6 C.
+template <typename KT>
+__device__ __forceinline__ void blocks_generic(const KT (&C)[6][6], const double (&Gd)[4][3],
+                                               const double (&Qd)[3][3], double w, KT* __restrict__ out) {
+    KT G[4][3], Q[3][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) G[a][i] = (KT)Gd[a][i];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j) Q[i][j] = (KT)Qd[i][j];
+    const KT W = (KT)w;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        KT CE[3][6];  // (C E_b) columns
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            KT e[6];
+            KT u[3] = {Q[j][0], Q[j][1], Q[j][2]};
+            Ecol<KT>(G[b], u, e);
+#pragma unroll
+            for (int p = 0; p < 6; ++p) {
+                KT s = 0;
+#pragma unroll
+                for (int q = 0; q < 6; ++q) s += C[p][q] * e[q];
+                CE[j][p] = s * W;
+            }
+        }
+#pragma unroll
+        for (int a = 0; a <= b; ++a) {
+            KT* o = out + 9 * pair_index(a, b);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                KT e[6];
+                KT u[3] = {Q[i][0], Q[i][1], Q[i][2]};
+                Ecol<KT>(G[a], u, e);
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    KT s = 0;
+#pragma unroll
+                    for (int p = 0; p < 6; ++p) s += e[p] * CE[j][p];
+                    o[3 * i + j] = s;
+                }
+            }
+        }
+    }
+}
+
+// ARAP / co-rotational blocks in closed form:
+// K_ab = W [mu (G_a.G_b) I + mu h_b h_a^T + lam h_a h_b^T], h_a = Q G_a.
+template <typename KT>
+__device__ __forceinline__ void blocks_quadratic(const double (&Gd)[4][3], const double (&Qd)[3][3],
+                                                 double w, double mu, double lam, KT* __restrict__ out) {
+    KT G[4][3], h[4][3];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) G[a][i] = (KT)Gd[a][i];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            h[a][i] = (KT)Qd[i][0] * G[a][0] + (KT)Qd[i][1] * G[a][1] + (KT)Qd[i][2] * G[a][2];
+    const KT wm = (KT)(w * mu), wl = (KT)(w * lam);
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = a; b < 4; ++b) {
+            KT* o = out + 9 * pair_index(a, b);
+            const KT gg = wm * (G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2]);
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    o[3 * i + j] = (i == j ? gg : (KT)0) + wm * h[b][i] * h[a][j] + wl * h[a][i] * h[b][j];
+        }
+}
+
+// ---------------------------------------------------------------------------
+template <typename KT, int MODEL>
+__global__ void __launch_bounds__(kTetTile) k_element(ElemArgs A) {
+    const int b = blockIdx.y;
+    if (!A.slot.active[b]) return;
+    const MeshDev& M = A.mesh;
+    const int m = M.m, n = M.n;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double en[1] = {0.0};
+    if (k < m) {
+        const double* x = A.slot.x + (size_t)b * n * 3;
+        const double* xf = A.slot.xf + (size_t)b * M.H * 12;
+        double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6], sig[6];
+        const int4 tv = M.tet[k];
+        gather_x<float>(x, nullptr, 0.0, tv, xa);
+        load_G(M.Dminv64, m, k, G);
+        load_Q(xf, M.cluster[k], Q);
+        stretch(xa, G, Q, F, S);
+        const double mu = M.mu[k], lam = M.lam[k], w = M.vol[k];
+        en[0] = w * psi_sigma<MODEL>(S, mu, lam, sig);
+        // Lambda = Q sigma; forces f_a = W Lambda G_a
+        const double sm[3][3] = {{sig[0], sig[5], sig[4]}, {sig[5], sig[1], sig[3]}, {sig[4], sig[3], sig[2]}};
+        double P[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) P[i][j] = w * (Q[i][0] * sm[0][j] + Q[i][1] * sm[1][j] + Q[i][2] * sm[2][j]);
+        double* ge = A.slot.ge + ((size_t)b * m + k) * 12;
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) ge[3 * a + i] = P[i][0] * G[a][0] + P[i][1] * G[a][1] + P[i][2] * G[a][2];
+        KT* ke = (KT*)A.slot.Ke + ((size_t)b * m + k) * kKe;
+        if (MODEL == 2) {
+            bool fp64 = sizeof(KT) == 8;
+            if (!fp64) {  // near-degenerate or inverted stretch: FP64 Hessian
+                const double J = S[0] * (S[1] * S[2] - S[3] * S[3]) + S[5] * (S[4] * S[3] - S[2] * S[5]) +
+                                 S[4] * (S[5] * S[3] - S[1] * S[4]);
+                fp64 = J < kFallbackJ;
+            }
+            if (fp64) {
+                double C[6][6];
+                snh_hessian<double>(S, mu, lam, C);
+                if (!chol_shifted_ok<double>(C, kSpdEps * mu)) filter_spd<double>(C, kSpdEps * mu);
+                KT Ck[6][6];
+#pragma unroll
+                for (int p = 0; p < 6; ++p)
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) Ck[p][q] = (KT)C[p][q];
+                blocks_generic<KT>(Ck, G, Q, w, ke);
+            } else {
+                KT C[6][6];
+                snh_hessian<KT>(S, mu, lam, C);
+                if (!chol_shifted_ok<KT>(C, (KT)(kSpdEps * mu))) filter_spd<KT>(C, (KT)(kSpdEps * mu));
+                blocks_generic<KT>(C, G, Q, w, ke);
+            }
+        } else {
+            blocks_quadratic<KT>(G, Q, w, mu, MODEL == 1 ? lam : 0.0, ke);
+        }
+    }
+    double tot[1];
+    double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
+    if (tile_commit<1>(en, part, blockIdx.x, gridDim.x, &A.slot.sc[b].tk_e, 0, tot) && threadIdx.x == 0)
+        A.slot.sc[b].energy = tot[0];
+}
+
+// Energy at x + alpha_b dx_b (line search trial, a6).
+template <typename T, int MODEL>
+__global__ void __launch_bounds__(kTetTile) k_energy_trial(ElemArgs A) {
+    const int b = blockIdx.y;
+    if (!A.slot.active[b]) return;
+    const MeshDev& M = A.mesh;
+    const int m = M.m, n = M.n;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double en[1] = {0.0};
+    if (k < m) {
+        const double* x = A.slot.x + (size_t)b * n * 3;
+        const T* dx = (const T*)A.slot.vec + (size_t)b * 6 * n * 3;
+        const double* xf = A.slot.xf + (size_t)b * M.H * 12;
+        double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6], sig[6];
+        gather_x<T>(x, dx, A.slot.alpha[b], M.tet[k], xa);
+        load_G(M.Dminv64, m, k, G);
+        load_Q(xf, M.cluster[k], Q);
+        stretch(xa, G, Q, F, S);
+        en[0] = M.vol[k] * psi_sigma<MODEL>(S, M.mu[k], M.lam[k], sig);
+    }
+    double tot[1];
+    double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
+    if (tile_commit<1>(en, part, blockIdx.x, gridDim.x, &A.slot.sc[b].tk_e, 0, tot) && threadIdx.x == 0)
+        A.slot.sc[b].energy_trial = tot[0];
+}
+
+// Pin targets x_p = Q_h X_v + t_h (§3.2) and the initial guess (a0).
+__global__ void k_pose_init(ElemArgs A, int init) {
+    const int b = blockIdx.y;
+    if (!A.slot.active[b]) return;
+    const MeshDev& M = A.mesh;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= M.n) return;
+    const double* xf = A.slot.xf + (size_t)b * M.H * 12;
+    double* x = A.slot.x + ((size_t)b * M.n + v) * 3;
+    const double* X = M.X + 3 * (size_t)v;
+    const int ph = M.pin_handle_v[v];
+    int h = ph >= 0 ? ph : (init == 0 ? M.vhandle[v] : -1);
+    if (h >= 0) {
+        const double* T = xf + 12 * h;
+        double y[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) y[i] = (T[4 * i] * X[0] + T[4 * i + 1] * X[1]) + T[4 * i + 2] * X[2] + T[4 * i + 3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) x[i] = y[i];
+        if (ph >= 0) {
+            double* xp = A.slot.xp + ((size_t)b * M.n + v) * 3;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) xp[i] = y[i];
+        }
+    } else if (init == 1) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) x[i] = X[i];
+    }
+}
+
+template <int MODEL>
+__global__ void k_elem_out(ElemArgs A, int b, double* __restrict__ s_out, double* __restrict__ lam_out) {
+    const MeshDev& M = A.mesh;
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= M.m) return;
+    const int k = M.tperm[o];
+    const double* x = A.slot.x + (size_t)b * M.n * 3;
+    const double* xf = A.slot.xf + (size_t)b * M.H * 12;
+    double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6], sig[6];
+    gather_x<float>(x, nullptr, 0.0, M.tet[k], xa);
+    load_G(M.Dminv64, M.m, k, G);
+    load_Q(xf, M.cluster[k], Q);
+    stretch(xa, G, Q, F, S);
+    psi_sigma<MODEL>(S, M.mu[k], M.lam[k], sig);
+    if (s_out)
+        for (int i = 0; i < 6; ++i) s_out[6 * (size_t)o + i] = S[i];
+    if (lam_out) {
+        const double sm[3][3] = {{sig[0], sig[5], sig[4]}, {sig[5], sig[1], sig[3]}, {sig[4], sig[3], sig[2]}};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                lam_out[9 * (size_t)o + 3 * i + j] = Q[i][0] * sm[0][j] + Q[i][1] * sm[1][j] + Q[i][2] * sm[2][j];
+    }
+}
+
+// Orthogonal polar factor by Higham's scaled Newton iteration
+// X <- (gamma X + X^{-T} / gamma) / 2 (N. J. Higham, "Computing the polar
+// decomposition -- with applications", SIAM J. Sci. Stat. Comput. 1986).
+template <typename RT>
+__device__ bool polar_newton(const double (&F)[3][3], RT (&R)[3][3]) {
+    RT X[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) X[i][j] = (RT)F[i][j];
+    const RT tol = sizeof(RT) == 8 ? (RT)1e-13 : (RT)1e-6;
+    for (int it = 0; it < 30; ++it) {
+        RT c00 = X[1][1] * X[2][2] - X[1][2] * X[2][1], c01 = X[1][2] * X[2][0] - X[1][0] * X[2][2],
+           c02 = X[1][0] * X[2][1] - X[1][1] * X[2][0];
+        RT c10 = X[0][2] * X[2][1] - X[0][1] * X[2][2], c11 = X[0][0] * X[2][2] - X[0][2] * X[2][0],
+           c12 = X[0][1] * X[2][0] - X[0][0] * X[2][1];
+        RT c20 = X[0][1] * X[1][2] - X[0][2] * X[1][1], c21 = X[0][2] * X[1][0] - X[0][0] * X[1][2],
+           c22 = X[0][0] * X[1][1] - X[0][1] * X[1][0];
+        RT det = X[0][0] * c00 + X[0][1] * c01 + X[0][2] * c02;
+        if (det == (RT)0) return false;
+        // X^{-T} = cof(X) / det
+        RT IT[3][3] = {{c00 / det, c01 / det, c02 / det}, {c10 / det, c11 / det, c12 / det},
+                       {c20 / det, c21 / det, c22 / det}};
+        RT nx = 0, ni = 0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                nx += X[i][j] * X[i][j];
+                ni += IT[i][j] * IT[i][j];
+            }
+        RT gam = sqrt(sqrt(ni / nx));
+        RT diff = 0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                RT y = (RT)0.5 * (gam * X[i][j] + IT[i][j] / gam);
+                diff += (y - X[i][j]) * (y - X[i][j]);
+                X[i][j] = y;
+            }
+        if (diff <= tol * tol * (RT)3) break;
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) R[i][j] = X[i][j];
+    return true;
+}
+
+// Diagnostics: inverted tets, max |skew(Q^T F)|/|F|, max angle(Q, polar(F)).
+// out3: [0] count, [1] float bits of max skew, [2] float bits of max angle.
+__global__ void k_diag(ElemArgs A, int b, unsigned* __restrict__ out3) {
+    const MeshDev& M = A.mesh;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= M.m) return;
+    const double* x = A.slot.x + (size_t)b * M.n * 3;
+    const double* xf = A.slot.xf + (size_t)b * M.H * 12;
+    double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6];
+    gather_x<float>(x, nullptr, 0.0, M.tet[k], xa);
+    load_G(M.Dminv64, M.m, k, G);
+    load_Q(xf, M.cluster[k], Q);
+    stretch(xa, G, Q, F, S);
+    const double detF = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
+                        F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
+                        F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
+    double nF = 0, nK = 0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            nF += F[i][j] * F[i][j];
+            double aij = Q[0][i] * F[0][j] + Q[1][i] * F[1][j] + Q[2][i] * F[2][j];
+            double aji = Q[0][j] * F[0][i] + Q[1][j] * F[1][i] + Q[2][j] * F[2][i];
+            nK += 0.25 * (aij - aji) * (aij - aji);
+        }
+    const float skew = (float)(sqrt(nK) / fmax(sqrt(nF), 1e-300));
+    atomicMax(&out3[1], __float_as_uint(skew));
+    if (detF <= 0.0) {
+        atomicAdd(&out3[0], 1u);
+        return;
+    }
+    // polar rotation in FP32; FP64 when the tet is nearly degenerate
+    double ang;
+    const double cube = pow(sqrt(nF / 3.0), 3.0);
+    if (detF < 1e-2 * cube) {
+        double R[3][3];
+        if (!polar_newton<double>(F, R)) return;
+        double tr = 0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) tr += Q[i][j] * R[i][j];
+        ang = acos(fmin(1.0, fmax(-1.0, 0.5 * (tr - 1.0))));
+    } else {
+        float R[3][3];
+        if (!polar_newton<float>(F, R)) return;
+        double tr = 0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) tr += Q[i][j] * (double)R[i][j];
+        ang = acos(fmin(1.0, fmax(-1.0, 0.5 * (tr - 1.0))));
+    }
+    atomicMax(&out3[2], __float_as_uint((float)ang));
+}
+
+template <typename KT>
+void launch_element_t(const ElemArgs& a, int B, cudaStream_t s) {
+    dim3 grid((a.mesh.m + kTetTile - 1) / kTetTile, B);
+    switch (a.model) {
+        case 0: k_element<KT, 0><<<grid, kTetTile, 0, s>>>(a); break;
+        case 1: k_element<KT, 1><<<grid, kTetTile, 0, s>>>(a); break;
+        default: k_element<KT, 2><<<grid, kTetTile, 0, s>>>(a); break;
+    }
+}
+
+template <typename T>
+void launch_trial_t(const ElemArgs& a, int B, cudaStream_t s) {
+    dim3 grid((a.mesh.m + kTetTile - 1) / kTetTile, B);
+    switch (a.model) {
+        case 0: k_energy_trial<T, 0><<<grid, kTetTile, 0, s>>>(a); break;
+        case 1: k_energy_trial<T, 1><<<grid, kTetTile, 0, s>>>(a); break;
+        default: k_energy_trial<T, 2><<<grid, kTetTile, 0, s>>>(a); break;
+    }
+}
+
+}  // namespace
+
+void launch_pose_init(const ElemArgs& a, int B, int init, cudaStream_t s) {
+    dim3 grid((a.mesh.n + 255) / 256, B);
+    k_pose_init<<<grid, 256, 0, s>>>(a, init);
+}
+
+void launch_element(const ElemArgs& a, int B, cudaStream_t s) {
+    if (a.slot.prec == 1) launch_element_t<float>(a, B, s);
+    else launch_element_t<double>(a, B, s);
+}
+
+void launch_energy_trial(const ElemArgs& a, int B, cudaStream_t s) {
+    if (a.slot.prec == 1) launch_trial_t<float>(a, B, s);
+    else launch_trial_t<double>(a, B, s);
+}
+
+void launch_elem_out(const ElemArgs& a, int b, double* s_out, double* lam_out, cudaStream_t s) {
+    int grid = (a.mesh.m + 127) / 128;
+    switch (a.model) {
+        case 0: k_elem_out<0><<<grid, 128, 0, s>>>(a, b, s_out, lam_out); break;
+        case 1: k_elem_out<1><<<grid, 128, 0, s>>>(a, b, s_out, lam_out); break;
+        default: k_elem_out<2><<<grid, 128, 0, s>>>(a, b, s_out, lam_out); break;
+    }
+}
+
+void launch_diag(const ElemArgs& a, int b, unsigned* out3, cudaStream_t s) {
+    k_diag<<<(a.mesh.m + 127) / 128, 128, 0, s>>>(a, b, out3);
+}
+
+}  // namespace mfem

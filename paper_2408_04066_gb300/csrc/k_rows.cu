@@ -1,0 +1,431 @@
+// Row-parallel kernels: assembly of the condensed matrix (a2) with pin
+// elimination (a3) and block-Jacobi inverse (a4), gradient gather, slope and
+// update (a6), permutations (a7), and the persistent PCG solve (a5).
+//
+// Paper §3, Eq. 12 and Algorithm 1 ("assemble", "x = A^{-1} b"): the matrix
+// sum_k W_k A_k^T H_s A_k is gathered per 3x3 block from the element blocks of
+// every tet that contains both vertices, in a fixed order (deterministic, no
+// atomics).  Pinned vertices (Eq. 6 C(x), §3.2 targets) are eliminated: their
+// rows and columns become identity/zero and their gradient entries zero, so the
+// Newton increment keeps them at x_p; the penalty form adds k_s I instead.
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+
+namespace mfem {
+
+namespace {
+
+__device__ __forceinline__ int pair_index(int a, int b) { return a * 4 - (a * (a - 1)) / 2 + (b - a); }
+
+template <typename T>
+__device__ __forceinline__ T* vecp(const SlotDev& S, int b, int which, int n) {
+    return (T*)S.vec + ((size_t)b * 6 + which) * (size_t)n * 3;
+}
+
+// One thread per block row: the row's matrix blocks, its inverse diagonal
+// block, and its gradient entry; |g_free|^2 per problem.
+template <typename KT>
+__global__ void __launch_bounds__(kRowTile) k_assemble_grad(ElemArgs A) {
+    const int b = blockIdx.y;
+    if (!A.slot.active[b]) return;
+    const MeshDev& M = A.mesh;
+    const int n = M.n;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    double gn[1] = {0.0};
+    if (row < n) {
+        const int s = row >> 5, lane = row & 31;
+        const int base = M.slice_ptr[s], w = (M.slice_ptr[s + 1] - base) >> 5;
+        const bool pin_r = M.pin_handle_v[row] >= 0;
+        const KT* Ke = (const KT*)A.slot.Ke + (size_t)b * M.m * kKe;
+        KT* val = (KT*)A.slot.val + (size_t)b * M.slots * 9;
+        for (int k = 0; k < w; ++k) {
+            const int g = base + (k << 5);
+            const int slot = g + lane;
+            const int c = M.col[slot];
+            if (c < 0) continue;
+            KT acc[9];
+#pragma unroll
+            for (int e = 0; e < 9; ++e) acc[e] = (KT)0;
+            const int c0 = M.contrib_ptr[slot], c1 = M.contrib_ptr[slot + 1];
+            for (int ci = c0; ci < c1; ++ci) {
+                const int code = M.contrib[ci];
+                const int t = code >> 4, ea = (code >> 2) & 3, eb = code & 3;
+                if (ea <= eb) {
+                    const KT* blk = Ke + (size_t)t * kKe + 9 * pair_index(ea, eb);
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) acc[e] += blk[e];
+                } else {
+                    const KT* blk = Ke + (size_t)t * kKe + 9 * pair_index(eb, ea);
+#pragma unroll
+                    for (int i = 0; i < 3; ++i)
+#pragma unroll
+                        for (int j = 0; j < 3; ++j) acc[3 * i + j] += blk[3 * j + i];
+                }
+            }
+            const bool diag = (c == row);
+            if (A.constraint == 0) {
+                if (pin_r || M.pin_handle_v[c] >= 0) {
+#pragma unroll
+                    for (int e = 0; e < 9; ++e) acc[e] = (diag && (e % 4 == 0)) ? (KT)1 : (KT)0;
+                }
+            } else if (diag && pin_r) {
+                acc[0] += (KT)A.ks;
+                acc[4] += (KT)A.ks;
+                acc[8] += (KT)A.ks;
+            }
+            KT* out = val + (size_t)g * 9 + lane;
+#pragma unroll
+            for (int e = 0; e < 9; ++e) out[32 * e] = acc[e];
+            if (diag) {  // block-Jacobi: inverse of the diagonal block, formed in FP64
+                double a[9];
+#pragma unroll
+                for (int e = 0; e < 9; ++e) a[e] = (double)acc[e];
+                double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8],
+                       c02 = a[3] * a[7] - a[4] * a[6];
+                double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+                double id = det != 0.0 ? 1.0 / det : 0.0;
+                KT* di = (KT*)A.slot.dinv + ((size_t)b * n + row) * 9;
+                di[0] = (KT)(c00 * id);
+                di[1] = (KT)((a[2] * a[7] - a[1] * a[8]) * id);
+                di[2] = (KT)((a[1] * a[5] - a[2] * a[4]) * id);
+                di[3] = (KT)(c01 * id);
+                di[4] = (KT)((a[0] * a[8] - a[2] * a[6]) * id);
+                di[5] = (KT)((a[2] * a[3] - a[0] * a[5]) * id);
+                di[6] = (KT)(c02 * id);
+                di[7] = (KT)((a[1] * a[6] - a[0] * a[7]) * id);
+                di[8] = (KT)((a[0] * a[4] - a[1] * a[3]) * id);
+            }
+        }
+        // gradient of row: sum of element forces in fixed incidence order
+        const double* ge = A.slot.ge + (size_t)b * M.m * 12;
+        double g0 = 0, g1 = 0, g2 = 0;
+        for (int ii = M.vinc_ptr[row]; ii < M.vinc_ptr[row + 1]; ++ii) {
+            const int code = M.vinc[ii];
+            const double* f = ge + (size_t)(code >> 2) * 12 + 3 * (code & 3);
+            g0 += f[0];
+            g1 += f[1];
+            g2 += f[2];
+        }
+        if (pin_r) {
+            if (A.constraint == 0) {
+                g0 = g1 = g2 = 0.0;
+            } else {
+                const double* x = A.slot.x + ((size_t)b * n + row) * 3;
+                const double* xp = A.slot.xp + ((size_t)b * n + row) * 3;
+                g0 += A.ks * (x[0] - xp[0]);
+                g1 += A.ks * (x[1] - xp[1]);
+                g2 += A.ks * (x[2] - xp[2]);
+            }
+        }
+        double* gout = A.slot.g + ((size_t)b * n + row) * 3;
+        gout[0] = g0;
+        gout[1] = g1;
+        gout[2] = g2;
+        gn[0] = g0 * g0 + g1 * g1 + g2 * g2;
+    }
+    double tot[1];
+    double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
+    if (tile_commit<1>(gn, part, blockIdx.x, gridDim.x, &A.slot.sc[b].tk_g, 0, tot) && threadIdx.x == 0)
+        A.slot.sc[b].gnorm2 = tot[0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRowTile) k_slope(ElemArgs A) {
+    const int b = blockIdx.y;
+    if (!A.slot.active[b]) return;
+    const int n = A.mesh.n;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[1] = {0.0};
+    if (row < n) {
+        const double* g = A.slot.g + ((size_t)b * n + row) * 3;
+        const T* dx = vecp<T>(A.slot, b, 0, n) + 3 * (size_t)row;
+        v[0] = g[0] * (double)dx[0] + g[1] * (double)dx[1] + g[2] * (double)dx[2];
+    }
+    double tot[1];
+    double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
+    if (tile_commit<1>(v, part, blockIdx.x, gridDim.x, &A.slot.sc[b].tk_s, 0, tot) && threadIdx.x == 0)
+        A.slot.sc[b].slope = tot[0];
+}
+
+template <typename T>
+__global__ void k_update(ElemArgs A) {
+    const int b = blockIdx.y;
+    if (!A.slot.active[b]) return;
+    const int n = A.mesh.n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    const T* dx = vecp<T>(A.slot, b, 0, n);
+    double* x = A.slot.x + (size_t)b * n * 3;
+    x[i] = fma(A.slot.alpha[b], (double)dx[i], x[i]);
+}
+
+__global__ void k_unpermute(ElemArgs A, double* __restrict__ out) {
+    const int b = blockIdx.y;
+    const int n = A.mesh.n;
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const int v = A.mesh.vperm[o];
+    const double* x = A.slot.x + ((size_t)b * n + v) * 3;
+    double* y = out + ((size_t)b * n + o) * 3;
+    y[0] = x[0];
+    y[1] = x[1];
+    y[2] = x[2];
+}
+
+__global__ void k_permute_in(ElemArgs A, int b, const double* __restrict__ xin) {
+    const int n = A.mesh.n;
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= n) return;
+    const int v = A.mesh.vperm[o];
+    double* x = A.slot.x + ((size_t)b * n + v) * 3;
+    x[0] = xin[3 * (size_t)o];
+    x[1] = xin[3 * (size_t)o + 1];
+    x[2] = xin[3 * (size_t)o + 2];
+}
+
+// r = -g, z = D^{-1} r, dx = 0, p_old = 0; rho = r.z, rr0 = r.r per problem.
+template <typename T>
+__global__ void k_pcg_init(ElemArgs A, double tol2, int maxit) {
+    const int b = blockIdx.y;
+    if (!A.slot.active[b]) return;
+    const int n = A.mesh.n;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    double v[2] = {0.0, 0.0};
+    if (row < n) {
+        const double* g = A.slot.g + ((size_t)b * n + row) * 3;
+        const T* di = (const T*)A.slot.dinv + ((size_t)b * n + row) * 9;
+        T* dx = vecp<T>(A.slot, b, 0, n) + 3 * (size_t)row;
+        T* r = vecp<T>(A.slot, b, 1, n) + 3 * (size_t)row;
+        T* z = vecp<T>(A.slot, b, 2, n) + 3 * (size_t)row;
+        T* p0 = vecp<T>(A.slot, b, 3, n) + 3 * (size_t)row;
+        T rr[3] = {(T)(-g[0]), (T)(-g[1]), (T)(-g[2])};
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            T zi = di[3 * i] * rr[0] + di[3 * i + 1] * rr[1] + di[3 * i + 2] * rr[2];
+            dx[i] = (T)0;
+            r[i] = rr[i];
+            z[i] = zi;
+            p0[i] = (T)0;
+            v[0] += (double)rr[i] * (double)zi;
+            v[1] += (double)rr[i] * (double)rr[i];
+        }
+    }
+    double tot[2];
+    double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
+    if (tile_commit<2>(v, part, blockIdx.x, gridDim.x, &A.slot.sc[b].tk_init, 1, tot) && threadIdx.x == 0) {
+        ProbScal* sc = &A.slot.sc[b];
+        sc->rho = tot[0];
+        sc->rr0 = tot[1];
+        sc->rr = tot[1];
+        sc->beta = 0.0;
+        sc->alpha = 0.0;
+        sc->iter = 0;
+        sc->tol2 = tol2;
+        sc->maxit = maxit;
+        sc->state = (tot[1] > 0.0 && tot[0] > 0.0 && maxit > 0) ? kActive : kConverged;
+    }
+}
+
+// ---- persistent PCG ---------------------------------------------------------
+// One cooperative launch runs PCG iterations for every problem in the
+// descriptor table until all have converged (|r| <= tol |r0|) or hit their cap.
+// Work unit = (problem, tile of TILE rows); each block strides over units.
+// Phase A: p_new = z + beta p_old (neighbours recomputed on the fly, so no extra
+// barrier), q = K p_new, tile partial of p.q; the last tile of a problem sets
+// alpha.  Phase B: dx += alpha p, r -= alpha q, z = D^{-1} r, partials of r.z
+// and r.r; the last tile sets beta and the convergence state.
+template <typename T, int TILE>
+__global__ void __launch_bounds__(TILE) k_pcg(const PcgDesc<T>* __restrict__ D, int n_probs, int n_units,
+                                              GridBar* bar, int max_iters) {
+    __shared__ int s_any;
+    for (int it = 0; it < max_iters; ++it) {
+        if (threadIdx.x == 0) {
+            int any = 0;
+            for (int p = 0; p < n_probs; ++p) any |= (ld_volatile_i32(&D[p].sc->state) == kActive);
+            s_any = any;
+        }
+        __syncthreads();
+        if (!s_any) break;
+        // ---------------- phase A ----------------
+        int p = 0;
+        for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+            while (p + 1 < n_probs && D[p + 1].unit_begin <= u) ++p;
+            const PcgDesc<T>& d = D[p];
+            ProbScal* sc = d.sc;
+            if (ld_volatile_i32(&sc->state) != kActive) continue;
+            const int tile = u - d.unit_begin;
+            const int row = tile * TILE + threadIdx.x;
+            const int iter = ld_volatile_i32(&sc->iter);
+            const T* __restrict__ po = (iter & 1) ? d.p1 : d.p0;
+            T* __restrict__ pn = (iter & 1) ? d.p0 : d.p1;
+            const T beta = (T)(*(volatile double*)&sc->beta);
+            const T* __restrict__ z = d.z;
+            double v[1] = {0.0};
+            if (row < d.n_rows) {
+                const int s = row >> 5, lane = row & 31;
+                const int base = d.slice_ptr[s], w = (d.slice_ptr[s + 1] - base) >> 5;
+                T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll 4
+                for (int k = 0; k < w; ++k) {
+                    const int g = base + (k << 5);
+                    const int c = __ldg(d.col + g + lane);
+                    if (c >= 0) {
+                        const T* vv = d.val + (size_t)g * 9 + lane;
+                        const T pc0 = fma(beta, po[3 * c], z[3 * c]);
+                        const T pc1 = fma(beta, po[3 * c + 1], z[3 * c + 1]);
+                        const T pc2 = fma(beta, po[3 * c + 2], z[3 * c + 2]);
+                        a0 += __ldg(vv) * pc0 + __ldg(vv + 32) * pc1 + __ldg(vv + 64) * pc2;
+                        a1 += __ldg(vv + 96) * pc0 + __ldg(vv + 128) * pc1 + __ldg(vv + 160) * pc2;
+                        a2 += __ldg(vv + 192) * pc0 + __ldg(vv + 224) * pc1 + __ldg(vv + 256) * pc2;
+                    }
+                }
+                const T pr0 = fma(beta, po[3 * row], z[3 * row]);
+                const T pr1 = fma(beta, po[3 * row + 1], z[3 * row + 1]);
+                const T pr2 = fma(beta, po[3 * row + 2], z[3 * row + 2]);
+                pn[3 * row] = pr0;
+                pn[3 * row + 1] = pr1;
+                pn[3 * row + 2] = pr2;
+                d.q[3 * row] = a0;
+                d.q[3 * row + 1] = a1;
+                d.q[3 * row + 2] = a2;
+                v[0] = (double)pr0 * (double)a0 + (double)pr1 * (double)a1 + (double)pr2 * (double)a2;
+            }
+            double tot[1];
+            if (tile_commit<1>(v, d.part, tile, d.n_tiles, &sc->tk_a, 0, tot) && threadIdx.x == 0) {
+                const double pq = tot[0];
+                if (pq > 0.0 && isfinite(pq)) {
+                    sc->alpha = sc->rho / pq;
+                } else {  // breakdown (p = 0 or K not SPD along p): stop with current dx
+                    sc->alpha = 0.0;
+                    sc->state = kConverged;
+                }
+            }
+        }
+        grid_sync(bar);
+        if (grid_failed(bar)) break;
+        // ---------------- phase B ----------------
+        p = 0;
+        for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
+            while (p + 1 < n_probs && D[p + 1].unit_begin <= u) ++p;
+            const PcgDesc<T>& d = D[p];
+            ProbScal* sc = d.sc;
+            if (ld_volatile_i32(&sc->state) != kActive) continue;
+            const int tile = u - d.unit_begin;
+            const int row = tile * TILE + threadIdx.x;
+            const int iter = ld_volatile_i32(&sc->iter);
+            const T* __restrict__ pn = (iter & 1) ? d.p0 : d.p1;
+            const T alpha = (T)(*(volatile double*)&sc->alpha);
+            double v[2] = {0.0, 0.0};
+            if (row < d.n_rows) {
+                const T* di = d.dinv + 9 * (size_t)row;
+                T rr[3];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    d.dx[3 * row + i] = fma(alpha, pn[3 * row + i], d.dx[3 * row + i]);
+                    rr[i] = fma(-alpha, d.q[3 * row + i], d.r[3 * row + i]);
+                    d.r[3 * row + i] = rr[i];
+                }
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const T zi = di[3 * i] * rr[0] + di[3 * i + 1] * rr[1] + di[3 * i + 2] * rr[2];
+                    d.z[3 * row + i] = zi;
+                    v[0] += (double)rr[i] * (double)zi;
+                    v[1] += (double)rr[i] * (double)rr[i];
+                }
+            }
+            double tot[2];
+            if (tile_commit<2>(v, d.part, tile, d.n_tiles, &sc->tk_b, 1, tot) && threadIdx.x == 0) {
+                const double rho_new = tot[0];
+                sc->beta = sc->rho != 0.0 ? rho_new / sc->rho : 0.0;
+                sc->rho = rho_new;
+                sc->rr = tot[1];
+                const int itn = sc->iter + 1;
+                sc->iter = itn;
+                if (!(tot[1] > sc->tol2 * sc->rr0)) sc->state = kConverged;
+                else if (itn >= sc->maxit) sc->state = kMaxIter;
+            }
+        }
+        grid_sync(bar);
+        if (grid_failed(bar)) break;
+    }
+}
+
+template <typename T, int TILE>
+int max_blocks_t() {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg<T, TILE>, TILE, 0);
+    return sms * per;
+}
+
+template <typename T, int TILE>
+cudaError_t launch_pcg_t(const PcgDesc<T>* descs, int n_probs, int n_units, GridBar* bar, int max_iters,
+                         int grid, cudaStream_t s) {
+    void* args[] = {(void*)&descs, (void*)&n_probs, (void*)&n_units, (void*)&bar, (void*)&max_iters};
+    return cudaLaunchCooperativeKernel((const void*)k_pcg<T, TILE>, dim3(grid), dim3(TILE), args, 0, s);
+}
+
+}  // namespace
+
+void launch_assemble(const ElemArgs& a, int B, cudaStream_t s) {
+    dim3 grid((a.mesh.n + kRowTile - 1) / kRowTile, B);
+    if (a.slot.prec == 1) k_assemble_grad<float><<<grid, kRowTile, 0, s>>>(a);
+    else k_assemble_grad<double><<<grid, kRowTile, 0, s>>>(a);
+}
+
+void launch_gradient(const ElemArgs& a, int B, cudaStream_t s) { launch_assemble(a, B, s); }
+
+void launch_slope(const ElemArgs& a, int B, cudaStream_t s) {
+    dim3 grid((a.mesh.n + kRowTile - 1) / kRowTile, B);
+    if (a.slot.prec == 1) k_slope<float><<<grid, kRowTile, 0, s>>>(a);
+    else k_slope<double><<<grid, kRowTile, 0, s>>>(a);
+}
+
+void launch_update(const ElemArgs& a, int B, cudaStream_t s) {
+    dim3 grid((3 * a.mesh.n + 255) / 256, B);
+    if (a.slot.prec == 1) k_update<float><<<grid, 256, 0, s>>>(a);
+    else k_update<double><<<grid, 256, 0, s>>>(a);
+}
+
+void launch_unpermute(const ElemArgs& a, int B, double* out, cudaStream_t s) {
+    dim3 grid((a.mesh.n + 255) / 256, B);
+    k_unpermute<<<grid, 256, 0, s>>>(a, out);
+}
+
+void launch_permute_in(const ElemArgs& a, int b, const double* xin, cudaStream_t s) {
+    k_permute_in<<<(a.mesh.n + 255) / 256, 256, 0, s>>>(a, b, xin);
+}
+
+void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int maxit, cudaStream_t s) {
+    dim3 grid((a.mesh.n + tile_rows - 1) / tile_rows, B);
+    if (a.slot.prec == 1) k_pcg_init<float><<<grid, tile_rows, 0, s>>>(a, tol2, maxit);
+    else k_pcg_init<double><<<grid, tile_rows, 0, s>>>(a, tol2, maxit);
+}
+
+template <typename T>
+int pcg_max_blocks(int tile_rows) {
+    switch (tile_rows) {
+        case 64: return max_blocks_t<T, 64>();
+        case 128: return max_blocks_t<T, 128>();
+        default: return max_blocks_t<T, 256>();
+    }
+}
+
+template <typename T>
+cudaError_t launch_pcg(const PcgDesc<T>* descs, int n_probs, int n_units, GridBar* bar, int max_iters,
+                       int tile_rows, int grid, cudaStream_t s) {
+    switch (tile_rows) {
+        case 64: return launch_pcg_t<T, 64>(descs, n_probs, n_units, bar, max_iters, grid, s);
+        case 128: return launch_pcg_t<T, 128>(descs, n_probs, n_units, bar, max_iters, grid, s);
+        default: return launch_pcg_t<T, 256>(descs, n_probs, n_units, bar, max_iters, grid, s);
+    }
+}
+
+template int pcg_max_blocks<float>(int);
+template int pcg_max_blocks<double>(int);
+template cudaError_t launch_pcg<float>(const PcgDesc<float>*, int, int, GridBar*, int, int, int, cudaStream_t);
+template cudaError_t launch_pcg<double>(const PcgDesc<double>*, int, int, GridBar*, int, int, int, cudaStream_t);
+
+}  // namespace mfem

@@ -1,0 +1,95 @@
+// Launch wrappers of the pose-solver kernels (host-callable).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "dev.cuh"
+
+namespace mfem {
+
+// Static per-mesh data on the device (internal vertex/tet order).
+struct MeshDev {
+    int n = 0, m = 0, H = 0, n_slices = 0, n_pins = 0;
+    int64_t slots = 0;
+    int4* tet = nullptr;          // [m]
+    double* Dminv64 = nullptr;    // [9][m]
+    float* Dminv32 = nullptr;     // [9][m]
+    double* vol = nullptr;        // [m]
+    int* cluster = nullptr;       // [m]
+    double* mu = nullptr;         // [m]
+    double* lam = nullptr;        // [m]
+    double* X = nullptr;          // [n][3]
+    int* vhandle = nullptr;       // [n]
+    int* pin_handle_v = nullptr;  // [n] handle or -1
+    int* vperm = nullptr;         // [n] caller vertex -> internal
+    int* tperm = nullptr;         // [m] caller tet -> internal
+    int* slice_ptr = nullptr;     // [n_slices+1]
+    int* col = nullptr;           // [slots]
+    int* contrib_ptr = nullptr;   // [slots+1]
+    int* contrib = nullptr;       // [16m]
+    int* vinc_ptr = nullptr;      // [n+1]
+    int* vinc = nullptr;          // [4m]
+};
+
+// Per-batch problem buffers of one mesh (B problems, strides in elements).
+struct SlotDev {
+    int cap = 0;
+    int prec = 1;            // 1 = mixed (float K and PCG vectors), 0 = FP64
+    double* xf = nullptr;    // [B][H][12]
+    double* x = nullptr;     // [B][n][3]
+    double* xp = nullptr;    // [B][n][3] pin targets (pinned rows only)
+    double* g = nullptr;     // [B][n][3] masked gradient
+    double* ge = nullptr;    // [B][m][12] element forces
+    void* Ke = nullptr;      // [B][m][90]  (float or double)
+    void* val = nullptr;     // [B][slots*9]
+    void* dinv = nullptr;    // [B][n][9]
+    void* vec = nullptr;     // [B][6][n][3]: dx r z p0 p1 q
+    double* part = nullptr;  // [B][tiles][4]
+    int part_tiles = 0;
+    ProbScal* sc = nullptr;  // [B]
+    int* active = nullptr;   // [B]
+    double* alpha = nullptr; // [B] step length for update / trial
+    double* outbuf = nullptr;  // [B][n][3] caller-order staging
+};
+
+struct ElemArgs {
+    MeshDev mesh;
+    SlotDev slot;
+    int model;        // mfem_model
+    int constraint;   // 0 eliminate, 1 penalty
+    double ks;
+};
+
+// a0: pose -> pin targets and initial guess (init: 0 rigid, 1 rest, 2 warm)
+void launch_pose_init(const ElemArgs& a, int B, int init, cudaStream_t s);
+// a1: element step (Ke, element forces, energy) for active problems
+void launch_element(const ElemArgs& a, int B, cudaStream_t s);
+// a6: energy at x + alpha dx for active problems (line-search trial)
+void launch_energy_trial(const ElemArgs& a, int B, cudaStream_t s);
+// a2/a3/a4: gather matrix blocks with pin elimination, block-Jacobi inverse
+void launch_assemble(const ElemArgs& a, int B, cudaStream_t s);
+// gradient gather with pin elimination/penalty and |g|^2 per problem
+void launch_gradient(const ElemArgs& a, int B, cudaStream_t s);
+// slope g.dx per problem
+void launch_slope(const ElemArgs& a, int B, cudaStream_t s);
+// x += alpha dx
+void launch_update(const ElemArgs& a, int B, cudaStream_t s);
+// x (internal order) -> out [B][n][3] caller order
+void launch_unpermute(const ElemArgs& a, int B, double* out, cudaStream_t s);
+// warm state import: caller-order [n][3] -> slot x
+void launch_permute_in(const ElemArgs& a, int b, const double* xin, cudaStream_t s);
+// element outputs (s, lambda) in caller tet order for problem b
+void launch_elem_out(const ElemArgs& a, int b, double* s_out, double* lam_out, cudaStream_t s);
+// diagnostics: inverted count, max rel skew, max angle for problem b
+void launch_diag(const ElemArgs& a, int b, unsigned* out3, cudaStream_t s);
+
+// PCG init and persistent solve
+void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int maxit, cudaStream_t s);
+template <typename T>
+cudaError_t launch_pcg(const PcgDesc<T>* descs_dev, int n_probs, int n_units, GridBar* bar,
+                       int max_iters, int tile_rows, int grid_blocks, cudaStream_t s);
+template <typename T>
+int pcg_max_blocks(int tile_rows);
+
+}  // namespace mfem

@@ -1,0 +1,86 @@
+"""The C-ABI library without a GPU: it builds, loads, exports every symbol the
+header declares, and its host-only planning matches the oracle."""
+import re
+import os
+
+import numpy as np
+import pytest
+
+from paper_2408_04066_gb300 import build as B
+from paper_2408_04066_gb300 import mfem
+from oracle import solve as S
+from synth import bar_twist_config, figure_config, bar_mesh
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "mfem.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return mfem.load()
+
+
+def _declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(mfem_\w+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert lib.mfem_abi_version() == 1
+    # the binding declares the same set
+    assert sorted(n for n, _, _ in mfem._SIGS) == names
+
+
+def test_status_strings(lib):
+    for s in range(8):
+        assert lib.mfem_status_string(s)
+
+
+@pytest.mark.parametrize("which", ["bar", "figure"])
+def test_host_plan_matches_oracle(lib, which):
+    cfg = bar_twist_config() if which == "bar" else figure_config(10000, seeds=[])
+    tc, pinned, ph = mfem.plan(cfg["X"], cfg["T"], cfg["joints"], cfg["parent"], cfg["cluster_rule"],
+                               cfg["pin_verts"], cfg["pin_handle"], cfg["pin_radius"])
+    st = S.Setup.from_config(cfg)
+    assert np.array_equal(tc, st.cluster)
+    assert np.array_equal(np.nonzero(pinned)[0], np.sort(st.pin_verts))
+    order = np.argsort(st.pin_verts)
+    assert np.array_equal(ph[pinned], st.pin_handle[order])
+
+
+def test_host_plan_rejects_bad_inputs(lib):
+    X, T = bar_mesh(1, 1, 2)
+    joints, parent = np.zeros((1, 3)), [-1]
+    bad = T.copy()
+    bad[3, 2] = len(X)
+    with pytest.raises(mfem.MfemError) as e:
+        mfem.plan(X, bad, joints, parent, pin_radius=0.5)
+    assert e.value.status == mfem.MFEM_EINVAL and "out of range" in str(e.value)
+    flip = T.copy()
+    flip[5, [1, 2]] = flip[5, [2, 1]]            # inverted rest tet
+    with pytest.raises(mfem.MfemError) as e:
+        mfem.plan(X, flip, joints, parent, pin_radius=0.5)
+    assert e.value.status == mfem.MFEM_EDEGEN and "tet 5" in str(e.value)
+    Xn = X.copy()
+    Xn[2, 1] = np.nan
+    with pytest.raises(mfem.MfemError) as e:
+        mfem.plan(Xn, T, joints, parent, pin_radius=0.5)
+    assert e.value.status == mfem.MFEM_EINVAL
+    with pytest.raises(mfem.MfemError) as e:
+        mfem.plan(X, T, np.zeros((2, 3)), [-1, 1], pin_radius=0.5)     # a joint cannot parent itself
+    assert "parent[1]" in str(e.value)
+    with pytest.raises(mfem.MfemError):
+        mfem.plan(X, T, np.zeros((1, 3)), [-1], pin_verts=[0, 0], pin_handle=[0, 0])
+
+
+def test_user_clusters_override(lib):
+    cfg = figure_config(3000, seeds=[])
+    user = np.random.default_rng(0).integers(0, 15, size=len(cfg["T"]))
+    tc, _, _ = mfem.plan(cfg["X"], cfg["T"], cfg["joints"], cfg["parent"], pin_radius=cfg["pin_radius"],
+                         tet_cluster=user)
+    assert np.array_equal(tc, user)

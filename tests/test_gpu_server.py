@@ -1,0 +1,72 @@
+"""Serving on the GPU: continuous batching over resident meshes.  Every request's
+result equals the same pose solved alone (same kernels, per-problem
+deterministic reductions)."""
+import numpy as np
+import pytest
+
+from synth import bar_twist_config, figure_config
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mfem():
+    from paper_2408_04066_gb300 import build, mfem as m
+    build.build()
+    m.load()
+    return m
+
+
+def test_served_results_equal_alone(mfem):
+    figA = dict(figure_config(3000, seeds=range(5)), model="snh")
+    figB = dict(figure_config(10000, seeds=range(5, 10)), model="corot")
+    opts = dict(precision="mixed", tile_rows=128)
+    alone = {}
+    for name, cfg in (("A", figA), ("B", figB)):
+        ctx = mfem.Context.from_config(cfg, **opts)
+        for i, xf in enumerate(cfg["xfs"]):
+            x, st = ctx.solve_batch(xf[None])
+            alone[(name, i)] = (x[0], st[0])
+        ctx.close()
+    srv = mfem.Server(device_mem_budget=0, max_slots=4)
+    ids = {"A": srv.add(mfem.Context.from_config(figA, **opts)),
+           "B": srv.add(mfem.Context.from_config(figB, **opts))}
+    tickets = []
+    for i in range(5):   # interleave meshes; more requests than slots
+        for name, cfg in (("A", figA), ("B", figB)):
+            tickets.append(((name, i), srv.submit(ids[name], cfg["xfs"][i])))
+    for key, t in tickets:
+        out, st, lat = srv.wait(t, timeout_ms=120000)
+        xa, sa = alone[key]
+        assert np.array_equal(out, xa), key
+        assert st["newton_iters"] == sa["newton_iters"]
+        assert lat > 0
+    c = srv.counters()
+    assert c["completed"] == 10 and c["peak_slots"] <= 4
+    srv.close()
+
+
+def test_server_rejects_bad_requests(mfem):
+    cfg = bar_twist_config()
+    srv = mfem.Server(max_slots=2)
+    mid = srv.add(mfem.Context.from_config(cfg, precision="mixed"))
+    bad = cfg["xfs"][0].copy()
+    bad[1, 0] = 2.0
+    with pytest.raises(mfem.MfemError):
+        srv.submit(mid, bad)
+    with pytest.raises(mfem.MfemError):
+        srv.submit(mid + 5, cfg["xfs"][0])
+    t = srv.submit(mid, cfg["xfs"][0])
+    res = srv.wait(t, timeout_ms=60000)
+    assert res is not None and res[1]["converged"] == 1
+    srv.close()
+
+
+def test_server_budget_refuses_too_large_mesh(mfem):
+    cfg = figure_config(3000, seeds=[])
+    cfg["model"] = "corot"
+    srv = mfem.Server(device_mem_budget=1 << 16, max_slots=2)   # 64 KiB: no slot fits
+    with pytest.raises(mfem.MfemError) as e:
+        srv.add(mfem.Context.from_config(cfg, precision="mixed"))
+    assert e.value.status == mfem.MFEM_ENOMEM
+    srv.close()
