@@ -8,7 +8,9 @@ Newton iterations.  This driver runs Newton on E(x) for every model:
 
   x <- initial guess; pinned x_v <- x_p                     (elimination mode)
   repeat up to newton_max times:
-      g = dE/dx on free DOFs; stop if |g| <= newton_tol * |g(x_0)|
+      g = dE/dx on free DOFs; stop if |g| <= newton_tol * |g(x_ref)|, where
+      x_ref is the rigid initial guess (so the test does not depend on the
+      start: a warm start at the solution stops at once)
       K = sum_k W_k A_k^T H_s A_k on free DOFs (Eq. 12; SNH: H_s SPD-projected)
       solve K d = -g              (sparse direct LU, or FP64 Jacobi-PCG)
       SNH: backtracking alpha in {1, 1/2, ..., 2^-ls_max} until
@@ -136,13 +138,13 @@ def solve(st, xf, model, constraint="eliminate", ks=0.0, newton_max=50, newton_t
         return g
 
     info = dict(gnorm=[], alpha=[], energy=[], cg_iters=[], converged=False)
-    g0 = None
+    x_ref = initial_guess(st, Q, t, "rigid")
+    x_ref[st.pin_verts] = xp
+    g0 = float(np.linalg.norm(grad(x_ref).reshape(-1)[fidx]))
     for it in range(newton_max + 1):
         g = grad(x).reshape(-1)[fidx]
         gn = float(np.linalg.norm(g))
         info["gnorm"].append(gn)
-        if g0 is None:
-            g0 = gn
         if gn == 0.0 or gn <= newton_tol * g0:
             info["converged"] = True
             break

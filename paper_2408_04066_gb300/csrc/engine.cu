@@ -396,7 +396,10 @@ mfem_status autotune_tile(mfem_ctx* c, std::vector<Group>& gs) {
 mfem_status newton_step(std::vector<Group>& gs) {
     mfem_ctx* c = gs[0].ctx;
     cudaStream_t s = c->stream;
-    // a0: apply poses of newly admitted problems
+    // a0: apply poses of newly admitted problems.  The Newton stop test is
+    // relative to |g_free| at the rigid initial guess; for REST and WARM starts
+    // that reference needs one gradient pass at the rigid guess first (the warm
+    // state is parked in outbuf meanwhile).
     for (auto& g : gs) {
         std::vector<int> f(g.B, 0);
         bool any = false;
@@ -406,14 +409,32 @@ mfem_status newton_step(std::vector<Group>& gs) {
         mfem_ctx* gc = g.ctx;
         mfem_status st = upload_active(gc, g.B, f);
         if (st != MFEM_OK) return st;
-        launch_pose_init(elem_args(gc), g.B, gc->opt.init == MFEM_INIT_RIGID ? 0 : (gc->opt.init == MFEM_INIT_REST ? 1 : 2), s);
+        const int init = gc->opt.init == MFEM_INIT_RIGID ? 0 : (gc->opt.init == MFEM_INIT_REST ? 1 : 2);
+        std::vector<double> gref(g.B, -1.0);
+        if (init != 0) {
+            const size_t xbytes = sizeof(double) * 3 * (size_t)gc->plan.n * g.B;
+            if (init == 2) CK(cudaMemcpyAsync(gc->slot.outbuf, gc->slot.x, xbytes, cudaMemcpyDeviceToDevice, s));
+            ElemArgs a = elem_args(gc);
+            launch_pose_init(a, g.B, 0, s);
+            launch_element(a, g.B, s);
+            launch_assemble(a, g.B, s);
+            gc->prof.launches += 3;
+            st = read_scalars(gc, g.B);
+            if (st != MFEM_OK) return st;
+            CK(cudaStreamSynchronize(s));
+            synced(gs);
+            for (int b = 0; b < g.B; ++b)
+                if (f[b]) gref[b] = std::sqrt(gc->sc_host[b].gnorm2);
+            if (init == 2) CK(cudaMemcpyAsync(gc->slot.x, gc->slot.outbuf, xbytes, cudaMemcpyDeviceToDevice, s));
+        }
+        launch_pose_init(elem_args(gc), g.B, init, s);
         gc->prof.launches++;
         for (int b = 0; b < g.B; ++b)
             if (g.ph[b].need_init) {
                 g.ph[b].need_init = 0;
                 g.ph[b].active = 1;
                 g.ph[b].it = 0;
-                g.ph[b].g0 = -1.0;
+                g.ph[b].g0 = gref[b];
                 g.ph[b].pcg_iters = 0;
                 g.ph[b].ran_pcg = 0;
                 g.ph[b].status = MFEM_OK;

@@ -345,6 +345,8 @@ class Server:
         return mid.value
 
     def submit(self, mesh_id, xf, out=None):
+        if mesh_id not in self._meshes:
+            raise MfemError(MFEM_EINVAL, f"unknown mesh id {mesh_id}")
         n, H = self._meshes[mesh_id]
         xf = _f64(xf, (H, 12))
         out = np.empty((n, 3)) if out is None else out
