@@ -192,6 +192,27 @@ mfem_status mfem_solve_batch(mfem_ctx* ctx, const double* xf, int32_t B, double*
  * Host arrays, caller's tet order; either may be NULL. */
 mfem_status mfem_get_elem(mfem_ctx* ctx, double* s, double* lam);
 
+/* mfem_get_elem for callers that cannot allocate device memory after set-up.
+ * The paper has no counterpart; this is a deployment variant.  mfem_get_elem
+ * allocates and frees a device staging buffer on every call, and cudaFree
+ * waits for the whole device; a per-frame animation loop or a host
+ * application's plugin that owns a fixed device budget may allocate only while
+ * it sets up, so it cannot call that.  This entry point runs the same kernel
+ * but stages through a fixed file-scope device array of 15 doubles per tet for
+ * at most MFEM_ELEM_STATIC_MAX_TETS tets (7.5 MiB), held by every GPU that
+ * loads the library until the process exits; it calls no cudaMalloc, cudaFree
+ * or allocating library routine.  Arguments and outputs are those of
+ * mfem_get_elem (host s [m][6], lam [m][9], caller tet order, either may be
+ * NULL).  The context's device must be current.  The first call on a device
+ * looks up the array's device address (cudaGetSymbolAddress): make that first
+ * call before any stream capture.  All calls on a device share the one array,
+ * which keeps the last call's contents (each call overwrites every entry it
+ * returns); two calls whose work overlaps on the GPU (other streams or
+ * threads) race on it.  Meshes with more than MFEM_ELEM_STATIC_MAX_TETS tets
+ * are rejected with MFEM_EINVAL. */
+#define MFEM_ELEM_STATIC_MAX_TETS 65536
+mfem_status mfem_get_elem_static(mfem_ctx* ctx, double* s, double* lam);
+
 /* Warm-start state (the last solution, host [n][3], caller order). */
 mfem_status mfem_get_state(const mfem_ctx* ctx, double* x);
 mfem_status mfem_set_state(mfem_ctx* ctx, const double* x);

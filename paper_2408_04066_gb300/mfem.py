@@ -80,6 +80,7 @@ _SIGS = [
     ("mfem_solve_batch", C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
                                      C.POINTER(Stats)]),
     ("mfem_get_elem", C.c_int32, [C.c_void_p, _dp, _dp]),
+    ("mfem_get_elem_static", C.c_int32, [C.c_void_p, _dp, _dp]),
     ("mfem_get_state", C.c_int32, [C.c_void_p, _dp]),
     ("mfem_set_state", C.c_int32, [C.c_void_p, _dp]),
     ("mfem_get_profile", C.c_int32, [C.c_void_p, C.POINTER(Profile)]),
@@ -301,6 +302,14 @@ class Context:
         s = np.empty((self.m, 6))
         lam = np.empty((self.m, 9))
         _check(self._lib.mfem_get_elem(self._ctx, _p(s), _p(lam)), self._ctx)
+        return s, lam
+
+    def get_elem_static(self, s=None, lam=None):
+        """mfem_get_elem_static: same outputs, staged through the library's
+        fixed device array (no device allocation)."""
+        s = np.empty((self.m, 6)) if s is None else s
+        lam = np.empty((self.m, 9)) if lam is None else lam
+        _check(self._lib.mfem_get_elem_static(self._ctx, _p(s), _p(lam)), self._ctx)
         return s, lam
 
     def get_state(self):
