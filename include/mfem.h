@@ -55,7 +55,7 @@ typedef enum { MFEM_ARAP = 0, MFEM_COROT = 1, MFEM_SNH = 2 } mfem_model;
 typedef enum { MFEM_FP64 = 0, MFEM_MIXED = 1 } mfem_precision;
 typedef enum { MFEM_ELIMINATE = 0, MFEM_PENALTY = 1 } mfem_constraint;
 typedef enum { MFEM_CLUSTER_BONE = 0, MFEM_CLUSTER_JOINT = 1 } mfem_cluster_rule;
-typedef enum { MFEM_INIT_RIGID = 0, MFEM_INIT_REST = 1, MFEM_INIT_WARM = 2 } mfem_init;
+typedef enum { MFEM_INIT_RIGID = 0, MFEM_INIT_REST = 1, MFEM_INIT_WARM = 2, MFEM_INIT_COROT = 3 } mfem_init;
 typedef enum { MFEM_MEM_HOST = 0, MFEM_MEM_DEVICE = 1 } mfem_memory;
 
 /* Material (§4 "A solver friendly to variant energies"; §4 "Allowing
@@ -102,14 +102,21 @@ typedef struct {
                             MFEM_PENALTY: k_s/2 |x_v - x_p|^2 per pin (Eq. 6) */
     double k_s;          /* penalty stiffness (PENALTY only) */
     double newton_tol;   /* stop when |g_free| <= newton_tol |g_free(x_0)| (1e-6) */
-    double cg_tol;       /* PCG relative residual per Newton step (1e-3 MIXED, 1e-6 FP64) */
+    double cg_tol;       /* PCG relative residual per Newton step, inexact Newton (1e-2) */
     int32_t newton_max;  /* Newton step cap (50) */
     int32_t cg_max;      /* PCG iteration cap per Newton step (5000) */
-    int32_t init;        /* mfem_init: RIGID (default) moves every vertex with the
-                            handle its rest position clusters to; REST uses X
-                            (Algorithm 1); WARM continues from the last solution */
+    int32_t init;        /* mfem_init: COROT (default) -- for SNH, first one Newton
+                            step of the co-rotational energy (same mu, lambda;
+                            quadratic, same rest Hessian) from the rigid guess,
+                            counted as a Newton step; for ARAP/corot the rigid
+                            guess.  RIGID moves every vertex with the handle its
+                            rest position clusters to; REST uses X (Algorithm 1);
+                            WARM continues from the last solution */
     int32_t max_batch;   /* poses per mfem_solve_batch call allocated for (16) */
-    int32_t tile_rows;   /* PCG rows per work tile: 64, 128 or 256; 0 = autotune */
+    int32_t tile_rows;   /* PCG rows per work tile; 0 = autotune (tile and threads
+                            per row are timed on the first assembled system) */
+    int32_t pcg_threads_per_row; /* 1 or 4 threads per matrix row in PCG (with
+                            tile_rows 64/128/256 for 1, 32/64/128 for 4); 0 = 1 */
     int32_t diagnostics; /* 1: fill inverted/skew/angle fields of mfem_stats (0) */
 } mfem_options;
 
@@ -142,6 +149,7 @@ typedef struct {
     double linesearch_ms;
     double total_ms;          /* first to last library event of the call */
     int32_t tile_rows;        /* PCG tile in use */
+    int32_t threads_per_row;  /* PCG threads per matrix row in use */
     int32_t grid_blocks;      /* PCG persistent grid */
 } mfem_profile;
 

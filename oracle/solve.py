@@ -22,7 +22,13 @@ Newton iterations.  This driver runs Newton on E(x) for every model:
 Constraint C(x) (Eq. 6): "eliminate" fixes pinned vertices at x_p (k_s -> inf,
 the default); "penalty" adds k_s/2 |x_v - x_p|^2 per pin as written in Eq. 6.
 Initial guess: "rest" (x = X, as in Algorithm 1), "rigid" (every vertex moved by
-the transform of the handle its position clusters to), or an explicit array.
+the transform of the handle its position clusters to), "corot", or an explicit
+array.  "corot" (the default) starts SNH from one Newton step of the
+co-rotational energy with the same mu, lambda taken at the rigid guess: that
+energy is quadratic with the same rest Hessian as SNH (lambda_SNH = lambda +
+mu), so the step lands near the SNH minimiser instead of on the rigid guess,
+whose vertex field jumps across every cluster boundary.  The step counts as a
+Newton step; for ARAP and co-rotational Psi "corot" is the rigid guess.
 """
 import numpy as np
 import scipy.sparse as sp
@@ -78,7 +84,7 @@ def initial_guess(st, Q, t, init):
     if isinstance(init, str):
         if init == "rest":
             return st.X.copy()
-        if init == "rigid":
+        if init in ("rigid", "corot"):
             return np.einsum("kij,kj->ki", Q[st.vhandle], st.X) + t[st.vhandle]
         raise ValueError(init)
     return np.array(init, dtype=np.float64, copy=True)
@@ -108,7 +114,7 @@ def _pcg(K, b, tol, maxit):
 
 
 def solve(st, xf, model, constraint="eliminate", ks=0.0, newton_max=50, newton_tol=1e-12,
-          init="rigid", linear="direct", cg_tol=1e-13, cg_max=100000):
+          init="corot", linear="direct", cg_tol=1e-13, cg_max=100000):
     """Solve one pose.  Returns (x (n,3), info dict)."""
     Q, t = rig.unpack_pose(xf)
     R = Q[st.cluster]
@@ -123,6 +129,18 @@ def solve(st, xf, model, constraint="eliminate", ks=0.0, newton_max=50, newton_t
         raise ValueError(constraint)
     fidx = np.nonzero(free.reshape(-1))[0]
     args = (st.T, st.G, st.vol, R, model, st.mu, st.lam)
+
+    def newton_direction(y, g, mdl):
+        a = (st.T, st.G, st.vol, R, mdl, st.mu, st.lam)
+        Ke = element.element_hessians(y, *a, project=True)
+        K = element.assemble(Ke, st.T, n)
+        if constraint == "penalty":
+            pd = (3 * st.pin_verts[:, None] + np.arange(3)).reshape(-1)
+            K = K + sp.coo_matrix((np.full(len(pd), ks), (pd, pd)), shape=K.shape).tocsr()
+        Kff = K[fidx][:, fidx].tocsc()
+        if linear == "direct":
+            return spla.spsolve(Kff, -g), 0
+        return _pcg(Kff.tocsr(), -g, cg_tol, cg_max)
 
     def energy(y):
         e = element.element_energy(y, *args).sum()
@@ -141,7 +159,19 @@ def solve(st, xf, model, constraint="eliminate", ks=0.0, newton_max=50, newton_t
     x_ref = initial_guess(st, Q, t, "rigid")
     x_ref[st.pin_verts] = xp
     g0 = float(np.linalg.norm(grad(x_ref).reshape(-1)[fidx]))
-    for it in range(newton_max + 1):
+    n_pred = 0
+    if isinstance(init, str) and init == "corot" and model == "snh" and newton_max > 0:
+        gc = element.gradient(x, st.T, st.G, st.vol, R, "corot", st.mu, st.lam)
+        if constraint == "penalty":
+            np.add.at(gc, st.pin_verts, ks * (x[st.pin_verts] - xp))
+        df, cit = newton_direction(x, gc.reshape(-1)[fidx], "corot")
+        d = np.zeros(3 * n)
+        d[fidx] = df
+        x = x + d.reshape(n, 3)
+        info["cg_iters"].append(cit)
+        info["alpha"].append(1.0)
+        n_pred = 1
+    for it in range(n_pred, newton_max + 1):
         g = grad(x).reshape(-1)[fidx]
         gn = float(np.linalg.norm(g))
         info["gnorm"].append(gn)
@@ -150,18 +180,8 @@ def solve(st, xf, model, constraint="eliminate", ks=0.0, newton_max=50, newton_t
             break
         if it == newton_max:
             break
-        Ke = element.element_hessians(x, *args, project=True)
-        K = element.assemble(Ke, st.T, n)
-        if constraint == "penalty":
-            pd = (3 * st.pin_verts[:, None] + np.arange(3)).reshape(-1)
-            K = K + sp.coo_matrix((np.full(len(pd), ks), (pd, pd)), shape=K.shape).tocsr()
-        Kff = K[fidx][:, fidx].tocsc()
-        if linear == "direct":
-            df = spla.spsolve(Kff, -g)
-            info["cg_iters"].append(0)
-        else:
-            df, cit = _pcg(Kff.tocsr(), -g, cg_tol, cg_max)
-            info["cg_iters"].append(cit)
+        df, cit = newton_direction(x, g, model)
+        info["cg_iters"].append(cit)
         d = np.zeros(3 * n)
         d[fidx] = df
         d = d.reshape(n, 3)

@@ -19,6 +19,13 @@ constexpr int kRowTile = 256;        // rows per block in row kernels other than
 constexpr int kKe = 90;              // 10 upper 3x3 blocks of a symmetric 12x12
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
 
+// Per-problem PCG vector area, in elements of the PCG type, rows padded to 32:
+// two ping-pong records zp[n][8] = (z.xyz, 0, p.xyz, 0) so a neighbour's z and
+// previous p come from one 32-byte (FP32) record, then dx, r, q as [n][3].
+constexpr int kVecStride = 25;                 // times npad32(n)
+constexpr int kOffZP0 = 0, kOffZP1 = 8, kOffDX = 16, kOffR = 19, kOffQ = 22;
+__host__ __device__ __forceinline__ size_t npad32(int n) { return ((size_t)n + 31) & ~(size_t)31; }
+
 // Problem states (PCG)
 enum : int { kIdle = 0, kActive = 1, kConverged = 2, kMaxIter = 3 };
 
@@ -46,11 +53,10 @@ struct PcgDesc {
     const int* col;        // [slots] column block or -1
     const T* val;          // [slots/32][9][32]
     const T* dinv;         // [n][9] inverse diagonal blocks
+    T* zp0;                // [n][8] (z, p) records, read at even iterations
+    T* zp1;                // [n][8] read at odd iterations
     T* dx;
     T* r;
-    T* z;
-    T* p0;
-    T* p1;
     T* q;                  // [n][3] each
     double* part;          // [tiles][4] tile partials
     ProbScal* sc;

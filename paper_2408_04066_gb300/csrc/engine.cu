@@ -18,7 +18,8 @@ thread_local std::string g_thread_err = "no error";
 constexpr double kLsC = 1.0e-4;      // Armijo constant
 constexpr int kLsMax = 20;           // halvings
 constexpr double kLsNoise = 1.0e-10; // predicted decrease below this * |E|: take the step
-constexpr int kPcgTiles[3] = {64, 128, 256};
+// PCG work shapes the autotuner times: (rows per tile, threads per row)
+constexpr int kPcgShapes[6][2] = {{64, 1}, {128, 1}, {256, 1}, {32, 4}, {64, 4}, {128, 4}};
 }  // namespace
 
 namespace mfem {
@@ -87,7 +88,7 @@ void free_slots(mfem_ctx* c) {
 }
 
 int part_tiles_for(const mfem_ctx* c) {
-    int a = (c->plan.n + 63) / 64, b = (c->plan.m + kTetTile - 1) / kTetTile;
+    int a = (c->plan.n + 31) / 32, b = (c->plan.m + kTetTile - 1) / kTetTile;
     return std::max(std::max(a, b), 1);
 }
 
@@ -96,7 +97,7 @@ size_t bytes_per_slot(const mfem_ctx* c) {
     const size_t kt = c->slot.prec == 1 ? 4 : 8;
     const size_t slots = (size_t)c->plan.slice_ptr.back();
     return H * 12 * 8 + 4 * n * 3 * 8 + m * 12 * 8 + m * kKe * kt + slots * 9 * kt + n * 9 * kt +
-           6 * n * 3 * kt + (size_t)part_tiles_for(c) * 4 * 8 + sizeof(ProbScal) + 4 + 8;
+           kVecStride * npad32((int)n) * kt + (size_t)part_tiles_for(c) * 4 * 8 + sizeof(ProbScal) + 4 + 8;
 }
 
 mfem_status alloc_slots(mfem_ctx* c, int B) {
@@ -122,7 +123,7 @@ mfem_status alloc_slots(mfem_ctx* c, int B) {
     AL(S.Ke, B * m * kKe * kt);
     AL(S.val, B * slots * 9 * kt);
     AL(S.dinv, B * n * 9 * kt);
-    AL(S.vec, B * 6 * n * 3 * kt);
+    AL(S.vec, B * kVecStride * npad32((int)n) * kt);
     AL(S.part, B * (size_t)S.part_tiles * 4 * 8);
     AL(S.sc, B * sizeof(ProbScal));
     AL(S.active, B * sizeof(int));
@@ -130,7 +131,7 @@ mfem_status alloc_slots(mfem_ctx* c, int B) {
 #undef AL
     CK(cudaMemset(S.sc, 0, B * sizeof(ProbScal)));
     CK(cudaMemset(S.val, 0, B * slots * 9 * kt));   // padding slots stay zero
-    CK(cudaMemset(S.vec, 0, B * 6 * n * 3 * kt));
+    CK(cudaMemset(S.vec, 0, B * kVecStride * npad32((int)n) * kt));
     S.cap = B;
     // every slot starts at the rest shape (the WARM start without history)
     for (int b = 0; b < B; ++b)
@@ -184,6 +185,7 @@ void end_profile(mfem_ctx* c) {
     P.element_bytes = c->prof.element_bytes;
     P.pcg_iters = c->prof.pcg_iters;
     P.tile_rows = c->tile_rows;
+    P.threads_per_row = c->tpr;
     P.grid_blocks = c->grid_blocks;
     for (int i = 0; i < c->prof.used; ++i) {
         float ms = 0.f;
@@ -236,13 +238,13 @@ void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc
             d.col = c->mesh.col;
             d.val = (const T*)c->slot.val + (size_t)b * slots * 9;
             d.dinv = (const T*)c->slot.dinv + (size_t)b * n * 9;
-            T* v = (T*)c->slot.vec + (size_t)b * 6 * n * 3;
-            d.dx = v;
-            d.r = v + 3 * (size_t)n;
-            d.z = v + 6 * (size_t)n;
-            d.p0 = v + 9 * (size_t)n;
-            d.p1 = v + 12 * (size_t)n;
-            d.q = v + 15 * (size_t)n;
+            const size_t np = npad32(n);
+            T* v = (T*)c->slot.vec + (size_t)b * kVecStride * np;
+            d.zp0 = v + kOffZP0 * np;
+            d.zp1 = v + kOffZP1 * np;
+            d.dx = v + kOffDX * np;
+            d.r = v + kOffR * np;
+            d.q = v + kOffQ * np;
             d.part = c->slot.part + (size_t)b * c->slot.part_tiles * 4;
             d.sc = c->slot.sc + b;
             d.n_rows = n;
@@ -295,7 +297,7 @@ mfem_status read_scalars(mfem_ctx* c, int B) {
 }
 
 template <typename T>
-mfem_status launch_pcg_group(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, int max_iters,
+mfem_status launch_pcg_group(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, int tpr, int max_iters,
                              bool count) {
     mfem_ctx* c = c0;
     std::vector<PcgDesc<T>> d;
@@ -320,11 +322,11 @@ mfem_status launch_pcg_group(mfem_ctx* c0, std::vector<Group>& gs, int prec, int
     CK(cudaMemcpyAsync(dst, hst, bytes, cudaMemcpyHostToDevice, c->stream));
     GridBar* bar = c->bar + prec;
     CK(cudaMemsetAsync(bar, 0, sizeof(GridBar), c->stream));
-    int grid = std::min(pcg_max_blocks<T>(tile), units);
+    int grid = std::min(pcg_max_blocks<T>(tile, tpr), units);
     grid = std::max(grid, 1);
     c->grid_blocks = grid;
     int pe = count ? c->prof.begin(2, c->stream) : -1;
-    CK(launch_pcg<T>((const PcgDesc<T>*)dst, (int)d.size(), units, bar, max_iters, tile, grid, c->stream));
+    CK(launch_pcg<T>((const PcgDesc<T>*)dst, (int)d.size(), units, bar, max_iters, tile, tpr, grid, c->stream));
     if (count) {
         c->prof.end(pe, c->stream);
         c->prof.launches++;
@@ -333,8 +335,9 @@ mfem_status launch_pcg_group(mfem_ctx* c0, std::vector<Group>& gs, int prec, int
     return MFEM_OK;
 }
 
-// Pick the PCG tile by timing a capped number of iterations of each candidate
-// on the first assembled system (results are discarded; PCG is re-initialised).
+// Pick the PCG work shape by timing a capped number of iterations of each
+// candidate on the first assembled system (results are discarded; PCG is
+// re-initialised afterwards).  MFEM_AUTOTUNE_CACHE names a file of earlier picks.
 mfem_status autotune_tile(mfem_ctx* c, std::vector<Group>& gs) {
     const char* cache = std::getenv("MFEM_AUTOTUNE_CACHE");
     char key[128];
@@ -344,11 +347,12 @@ mfem_status autotune_tile(mfem_ctx* c, std::vector<Group>& gs) {
         if (FILE* f = fopen(cache, "r")) {
             char line[256];
             while (fgets(line, sizeof line, f)) {
-                int tile = 0;
+                int tile = 0, tpr = 0;
                 size_t kl = strlen(key);
-                if (strncmp(line, key, kl) == 0 && sscanf(line + kl, " %d", &tile) == 1 &&
-                    (tile == 64 || tile == 128 || tile == 256)) {
+                if (strncmp(line, key, kl) == 0 && sscanf(line + kl, " %d %d", &tile, &tpr) == 2 &&
+                    pcg_shape_supported(tile, tpr)) {
                     c->tile_rows = tile;
+                    c->tpr = tpr;
                 }
             }
             fclose(f);
@@ -359,14 +363,14 @@ mfem_status autotune_tile(mfem_ctx* c, std::vector<Group>& gs) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_tile = 128;
+    int best_tile = 128, best_tpr = 1;
     ElemArgs a = elem_args(c);
-    for (int tile : kPcgTiles) {
+    for (const auto& sh : kPcgShapes) {
         for (int rep = 0; rep < 2; ++rep) {
-            launch_pcg_init(a, gs[0].B, tile, 0.0, 1 << 30, c->stream);
+            launch_pcg_init(a, gs[0].B, sh[0], 0.0, 1 << 30, c->stream);
             CK(cudaEventRecord(e0, c->stream));
-            mfem_status st = c->slot.prec == 1 ? launch_pcg_group<float>(c, gs, 1, tile, 25, false)
-                                               : launch_pcg_group<double>(c, gs, 0, tile, 25, false);
+            mfem_status st = c->slot.prec == 1 ? launch_pcg_group<float>(c, gs, 1, sh[0], sh[1], 25, false)
+                                               : launch_pcg_group<double>(c, gs, 0, sh[0], sh[1], 25, false);
             if (st != MFEM_OK) return st;
             CK(cudaEventRecord(e1, c->stream));
             CK(cudaEventSynchronize(e1));
@@ -375,16 +379,18 @@ mfem_status autotune_tile(mfem_ctx* c, std::vector<Group>& gs) {
             cudaEventElapsedTime(&ms, e0, e1);
             if (rep == 1 && ms < best) {
                 best = ms;
-                best_tile = tile;
+                best_tile = sh[0];
+                best_tpr = sh[1];
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->tile_rows = best_tile;
+    c->tpr = best_tpr;
     if (cache) {
         if (FILE* f = fopen(cache, "a")) {
-            fprintf(f, "%s %d\n", key, best_tile);
+            fprintf(f, "%s %d %d\n", key, best_tile, best_tpr);
             fclose(f);
         }
     }
@@ -409,9 +415,23 @@ mfem_status newton_step(std::vector<Group>& gs) {
         mfem_ctx* gc = g.ctx;
         mfem_status st = upload_active(gc, g.B, f);
         if (st != MFEM_OK) return st;
-        const int init = gc->opt.init == MFEM_INIT_RIGID ? 0 : (gc->opt.init == MFEM_INIT_REST ? 1 : 2);
+        const bool predict = gc->opt.init == MFEM_INIT_COROT && gc->model == MFEM_SNH;
+        const int init = (gc->opt.init == MFEM_INIT_RIGID || gc->opt.init == MFEM_INIT_COROT)
+                             ? 0 : (gc->opt.init == MFEM_INIT_REST ? 1 : 2);
         std::vector<double> gref(g.B, -1.0);
-        if (init != 0) {
+        if (predict) {   // SNH reference gradient at the rigid guess, then the predictor step
+            ElemArgs a = elem_args(gc);
+            launch_pose_init(a, g.B, 0, s);
+            launch_element(a, g.B, s);
+            launch_assemble(a, g.B, s);
+            gc->prof.launches += 3;
+            st = read_scalars(gc, g.B);
+            if (st != MFEM_OK) return st;
+            CK(cudaStreamSynchronize(s));
+            synced(gs);
+            for (int b = 0; b < g.B; ++b)
+                if (f[b]) gref[b] = std::sqrt(gc->sc_host[b].gnorm2);
+        } else if (init != 0) {
             const size_t xbytes = sizeof(double) * 3 * (size_t)gc->plan.n * g.B;
             if (init == 2) CK(cudaMemcpyAsync(gc->slot.outbuf, gc->slot.x, xbytes, cudaMemcpyDeviceToDevice, s));
             ElemArgs a = elem_args(gc);
@@ -427,10 +447,13 @@ mfem_status newton_step(std::vector<Group>& gs) {
                 if (f[b]) gref[b] = std::sqrt(gc->sc_host[b].gnorm2);
             if (init == 2) CK(cudaMemcpyAsync(gc->slot.x, gc->slot.outbuf, xbytes, cudaMemcpyDeviceToDevice, s));
         }
-        launch_pose_init(elem_args(gc), g.B, init, s);
-        gc->prof.launches++;
+        if (!predict) {
+            launch_pose_init(elem_args(gc), g.B, init, s);
+            gc->prof.launches++;
+        }
         for (int b = 0; b < g.B; ++b)
             if (g.ph[b].need_init) {
+                g.ph[b].pred = predict ? 1 : 0;
                 g.ph[b].need_init = 0;
                 g.ph[b].active = 1;
                 g.ph[b].it = 0;
@@ -441,29 +464,36 @@ mfem_status newton_step(std::vector<Group>& gs) {
                 g.ph[b].converged = 0;
             }
     }
-    // a1-a4: element step, assembly, gradient for active problems
+    // a1-a4: element step, assembly, gradient for active problems (problems with
+    // the co-rotational predictor pending use that energy in this step)
     for (auto& g : gs) {
-        std::vector<int> f(g.B, 0);
-        bool any = false;
-        for (int b = 0; b < g.B; ++b)
-            if (g.ph[b].active) { f[b] = 1; any = true; }
-        if (!any) continue;
         mfem_ctx* gc = g.ctx;
-        mfem_status st = upload_active(gc, g.B, f);
-        if (st != MFEM_OK) return st;
-        ElemArgs a = elem_args(gc);
-        int pe = gc->prof.begin(0, s);
-        launch_element(a, g.B, s);
-        gc->prof.end(pe, s);
-        int pa = gc->prof.begin(1, s);
-        launch_assemble(a, g.B, s);
-        gc->prof.end(pa, s);
-        gc->prof.launches += 2;
-        gc->prof.element_launches++;
-        int na = 0;
-        for (int b = 0; b < g.B; ++b) na += f[b];
-        gc->prof.element_bytes += na * element_bytes(gc);
-        st = read_scalars(gc, g.B);
+        bool any = false;
+        for (int pass = 0; pass < 2; ++pass) {
+            std::vector<int> f(g.B, 0);
+            bool anyp = false;
+            for (int b = 0; b < g.B; ++b)
+                if (g.ph[b].active && g.ph[b].pred == pass) { f[b] = 1; anyp = true; }
+            if (!anyp) continue;
+            any = true;
+            mfem_status st = upload_active(gc, g.B, f);
+            if (st != MFEM_OK) return st;
+            ElemArgs a = elem_args(gc);
+            if (pass == 1) a.model = MFEM_COROT;
+            int pe = gc->prof.begin(0, s);
+            launch_element(a, g.B, s);
+            gc->prof.end(pe, s);
+            int pa = gc->prof.begin(1, s);
+            launch_assemble(a, g.B, s);
+            gc->prof.end(pa, s);
+            gc->prof.launches += 2;
+            gc->prof.element_launches++;
+            int na = 0;
+            for (int b = 0; b < g.B; ++b) na += f[b];
+            gc->prof.element_bytes += na * element_bytes(gc);
+        }
+        if (!any) continue;
+        mfem_status st = read_scalars(gc, g.B);
         if (st != MFEM_OK) return st;
     }
     CK(cudaStreamSynchronize(s));
@@ -475,6 +505,10 @@ mfem_status newton_step(std::vector<Group>& gs) {
         for (int b = 0; b < g.B; ++b) {
             ProbHost& p = g.ph[b];
             if (!p.active) continue;
+            if (p.pred) {   // predictor step: its gradient is not the SNH residual
+                any_active = true;
+                continue;
+            }
             const ProbScal& sc = gc->sc_host[b];
             p.gn = std::sqrt(sc.gnorm2);
             p.energy = sc.energy;
@@ -510,7 +544,7 @@ mfem_status newton_step(std::vector<Group>& gs) {
         mfem_status st = autotune_tile(c, gs);
         if (st != MFEM_OK) return st;
     }
-    const int tile = c->tile_rows;
+    const int tile = c->tile_rows, tpr = c->tpr;
     for (auto& g : gs) {
         bool any = false;
         for (int b = 0; b < g.B; ++b) any |= g.ph[b].active != 0;
@@ -526,8 +560,8 @@ mfem_status newton_step(std::vector<Group>& gs) {
             if (g.ctx->slot.prec == prec)
                 for (int b = 0; b < g.B; ++b) any |= g.ph[b].active != 0;
         if (!any) continue;
-        mfem_status st = prec == 1 ? launch_pcg_group<float>(c, gs, 1, tile, 1 << 30, true)
-                                   : launch_pcg_group<double>(c, gs, 0, tile, 1 << 30, true);
+        mfem_status st = prec == 1 ? launch_pcg_group<float>(c, gs, 1, tile, tpr, 1 << 30, true)
+                                   : launch_pcg_group<double>(c, gs, 0, tile, tpr, 1 << 30, true);
         if (st != MFEM_OK) return st;
     }
     // a6: slope for line search (SNH) and PCG statistics
@@ -572,7 +606,7 @@ mfem_status newton_step(std::vector<Group>& gs) {
         std::vector<double> e0(g.B, 0.0), slope(g.B, 0.0);
         bool any = false;
         for (int b = 0; b < g.B; ++b) {
-            if (!g.ph[b].active) continue;
+            if (!g.ph[b].active || g.ph[b].pred) continue;   // predictor: quadratic, alpha = 1
             e0[b] = g.ph[b].energy;
             slope[b] = gc->sc_host[b].slope;
             if (-slope[b] > kLsNoise * std::fabs(e0[b])) { testing[b] = 1; any = true; }
@@ -622,6 +656,7 @@ mfem_status newton_step(std::vector<Group>& gs) {
             if (g.ph[b].active) {
                 g.ph[b].it++;
                 g.ph[b].ran_pcg = 1;
+                g.ph[b].pred = 0;
             }
     }
     CK(cudaGetLastError());
@@ -676,10 +711,10 @@ void mfem_default_options(mfem_options* o) {
     o->constraint = MFEM_ELIMINATE;
     o->k_s = 0.0;
     o->newton_tol = 1e-6;
-    o->cg_tol = 1e-3;
+    o->cg_tol = 1e-2;
     o->newton_max = 50;
     o->cg_max = 5000;
-    o->init = MFEM_INIT_RIGID;
+    o->init = MFEM_INIT_COROT;
     o->max_batch = 16;
     o->tile_rows = 0;
     o->diagnostics = 0;
@@ -756,9 +791,9 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
     if (o.constraint == MFEM_PENALTY && !(o.k_s > 0.0)) return fail(MFEM_EINVAL, "penalty needs k_s > 0");
     if (!(o.newton_tol >= 0.0) || !(o.cg_tol >= 0.0) || o.newton_max < 0 || o.cg_max < 1)
         return fail(MFEM_EINVAL, "bad tolerances or iteration caps");
-    if (o.init < MFEM_INIT_RIGID || o.init > MFEM_INIT_WARM) return fail(MFEM_EINVAL, "bad init");
-    if (o.tile_rows != 0 && o.tile_rows != 64 && o.tile_rows != 128 && o.tile_rows != 256)
-        return fail(MFEM_EINVAL, "tile_rows must be 0, 64, 128 or 256");
+    if (o.init < MFEM_INIT_RIGID || o.init > MFEM_INIT_COROT) return fail(MFEM_EINVAL, "bad init");
+    if (o.tile_rows != 0 && !pcg_shape_supported(o.tile_rows, o.pcg_threads_per_row ? o.pcg_threads_per_row : 1))
+        return fail(MFEM_EINVAL, "unsupported PCG shape (tile_rows, pcg_threads_per_row)");
     if (!mat) return fail(MFEM_EINVAL, "null material");
     std::string err;
     mfem_status st = plan_rig(rest_verts, n, tets, m, hs, c->plan, err);
@@ -768,6 +803,7 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
     c->model = mat->model;
     c->slot.prec = o.precision == MFEM_MIXED ? 1 : 0;
     c->tile_rows = o.tile_rows;
+    c->tpr = o.pcg_threads_per_row ? o.pcg_threads_per_row : 1;
     const Plan& P = c->plan;
     if (cudaGetDevice(&c->device) != cudaSuccess) return fail(MFEM_ECUDA, "no CUDA device");
     if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)

@@ -22,6 +22,7 @@ struct ProbHost {
     int ran_pcg = 0;     // PCG ran in the current step
     int status = MFEM_OK;
     int converged = 0;
+    int pred = 0;        // co-rotational predictor step pending (SNH, COROT init)
     double g0 = -1.0, gn = 0.0, energy = 0.0;
 };
 
@@ -73,7 +74,8 @@ struct mfem_ctx {
     void* descs_host = nullptr;
     unsigned* diag_dev = nullptr;
     unsigned* diag_host = nullptr;
-    int tile_rows = 0;
+    int tile_rows = 0;       // PCG work shape: rows per tile
+    int tpr = 1;             // and threads per row
     int grid_blocks = 0;
     bool pose_set = false;
     std::vector<int> has_state;   // per slot: x holds a previous solution

@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(kTetTile) k_energy_trial(ElemArgs A) {
     double en[1] = {0.0};
     if (k < m) {
         const double* x = A.slot.x + (size_t)b * n * 3;
-        const T* dx = (const T*)A.slot.vec + (size_t)b * 6 * n * 3;
+        const T* dx = (const T*)A.slot.vec + (size_t)b * kVecStride * npad32(n) + kOffDX * npad32(n);
         const double* xf = A.slot.xf + (size_t)b * M.H * 12;
         double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6], sig[6];
         gather_x<T>(x, dx, A.slot.alpha[b], M.tet[k], xa);

@@ -19,8 +19,9 @@ namespace {
 __device__ __forceinline__ int pair_index(int a, int b) { return a * 4 - (a * (a - 1)) / 2 + (b - a); }
 
 template <typename T>
-__device__ __forceinline__ T* vecp(const SlotDev& S, int b, int which, int n) {
-    return (T*)S.vec + ((size_t)b * 6 + which) * (size_t)n * 3;
+__device__ __forceinline__ T* vecp(const SlotDev& S, int b, int off, int n) {
+    const size_t np = npad32(n);
+    return (T*)S.vec + (size_t)b * kVecStride * np + (size_t)off * np;
 }
 
 // One thread per block row: the row's matrix blocks, its inverse diagonal
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(kRowTile) k_slope(ElemArgs A) {
     double v[1] = {0.0};
     if (row < n) {
         const double* g = A.slot.g + ((size_t)b * n + row) * 3;
-        const T* dx = vecp<T>(A.slot, b, 0, n) + 3 * (size_t)row;
+        const T* dx = vecp<T>(A.slot, b, kOffDX, n) + 3 * (size_t)row;
         v[0] = g[0] * (double)dx[0] + g[1] * (double)dx[1] + g[2] * (double)dx[2];
     }
     double tot[1];
@@ -155,7 +156,7 @@ __global__ void k_update(ElemArgs A) {
     const int n = A.mesh.n;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 3 * n) return;
-    const T* dx = vecp<T>(A.slot, b, 0, n);
+    const T* dx = vecp<T>(A.slot, b, kOffDX, n);
     double* x = A.slot.x + (size_t)b * n * 3;
     x[i] = fma(A.slot.alpha[b], (double)dx[i], x[i]);
 }
@@ -195,21 +196,22 @@ __global__ void k_pcg_init(ElemArgs A, double tol2, int maxit) {
     if (row < n) {
         const double* g = A.slot.g + ((size_t)b * n + row) * 3;
         const T* di = (const T*)A.slot.dinv + ((size_t)b * n + row) * 9;
-        T* dx = vecp<T>(A.slot, b, 0, n) + 3 * (size_t)row;
-        T* r = vecp<T>(A.slot, b, 1, n) + 3 * (size_t)row;
-        T* z = vecp<T>(A.slot, b, 2, n) + 3 * (size_t)row;
-        T* p0 = vecp<T>(A.slot, b, 3, n) + 3 * (size_t)row;
+        T* dx = vecp<T>(A.slot, b, kOffDX, n) + 3 * (size_t)row;
+        T* r = vecp<T>(A.slot, b, kOffR, n) + 3 * (size_t)row;
+        T* zp = vecp<T>(A.slot, b, kOffZP0, n) + 8 * (size_t)row;
         T rr[3] = {(T)(-g[0]), (T)(-g[1]), (T)(-g[2])};
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             T zi = di[3 * i] * rr[0] + di[3 * i + 1] * rr[1] + di[3 * i + 2] * rr[2];
             dx[i] = (T)0;
             r[i] = rr[i];
-            z[i] = zi;
-            p0[i] = (T)0;
+            zp[i] = zi;
+            zp[4 + i] = (T)0;
             v[0] += (double)rr[i] * (double)zi;
             v[1] += (double)rr[i] * (double)rr[i];
         }
+        zp[3] = (T)0;
+        zp[7] = (T)0;
     }
     double tot[2];
     double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
@@ -230,15 +232,36 @@ __global__ void k_pcg_init(ElemArgs A, double tol2, int maxit) {
 // ---- persistent PCG ---------------------------------------------------------
 // One cooperative launch runs PCG iterations for every problem in the
 // descriptor table until all have converged (|r| <= tol |r0|) or hit their cap.
-// Work unit = (problem, tile of TILE rows); each block strides over units.
-// Phase A: p_new = z + beta p_old (neighbours recomputed on the fly, so no extra
-// barrier), q = K p_new, tile partial of p.q; the last tile of a problem sets
-// alpha.  Phase B: dx += alpha p, r -= alpha q, z = D^{-1} r, partials of r.z
-// and r.r; the last tile sets beta and the convergence state.
-template <typename T, int TILE>
-__global__ void __launch_bounds__(TILE) k_pcg(const PcgDesc<T>* __restrict__ D, int n_probs, int n_units,
-                                              GridBar* bar, int max_iters) {
+// Work unit = (problem, tile of TILE rows); a block of 4*TILE threads gives
+// every row four threads, which take its SELL slots k = t, t+4, ... and combine
+// their partial products by shuffles.  Phase A: p_new = z + beta p_old (for
+// neighbours recomputed on the fly, so no extra barrier), q = K p_new, tile
+// partial of p.q; the last tile of a problem sets alpha.  Phase B: dx += alpha
+// p, r -= alpha q, z = D^{-1} r, partials of r.z and r.r; the last tile sets
+// beta and the convergence state.  z and p live in interleaved (z, p) records
+// so one neighbour costs two 16-byte loads from a single 32-byte sector.
+// The records change during the launch (across grid barriers), so they are read
+// with ordinary coherent loads, never the read-only (non-coherent) path.
+__device__ __forceinline__ void ld_zp(const float* zp, int c, float (&z)[3], float (&p)[3]) {
+    const float4 a = *reinterpret_cast<const float4*>(zp + 8 * (size_t)c);
+    const float4 b = *reinterpret_cast<const float4*>(zp + 8 * (size_t)c + 4);
+    z[0] = a.x; z[1] = a.y; z[2] = a.z;
+    p[0] = b.x; p[1] = b.y; p[2] = b.z;
+}
+
+__device__ __forceinline__ void ld_zp(const double* zp, int c, double (&z)[3], double (&p)[3]) {
+    const double2* r = reinterpret_cast<const double2*>(zp + 8 * (size_t)c);
+    const double2 a = r[0], b = r[1], e = r[2], f = r[3];
+    z[0] = a.x; z[1] = a.y; z[2] = b.x;
+    p[0] = e.x; p[1] = e.y; p[2] = f.x;
+}
+
+template <typename T, int TILE, int TPR>
+__global__ void __launch_bounds__(TPR * TILE) k_pcg(const PcgDesc<T>* __restrict__ D, int n_probs, int n_units,
+                                                    GridBar* bar, int max_iters) {
     __shared__ int s_any;
+    const int sub = TPR == 1 ? 0 : (threadIdx.x & (TPR - 1));  // slot phase of this thread within its row
+    const int lrow = threadIdx.x / TPR;       // row within the tile
     for (int it = 0; it < max_iters; ++it) {
         if (threadIdx.x == 0) {
             int any = 0;
@@ -255,41 +278,54 @@ __global__ void __launch_bounds__(TILE) k_pcg(const PcgDesc<T>* __restrict__ D, 
             ProbScal* sc = d.sc;
             if (ld_volatile_i32(&sc->state) != kActive) continue;
             const int tile = u - d.unit_begin;
-            const int row = tile * TILE + threadIdx.x;
+            const int row = tile * TILE + lrow;
             const int iter = ld_volatile_i32(&sc->iter);
-            const T* __restrict__ po = (iter & 1) ? d.p1 : d.p0;
-            T* __restrict__ pn = (iter & 1) ? d.p0 : d.p1;
+            const T* zpo = (iter & 1) ? d.zp1 : d.zp0;
+            T* zpn = (iter & 1) ? d.zp0 : d.zp1;
             const T beta = (T)(*(volatile double*)&sc->beta);
-            const T* __restrict__ z = d.z;
-            double v[1] = {0.0};
+            T a0 = 0, a1 = 0, a2 = 0;
             if (row < d.n_rows) {
                 const int s = row >> 5, lane = row & 31;
                 const int base = d.slice_ptr[s], w = (d.slice_ptr[s + 1] - base) >> 5;
-                T a0 = 0, a1 = 0, a2 = 0;
-#pragma unroll 4
-                for (int k = 0; k < w; ++k) {
+#pragma unroll(TPR == 1 ? 4 : 2)
+                for (int k = sub; k < w; k += TPR) {
                     const int g = base + (k << 5);
                     const int c = __ldg(d.col + g + lane);
                     if (c >= 0) {
                         const T* vv = d.val + (size_t)g * 9 + lane;
-                        const T pc0 = fma(beta, po[3 * c], z[3 * c]);
-                        const T pc1 = fma(beta, po[3 * c + 1], z[3 * c + 1]);
-                        const T pc2 = fma(beta, po[3 * c + 2], z[3 * c + 2]);
-                        a0 += __ldg(vv) * pc0 + __ldg(vv + 32) * pc1 + __ldg(vv + 64) * pc2;
-                        a1 += __ldg(vv + 96) * pc0 + __ldg(vv + 128) * pc1 + __ldg(vv + 160) * pc2;
-                        a2 += __ldg(vv + 192) * pc0 + __ldg(vv + 224) * pc1 + __ldg(vv + 256) * pc2;
+                        T zc[3], pc[3];
+                        ld_zp(zpo, c, zc, pc);
+                        const T q0 = fma(beta, pc[0], zc[0]);
+                        const T q1 = fma(beta, pc[1], zc[1]);
+                        const T q2 = fma(beta, pc[2], zc[2]);
+                        a0 += __ldg(vv) * q0 + __ldg(vv + 32) * q1 + __ldg(vv + 64) * q2;
+                        a1 += __ldg(vv + 96) * q0 + __ldg(vv + 128) * q1 + __ldg(vv + 160) * q2;
+                        a2 += __ldg(vv + 192) * q0 + __ldg(vv + 224) * q1 + __ldg(vv + 256) * q2;
                     }
                 }
-                const T pr0 = fma(beta, po[3 * row], z[3 * row]);
-                const T pr1 = fma(beta, po[3 * row + 1], z[3 * row + 1]);
-                const T pr2 = fma(beta, po[3 * row + 2], z[3 * row + 2]);
-                pn[3 * row] = pr0;
-                pn[3 * row + 1] = pr1;
-                pn[3 * row + 2] = pr2;
+            }
+            // combine the slot phases of each row (fixed xor tree)
+#pragma unroll
+            for (int o = 1; o < TPR; o <<= 1) {
+                a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+            }
+            double v[1] = {0.0};
+            if (sub == 0 && row < d.n_rows) {
+                T zr[3], pr[3];
+                ld_zp(zpo, row, zr, pr);
+                const T pn0 = fma(beta, pr[0], zr[0]);
+                const T pn1 = fma(beta, pr[1], zr[1]);
+                const T pn2 = fma(beta, pr[2], zr[2]);
+                T* rec = zpn + 8 * (size_t)row;
+                rec[4] = pn0;
+                rec[5] = pn1;
+                rec[6] = pn2;
                 d.q[3 * row] = a0;
                 d.q[3 * row + 1] = a1;
                 d.q[3 * row + 2] = a2;
-                v[0] = (double)pr0 * (double)a0 + (double)pr1 * (double)a1 + (double)pr2 * (double)a2;
+                v[0] = (double)pn0 * (double)a0 + (double)pn1 * (double)a1 + (double)pn2 * (double)a2;
             }
             double tot[1];
             if (tile_commit<1>(v, d.part, tile, d.n_tiles, &sc->tk_a, 0, tot) && threadIdx.x == 0) {
@@ -312,24 +348,25 @@ __global__ void __launch_bounds__(TILE) k_pcg(const PcgDesc<T>* __restrict__ D, 
             ProbScal* sc = d.sc;
             if (ld_volatile_i32(&sc->state) != kActive) continue;
             const int tile = u - d.unit_begin;
-            const int row = tile * TILE + threadIdx.x;
+            const int row = tile * TILE + lrow;
             const int iter = ld_volatile_i32(&sc->iter);
-            const T* __restrict__ pn = (iter & 1) ? d.p0 : d.p1;
+            T* zpn = (iter & 1) ? d.zp0 : d.zp1;
             const T alpha = (T)(*(volatile double*)&sc->alpha);
             double v[2] = {0.0, 0.0};
-            if (row < d.n_rows) {
+            if (sub == 0 && row < d.n_rows) {
+                T* rec = zpn + 8 * (size_t)row;
                 const T* di = d.dinv + 9 * (size_t)row;
                 T rr[3];
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
-                    d.dx[3 * row + i] = fma(alpha, pn[3 * row + i], d.dx[3 * row + i]);
+                    d.dx[3 * row + i] = fma(alpha, rec[4 + i], d.dx[3 * row + i]);
                     rr[i] = fma(-alpha, d.q[3 * row + i], d.r[3 * row + i]);
                     d.r[3 * row + i] = rr[i];
                 }
 #pragma unroll
                 for (int i = 0; i < 3; ++i) {
                     const T zi = di[3 * i] * rr[0] + di[3 * i + 1] * rr[1] + di[3 * i + 2] * rr[2];
-                    d.z[3 * row + i] = zi;
+                    rec[i] = zi;
                     v[0] += (double)rr[i] * (double)zi;
                     v[1] += (double)rr[i] * (double)rr[i];
                 }
@@ -351,20 +388,20 @@ __global__ void __launch_bounds__(TILE) k_pcg(const PcgDesc<T>* __restrict__ D, 
     }
 }
 
-template <typename T, int TILE>
+template <typename T, int TILE, int TPR>
 int max_blocks_t() {
     int dev = 0, sms = 0, per = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg<T, TILE>, TILE, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg<T, TILE, TPR>, TPR * TILE, 0);
     return sms * per;
 }
 
-template <typename T, int TILE>
+template <typename T, int TILE, int TPR>
 cudaError_t launch_pcg_t(const PcgDesc<T>* descs, int n_probs, int n_units, GridBar* bar, int max_iters,
                          int grid, cudaStream_t s) {
     void* args[] = {(void*)&descs, (void*)&n_probs, (void*)&n_units, (void*)&bar, (void*)&max_iters};
-    return cudaLaunchCooperativeKernel((const void*)k_pcg<T, TILE>, dim3(grid), dim3(TILE), args, 0, s);
+    return cudaLaunchCooperativeKernel((const void*)k_pcg<T, TILE, TPR>, dim3(grid), dim3(TPR * TILE), args, 0, s);
 }
 
 }  // namespace
@@ -404,28 +441,39 @@ void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int m
     else k_pcg_init<double><<<grid, tile_rows, 0, s>>>(a, tol2, maxit);
 }
 
+// PCG work shapes: (rows per tile, threads per row).
+#define MFEM_PCG_SHAPES(X) X(64, 1) X(128, 1) X(256, 1) X(32, 4) X(64, 4) X(128, 4)
+
 template <typename T>
-int pcg_max_blocks(int tile_rows) {
-    switch (tile_rows) {
-        case 64: return max_blocks_t<T, 64>();
-        case 128: return max_blocks_t<T, 128>();
-        default: return max_blocks_t<T, 256>();
-    }
+int pcg_max_blocks(int tile_rows, int tpr) {
+#define X(TI, TP) \
+    if (tile_rows == TI && tpr == TP) return max_blocks_t<T, TI, TP>();
+    MFEM_PCG_SHAPES(X)
+#undef X
+    return 0;
 }
 
 template <typename T>
 cudaError_t launch_pcg(const PcgDesc<T>* descs, int n_probs, int n_units, GridBar* bar, int max_iters,
-                       int tile_rows, int grid, cudaStream_t s) {
-    switch (tile_rows) {
-        case 64: return launch_pcg_t<T, 64>(descs, n_probs, n_units, bar, max_iters, grid, s);
-        case 128: return launch_pcg_t<T, 128>(descs, n_probs, n_units, bar, max_iters, grid, s);
-        default: return launch_pcg_t<T, 256>(descs, n_probs, n_units, bar, max_iters, grid, s);
-    }
+                       int tile_rows, int tpr, int grid, cudaStream_t s) {
+#define X(TI, TP) \
+    if (tile_rows == TI && tpr == TP) return launch_pcg_t<T, TI, TP>(descs, n_probs, n_units, bar, max_iters, grid, s);
+    MFEM_PCG_SHAPES(X)
+#undef X
+    return cudaErrorInvalidValue;
 }
 
-template int pcg_max_blocks<float>(int);
-template int pcg_max_blocks<double>(int);
-template cudaError_t launch_pcg<float>(const PcgDesc<float>*, int, int, GridBar*, int, int, int, cudaStream_t);
-template cudaError_t launch_pcg<double>(const PcgDesc<double>*, int, int, GridBar*, int, int, int, cudaStream_t);
+bool pcg_shape_supported(int tile_rows, int tpr) {
+#define X(TI, TP) \
+    if (tile_rows == TI && tpr == TP) return true;
+    MFEM_PCG_SHAPES(X)
+#undef X
+    return false;
+}
+
+template int pcg_max_blocks<float>(int, int);
+template int pcg_max_blocks<double>(int, int);
+template cudaError_t launch_pcg<float>(const PcgDesc<float>*, int, int, GridBar*, int, int, int, int, cudaStream_t);
+template cudaError_t launch_pcg<double>(const PcgDesc<double>*, int, int, GridBar*, int, int, int, int, cudaStream_t);
 
 }  // namespace mfem

@@ -88,8 +88,9 @@ void launch_diag(const ElemArgs& a, int b, unsigned* out3, cudaStream_t s);
 void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int maxit, cudaStream_t s);
 template <typename T>
 cudaError_t launch_pcg(const PcgDesc<T>* descs_dev, int n_probs, int n_units, GridBar* bar,
-                       int max_iters, int tile_rows, int grid_blocks, cudaStream_t s);
+                       int max_iters, int tile_rows, int threads_per_row, int grid_blocks, cudaStream_t s);
 template <typename T>
-int pcg_max_blocks(int tile_rows);
+int pcg_max_blocks(int tile_rows, int threads_per_row);
+bool pcg_shape_supported(int tile_rows, int threads_per_row);
 
 }  // namespace mfem

@@ -201,8 +201,14 @@ mfem_status mfem_server_add(mfem_server* s, mfem_ctx* c, int32_t* mesh_id) {
     }
     cudaStreamSynchronize(c->stream);
     c->stream = s->stream;
-    if (c->tile_rows == 0) c->tile_rows = 128;   // one tile for every mesh in a shared launch
-    if (!s->meshes.empty()) c->tile_rows = s->meshes[0].ctx->tile_rows;
+    if (c->tile_rows == 0) {   // one work shape for every mesh in a shared launch
+        c->tile_rows = 128;
+        c->tpr = 1;
+    }
+    if (!s->meshes.empty()) {
+        c->tile_rows = s->meshes[0].ctx->tile_rows;
+        c->tpr = s->meshes[0].ctx->tpr;
+    }
     mfem_status st = ensure_slots(c, cap);
     if (st != MFEM_OK) return st;
     c->owned_by_server = true;
