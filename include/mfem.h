@@ -113,10 +113,8 @@ typedef struct {
                             rest position clusters to; REST uses X (Algorithm 1);
                             WARM continues from the last solution */
     int32_t max_batch;   /* poses per mfem_solve_batch call allocated for (16) */
-    int32_t tile_rows;   /* PCG rows per work tile; 0 = autotune (tile and threads
-                            per row are timed on the first assembled system) */
-    int32_t pcg_threads_per_row; /* 1 or 4 threads per matrix row in PCG (with
-                            tile_rows 64/128/256 for 1, 32/64/128 for 4); 0 = 1 */
+    int32_t tile_rows;   /* PCG rows per block: 64, 128 or 256; 0 = autotune (timed
+                            on the first assembled system) */
     int32_t diagnostics; /* 1: fill inverted/skew/angle fields of mfem_stats (0) */
 } mfem_options;
 
@@ -135,12 +133,13 @@ typedef struct {
 } mfem_stats;
 
 /* Device-side profile of the last solve call, timed with CUDA events on the
- * context's stream.  The dominant kernel is the persistent PCG kernel. */
+ * context's stream.  The dominant work is the PCG iteration: one SpMV+dot
+ * kernel and one update kernel per iteration, enqueued in chunks. */
 typedef struct {
     int32_t kernel_launches;  /* all library kernels launched in the call */
-    int32_t pcg_launches;
-    double pcg_ms;            /* summed PCG kernel time */
-    double pcg_bytes;         /* algorithmic bytes moved by those launches */
+    int32_t pcg_launches;     /* PCG kernel launches (two per iteration) */
+    double pcg_ms;            /* summed time of the PCG iteration kernels */
+    double pcg_bytes;         /* algorithmic bytes moved by those kernels */
     int64_t pcg_iters;        /* PCG iterations summed over poses */
     int32_t element_launches;
     double element_ms;
@@ -149,8 +148,7 @@ typedef struct {
     double linesearch_ms;
     double total_ms;          /* first to last library event of the call */
     int32_t tile_rows;        /* PCG tile in use */
-    int32_t threads_per_row;  /* PCG threads per matrix row in use */
-    int32_t grid_blocks;      /* PCG persistent grid */
+    int32_t grid_blocks;      /* PCG blocks per launch (tiles of all problems) */
 } mfem_profile;
 
 typedef struct mfem_ctx mfem_ctx;
@@ -186,8 +184,8 @@ mfem_status mfem_set_pose(mfem_ctx* ctx, const double* xf, int32_t H);
  * vertex order.  stats may be NULL.  MFEM_ENOTCONV still writes x. */
 mfem_status mfem_solve(mfem_ctx* ctx, double* out_verts, mfem_stats* stats);
 
-/* Solve B independent poses of this mesh together (one persistent PCG launch
- * per Newton step serves all of them).  xf [B][H][12], out [B][n][3]; both host
+/* Solve B independent poses of this mesh together (each PCG iteration launch
+ * serves all of them).  xf [B][H][12], out [B][n][3]; both host
  * (MFEM_MEM_HOST: copies happen inside the call) or both device
  * (MFEM_MEM_DEVICE).  stats: host [B] or NULL.  B <= max_batch grows the
  * allocation if needed.  Each pose's result does not depend on the others. */
@@ -252,7 +250,7 @@ const char* mfem_last_error(const mfem_ctx* ctx);
  * A server owns meshes (contexts) and a worker thread.  Requests that arrive
  * while others are on the GPU are admitted at the next Newton-step boundary as
  * slots and device memory allow; all admitted requests of all meshes advance
- * together (one persistent PCG launch per step serves every admitted request).
+ * together (each PCG iteration launch serves every admitted request).
  * Each request's result equals the same pose solved alone by mfem_solve_batch. */
 
 /* device_mem_budget: bytes the server may hold for request slots (0 = no

@@ -17,7 +17,6 @@ constexpr int kSliceRows = 32;       // rows per SELL slice (one warp)
 constexpr int kTetTile = 128;        // tets per element-kernel block
 constexpr int kRowTile = 256;        // rows per block in row kernels other than PCG
 constexpr int kKe = 90;              // 10 upper 3x3 blocks of a symmetric 12x12
-constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s
 
 // Per-problem PCG vector area, in elements of the PCG type, rows padded to 32:
 // two ping-pong records zp[n][8] = (z.xyz, 0, p.xyz, 0) so a neighbour's z and
@@ -38,15 +37,7 @@ struct ProbScal {
     unsigned tk_a, tk_b, tk_g, tk_e, tk_s, tk_init, tk_pad0, tk_pad1;
 };
 
-// Grid barrier state of one persistent launch.
-struct GridBar {
-    unsigned count;
-    unsigned gen;
-    int err;
-    int pad;
-};
-
-// One PCG problem (a pose of a mesh) inside a persistent launch.
+// One PCG problem (a pose of a mesh) in a descriptor table.
 template <typename T>
 struct PcgDesc {
     const int* slice_ptr;  // [n_slices+1] first slot of each slice
@@ -62,22 +53,6 @@ struct PcgDesc {
     ProbScal* sc;
     int n_rows, n_tiles, unit_begin, pad;
 };
-
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-    return v;
-}
-
-__device__ __forceinline__ void st_release_u32(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
 
 __device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(volatile const int*)p; }
 
@@ -140,36 +115,5 @@ __device__ __forceinline__ bool tile_commit(double (&v)[NV], double* part, int t
     }
     return true;
 }
-
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The wait
-// is bounded: after kBarrierTimeoutNs the block records bar->err = 1 and leaves;
-// callers check grid_failed() after every barrier and stop.
-__device__ __forceinline__ void grid_sync(GridBar* bar) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const unsigned nb = gridDim.x * gridDim.y * gridDim.z;
-        unsigned g = ld_acquire_u32(&bar->gen);
-        __threadfence();
-        unsigned arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == nb - 1) {
-            bar->count = 0u;
-            __threadfence();
-            st_release_u32(&bar->gen, g + 1u);
-        } else {
-            unsigned long long t0 = globaltimer_ns();
-            while (ld_acquire_u32(&bar->gen) == g) {
-                __nanosleep(40);
-                if (globaltimer_ns() - t0 > kBarrierTimeoutNs) {
-                    atomicExch(&bar->err, 1);
-                    break;
-                }
-            }
-        }
-        __threadfence();
-    }
-    __syncthreads();
-}
-
-__device__ __forceinline__ bool grid_failed(const GridBar* bar) { return ld_volatile_i32(&bar->err) != 0; }
 
 }  // namespace mfem

@@ -18,8 +18,8 @@ thread_local std::string g_thread_err = "no error";
 constexpr double kLsC = 1.0e-4;      // Armijo constant
 constexpr int kLsMax = 20;           // halvings
 constexpr double kLsNoise = 1.0e-10; // predicted decrease below this * |E|: take the step
-// PCG work shapes the autotuner times: (rows per tile, threads per row)
-constexpr int kPcgShapes[6][2] = {{64, 1}, {128, 1}, {256, 1}, {32, 4}, {64, 4}, {128, 4}};
+constexpr int kPcgTiles[3] = {64, 128, 256};   // PCG rows per block the autotuner times
+constexpr int kPcgChunk = 16;                   // PCG iterations enqueued between convergence checks
 }  // namespace
 
 namespace mfem {
@@ -185,7 +185,6 @@ void end_profile(mfem_ctx* c) {
     P.element_bytes = c->prof.element_bytes;
     P.pcg_iters = c->prof.pcg_iters;
     P.tile_rows = c->tile_rows;
-    P.threads_per_row = c->tpr;
     P.grid_blocks = c->grid_blocks;
     for (int i = 0; i < c->prof.used; ++i) {
         float ms = 0.f;
@@ -296,9 +295,12 @@ mfem_status read_scalars(mfem_ctx* c, int B) {
     return MFEM_OK;
 }
 
+// Enqueue PCG for every active problem of precision `prec` in every group: the
+// descriptor table is uploaded once, then chunks of kPcgChunk iterations are
+// enqueued and the problem states read back after each chunk (max_iters > 0:
+// exactly that many iterations, no checks -- used by the autotuner).
 template <typename T>
-mfem_status launch_pcg_group(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, int tpr, int max_iters,
-                             bool count) {
+mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, int max_iters, bool count) {
     mfem_ctx* c = c0;
     std::vector<PcgDesc<T>> d;
     int units = 0;
@@ -313,31 +315,51 @@ mfem_status launch_pcg_group(mfem_ctx* c0, std::vector<Group>& gs, int prec, int
         CK(cudaMallocHost(&c->descs_host, 2 * bytes));
         c->descs_cap = 2 * bytes;
     }
-    // each precision class has its own half, so two launches of one step never
+    // each precision class has its own half, so two tables of one step never
     // share a staging region; a step starts only after the previous one synced
     const size_t off = (size_t)prec * (c->descs_cap / 2);
     char* hst = (char*)c->descs_host + off;
-    char* dst = (char*)c->descs_dev + off;
+    const PcgDesc<T>* dst = (const PcgDesc<T>*)((char*)c->descs_dev + off);
     std::memcpy(hst, d.data(), bytes);
-    CK(cudaMemcpyAsync(dst, hst, bytes, cudaMemcpyHostToDevice, c->stream));
-    GridBar* bar = c->bar + prec;
-    CK(cudaMemsetAsync(bar, 0, sizeof(GridBar), c->stream));
-    int grid = std::min(pcg_max_blocks<T>(tile, tpr), units);
-    grid = std::max(grid, 1);
-    c->grid_blocks = grid;
-    int pe = count ? c->prof.begin(2, c->stream) : -1;
-    CK(launch_pcg<T>((const PcgDesc<T>*)dst, (int)d.size(), units, bar, max_iters, tile, tpr, grid, c->stream));
-    if (count) {
-        c->prof.end(pe, c->stream);
-        c->prof.launches++;
-        c->prof.pcg_launches++;
+    CK(cudaMemcpyAsync((void*)dst, hst, bytes, cudaMemcpyHostToDevice, c->stream));
+    c->grid_blocks = units;
+    if (max_iters > 0) {
+        CK(launch_pcg_iters<T>(dst, (int)d.size(), units, tile, max_iters, c->stream));
+        return MFEM_OK;
+    }
+    int cap = 0;
+    for (auto& g : gs)
+        if (g.ctx->slot.prec == prec) cap = std::max(cap, g.ctx->opt.cg_max);
+    for (int done = 0; done < cap; done += kPcgChunk) {
+        const int n_it = std::min(kPcgChunk, cap - done);
+        int pe = count ? c->prof.begin(2, c->stream) : -1;
+        CK(launch_pcg_iters<T>(dst, (int)d.size(), units, tile, n_it, c->stream));
+        if (count) {
+            c->prof.end(pe, c->stream);
+            c->prof.launches += 2 * n_it;
+            c->prof.pcg_launches += 2 * n_it;
+        }
+        bool any = false;
+        for (auto& g : gs)
+            if (g.ctx->slot.prec == prec) {
+                mfem_status st = read_scalars(g.ctx, g.B);
+                if (st != MFEM_OK) return st;
+            }
+        CK(cudaStreamSynchronize(c->stream));
+        synced(gs);
+        for (auto& g : gs) {
+            if (g.ctx->slot.prec != prec) continue;
+            for (int b = 0; b < g.B; ++b)
+                if (g.ph[b].active && g.ctx->sc_host[b].state == kActive) any = true;
+        }
+        if (!any) break;
     }
     return MFEM_OK;
 }
 
-// Pick the PCG work shape by timing a capped number of iterations of each
-// candidate on the first assembled system (results are discarded; PCG is
-// re-initialised afterwards).  MFEM_AUTOTUNE_CACHE names a file of earlier picks.
+// Pick the PCG tile by timing a fixed number of iterations of each candidate on
+// the first assembled system (results are discarded; PCG is re-initialised
+// afterwards).  MFEM_AUTOTUNE_CACHE names a file of earlier picks.
 mfem_status autotune_tile(mfem_ctx* c, std::vector<Group>& gs) {
     const char* cache = std::getenv("MFEM_AUTOTUNE_CACHE");
     char key[128];
@@ -347,13 +369,10 @@ mfem_status autotune_tile(mfem_ctx* c, std::vector<Group>& gs) {
         if (FILE* f = fopen(cache, "r")) {
             char line[256];
             while (fgets(line, sizeof line, f)) {
-                int tile = 0, tpr = 0;
+                int tile = 0;
                 size_t kl = strlen(key);
-                if (strncmp(line, key, kl) == 0 && sscanf(line + kl, " %d %d", &tile, &tpr) == 2 &&
-                    pcg_shape_supported(tile, tpr)) {
+                if (strncmp(line, key, kl) == 0 && sscanf(line + kl, " %d", &tile) == 1 && pcg_tile_supported(tile))
                     c->tile_rows = tile;
-                    c->tpr = tpr;
-                }
             }
             fclose(f);
             if (c->tile_rows) return MFEM_OK;
@@ -363,14 +382,14 @@ mfem_status autotune_tile(mfem_ctx* c, std::vector<Group>& gs) {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_tile = 128, best_tpr = 1;
+    int best_tile = 256;
     ElemArgs a = elem_args(c);
-    for (const auto& sh : kPcgShapes) {
+    for (int tile : kPcgTiles) {
         for (int rep = 0; rep < 2; ++rep) {
-            launch_pcg_init(a, gs[0].B, sh[0], 0.0, 1 << 30, c->stream);
+            launch_pcg_init(a, gs[0].B, tile, 0.0, 1 << 30, c->stream);
             CK(cudaEventRecord(e0, c->stream));
-            mfem_status st = c->slot.prec == 1 ? launch_pcg_group<float>(c, gs, 1, sh[0], sh[1], 25, false)
-                                               : launch_pcg_group<double>(c, gs, 0, sh[0], sh[1], 25, false);
+            mfem_status st = c->slot.prec == 1 ? run_pcg<float>(c, gs, 1, tile, 20, false)
+                                               : run_pcg<double>(c, gs, 0, tile, 20, false);
             if (st != MFEM_OK) return st;
             CK(cudaEventRecord(e1, c->stream));
             CK(cudaEventSynchronize(e1));
@@ -379,18 +398,16 @@ mfem_status autotune_tile(mfem_ctx* c, std::vector<Group>& gs) {
             cudaEventElapsedTime(&ms, e0, e1);
             if (rep == 1 && ms < best) {
                 best = ms;
-                best_tile = sh[0];
-                best_tpr = sh[1];
+                best_tile = tile;
             }
         }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->tile_rows = best_tile;
-    c->tpr = best_tpr;
     if (cache) {
         if (FILE* f = fopen(cache, "a")) {
-            fprintf(f, "%s %d %d\n", key, best_tile, best_tpr);
+            fprintf(f, "%s %d\n", key, best_tile);
             fclose(f);
         }
     }
@@ -529,7 +546,7 @@ mfem_status newton_step(std::vector<Group>& gs) {
         }
     }
     if (!any_active) return MFEM_OK;
-    // a5: PCG for every active problem of every group, one persistent launch per precision
+    // a5: PCG for every active problem of every group, one launch sequence per precision
     for (auto& g : gs) {
         std::vector<int> f(g.B, 0);
         bool any = false;
@@ -544,7 +561,7 @@ mfem_status newton_step(std::vector<Group>& gs) {
         mfem_status st = autotune_tile(c, gs);
         if (st != MFEM_OK) return st;
     }
-    const int tile = c->tile_rows, tpr = c->tpr;
+    const int tile = c->tile_rows;
     for (auto& g : gs) {
         bool any = false;
         for (int b = 0; b < g.B; ++b) any |= g.ph[b].active != 0;
@@ -560,8 +577,8 @@ mfem_status newton_step(std::vector<Group>& gs) {
             if (g.ctx->slot.prec == prec)
                 for (int b = 0; b < g.B; ++b) any |= g.ph[b].active != 0;
         if (!any) continue;
-        mfem_status st = prec == 1 ? launch_pcg_group<float>(c, gs, 1, tile, tpr, 1 << 30, true)
-                                   : launch_pcg_group<double>(c, gs, 0, tile, tpr, 1 << 30, true);
+        mfem_status st = prec == 1 ? run_pcg<float>(c, gs, 1, tile, 0, true)
+                                   : run_pcg<double>(c, gs, 0, tile, 0, true);
         if (st != MFEM_OK) return st;
     }
     // a6: slope for line search (SNH) and PCG statistics
@@ -579,14 +596,9 @@ mfem_status newton_step(std::vector<Group>& gs) {
         mfem_status st = read_scalars(gc, g.B);
         if (st != MFEM_OK) return st;
     }
-    CK(cudaMemcpyAsync(c->bar_host, c->bar, 2 * sizeof(GridBar), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     synced(gs);
     CK(cudaGetLastError());
-    if (c->bar_host[0].err || c->bar_host[1].err) {
-        cudaMemsetAsync(c->bar, 0, 2 * sizeof(GridBar), s);
-        return ctx_fail(c, MFEM_ETIMEOUT, "PCG grid barrier wait timed out");
-    }
     for (auto& g : gs) {
         mfem_ctx* gc = g.ctx;
         for (int b = 0; b < g.B; ++b) {
@@ -758,10 +770,10 @@ void mfem_destroy(mfem_ctx* c) {
     MeshDev& M = c->mesh;
     void* ptrs[] = {M.tet, M.Dminv64, M.Dminv32, M.vol, M.cluster, M.mu, M.lam, M.X, M.vhandle, M.pin_handle_v,
                     M.vperm, M.tperm, M.slice_ptr, M.col, M.contrib_ptr, M.contrib, M.vinc_ptr, M.vinc,
-                    c->bar, c->descs_dev, c->diag_dev};
+                    c->descs_dev, c->diag_dev};
     for (void* p : ptrs)
         if (p) cudaFree(p);
-    void* hp[] = {c->sc_host, c->active_host, c->alpha_host, c->alpha_ring, c->bar_host, c->descs_host,
+    void* hp[] = {c->sc_host, c->active_host, c->alpha_host, c->alpha_ring, c->descs_host,
                   c->diag_host};
     for (void* p : hp)
         if (p) cudaFreeHost(p);
@@ -792,8 +804,8 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
     if (!(o.newton_tol >= 0.0) || !(o.cg_tol >= 0.0) || o.newton_max < 0 || o.cg_max < 1)
         return fail(MFEM_EINVAL, "bad tolerances or iteration caps");
     if (o.init < MFEM_INIT_RIGID || o.init > MFEM_INIT_COROT) return fail(MFEM_EINVAL, "bad init");
-    if (o.tile_rows != 0 && !pcg_shape_supported(o.tile_rows, o.pcg_threads_per_row ? o.pcg_threads_per_row : 1))
-        return fail(MFEM_EINVAL, "unsupported PCG shape (tile_rows, pcg_threads_per_row)");
+    if (o.tile_rows != 0 && !pcg_tile_supported(o.tile_rows))
+        return fail(MFEM_EINVAL, "tile_rows must be 0, 64, 128 or 256");
     if (!mat) return fail(MFEM_EINVAL, "null material");
     std::string err;
     mfem_status st = plan_rig(rest_verts, n, tets, m, hs, c->plan, err);
@@ -803,7 +815,6 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
     c->model = mat->model;
     c->slot.prec = o.precision == MFEM_MIXED ? 1 : 0;
     c->tile_rows = o.tile_rows;
-    c->tpr = o.pcg_threads_per_row ? o.pcg_threads_per_row : 1;
     const Plan& P = c->plan;
     if (cudaGetDevice(&c->device) != cudaSuccess) return fail(MFEM_ECUDA, "no CUDA device");
     if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -851,10 +862,7 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
     UP(M.vinc_ptr, P.vinc_ptr.data(), P.vinc_ptr.size());
     UP(M.vinc, P.vinc.data(), P.vinc.size());
 #undef UP
-    if (cudaMalloc((void**)&c->bar, 2 * sizeof(GridBar)) != cudaSuccess ||
-        cudaMemset(c->bar, 0, 2 * sizeof(GridBar)) != cudaSuccess ||
-        cudaMallocHost((void**)&c->bar_host, 2 * sizeof(GridBar)) != cudaSuccess ||
-        cudaMalloc((void**)&c->diag_dev, 4 * sizeof(unsigned)) != cudaSuccess ||
+    if (cudaMalloc((void**)&c->diag_dev, 4 * sizeof(unsigned)) != cudaSuccess ||
         cudaMallocHost((void**)&c->diag_host, 4 * sizeof(unsigned)) != cudaSuccess)
         return fail(MFEM_ENOMEM, "small device/host buffers");
     c->prof.ev.resize(2 * 4096);

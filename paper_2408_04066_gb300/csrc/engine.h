@@ -59,7 +59,6 @@ struct mfem_ctx {
     mfem::MeshDev mesh;
     mfem::SlotDev slot;
     size_t mesh_bytes = 0, slot_bytes = 0;
-    mfem::GridBar* bar = nullptr;     // [2]: one per PCG precision class
     void* descs_dev = nullptr;
     size_t descs_cap = 0;
     // pinned host staging.  Async uploads read from a ring of regions so that a
@@ -70,12 +69,10 @@ struct mfem_ctx {
     double* alpha_host = nullptr;    // current step lengths [cap]
     double* alpha_ring = nullptr;    // [kStageRing][cap]
     int ring_pos = 0;
-    mfem::GridBar* bar_host = nullptr;
     void* descs_host = nullptr;
     unsigned* diag_dev = nullptr;
     unsigned* diag_host = nullptr;
-    int tile_rows = 0;       // PCG work shape: rows per tile
-    int tpr = 1;             // and threads per row
+    int tile_rows = 0;       // PCG rows per block
     int grid_blocks = 0;
     bool pose_set = false;
     std::vector<int> has_state;   // per slot: x holds a previous solution

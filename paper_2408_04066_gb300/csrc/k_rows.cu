@@ -1,6 +1,6 @@
 // Row-parallel kernels: assembly of the condensed matrix (a2) with pin
 // elimination (a3) and block-Jacobi inverse (a4), gradient gather, slope and
-// update (a6), permutations (a7), and the persistent PCG solve (a5).
+// update (a6), permutations (a7), and the PCG iteration kernels (a5).
 //
 // Paper §3, Eq. 12 and Algorithm 1 ("assemble", "x = A^{-1} b"): the matrix
 // sum_k W_k A_k^T H_s A_k is gathered per 3x3 block from the element blocks of
@@ -229,19 +229,20 @@ __global__ void k_pcg_init(ElemArgs A, double tol2, int maxit) {
     }
 }
 
-// ---- persistent PCG ---------------------------------------------------------
-// One cooperative launch runs PCG iterations for every problem in the
-// descriptor table until all have converged (|r| <= tol |r0|) or hit their cap.
-// Work unit = (problem, tile of TILE rows); a block of 4*TILE threads gives
-// every row four threads, which take its SELL slots k = t, t+4, ... and combine
-// their partial products by shuffles.  Phase A: p_new = z + beta p_old (for
-// neighbours recomputed on the fly, so no extra barrier), q = K p_new, tile
-// partial of p.q; the last tile of a problem sets alpha.  Phase B: dx += alpha
-// p, r -= alpha q, z = D^{-1} r, partials of r.z and r.r; the last tile sets
-// beta and the convergence state.  z and p live in interleaved (z, p) records
-// so one neighbour costs two 16-byte loads from a single 32-byte sector.
-// The records change during the launch (across grid barriers), so they are read
-// with ordinary coherent loads, never the read-only (non-coherent) path.
+// ---- PCG iteration kernels ----------------------------------------------------
+// One PCG iteration is two ordinary launches over every problem of the
+// descriptor table; a block is one (problem, tile of TILE rows) unit and returns
+// at once when its problem is not active.
+//   k_pcg_spmv:   p_new = z + beta p_old (also for neighbours, recomputed on the
+//                 fly from their (z, p_old) record), q = K p_new, tile partial of
+//                 p.q; the last tile of a problem sets alpha = rho / p.q.
+//   k_pcg_update: dx += alpha p, r -= alpha q, z = D^{-1} r, partials of r.z and
+//                 r.r; the last tile sets beta, rho, the iteration count and the
+//                 convergence state (|r| <= tol |r0| or the iteration cap).
+// Kernel boundaries order every write before the next iteration's reads, so no
+// block ever waits on another.  z and p of a vertex share one 32-byte record
+// (two ping-pong buffers by iteration parity); the matrix streams through with
+// evict-first loads.
 __device__ __forceinline__ void ld_zp(const float* zp, int c, float (&z)[3], float (&p)[3]) {
     const float4 a = *reinterpret_cast<const float4*>(zp + 8 * (size_t)c);
     const float4 b = *reinterpret_cast<const float4*>(zp + 8 * (size_t)c + 4);
@@ -256,152 +257,127 @@ __device__ __forceinline__ void ld_zp(const double* zp, int c, double (&z)[3], d
     p[0] = e.x; p[1] = e.y; p[2] = f.x;
 }
 
-template <typename T, int TILE, int TPR>
-__global__ void __launch_bounds__(TPR * TILE) k_pcg(const PcgDesc<T>* __restrict__ D, int n_probs, int n_units,
-                                                    GridBar* bar, int max_iters) {
-    __shared__ int s_any;
-    const int sub = TPR == 1 ? 0 : (threadIdx.x & (TPR - 1));  // slot phase of this thread within its row
-    const int lrow = threadIdx.x / TPR;       // row within the tile
-    for (int it = 0; it < max_iters; ++it) {
-        if (threadIdx.x == 0) {
-            int any = 0;
-            for (int p = 0; p < n_probs; ++p) any |= (ld_volatile_i32(&D[p].sc->state) == kActive);
-            s_any = any;
-        }
-        __syncthreads();
-        if (!s_any) break;
-        // ---------------- phase A ----------------
-        int p = 0;
-        for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
-            while (p + 1 < n_probs && D[p + 1].unit_begin <= u) ++p;
-            const PcgDesc<T>& d = D[p];
-            ProbScal* sc = d.sc;
-            if (ld_volatile_i32(&sc->state) != kActive) continue;
-            const int tile = u - d.unit_begin;
-            const int row = tile * TILE + lrow;
-            const int iter = ld_volatile_i32(&sc->iter);
-            const T* zpo = (iter & 1) ? d.zp1 : d.zp0;
-            T* zpn = (iter & 1) ? d.zp0 : d.zp1;
-            const T beta = (T)(*(volatile double*)&sc->beta);
-            T a0 = 0, a1 = 0, a2 = 0;
-            if (row < d.n_rows) {
-                const int s = row >> 5, lane = row & 31;
-                const int base = d.slice_ptr[s], w = (d.slice_ptr[s + 1] - base) >> 5;
-#pragma unroll(TPR == 1 ? 4 : 2)
-                for (int k = sub; k < w; k += TPR) {
-                    const int g = base + (k << 5);
-                    const int c = __ldg(d.col + g + lane);
-                    if (c >= 0) {
-                        const T* vv = d.val + (size_t)g * 9 + lane;
-                        T zc[3], pc[3];
-                        ld_zp(zpo, c, zc, pc);
-                        const T q0 = fma(beta, pc[0], zc[0]);
-                        const T q1 = fma(beta, pc[1], zc[1]);
-                        const T q2 = fma(beta, pc[2], zc[2]);
-                        a0 += __ldg(vv) * q0 + __ldg(vv + 32) * q1 + __ldg(vv + 64) * q2;
-                        a1 += __ldg(vv + 96) * q0 + __ldg(vv + 128) * q1 + __ldg(vv + 160) * q2;
-                        a2 += __ldg(vv + 192) * q0 + __ldg(vv + 224) * q1 + __ldg(vv + 256) * q2;
-                    }
-                }
-            }
-            // combine the slot phases of each row (fixed xor tree)
-#pragma unroll
-            for (int o = 1; o < TPR; o <<= 1) {
-                a0 += __shfl_xor_sync(0xffffffffu, a0, o);
-                a1 += __shfl_xor_sync(0xffffffffu, a1, o);
-                a2 += __shfl_xor_sync(0xffffffffu, a2, o);
-            }
-            double v[1] = {0.0};
-            if (sub == 0 && row < d.n_rows) {
-                T zr[3], pr[3];
-                ld_zp(zpo, row, zr, pr);
-                const T pn0 = fma(beta, pr[0], zr[0]);
-                const T pn1 = fma(beta, pr[1], zr[1]);
-                const T pn2 = fma(beta, pr[2], zr[2]);
-                T* rec = zpn + 8 * (size_t)row;
-                rec[4] = pn0;
-                rec[5] = pn1;
-                rec[6] = pn2;
-                d.q[3 * row] = a0;
-                d.q[3 * row + 1] = a1;
-                d.q[3 * row + 2] = a2;
-                v[0] = (double)pn0 * (double)a0 + (double)pn1 * (double)a1 + (double)pn2 * (double)a2;
-            }
-            double tot[1];
-            if (tile_commit<1>(v, d.part, tile, d.n_tiles, &sc->tk_a, 0, tot) && threadIdx.x == 0) {
-                const double pq = tot[0];
-                if (pq > 0.0 && isfinite(pq)) {
-                    sc->alpha = sc->rho / pq;
-                } else {  // breakdown (p = 0 or K not SPD along p): stop with current dx
-                    sc->alpha = 0.0;
-                    sc->state = kConverged;
-                }
+// problem of unit u: last descriptor whose unit_begin <= u
+template <typename T>
+__device__ __forceinline__ int unit_problem(const PcgDesc<T>* __restrict__ D, int n_probs, int u) {
+    int lo = 0, hi = n_probs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (D[mid].unit_begin <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+template <typename T, int TILE>
+__global__ void __launch_bounds__(TILE) k_pcg_spmv(const PcgDesc<T>* __restrict__ D, int n_probs) {
+    const int u = blockIdx.x;
+    const PcgDesc<T>& d = D[unit_problem(D, n_probs, u)];
+    ProbScal* sc = d.sc;
+    if (sc->state != kActive) return;
+    const int tile = u - d.unit_begin;
+    const int row = tile * TILE + threadIdx.x;
+    const int iter = sc->iter;
+    const T* zpo = (iter & 1) ? d.zp1 : d.zp0;
+    T* zpn = (iter & 1) ? d.zp0 : d.zp1;
+    const T beta = (T)sc->beta;
+    double v[1] = {0.0};
+    if (row < d.n_rows) {
+        const int s = row >> 5, lane = row & 31;
+        const int base = __ldg(d.slice_ptr + s), w = (__ldg(d.slice_ptr + s + 1) - base) >> 5;
+        T a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll 4
+        for (int k = 0; k < w; ++k) {
+            const int g = base + (k << 5);
+            const int c = __ldcs(d.col + g + lane);
+            if (c >= 0) {
+                const T* vv = d.val + (size_t)g * 9 + lane;
+                T zc[3], pc[3];
+                ld_zp(zpo, c, zc, pc);
+                const T q0 = fma(beta, pc[0], zc[0]);
+                const T q1 = fma(beta, pc[1], zc[1]);
+                const T q2 = fma(beta, pc[2], zc[2]);
+                a0 += __ldcs(vv) * q0 + __ldcs(vv + 32) * q1 + __ldcs(vv + 64) * q2;
+                a1 += __ldcs(vv + 96) * q0 + __ldcs(vv + 128) * q1 + __ldcs(vv + 160) * q2;
+                a2 += __ldcs(vv + 192) * q0 + __ldcs(vv + 224) * q1 + __ldcs(vv + 256) * q2;
             }
         }
-        grid_sync(bar);
-        if (grid_failed(bar)) break;
-        // ---------------- phase B ----------------
-        p = 0;
-        for (int u = blockIdx.x; u < n_units; u += gridDim.x) {
-            while (p + 1 < n_probs && D[p + 1].unit_begin <= u) ++p;
-            const PcgDesc<T>& d = D[p];
-            ProbScal* sc = d.sc;
-            if (ld_volatile_i32(&sc->state) != kActive) continue;
-            const int tile = u - d.unit_begin;
-            const int row = tile * TILE + lrow;
-            const int iter = ld_volatile_i32(&sc->iter);
-            T* zpn = (iter & 1) ? d.zp0 : d.zp1;
-            const T alpha = (T)(*(volatile double*)&sc->alpha);
-            double v[2] = {0.0, 0.0};
-            if (sub == 0 && row < d.n_rows) {
-                T* rec = zpn + 8 * (size_t)row;
-                const T* di = d.dinv + 9 * (size_t)row;
-                T rr[3];
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    d.dx[3 * row + i] = fma(alpha, rec[4 + i], d.dx[3 * row + i]);
-                    rr[i] = fma(-alpha, d.q[3 * row + i], d.r[3 * row + i]);
-                    d.r[3 * row + i] = rr[i];
-                }
-#pragma unroll
-                for (int i = 0; i < 3; ++i) {
-                    const T zi = di[3 * i] * rr[0] + di[3 * i + 1] * rr[1] + di[3 * i + 2] * rr[2];
-                    rec[i] = zi;
-                    v[0] += (double)rr[i] * (double)zi;
-                    v[1] += (double)rr[i] * (double)rr[i];
-                }
-            }
-            double tot[2];
-            if (tile_commit<2>(v, d.part, tile, d.n_tiles, &sc->tk_b, 1, tot) && threadIdx.x == 0) {
-                const double rho_new = tot[0];
-                sc->beta = sc->rho != 0.0 ? rho_new / sc->rho : 0.0;
-                sc->rho = rho_new;
-                sc->rr = tot[1];
-                const int itn = sc->iter + 1;
-                sc->iter = itn;
-                if (!(tot[1] > sc->tol2 * sc->rr0)) sc->state = kConverged;
-                else if (itn >= sc->maxit) sc->state = kMaxIter;
-            }
+        T zr[3], pr[3];
+        ld_zp(zpo, row, zr, pr);
+        const T pn0 = fma(beta, pr[0], zr[0]);
+        const T pn1 = fma(beta, pr[1], zr[1]);
+        const T pn2 = fma(beta, pr[2], zr[2]);
+        T* rec = zpn + 8 * (size_t)row;
+        rec[4] = pn0;
+        rec[5] = pn1;
+        rec[6] = pn2;
+        d.q[3 * row] = a0;
+        d.q[3 * row + 1] = a1;
+        d.q[3 * row + 2] = a2;
+        v[0] = (double)pn0 * (double)a0 + (double)pn1 * (double)a1 + (double)pn2 * (double)a2;
+    }
+    double tot[1];
+    if (tile_commit<1>(v, d.part, tile, d.n_tiles, &sc->tk_a, 0, tot) && threadIdx.x == 0) {
+        const double pq = tot[0];
+        if (pq > 0.0 && isfinite(pq)) {
+            sc->alpha = sc->rho / pq;
+        } else {  // breakdown (p = 0 or K not SPD along p): stop with the current dx
+            sc->alpha = 0.0;
+            sc->state = kConverged;
         }
-        grid_sync(bar);
-        if (grid_failed(bar)) break;
     }
 }
 
-template <typename T, int TILE, int TPR>
-int max_blocks_t() {
-    int dev = 0, sms = 0, per = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pcg<T, TILE, TPR>, TPR * TILE, 0);
-    return sms * per;
+template <typename T, int TILE>
+__global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restrict__ D, int n_probs) {
+    const int u = blockIdx.x;
+    const PcgDesc<T>& d = D[unit_problem(D, n_probs, u)];
+    ProbScal* sc = d.sc;
+    if (sc->state != kActive) return;
+    const int tile = u - d.unit_begin;
+    const int row = tile * TILE + threadIdx.x;
+    const int iter = sc->iter;
+    T* zpn = (iter & 1) ? d.zp0 : d.zp1;
+    const T alpha = (T)sc->alpha;
+    double v[2] = {0.0, 0.0};
+    if (row < d.n_rows) {
+        T* rec = zpn + 8 * (size_t)row;
+        const T* di = d.dinv + 9 * (size_t)row;
+        T rr[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            d.dx[3 * row + i] = fma(alpha, rec[4 + i], d.dx[3 * row + i]);
+            rr[i] = fma(-alpha, d.q[3 * row + i], d.r[3 * row + i]);
+            d.r[3 * row + i] = rr[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const T zi = di[3 * i] * rr[0] + di[3 * i + 1] * rr[1] + di[3 * i + 2] * rr[2];
+            rec[i] = zi;
+            v[0] += (double)rr[i] * (double)zi;
+            v[1] += (double)rr[i] * (double)rr[i];
+        }
+    }
+    double tot[2];
+    if (tile_commit<2>(v, d.part, tile, d.n_tiles, &sc->tk_b, 1, tot) && threadIdx.x == 0) {
+        const double rho_new = tot[0];
+        sc->beta = sc->rho != 0.0 ? rho_new / sc->rho : 0.0;
+        sc->rho = rho_new;
+        sc->rr = tot[1];
+        const int itn = sc->iter + 1;
+        sc->iter = itn;
+        if (!(tot[1] > sc->tol2 * sc->rr0)) sc->state = kConverged;
+        else if (itn >= sc->maxit) sc->state = kMaxIter;
+    }
 }
 
-template <typename T, int TILE, int TPR>
-cudaError_t launch_pcg_t(const PcgDesc<T>* descs, int n_probs, int n_units, GridBar* bar, int max_iters,
-                         int grid, cudaStream_t s) {
-    void* args[] = {(void*)&descs, (void*)&n_probs, (void*)&n_units, (void*)&bar, (void*)&max_iters};
-    return cudaLaunchCooperativeKernel((const void*)k_pcg<T, TILE, TPR>, dim3(grid), dim3(TPR * TILE), args, 0, s);
+template <typename T, int TILE>
+cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units, int iters, cudaStream_t s) {
+    for (int i = 0; i < iters; ++i) {
+        k_pcg_spmv<T, TILE><<<n_units, TILE, 0, s>>>(descs, n_probs);
+        k_pcg_update<T, TILE><<<n_units, TILE, 0, s>>>(descs, n_probs);
+    }
+    return cudaGetLastError();
 }
 
 }  // namespace
@@ -441,39 +417,20 @@ void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int m
     else k_pcg_init<double><<<grid, tile_rows, 0, s>>>(a, tol2, maxit);
 }
 
-// PCG work shapes: (rows per tile, threads per row).
-#define MFEM_PCG_SHAPES(X) X(64, 1) X(128, 1) X(256, 1) X(32, 4) X(64, 4) X(128, 4)
-
 template <typename T>
-int pcg_max_blocks(int tile_rows, int tpr) {
-#define X(TI, TP) \
-    if (tile_rows == TI && tpr == TP) return max_blocks_t<T, TI, TP>();
-    MFEM_PCG_SHAPES(X)
-#undef X
-    return 0;
+cudaError_t launch_pcg_iters(const PcgDesc<T>* descs, int n_probs, int n_units, int tile_rows, int iters,
+                             cudaStream_t s) {
+    switch (tile_rows) {
+        case 64: return launch_pcg_iters_t<T, 64>(descs, n_probs, n_units, iters, s);
+        case 128: return launch_pcg_iters_t<T, 128>(descs, n_probs, n_units, iters, s);
+        case 256: return launch_pcg_iters_t<T, 256>(descs, n_probs, n_units, iters, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
-template <typename T>
-cudaError_t launch_pcg(const PcgDesc<T>* descs, int n_probs, int n_units, GridBar* bar, int max_iters,
-                       int tile_rows, int tpr, int grid, cudaStream_t s) {
-#define X(TI, TP) \
-    if (tile_rows == TI && tpr == TP) return launch_pcg_t<T, TI, TP>(descs, n_probs, n_units, bar, max_iters, grid, s);
-    MFEM_PCG_SHAPES(X)
-#undef X
-    return cudaErrorInvalidValue;
-}
+bool pcg_tile_supported(int tile_rows) { return tile_rows == 64 || tile_rows == 128 || tile_rows == 256; }
 
-bool pcg_shape_supported(int tile_rows, int tpr) {
-#define X(TI, TP) \
-    if (tile_rows == TI && tpr == TP) return true;
-    MFEM_PCG_SHAPES(X)
-#undef X
-    return false;
-}
-
-template int pcg_max_blocks<float>(int, int);
-template int pcg_max_blocks<double>(int, int);
-template cudaError_t launch_pcg<float>(const PcgDesc<float>*, int, int, GridBar*, int, int, int, int, cudaStream_t);
-template cudaError_t launch_pcg<double>(const PcgDesc<double>*, int, int, GridBar*, int, int, int, int, cudaStream_t);
+template cudaError_t launch_pcg_iters<float>(const PcgDesc<float>*, int, int, int, int, cudaStream_t);
+template cudaError_t launch_pcg_iters<double>(const PcgDesc<double>*, int, int, int, int, cudaStream_t);
 
 }  // namespace mfem

@@ -84,13 +84,13 @@ void launch_elem_out(const ElemArgs& a, int b, double* s_out, double* lam_out, c
 // diagnostics: inverted count, max rel skew, max angle for problem b
 void launch_diag(const ElemArgs& a, int b, unsigned* out3, cudaStream_t s);
 
-// PCG init and persistent solve
+// PCG: init (r = -g, z = D^{-1} r, rho, |r0|) and `iters` iterations (two
+// launches each) over every problem of a descriptor table; tiles of
+// tile_rows rows (64, 128 or 256), n_units = total tiles.
 void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int maxit, cudaStream_t s);
 template <typename T>
-cudaError_t launch_pcg(const PcgDesc<T>* descs_dev, int n_probs, int n_units, GridBar* bar,
-                       int max_iters, int tile_rows, int threads_per_row, int grid_blocks, cudaStream_t s);
-template <typename T>
-int pcg_max_blocks(int tile_rows, int threads_per_row);
-bool pcg_shape_supported(int tile_rows, int threads_per_row);
+cudaError_t launch_pcg_iters(const PcgDesc<T>* descs_dev, int n_probs, int n_units, int tile_rows, int iters,
+                             cudaStream_t s);
+bool pcg_tile_supported(int tile_rows);
 
 }  // namespace mfem

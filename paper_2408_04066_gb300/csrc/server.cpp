@@ -4,7 +4,7 @@
 // requests into free slots (per-mesh slot sets sized by the device-memory
 // budget at mfem_server_add), then advances every admitted request of every
 // mesh by one Newton step together -- the element and assembly kernels per
-// mesh and one persistent PCG launch for all of them -- and hands finished
+// mesh and one sequence of PCG iteration launches for all of them -- and hands finished
 // requests back.  A request's arithmetic never depends on the others in the
 // step (per-problem deterministic reductions), so its result equals the same
 // pose solved alone.
@@ -201,14 +201,8 @@ mfem_status mfem_server_add(mfem_server* s, mfem_ctx* c, int32_t* mesh_id) {
     }
     cudaStreamSynchronize(c->stream);
     c->stream = s->stream;
-    if (c->tile_rows == 0) {   // one work shape for every mesh in a shared launch
-        c->tile_rows = 128;
-        c->tpr = 1;
-    }
-    if (!s->meshes.empty()) {
-        c->tile_rows = s->meshes[0].ctx->tile_rows;
-        c->tpr = s->meshes[0].ctx->tpr;
-    }
+    if (c->tile_rows == 0) c->tile_rows = 256;   // one tile for every mesh in a shared launch
+    if (!s->meshes.empty()) c->tile_rows = s->meshes[0].ctx->tile_rows;
     mfem_status st = ensure_slots(c, cap);
     if (st != MFEM_OK) return st;
     c->owned_by_server = true;

@@ -41,7 +41,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("constraint", C.c_int32), ("k_s", C.c_double),
                 ("newton_tol", C.c_double), ("cg_tol", C.c_double), ("newton_max", C.c_int32),
                 ("cg_max", C.c_int32), ("init", C.c_int32), ("max_batch", C.c_int32),
-                ("tile_rows", C.c_int32), ("pcg_threads_per_row", C.c_int32), ("diagnostics", C.c_int32)]
+                ("tile_rows", C.c_int32), ("diagnostics", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -59,7 +59,7 @@ class Profile(C.Structure):
                 ("pcg_bytes", C.c_double), ("pcg_iters", C.c_int64), ("element_launches", C.c_int32),
                 ("element_ms", C.c_double), ("element_bytes", C.c_double), ("assemble_ms", C.c_double),
                 ("linesearch_ms", C.c_double), ("total_ms", C.c_double), ("tile_rows", C.c_int32),
-                ("threads_per_row", C.c_int32), ("grid_blocks", C.c_int32)]
+                ("grid_blocks", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
