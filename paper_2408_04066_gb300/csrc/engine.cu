@@ -231,7 +231,7 @@ void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc
         const int n = c->plan.n;
         const size_t slots = (size_t)c->plan.slice_ptr.back();
         for (int b = 0; b < g.B; ++b) {
-            if (!g.ph[b].active) continue;
+            if (!g.ph[b].active || !g.ph[b].in_pcg) continue;
             PcgDesc<T> d;
             d.slice_ptr = c->mesh.slice_ptr;
             d.col = c->mesh.col;
@@ -300,7 +300,8 @@ mfem_status read_scalars(mfem_ctx* c, int B) {
 // enqueued and the problem states read back after each chunk (max_iters > 0:
 // exactly that many iterations, no checks -- used by the autotuner).
 template <typename T>
-mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, int max_iters, bool count) {
+mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, int max_iters, bool count,
+                    bool one_chunk = false) {
     mfem_ctx* c = c0;
     std::vector<PcgDesc<T>> d;
     int units = 0;
@@ -332,6 +333,7 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
         if (g.ctx->slot.prec == prec) cap = std::max(cap, g.ctx->opt.cg_max);
     for (int done = 0; done < cap; done += kPcgChunk) {
         const int n_it = std::min(kPcgChunk, cap - done);
+        if (one_chunk && done > 0) break;
         int pe = count ? c->prof.begin(2, c->stream) : -1;
         CK(launch_pcg_iters<T>(dst, (int)d.size(), units, tile, n_it, c->stream));
         if (count) {
@@ -350,7 +352,7 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
         for (auto& g : gs) {
             if (g.ctx->slot.prec != prec) continue;
             for (int b = 0; b < g.B; ++b)
-                if (g.ph[b].active && g.ctx->sc_host[b].state == kActive) any = true;
+                if (g.ph[b].active && g.ph[b].in_pcg && g.ctx->sc_host[b].state == kActive) any = true;
         }
         if (!any) break;
     }
@@ -416,19 +418,33 @@ mfem_status autotune_tile(mfem_ctx* c, std::vector<Group>& gs) {
 
 }  // namespace
 
-mfem_status newton_step(std::vector<Group>& gs) {
+namespace {
+
+std::vector<int> mask_of(const Group& g, bool (*pred)(const ProbHost&)) {
+    std::vector<int> f(g.B, 0);
+    for (int b = 0; b < g.B; ++b) f[b] = pred(g.ph[b]) ? 1 : 0;
+    return f;
+}
+
+bool any_of(const std::vector<int>& f) {
+    for (int v : f)
+        if (v) return true;
+    return false;
+}
+
+}  // namespace
+
+mfem_status advance(std::vector<Group>& gs) {
     mfem_ctx* c = gs[0].ctx;
     cudaStream_t s = c->stream;
-    // a0: apply poses of newly admitted problems.  The Newton stop test is
+    // ---- a0: apply poses of newly admitted problems.  The Newton stop test is
     // relative to |g_free| at the rigid initial guess; for REST and WARM starts
     // that reference needs one gradient pass at the rigid guess first (the warm
-    // state is parked in outbuf meanwhile).
+    // state is parked in outbuf meanwhile); SNH with the COROT start takes the
+    // reference there and then the co-rotational predictor step.
     for (auto& g : gs) {
-        std::vector<int> f(g.B, 0);
-        bool any = false;
-        for (int b = 0; b < g.B; ++b)
-            if (g.ph[b].need_init) { f[b] = 1; any = true; }
-        if (!any) continue;
+        std::vector<int> f = mask_of(g, [](const ProbHost& p) { return p.need_init != 0; });
+        if (!any_of(f)) continue;
         mfem_ctx* gc = g.ctx;
         mfem_status st = upload_active(gc, g.B, f);
         if (st != MFEM_OK) return st;
@@ -436,19 +452,7 @@ mfem_status newton_step(std::vector<Group>& gs) {
         const int init = (gc->opt.init == MFEM_INIT_RIGID || gc->opt.init == MFEM_INIT_COROT)
                              ? 0 : (gc->opt.init == MFEM_INIT_REST ? 1 : 2);
         std::vector<double> gref(g.B, -1.0);
-        if (predict) {   // SNH reference gradient at the rigid guess, then the predictor step
-            ElemArgs a = elem_args(gc);
-            launch_pose_init(a, g.B, 0, s);
-            launch_element(a, g.B, s);
-            launch_assemble(a, g.B, s);
-            gc->prof.launches += 3;
-            st = read_scalars(gc, g.B);
-            if (st != MFEM_OK) return st;
-            CK(cudaStreamSynchronize(s));
-            synced(gs);
-            for (int b = 0; b < g.B; ++b)
-                if (f[b]) gref[b] = std::sqrt(gc->sc_host[b].gnorm2);
-        } else if (init != 0) {
+        if (predict || init != 0) {
             const size_t xbytes = sizeof(double) * 3 * (size_t)gc->plan.n * g.B;
             if (init == 2) CK(cudaMemcpyAsync(gc->slot.outbuf, gc->slot.x, xbytes, cudaMemcpyDeviceToDevice, s));
             ElemArgs a = elem_args(gc);
@@ -469,29 +473,26 @@ mfem_status newton_step(std::vector<Group>& gs) {
             gc->prof.launches++;
         }
         for (int b = 0; b < g.B; ++b)
-            if (g.ph[b].need_init) {
-                g.ph[b].pred = predict ? 1 : 0;
-                g.ph[b].need_init = 0;
-                g.ph[b].active = 1;
-                g.ph[b].it = 0;
-                g.ph[b].g0 = gref[b];
-                g.ph[b].pcg_iters = 0;
-                g.ph[b].ran_pcg = 0;
-                g.ph[b].status = MFEM_OK;
-                g.ph[b].converged = 0;
+            if (f[b]) {
+                ProbHost& p = g.ph[b];
+                p = ProbHost();
+                p.active = 1;
+                p.pred = predict ? 1 : 0;
+                p.g0 = gref[b];
             }
     }
-    // a1-a4: element step, assembly, gradient for active problems (problems with
-    // the co-rotational predictor pending use that energy in this step)
+    // ---- a1-a4: element pass, assembly and gradient for problems that need it
+    // (the co-rotational predictor uses that energy), FP64 convergence test,
+    // PCG initialisation for those that continue.
+    bool any_elem = false;
     for (auto& g : gs) {
         mfem_ctx* gc = g.ctx;
         bool any = false;
         for (int pass = 0; pass < 2; ++pass) {
             std::vector<int> f(g.B, 0);
-            bool anyp = false;
             for (int b = 0; b < g.B; ++b)
-                if (g.ph[b].active && g.ph[b].pred == pass) { f[b] = 1; anyp = true; }
-            if (!anyp) continue;
+                f[b] = (g.ph[b].active && !g.ph[b].in_pcg && g.ph[b].pred == pass) ? 1 : 0;
+            if (!any_of(f)) continue;
             any = true;
             mfem_status st = upload_active(gc, g.B, f);
             if (st != MFEM_OK) return st;
@@ -510,115 +511,129 @@ mfem_status newton_step(std::vector<Group>& gs) {
             gc->prof.element_bytes += na * element_bytes(gc);
         }
         if (!any) continue;
+        any_elem = true;
         mfem_status st = read_scalars(gc, g.B);
         if (st != MFEM_OK) return st;
     }
-    CK(cudaStreamSynchronize(s));
-    synced(gs);
-    // convergence test on the FP64 free gradient
-    bool any_active = false;
-    for (auto& g : gs) {
-        mfem_ctx* gc = g.ctx;
-        for (int b = 0; b < g.B; ++b) {
-            ProbHost& p = g.ph[b];
-            if (!p.active) continue;
-            if (p.pred) {   // predictor step: its gradient is not the SNH residual
-                any_active = true;
-                continue;
+    if (any_elem) {
+        CK(cudaStreamSynchronize(s));
+        synced(gs);
+        for (auto& g : gs) {
+            mfem_ctx* gc = g.ctx;
+            std::vector<int> start(g.B, 0);
+            for (int b = 0; b < g.B; ++b) {
+                ProbHost& p = g.ph[b];
+                if (!p.active || p.in_pcg) continue;
+                if (!p.pred) {   // the predictor's gradient is not the SNH residual
+                    const ProbScal& sc = gc->sc_host[b];
+                    p.gn = std::sqrt(sc.gnorm2);
+                    p.energy = sc.energy;
+                    if (p.g0 < 0.0) p.g0 = p.gn;
+                    if (!std::isfinite(p.gn)) {
+                        p.active = 0;
+                        p.status = MFEM_ENOTCONV;
+                        continue;
+                    }
+                    if (p.gn == 0.0 || p.gn <= gc->opt.newton_tol * p.g0) {
+                        p.active = 0;
+                        p.converged = 1;
+                        p.status = MFEM_OK;
+                        continue;
+                    }
+                    if (p.it >= gc->opt.newton_max) {
+                        p.active = 0;
+                        p.status = MFEM_ENOTCONV;
+                        continue;
+                    }
+                }
+                start[b] = 1;
             }
-            const ProbScal& sc = gc->sc_host[b];
-            p.gn = std::sqrt(sc.gnorm2);
-            p.energy = sc.energy;
-            if (p.g0 < 0.0) p.g0 = p.gn;
-            if (!std::isfinite(p.gn)) {
-                p.active = 0;
-                p.status = MFEM_ENOTCONV;
-            } else if (p.gn == 0.0 || p.gn <= gc->opt.newton_tol * p.g0) {
-                p.active = 0;
-                p.converged = 1;
-                p.status = MFEM_OK;
-            } else if (p.it >= gc->opt.newton_max) {
-                p.active = 0;
-                p.status = MFEM_ENOTCONV;
-            } else {
-                any_active = true;
+            if (!any_of(start)) continue;
+            if (c->tile_rows == 0) {   // first PCG of this context: time the tiles
+                std::vector<Group> one{Group{gc, g.B, g.ph}};
+                for (int b = 0; b < g.B; ++b) g.ph[b].in_pcg = start[b];
+                mfem_status st = upload_active(gc, g.B, start);
+                if (st != MFEM_OK) return st;
+                st = autotune_tile(c, one);
+                if (st != MFEM_OK) return st;
             }
+            mfem_status st = upload_active(gc, g.B, start);
+            if (st != MFEM_OK) return st;
+            launch_pcg_init(elem_args(gc), g.B, c->tile_rows, gc->opt.cg_tol * gc->opt.cg_tol, gc->opt.cg_max, s);
+            gc->prof.launches++;
+            for (int b = 0; b < g.B; ++b)
+                if (start[b]) g.ph[b].in_pcg = 1;
         }
     }
-    if (!any_active) return MFEM_OK;
-    // a5: PCG for every active problem of every group, one launch sequence per precision
-    for (auto& g : gs) {
-        std::vector<int> f(g.B, 0);
-        bool any = false;
-        for (int b = 0; b < g.B; ++b)
-            if (g.ph[b].active) { f[b] = 1; any = true; }
-        if (!any) continue;
-        mfem_ctx* gc = g.ctx;
-        mfem_status st = upload_active(gc, g.B, f);
-        if (st != MFEM_OK) return st;
-    }
-    if (c->tile_rows == 0) {
-        mfem_status st = autotune_tile(c, gs);
-        if (st != MFEM_OK) return st;
-    }
-    const int tile = c->tile_rows;
-    for (auto& g : gs) {
-        bool any = false;
-        for (int b = 0; b < g.B; ++b) any |= g.ph[b].active != 0;
-        if (!any) continue;
-        mfem_ctx* gc = g.ctx;
-        const double tol2 = gc->opt.cg_tol * gc->opt.cg_tol;
-        launch_pcg_init(elem_args(gc), g.B, tile, tol2, gc->opt.cg_max, s);
-        gc->prof.launches++;
-    }
+    // ---- a5: one chunk of PCG iterations over every problem inside PCG
+    bool any_pcg = false;
+    for (auto& g : gs)
+        for (int b = 0; b < g.B; ++b) any_pcg |= g.ph[b].active && g.ph[b].in_pcg;
+    if (!any_pcg) return MFEM_OK;
     for (int prec = 0; prec < 2; ++prec) {
         bool any = false;
         for (auto& g : gs)
             if (g.ctx->slot.prec == prec)
-                for (int b = 0; b < g.B; ++b) any |= g.ph[b].active != 0;
+                for (int b = 0; b < g.B; ++b) any |= g.ph[b].active && g.ph[b].in_pcg;
         if (!any) continue;
-        mfem_status st = prec == 1 ? run_pcg<float>(c, gs, 1, tile, 0, true)
-                                   : run_pcg<double>(c, gs, 0, tile, 0, true);
+        mfem_status st = prec == 1 ? run_pcg<float>(c, gs, 1, c->tile_rows, 0, true, true)
+                                   : run_pcg<double>(c, gs, 0, c->tile_rows, 0, true, true);
         if (st != MFEM_OK) return st;
     }
-    // a6: slope for line search (SNH) and PCG statistics
-    for (auto& g : gs) {
-        mfem_ctx* gc = g.ctx;
-        bool any = false;
-        for (int b = 0; b < g.B; ++b) any |= g.ph[b].active != 0;
-        if (!any) continue;
-        if (gc->model == MFEM_SNH) {
-            int pl = gc->prof.begin(3, s);
-            launch_slope(elem_args(gc), g.B, s);
-            gc->prof.end(pl, s);
-            gc->prof.launches++;
-        }
-        mfem_status st = read_scalars(gc, g.B);
-        if (st != MFEM_OK) return st;
-    }
-    CK(cudaStreamSynchronize(s));
-    synced(gs);
     CK(cudaGetLastError());
-    for (auto& g : gs) {
-        mfem_ctx* gc = g.ctx;
+    // ---- a6: problems whose PCG ended finish their Newton step
+    bool any_fin = false;
+    std::vector<std::vector<int>> fin(gs.size());
+    for (size_t gi = 0; gi < gs.size(); ++gi) {
+        Group& g = gs[gi];
+        fin[gi].assign(g.B, 0);
         for (int b = 0; b < g.B; ++b) {
             ProbHost& p = g.ph[b];
-            if (!p.active) continue;
-            p.pcg_iters += gc->sc_host[b].iter;
-            gc->prof.pcg_iters += gc->sc_host[b].iter;
-            gc->prof.pcg_bytes += gc->sc_host[b].iter * pcg_bytes_per_iter(gc);
-            gc->alpha_host[b] = 1.0;
+            if (p.active && p.in_pcg && g.ctx->sc_host[b].state != kActive) {
+                fin[gi][b] = 1;
+                any_fin = true;
+                p.pcg_iters += g.ctx->sc_host[b].iter;
+                g.ctx->prof.pcg_iters += g.ctx->sc_host[b].iter;
+                g.ctx->prof.pcg_bytes += g.ctx->sc_host[b].iter * pcg_bytes_per_iter(g.ctx);
+                g.ctx->alpha_host[b] = 1.0;
+            }
         }
     }
-    // backtracking line search on E (SNH); quadratic models take alpha = 1
-    for (auto& g : gs) {
+    if (!any_fin) return MFEM_OK;
+    // slope g.dx for the line search (SNH Newton steps; the predictor is quadratic)
+    bool any_ls = false;
+    std::vector<std::vector<int>> ls(gs.size());
+    for (size_t gi = 0; gi < gs.size(); ++gi) {
+        Group& g = gs[gi];
+        ls[gi].assign(g.B, 0);
+        if (g.ctx->model != MFEM_SNH) continue;
+        for (int b = 0; b < g.B; ++b) ls[gi][b] = fin[gi][b] && !g.ph[b].pred;
+        if (!any_of(ls[gi])) continue;
+        any_ls = true;
         mfem_ctx* gc = g.ctx;
-        if (gc->model != MFEM_SNH) continue;
+        mfem_status st = upload_active(gc, g.B, ls[gi]);
+        if (st != MFEM_OK) return st;
+        int pl = gc->prof.begin(3, s);
+        launch_slope(elem_args(gc), g.B, s);
+        gc->prof.end(pl, s);
+        gc->prof.launches++;
+        st = read_scalars(gc, g.B);
+        if (st != MFEM_OK) return st;
+    }
+    if (any_ls) {
+        CK(cudaStreamSynchronize(s));
+        synced(gs);
+    }
+    // backtracking line search on E (SNH)
+    for (size_t gi = 0; gi < gs.size(); ++gi) {
+        Group& g = gs[gi];
+        mfem_ctx* gc = g.ctx;
+        if (gc->model != MFEM_SNH || !any_of(ls[gi])) continue;
         std::vector<int> testing(g.B, 0);
         std::vector<double> e0(g.B, 0.0), slope(g.B, 0.0);
         bool any = false;
         for (int b = 0; b < g.B; ++b) {
-            if (!g.ph[b].active || g.ph[b].pred) continue;   // predictor: quadratic, alpha = 1
+            if (!ls[gi][b]) continue;
             e0[b] = g.ph[b].energy;
             slope[b] = gc->sc_host[b].slope;
             if (-slope[b] > kLsNoise * std::fabs(e0[b])) { testing[b] = 1; any = true; }
@@ -650,24 +665,21 @@ mfem_status newton_step(std::vector<Group>& gs) {
             }
         }
     }
-    // x <- x + alpha dx
-    for (auto& g : gs) {
-        std::vector<int> f(g.B, 0);
-        bool any = false;
-        for (int b = 0; b < g.B; ++b)
-            if (g.ph[b].active) { f[b] = 1; any = true; }
-        if (!any) continue;
+    // x <- x + alpha dx; the problem's next step starts with its element pass
+    for (size_t gi = 0; gi < gs.size(); ++gi) {
+        Group& g = gs[gi];
+        if (!any_of(fin[gi])) continue;
         mfem_ctx* gc = g.ctx;
-        mfem_status st = upload_active(gc, g.B, f);
+        mfem_status st = upload_active(gc, g.B, fin[gi]);
         if (st != MFEM_OK) return st;
         st = upload_alpha(gc, g.B);
         if (st != MFEM_OK) return st;
         launch_update(elem_args(gc), g.B, s);
         gc->prof.launches++;
         for (int b = 0; b < g.B; ++b)
-            if (g.ph[b].active) {
+            if (fin[gi][b]) {
                 g.ph[b].it++;
-                g.ph[b].ran_pcg = 1;
+                g.ph[b].in_pcg = 0;
                 g.ph[b].pred = 0;
             }
     }
@@ -679,8 +691,8 @@ mfem_status run_batch(mfem_ctx* c, int B, std::vector<ProbHost>& ph) {
     ph.assign(B, ProbHost());
     for (int b = 0; b < B; ++b) ph[b].need_init = 1;
     std::vector<Group> gs{Group{c, B, ph.data()}};
-    for (int guard = 0; guard < 100000; ++guard) {
-        mfem_status st = newton_step(gs);
+    for (int guard = 0; guard < 10000000; ++guard) {
+        mfem_status st = advance(gs);
         if (st != MFEM_OK) return st;
         bool any = false;
         for (int b = 0; b < B; ++b) any |= ph[b].active || ph[b].need_init;

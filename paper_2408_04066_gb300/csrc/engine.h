@@ -17,6 +17,7 @@ namespace mfem {
 struct ProbHost {
     int active = 0;      // still iterating
     int need_init = 0;   // pose/initial guess not yet applied
+    int in_pcg = 0;      // active and inside its PCG solve (else next is the element pass)
     int it = 0;          // Newton steps taken
     int pcg_iters = 0;
     int ran_pcg = 0;     // PCG ran in the current step
@@ -99,10 +100,13 @@ mfem_status ensure_slots(mfem_ctx* c, int B);
 size_t slot_bytes_for(const mfem_ctx* c, int B);
 ElemArgs elem_args(const mfem_ctx* c);
 
-// Advance every active problem of every group by one Newton step.  All groups
-// must share one stream (groups[0].ctx->stream).  Problems with need_init get
-// their pose applied first.  Returns MFEM_OK or a device/timeout error.
-mfem_status newton_step(std::vector<Group>& groups);
+// One scheduling round over every problem of every group (all groups share
+// groups[0].ctx->stream): apply newly admitted poses; run the element pass,
+// assembly and convergence test of problems that need them and start their PCG;
+// run one chunk of PCG iterations over the problems inside PCG; finish the
+// Newton step (line search, update) of problems whose PCG ended.  Problems move
+// through their Newton steps independently, so none waits for another's PCG.
+mfem_status advance(std::vector<Group>& groups);
 
 // Whole solve of B problems of one context (poses already in slot.xf).
 mfem_status run_batch(mfem_ctx* c, int B, std::vector<ProbHost>& ph);

@@ -129,7 +129,7 @@ void mfem_server::run() {
             }
         }
         if (gs.empty()) continue;
-        mfem_status st = newton_step(gs);
+        mfem_status st = advance(gs);
         steps++;
         for (auto& g : gs) pcg_launches += g.ctx->prof.pcg_launches;
         if (st != MFEM_OK) {
