@@ -57,16 +57,19 @@ struct PcgDesc {
 __device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(volatile const int*)p; }
 
 // Sum NV doubles over the block with a fixed shuffle/shared-memory tree.  The
-// result is valid in thread 0.  All threads of the block must call it.
+// result is valid in thread 0.  All threads of the block must call it.  With
+// warp_done the values are already warp sums (equal in every lane).
 template <int NV>
-__device__ __forceinline__ void block_sum(double (&v)[NV]) {
+__device__ __forceinline__ void block_sum(double (&v)[NV], bool warp_done = false) {
     __shared__ double sm[32][NV];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int nwarps = (blockDim.x + 31) >> 5;
+    if (!warp_done) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+        for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+            for (int i = 0; i < NV; ++i) v[i] += __shfl_xor_sync(0xffffffffu, v[i], o);
+    }
     __syncthreads();
     if (lane == 0)
 #pragma unroll
@@ -83,14 +86,60 @@ __device__ __forceinline__ void block_sum(double (&v)[NV]) {
     __syncthreads();
 }
 
+// ---- float-float inner products -------------------------------------------
+// GB300 issues FP64 at a small fraction of its FP32 rate, so the FP32 PCG path
+// forms its inner products with error-free transformations in FP32 instead of
+// FP64 instructions: two-product by fused multiply-add (Dekker, "A floating-point
+// technique for extending the available precision", 1971) and two-sum (Knuth,
+// TAOCP vol. 2, 4.2.2).  A (hi, lo) pair carries about 48 significant bits; it
+// becomes one double per warp.
+struct FF {
+    float hi, lo;
+};
+
+__device__ __forceinline__ FF ff_two_sum(float a, float b) {
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return FF{s, e};
+}
+
+__device__ __forceinline__ FF ff_add(FF x, FF y) {
+    const FF s = ff_two_sum(x.hi, y.hi);
+    const float e = __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo));
+    const float hi = __fadd_rn(s.hi, e);
+    return FF{hi, __fsub_rn(e, __fsub_rn(hi, s.hi))};
+}
+
+__device__ __forceinline__ FF ff_prod(float a, float b) {
+    const float p = __fmul_rn(a, b);
+    return FF{p, __fmaf_rn(a, b, -p)};
+}
+
+// a0*b0 + a1*b1 + a2*b2 as a float-float
+__device__ __forceinline__ FF ff_dot3(const float (&a)[3], const float (&b)[3]) {
+    return ff_add(ff_add(ff_prod(a[0], b[0]), ff_prod(a[1], b[1])), ff_prod(a[2], b[2]));
+}
+
+// warp sum of float-float values (fixed xor tree); the double is valid in every lane
+__device__ __forceinline__ double ff_warp_sum(FF v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        FF w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+        v = ff_add(v, w);
+    }
+    return (double)v.hi + (double)v.lo;
+}
+
 // Commit this block's NV partial sums for `tile` of a problem; the block that
 // completes the ticket adds all tiles in order and returns true with the totals
 // in `tot` (valid in thread 0 only).  part layout: [n_tiles][4], NV <= 4.
 template <int NV>
 __device__ __forceinline__ bool tile_commit(double (&v)[NV], double* part, int tile, int n_tiles,
-                                            unsigned* ticket, int slot0, double (&tot)[NV]) {
+                                            unsigned* ticket, int slot0, double (&tot)[NV],
+                                            bool warp_done = false) {
     __shared__ int s_last;
-    block_sum<NV>(v);
+    block_sum<NV>(v, warp_done);
     if (threadIdx.x == 0) {
 #pragma unroll
         for (int i = 0; i < NV; ++i) part[4 * tile + slot0 + i] = v[i];

@@ -257,6 +257,43 @@ __device__ __forceinline__ void ld_zp(const double* zp, int c, double (&z)[3], d
     p[0] = e.x; p[1] = e.y; p[2] = f.x;
 }
 
+// Per-row contribution to an inner product and its warp sum: float-float in
+// the FP32 path (no FP64 instructions until one conversion per warp), plain
+// FP64 in the FP64 path.
+template <typename T>
+struct Partial;
+
+template <>
+struct Partial<float> {
+    FF v;
+    static __device__ __forceinline__ Partial zero() { return Partial{FF{0.f, 0.f}}; }
+};
+
+template <>
+struct Partial<double> {
+    double v;
+    static __device__ __forceinline__ Partial zero() { return Partial{0.0}; }
+};
+
+__device__ __forceinline__ Partial<float> dot3_partial(float a0, float a1, float a2, float b0, float b1, float b2) {
+    const float a[3] = {a0, a1, a2}, b[3] = {b0, b1, b2};
+    return Partial<float>{ff_dot3(a, b)};
+}
+
+__device__ __forceinline__ Partial<double> dot3_partial(double a0, double a1, double a2, double b0, double b1,
+                                                        double b2) {
+    return Partial<double>{a0 * b0 + a1 * b1 + a2 * b2};
+}
+
+__device__ __forceinline__ double warp_sum_partial(Partial<float> p) { return ff_warp_sum(p.v); }
+
+__device__ __forceinline__ double warp_sum_partial(Partial<double> p) {
+    double v = p.v;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
 // problem of unit u: last descriptor whose unit_begin <= u
 template <typename T>
 __device__ __forceinline__ int unit_problem(const PcgDesc<T>* __restrict__ D, int n_probs, int u) {
@@ -282,6 +319,7 @@ __global__ void __launch_bounds__(TILE) k_pcg_spmv(const PcgDesc<T>* __restrict_
     T* zpn = (iter & 1) ? d.zp0 : d.zp1;
     const T beta = (T)sc->beta;
     double v[1] = {0.0};
+    Partial<T> pq = Partial<T>::zero();
     if (row < d.n_rows) {
         const int s = row >> 5, lane = row & 31;
         const int base = __ldg(d.slice_ptr + s), w = (__ldg(d.slice_ptr + s + 1) - base) >> 5;
@@ -314,10 +352,11 @@ __global__ void __launch_bounds__(TILE) k_pcg_spmv(const PcgDesc<T>* __restrict_
         d.q[3 * row] = a0;
         d.q[3 * row + 1] = a1;
         d.q[3 * row + 2] = a2;
-        v[0] = (double)pn0 * (double)a0 + (double)pn1 * (double)a1 + (double)pn2 * (double)a2;
+        pq = dot3_partial(pn0, pn1, pn2, a0, a1, a2);
     }
+    v[0] = warp_sum_partial(pq);
     double tot[1];
-    if (tile_commit<1>(v, d.part, tile, d.n_tiles, &sc->tk_a, 0, tot) && threadIdx.x == 0) {
+    if (tile_commit<1>(v, d.part, tile, d.n_tiles, &sc->tk_a, 0, tot, true) && threadIdx.x == 0) {
         const double pq = tot[0];
         if (pq > 0.0 && isfinite(pq)) {
             sc->alpha = sc->rho / pq;
@@ -340,10 +379,11 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
     T* zpn = (iter & 1) ? d.zp0 : d.zp1;
     const T alpha = (T)sc->alpha;
     double v[2] = {0.0, 0.0};
+    Partial<T> rz = Partial<T>::zero(), rr2 = Partial<T>::zero();
     if (row < d.n_rows) {
         T* rec = zpn + 8 * (size_t)row;
         const T* di = d.dinv + 9 * (size_t)row;
-        T rr[3];
+        T rr[3], zz[3];
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             d.dx[3 * row + i] = fma(alpha, rec[4 + i], d.dx[3 * row + i]);
@@ -352,14 +392,16 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
         }
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            const T zi = di[3 * i] * rr[0] + di[3 * i + 1] * rr[1] + di[3 * i + 2] * rr[2];
-            rec[i] = zi;
-            v[0] += (double)rr[i] * (double)zi;
-            v[1] += (double)rr[i] * (double)rr[i];
+            zz[i] = di[3 * i] * rr[0] + di[3 * i + 1] * rr[1] + di[3 * i + 2] * rr[2];
+            rec[i] = zz[i];
         }
+        rz = dot3_partial(rr[0], rr[1], rr[2], zz[0], zz[1], zz[2]);
+        rr2 = dot3_partial(rr[0], rr[1], rr[2], rr[0], rr[1], rr[2]);
     }
+    v[0] = warp_sum_partial(rz);
+    v[1] = warp_sum_partial(rr2);
     double tot[2];
-    if (tile_commit<2>(v, d.part, tile, d.n_tiles, &sc->tk_b, 1, tot) && threadIdx.x == 0) {
+    if (tile_commit<2>(v, d.part, tile, d.n_tiles, &sc->tk_b, 1, tot, true) && threadIdx.x == 0) {
         const double rho_new = tot[0];
         sc->beta = sc->rho != 0.0 ? rho_new / sc->rho : 0.0;
         sc->rho = rho_new;
