@@ -20,9 +20,12 @@ constexpr int kKe = 90;              // 10 upper 3x3 blocks of a symmetric 12x12
 
 // Per-problem PCG vector area, in elements of the PCG type, rows padded to 32:
 // two ping-pong records zp[n][8] = (z.xyz, 0, p.xyz, 0) so a neighbour's z and
-// previous p come from one 32-byte (FP32) record, then dx, r, q as [n][3].
-constexpr int kVecStride = 25;                 // times npad32(n)
-constexpr int kOffZP0 = 0, kOffZP1 = 8, kOffDX = 16, kOffR = 19, kOffQ = 22;
+// previous p come from one 32-byte (FP32) record, then the row record
+// rec[n][12] = (dx.xyz, 0, r.xyz, 0, q.xyz, 0), three aligned 16-byte vectors.
+constexpr int kVecStride = 28;                 // times npad32(n)
+constexpr int kOffZP0 = 0, kOffZP1 = 8, kOffRec = 16;
+constexpr int kRec = 12;
+constexpr int kRecDX = 0, kRecR = 4, kRecQ = 8;
 __host__ __device__ __forceinline__ size_t npad32(int n) { return ((size_t)n + 31) & ~(size_t)31; }
 
 // Problem states (PCG)
@@ -46,13 +49,16 @@ struct PcgDesc {
     const T* dinv;         // [n][9] inverse diagonal blocks
     T* zp0;                // [n][8] (z, p) records, read at even iterations
     T* zp1;                // [n][8] read at odd iterations
-    T* dx;
-    T* r;
-    T* q;                  // [n][3] each
+    T* rec;                // [n][12] (dx, r, q) records
     double* part;          // [tiles][4] tile partials
     ProbScal* sc;
     int n_rows, n_tiles, unit_begin, pad;
 };
+
+// Programmatic dependent launch: wait for the preceding grid of the stream to
+// complete and its writes to be visible; let the next grid start launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 __device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(volatile const int*)p; }
 

@@ -206,9 +206,9 @@ void end_profile(mfem_ctx* c) {
 namespace {
 
 // Algorithmic bytes of one PCG iteration of one problem (each datum crossing
-// HBM once): matrix values and column ids, the own rows of z and p_old read
-// and p_new, q written (phase A); p_new, q, dx, r, D^-1 read and dx, r, z
-// written (phase B).
+// HBM once, 3-vectors counted as 3 elements): matrix values and column ids;
+// k_pcg_spmv reads the row's z and p_old and writes p_new and q; k_pcg_update
+// reads p_new, q, dx, r and the 9-element D^-1 and writes dx, r, z.
 double pcg_bytes_per_iter(const mfem_ctx* c) {
     const double kt = c->slot.prec == 1 ? 4.0 : 8.0;
     const double nnzb = (double)c->plan.nnz_blocks, n = c->plan.n;
@@ -241,9 +241,7 @@ void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc
             T* v = (T*)c->slot.vec + (size_t)b * kVecStride * np;
             d.zp0 = v + kOffZP0 * np;
             d.zp1 = v + kOffZP1 * np;
-            d.dx = v + kOffDX * np;
-            d.r = v + kOffR * np;
-            d.q = v + kOffQ * np;
+            d.rec = v + kOffRec * np;
             d.part = c->slot.part + (size_t)b * c->slot.part_tiles * 4;
             d.sc = c->slot.sc + b;
             d.n_rows = n;

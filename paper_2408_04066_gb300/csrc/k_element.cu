@@ -25,16 +25,17 @@ __device__ __forceinline__ int pair_index(int a, int b) {  // a <= b
 }
 
 // Gather the four vertex positions of tet k of problem b (optionally x + alpha dx).
+// dx, if given, is read with a stride of dx_stride elements per vertex.
 template <typename T>
 __device__ __forceinline__ void gather_x(const double* __restrict__ x, const T* __restrict__ dx,
-                                         double alpha, int4 tv, double (&xa)[4][3]) {
+                                         double alpha, int4 tv, double (&xa)[4][3], int dx_stride = 3) {
     const int id[4] = {tv.x, tv.y, tv.z, tv.w};
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             double v = x[3 * (size_t)id[a] + i];
-            if (dx) v = fma(alpha, (double)dx[3 * (size_t)id[a] + i], v);
+            if (dx) v = fma(alpha, (double)dx[(size_t)dx_stride * id[a] + i], v);
             xa[a][i] = v;
         }
 }
@@ -405,10 +406,10 @@ __global__ void __launch_bounds__(kTetTile) k_energy_trial(ElemArgs A) {
     double en[1] = {0.0};
     if (k < m) {
         const double* x = A.slot.x + (size_t)b * n * 3;
-        const T* dx = (const T*)A.slot.vec + (size_t)b * kVecStride * npad32(n) + kOffDX * npad32(n);
+        const T* dx = (const T*)A.slot.vec + (size_t)b * kVecStride * npad32(n) + kOffRec * npad32(n) + kRecDX;
         const double* xf = A.slot.xf + (size_t)b * M.H * 12;
         double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6], sig[6];
-        gather_x<T>(x, dx, A.slot.alpha[b], M.tet[k], xa);
+        gather_x<T>(x, dx, A.slot.alpha[b], M.tet[k], xa, kRec);
         load_G(M.Dminv64, m, k, G);
         load_Q(xf, M.cluster[k], Q);
         stretch(xa, G, Q, F, S);

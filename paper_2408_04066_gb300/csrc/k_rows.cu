@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(kRowTile) k_slope(ElemArgs A) {
     double v[1] = {0.0};
     if (row < n) {
         const double* g = A.slot.g + ((size_t)b * n + row) * 3;
-        const T* dx = vecp<T>(A.slot, b, kOffDX, n) + 3 * (size_t)row;
+        const T* dx = vecp<T>(A.slot, b, kOffRec, n) + kRec * (size_t)row + kRecDX;
         v[0] = g[0] * (double)dx[0] + g[1] * (double)dx[1] + g[2] * (double)dx[2];
     }
     double tot[1];
@@ -156,9 +156,9 @@ __global__ void k_update(ElemArgs A) {
     const int n = A.mesh.n;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= 3 * n) return;
-    const T* dx = vecp<T>(A.slot, b, kOffDX, n);
+    const T* rec = vecp<T>(A.slot, b, kOffRec, n);
     double* x = A.slot.x + (size_t)b * n * 3;
-    x[i] = fma(A.slot.alpha[b], (double)dx[i], x[i]);
+    x[i] = fma(A.slot.alpha[b], (double)rec[kRec * (size_t)(i / 3) + kRecDX + i % 3], x[i]);
 }
 
 __global__ void k_unpermute(ElemArgs A, double* __restrict__ out) {
@@ -196,15 +196,15 @@ __global__ void k_pcg_init(ElemArgs A, double tol2, int maxit) {
     if (row < n) {
         const double* g = A.slot.g + ((size_t)b * n + row) * 3;
         const T* di = (const T*)A.slot.dinv + ((size_t)b * n + row) * 9;
-        T* dx = vecp<T>(A.slot, b, kOffDX, n) + 3 * (size_t)row;
-        T* r = vecp<T>(A.slot, b, kOffR, n) + 3 * (size_t)row;
+        T* rec = vecp<T>(A.slot, b, kOffRec, n) + kRec * (size_t)row;
         T* zp = vecp<T>(A.slot, b, kOffZP0, n) + 8 * (size_t)row;
         T rr[3] = {(T)(-g[0]), (T)(-g[1]), (T)(-g[2])};
 #pragma unroll
+        for (int i = 0; i < kRec; ++i) rec[i] = (T)0;
+#pragma unroll
         for (int i = 0; i < 3; ++i) {
             T zi = di[3 * i] * rr[0] + di[3 * i + 1] * rr[1] + di[3 * i + 2] * rr[2];
-            dx[i] = (T)0;
-            r[i] = rr[i];
+            rec[kRecR + i] = rr[i];
             zp[i] = zi;
             zp[4 + i] = (T)0;
             v[0] += (double)rr[i] * (double)zi;
@@ -255,6 +255,30 @@ __device__ __forceinline__ void ld_zp(const double* zp, int c, double (&z)[3], d
     const double2 a = r[0], b = r[1], e = r[2], f = r[3];
     z[0] = a.x; z[1] = a.y; z[2] = b.x;
     p[0] = e.x; p[1] = e.y; p[2] = f.x;
+}
+
+// 3-vectors stored as aligned 4-element groups (x, y, z, 0)
+__device__ __forceinline__ void ld4(const float* p, float (&v)[3]) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+}
+
+__device__ __forceinline__ void ld4(const double* p, double (&v)[3]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+}
+
+__device__ __forceinline__ void st4(float* p, float a, float b, float c) {
+    *reinterpret_cast<float4*>(p) = make_float4(a, b, c, 0.f);
+}
+
+__device__ __forceinline__ void st4(double* p, double a, double b, double c) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(a, b);
+    reinterpret_cast<double2*>(p)[1] = make_double2(c, 0.0);
 }
 
 // Per-row contribution to an inner product and its warp sum: float-float in
@@ -308,6 +332,8 @@ __device__ __forceinline__ int unit_problem(const PcgDesc<T>* __restrict__ D, in
 
 template <typename T, int TILE>
 __global__ void __launch_bounds__(TILE) k_pcg_spmv(const PcgDesc<T>* __restrict__ D, int n_probs) {
+    pdl_wait();
+    pdl_trigger();
     const int u = blockIdx.x;
     const PcgDesc<T>& d = D[unit_problem(D, n_probs, u)];
     ProbScal* sc = d.sc;
@@ -345,13 +371,8 @@ __global__ void __launch_bounds__(TILE) k_pcg_spmv(const PcgDesc<T>* __restrict_
         const T pn0 = fma(beta, pr[0], zr[0]);
         const T pn1 = fma(beta, pr[1], zr[1]);
         const T pn2 = fma(beta, pr[2], zr[2]);
-        T* rec = zpn + 8 * (size_t)row;
-        rec[4] = pn0;
-        rec[5] = pn1;
-        rec[6] = pn2;
-        d.q[3 * row] = a0;
-        d.q[3 * row + 1] = a1;
-        d.q[3 * row + 2] = a2;
+        st4(zpn + 8 * (size_t)row + 4, pn0, pn1, pn2);
+        st4(d.rec + kRec * (size_t)row + kRecQ, a0, a1, a2);
         pq = dot3_partial(pn0, pn1, pn2, a0, a1, a2);
     }
     v[0] = warp_sum_partial(pq);
@@ -369,6 +390,8 @@ __global__ void __launch_bounds__(TILE) k_pcg_spmv(const PcgDesc<T>* __restrict_
 
 template <typename T, int TILE>
 __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restrict__ D, int n_probs) {
+    pdl_wait();
+    pdl_trigger();
     const int u = blockIdx.x;
     const PcgDesc<T>& d = D[unit_problem(D, n_probs, u)];
     ProbScal* sc = d.sc;
@@ -381,20 +404,24 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
     double v[2] = {0.0, 0.0};
     Partial<T> rz = Partial<T>::zero(), rr2 = Partial<T>::zero();
     if (row < d.n_rows) {
-        T* rec = zpn + 8 * (size_t)row;
+        T* zrec = zpn + 8 * (size_t)row;
+        T* rec = d.rec + kRec * (size_t)row;
         const T* di = d.dinv + 9 * (size_t)row;
-        T rr[3], zz[3];
+        T pp[3], dxv[3], r0[3], qv[3], rr[3], zz[3];
+        ld4(zrec + 4, pp);
+        ld4(rec + kRecDX, dxv);
+        ld4(rec + kRecR, r0);
+        ld4(rec + kRecQ, qv);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            d.dx[3 * row + i] = fma(alpha, rec[4 + i], d.dx[3 * row + i]);
-            rr[i] = fma(-alpha, d.q[3 * row + i], d.r[3 * row + i]);
-            d.r[3 * row + i] = rr[i];
+            dxv[i] = fma(alpha, pp[i], dxv[i]);
+            rr[i] = fma(-alpha, qv[i], r0[i]);
         }
+        st4(rec + kRecDX, dxv[0], dxv[1], dxv[2]);
+        st4(rec + kRecR, rr[0], rr[1], rr[2]);
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            zz[i] = di[3 * i] * rr[0] + di[3 * i + 1] * rr[1] + di[3 * i + 2] * rr[2];
-            rec[i] = zz[i];
-        }
+        for (int i = 0; i < 3; ++i) zz[i] = di[3 * i] * rr[0] + di[3 * i + 1] * rr[1] + di[3 * i + 2] * rr[2];
+        st4(zrec, zz[0], zz[1], zz[2]);
         rz = dot3_partial(rr[0], rr[1], rr[2], zz[0], zz[1], zz[2]);
         rr2 = dot3_partial(rr[0], rr[1], rr[2], rr[0], rr[1], rr[2]);
     }
@@ -413,11 +440,25 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
     }
 }
 
+// Each launch may start while the previous kernel of the stream drains
+// (programmatic stream serialization); the kernels wait on it first thing.
 template <typename T, int TILE>
 cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units, int iters, cudaStream_t s) {
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(n_units);
+    cfg.blockDim = dim3(TILE);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
     for (int i = 0; i < iters; ++i) {
-        k_pcg_spmv<T, TILE><<<n_units, TILE, 0, s>>>(descs, n_probs);
-        k_pcg_update<T, TILE><<<n_units, TILE, 0, s>>>(descs, n_probs);
+        cudaError_t e = cudaLaunchKernelEx(&cfg, k_pcg_spmv<T, TILE>, descs, n_probs);
+        if (e != cudaSuccess) return e;
+        e = cudaLaunchKernelEx(&cfg, k_pcg_update<T, TILE>, descs, n_probs);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
