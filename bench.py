@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-newton-steps", type=int, default=2)
+    p.add_argument("--ncu-case", action="store_true",
+                   help="one small solve for profiler captures: 8 poses, 3 Newton steps, 256-row tiles")
     return p.parse_args()
 
 
@@ -96,6 +98,15 @@ class ClockSampler:
         self.rows = []
         self.proc = None
         self.th = None
+        self.lo = 0
+        self.hi = None
+
+    def mark_start(self):
+        """Samples before this call (start-up, warm-up) are not reported."""
+        self.lo = len(self.rows)
+
+    def mark_end(self):
+        self.hi = len(self.rows)
 
     def start(self):
         try:
@@ -123,7 +134,8 @@ class ClockSampler:
         self.th.join(timeout=5)
         sm, smax, reasons, power = [], [], set(), []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for r in self.rows:
+        rows = self.rows[self.lo:self.hi] or self.rows[-1:]
+        for r in rows:
             try:
                 sm.append(float(r[1]))
                 smax.append(float(r[2]))
@@ -224,11 +236,19 @@ def cpu_baseline(args, steps_frame):
                        f"BLAS/OpenMP threads = 1")}
 
 
+def workload_config(m, n, H, pins, nb, precision):
+    return {"workload": f"figure{m // 1000}k-snh-batch{nb}", "tets": m, "verts": n,
+            "handles": H, "pins": pins, "batch_poses": nb, "precision": precision, "newton_tol": 1e-6,
+            "l2": "256 MiB buffer written between timed steps; per-step working set > L2"}
+
+
 def run_reference(args, dist):
     if dist.rank != 0:
         return
     from synth import figure_config
-    figure_config(args.tets, model=args.model, seeds=[0])   # mesh generation is setup, not timed
+    from oracle import solve as S
+    cfg = figure_config(args.tets, model=args.model, seeds=[0])   # mesh generation is setup, not timed
+    st = S.Setup.from_config(cfg)
     total = oracle_step_times(args.tets, args.model, 0, args.warmup + args.steps)
     times = total[args.warmup:]
     t = statistics.mean(times)
@@ -239,8 +259,8 @@ def run_reference(args, dist):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"figure{args.tets // 1000}k-{args.model}", "tets": args.tets,
-                   "model": args.model},
+        "config": dict(workload_config(st.m, st.n, len(cfg["joints"]), len(st.pin_verts), args.batch,
+                                       args.precision), parallelism="oracle, 1 CPU thread"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": f"each step = one oracle Newton step (FP64, Jacobi-PCG 1e-2) of pose 0; "
                                    f"frames/s = 1 / (mean step time x {spf:.2f} Newton steps per frame)"},
@@ -271,13 +291,17 @@ def run_mfem(args, dist):
     out = torch.empty((nb, info["n"], 3), dtype=torch.float64, device=dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)       # > 129 MB L2
 
+    # the clock sampler starts before the warm-up so that nvidia-smi's own
+    # start-up does not fall into the timed region
+    clocks = ClockSampler(dist.local)
+    clocks.start()
     for _ in range(args.warmup):
         ctx.solve_batch(xfs, out)
     torch.cuda.synchronize()
+    time.sleep(0.3)
 
-    clocks = ClockSampler(dist.local)
     step_ms, prof, stats_all = [], [], []
-    clocks.start()
+    clocks.mark_start()
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
@@ -292,7 +316,9 @@ def run_mfem(args, dist):
         prof.append(ctx.profile())
         stats_all.append(st)
     dist.barrier()
+    clocks.mark_end()
     clk = clocks.stop()
+    clk["step_ms"] = [round(t, 3) for t in step_ms]
     total_ms = sum(step_ms)
     total_ms_max = dist.max(total_ms)
     poses = dist.sum(nb * args.steps)
@@ -380,11 +406,8 @@ def run_mfem(args, dist):
             "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-            "config": {"workload": f"figure{info['m'] // 1000}k-{args.model}-batch{nb}", "tets": info["m"],
-                       "verts": info["n"], "handles": info["n_handles"], "pins": info["n_pins"],
-                       "batch_poses": nb, "precision": args.precision, "newton_tol": 1e-6,
-                       "l2": "256 MiB buffer written between timed steps; per-step working set > L2",
-                       "parallelism": f"replicas x{dist.world}"},
+            "config": dict(workload_config(info["m"], info["n"], info["n_handles"], info["n_pins"], nb,
+                                           args.precision), parallelism=f"replicas x{dist.world}"),
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                            "note": "per batch step; every pose of a batch completes with the step"},
             "plain_fp64": fp64,
@@ -399,8 +422,27 @@ def run_mfem(args, dist):
     ctx.close()
 
 
+def run_ncu_case(args):
+    """Small, fixed case for ncu captures (a few GB on the device, short kernels):
+    the 200k-tet figure, 8 poses, 3 Newton steps, PCG tiles of 256 rows."""
+    import torch
+    from paper_2408_04066_gb300 import build as B
+    B.build()
+    from paper_2408_04066_gb300 import mfem
+    from synth import figure_config
+    cfg = figure_config(args.tets, model=args.model, seeds=range(8))
+    ctx = mfem.Context.from_config(cfg, precision=args.precision, max_batch=8, newton_max=3, tile_rows=256)
+    ctx.solve_batch(torch.tensor(cfg["xfs"], dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    print(json.dumps({"ncu_case": ctx.profile()}), flush=True)
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.ncu_case:
+        run_ncu_case(args)
+        return
     dist = Dist()
     try:
         if args.impl == "reference":

@@ -36,6 +36,7 @@ struct ProbScal {
     double rho, alpha, beta, rr0, rr, tol2;
     double gnorm2, energy, slope, energy_trial;
     double alpha_ls, pad0;
+    float alpha_f, beta_f;   // FP32 copies of alpha and beta for the FP32 kernels
     int iter, state, maxit, active;
     unsigned tk_a, tk_b, tk_g, tk_e, tk_s, tk_init, tk_pad0, tk_pad1;
 };
@@ -64,7 +65,7 @@ __device__ __forceinline__ int ld_volatile_i32(const int* p) { return *(volatile
 
 // Sum NV doubles over the block with a fixed shuffle/shared-memory tree.  The
 // result is valid in thread 0.  All threads of the block must call it.  With
-// warp_done the values are already warp sums (equal in every lane).
+// warp_done the values are already warp sums, held by lane 0 of each warp.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], bool warp_done = false) {
     __shared__ double sm[32][NV];
@@ -127,14 +128,16 @@ __device__ __forceinline__ FF ff_dot3(const float (&a)[3], const float (&b)[3]) 
     return ff_add(ff_add(ff_prod(a[0], b[0]), ff_prod(a[1], b[1])), ff_prod(a[2], b[2]));
 }
 
-// warp sum of float-float values (fixed xor tree); the double is valid in every lane
+// warp sum of float-float values (fixed xor tree), as a double in lane 0 (0 elsewhere)
 __device__ __forceinline__ double ff_warp_sum(FF v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         FF w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
         v = ff_add(v, w);
     }
-    return (double)v.hi + (double)v.lo;
+    double d = 0.0;
+    if ((threadIdx.x & 31) == 0) d = (double)v.hi + (double)v.lo;
+    return d;
 }
 
 // Commit this block's NV partial sums for `tile` of a problem; the block that

@@ -222,6 +222,8 @@ __global__ void k_pcg_init(ElemArgs A, double tol2, int maxit) {
         sc->rr = tot[1];
         sc->beta = 0.0;
         sc->alpha = 0.0;
+        sc->alpha_f = 0.f;
+        sc->beta_f = 0.f;
         sc->iter = 0;
         sc->tol2 = tol2;
         sc->maxit = maxit;
@@ -318,6 +320,16 @@ __device__ __forceinline__ double warp_sum_partial(Partial<double> p) {
     return v;
 }
 
+// step coefficients in the kernel's precision
+__device__ __forceinline__ void coeffs(const ProbScal* sc, float& a, float& b) {
+    a = sc->alpha_f;
+    b = sc->beta_f;
+}
+__device__ __forceinline__ void coeffs(const ProbScal* sc, double& a, double& b) {
+    a = sc->alpha;
+    b = sc->beta;
+}
+
 // problem of unit u: last descriptor whose unit_begin <= u
 template <typename T>
 __device__ __forceinline__ int unit_problem(const PcgDesc<T>* __restrict__ D, int n_probs, int u) {
@@ -330,8 +342,10 @@ __device__ __forceinline__ int unit_problem(const PcgDesc<T>* __restrict__ D, in
     return lo;
 }
 
+// Full occupancy (2048 threads per SM) matters more than registers here: the
+// kernel is latency-bound on its dependent col -> gather loads.
 template <typename T, int TILE>
-__global__ void __launch_bounds__(TILE) k_pcg_spmv(const PcgDesc<T>* __restrict__ D, int n_probs) {
+__global__ void __launch_bounds__(TILE, 2048 / TILE) k_pcg_spmv(const PcgDesc<T>* __restrict__ D, int n_probs) {
     pdl_wait();
     pdl_trigger();
     const int u = blockIdx.x;
@@ -343,7 +357,8 @@ __global__ void __launch_bounds__(TILE) k_pcg_spmv(const PcgDesc<T>* __restrict_
     const int iter = sc->iter;
     const T* zpo = (iter & 1) ? d.zp1 : d.zp0;
     T* zpn = (iter & 1) ? d.zp0 : d.zp1;
-    const T beta = (T)sc->beta;
+    T alpha_unused, beta;
+    coeffs(sc, alpha_unused, beta);
     double v[1] = {0.0};
     Partial<T> pq = Partial<T>::zero();
     if (row < d.n_rows) {
@@ -385,6 +400,7 @@ __global__ void __launch_bounds__(TILE) k_pcg_spmv(const PcgDesc<T>* __restrict_
             sc->alpha = 0.0;
             sc->state = kConverged;
         }
+        sc->alpha_f = (float)sc->alpha;
     }
 }
 
@@ -400,7 +416,8 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
     const int row = tile * TILE + threadIdx.x;
     const int iter = sc->iter;
     T* zpn = (iter & 1) ? d.zp0 : d.zp1;
-    const T alpha = (T)sc->alpha;
+    T alpha, beta_unused;
+    coeffs(sc, alpha, beta_unused);
     double v[2] = {0.0, 0.0};
     Partial<T> rz = Partial<T>::zero(), rr2 = Partial<T>::zero();
     if (row < d.n_rows) {
@@ -431,6 +448,7 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
     if (tile_commit<2>(v, d.part, tile, d.n_tiles, &sc->tk_b, 1, tot, true) && threadIdx.x == 0) {
         const double rho_new = tot[0];
         sc->beta = sc->rho != 0.0 ? rho_new / sc->rho : 0.0;
+        sc->beta_f = (float)sc->beta;
         sc->rho = rho_new;
         sc->rr = tot[1];
         const int itn = sc->iter + 1;
