@@ -54,7 +54,7 @@ typedef enum {
 typedef enum { MFEM_ARAP = 0, MFEM_COROT = 1, MFEM_SNH = 2 } mfem_model;
 typedef enum { MFEM_FP64 = 0, MFEM_MIXED = 1 } mfem_precision;
 typedef enum { MFEM_ELIMINATE = 0, MFEM_PENALTY = 1 } mfem_constraint;
-typedef enum { MFEM_CLUSTER_BONE = 0, MFEM_CLUSTER_JOINT = 1 } mfem_cluster_rule;
+typedef enum { MFEM_CLUSTER_BONE = 0, MFEM_CLUSTER_JOINT = 1, MFEM_CLUSTER_MIDPOINT = 2 } mfem_cluster_rule;
 typedef enum { MFEM_INIT_RIGID = 0, MFEM_INIT_REST = 1, MFEM_INIT_WARM = 2, MFEM_INIT_COROT = 3 } mfem_init;
 typedef enum { MFEM_MEM_HOST = 0, MFEM_MEM_DEVICE = 1 } mfem_memory;
 
@@ -76,8 +76,9 @@ typedef struct {
  * parent joint's handle transform.  Tet rotation clusters (§3.1): by default
  * each tet takes the bone segment nearest its barycenter (MFEM_CLUSTER_BONE;
  * with no bones, the nearest joint); MFEM_CLUSTER_JOINT takes the nearest
- * joint; tet_cluster [m] (handle indices) overrides both (§4, user-defined
- * clusters).  Pins (Eq. 6 "pin vertices along the skeleton"): pin_verts /
+ * joint; MFEM_CLUSTER_MIDPOINT the bone whose midpoint is nearest (the
+ * variants compared in §4, "Exploring different rotation clustering");
+ * tet_cluster [m] (handle indices) overrides all (§4, user-defined clusters).  Pins (Eq. 6 "pin vertices along the skeleton"): pin_verts /
  * pin_handle [n_pins] if given, else every vertex within pin_radius of a joint
  * or a bone midpoint, following the handle its position clusters to.  Ties in
  * nearest-X searches go to the lowest index (a 1e-10 * bbox_diag^2 margin). */

@@ -3,12 +3,13 @@
 Paper §3.1: every tet takes the rotation of the bone segment closest to its
 barycenter; all tets of a cluster share that rotation.  A bone runs from a
 parent joint to a child joint and carries the parent joint's handle transform.
-A rig with no parent links has no segments; tets then take the nearest joint
-(one of the variants compared in §4, "Exploring different rotation
-clustering").  Ties go to the lowest bone (child-joint) index: a candidate wins
-only if its squared distance is smaller by more than TIE_EPS * L^2, L the
-bounding-box diagonal of the points, so mirror-symmetric geometry resolves the
-same way in any rounding order.
+A rig with no parent links has no segments; tets then take the nearest joint.
+§4 ("Exploring different rotation clustering") also compares the nearest
+joint and the nearest bone midpoint; both are available as rules.  Ties go to
+the lowest bone (child-joint) index: a candidate wins only if its squared
+distance is smaller by more than TIE_EPS * L^2, L the bounding-box diagonal of
+the points, so mirror-symmetric geometry resolves the same way in any rounding
+order.
 
 Eq. 6 pins vertices "along the skeleton"; §4 ("comparing to standard FEM")
 pins "around the handles and midpoints".  Reading: pin every vertex within
@@ -44,6 +45,11 @@ def nearest_handle(P, joints, parent, rule="bone", scale=None):
     bl = bones(parent)
     if rule == "bone" and bl:
         cands = [(_seg_dist2(P, joints[p], joints[j]), p) for p, j in bl]
+    elif rule == "midpoint" and bl:
+        cands = []
+        for p, j in bl:
+            d = P - 0.5 * (joints[p] + joints[j])
+            cands.append((np.einsum("ij,ij->i", d, d), p))
     else:
         cands = [(np.einsum("ij,ij->i", P - joints[j], P - joints[j]), j)
                  for j in range(len(joints))]

@@ -32,17 +32,24 @@ struct Rig {
     int rule = MFEM_CLUSTER_BONE;
     double tol = 0.0;
 
-    // §3.1: nearest bone segment (or nearest joint); a candidate wins only if
-    // closer by more than tol, so exact ties go to the lowest index.
+    // §3.1: nearest bone segment (or nearest joint, or nearest bone midpoint,
+    // §4); a candidate wins only if closer by more than tol, so exact ties go to
+    // the lowest index.
     int nearest(const double* P) const {
-        bool use_bones = rule == MFEM_CLUSTER_BONE && !bones.empty();
+        bool use_bones = (rule == MFEM_CLUSTER_BONE || rule == MFEM_CLUSTER_MIDPOINT) && !bones.empty();
         int ncand = use_bones ? (int)bones.size() : H;
         double best = 0.0;
         int hbest = -1;
         for (int c = 0; c < ncand; ++c) {
             double d;
             int h;
-            if (use_bones) {
+            if (use_bones && rule == MFEM_CLUSTER_MIDPOINT) {
+                const double* A = joints + 3 * bones[c].first;
+                const double* B = joints + 3 * bones[c].second;
+                double v[3] = {P[0] - 0.5 * (A[0] + B[0]), P[1] - 0.5 * (A[1] + B[1]), P[2] - 0.5 * (A[2] + B[2])};
+                d = dot3(v, v);
+                h = bones[c].first;
+            } else if (use_bones) {
                 d = seg_dist2(P, joints + 3 * bones[c].first, joints + 3 * bones[c].second);
                 h = bones[c].first;
             } else {
@@ -124,7 +131,8 @@ mfem_status plan_rig(const double* rest_verts, int32_t n, const int32_t* tets, i
             return MFEM_EINVAL;
         }
     }
-    if (hs->cluster_rule != MFEM_CLUSTER_BONE && hs->cluster_rule != MFEM_CLUSTER_JOINT) {
+    if (hs->cluster_rule != MFEM_CLUSTER_BONE && hs->cluster_rule != MFEM_CLUSTER_JOINT &&
+        hs->cluster_rule != MFEM_CLUSTER_MIDPOINT) {
         err = "unknown cluster_rule";
         return MFEM_EINVAL;
     }

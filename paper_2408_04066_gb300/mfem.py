@@ -19,7 +19,7 @@ STATUS_NAMES = ["OK", "EINVAL", "EDEGEN", "ENOMEM", "ENOTCONV", "ETIMEOUT", "EBU
 MODELS = {"arap": 0, "corot": 1, "snh": 2}
 PRECISIONS = {"fp64": 0, "mixed": 1}
 CONSTRAINTS = {"eliminate": 0, "penalty": 1}
-CLUSTER_RULES = {"bone": 0, "joint": 1}
+CLUSTER_RULES = {"bone": 0, "joint": 1, "midpoint": 2}
 INITS = {"rigid": 0, "rest": 1, "warm": 2, "corot": 3}
 MEM_HOST, MEM_DEVICE = 0, 1
 

@@ -84,3 +84,13 @@ def test_user_clusters_override(lib):
     tc, _, _ = mfem.plan(cfg["X"], cfg["T"], cfg["joints"], cfg["parent"], pin_radius=cfg["pin_radius"],
                          tet_cluster=user)
     assert np.array_equal(tc, user)
+
+
+@pytest.mark.parametrize("rule", ["joint", "midpoint"])
+def test_host_plan_other_cluster_rules_match_oracle(lib, rule):
+    cfg = figure_config(10000, seeds=[])
+    tc, pinned, ph = mfem.plan(cfg["X"], cfg["T"], cfg["joints"], cfg["parent"], rule, None, None,
+                               cfg["pin_radius"])
+    st = S.Setup.from_config(dict(cfg, cluster_rule=rule))
+    assert np.array_equal(tc, st.cluster)
+    assert np.array_equal(np.nonzero(pinned)[0], np.sort(st.pin_verts))

@@ -87,3 +87,14 @@ def test_polar_decomposition_properties(inverted, rng):
     Sp = np.einsum("kij,klj->kil", A, A) + np.eye(3)
     R2, P2 = diag.polar(Q @ Sp)
     assert np.allclose(R2, Q) and np.allclose(P2, Sp)
+
+
+def test_nearest_midpoint_by_brute_force(rng):
+    joints, parent = figure_rig()
+    P = rng.uniform([-0.7, -0.15, 0.0], [0.7, 0.15, 1.0], size=(300, 3))
+    h = rig.nearest_handle(P, joints, parent, "midpoint")
+    bl = rig.bones(parent)
+    mids = np.array([0.5 * (joints[p] + joints[j]) for p, j in bl])
+    d = ((P[:, None, :] - mids[None]) ** 2).sum(-1)
+    want = np.array([bl[k][0] for k in d.argmin(axis=1)])
+    assert np.array_equal(h, want)
