@@ -181,6 +181,17 @@ mfem_status mfem_set_stream(mfem_ctx* ctx, void* stream);
  * values must be finite, else MFEM_EINVAL. */
 mfem_status mfem_set_pose(mfem_ctx* ctx, const double* xf, int32_t H);
 
+/* External vertex forces (§4, "Collision response": a force applied to a few
+ * vertices): the energy gains -sum_v f_v . x_v, so the gradient gains -f and
+ * the Eq. 12 matrix is unchanged.  f is host [n_sets][n][3] FP64 in the caller's
+ * vertex order, copied during the call.  n_sets = 1: one field for every pose
+ * of mfem_solve / mfem_solve_batch; n_sets > 1: pose b of a batch takes field b
+ * (mfem_solve takes field 0) and a batch of more than n_sets poses is
+ * MFEM_EINVAL.  f = NULL or n_sets = 0 removes the forces.  Forces on pinned
+ * vertices have no effect under MFEM_ELIMINATE.  Non-finite values or
+ * n_sets < 0: MFEM_EINVAL.  Not available on contexts owned by a server. */
+mfem_status mfem_set_forces(mfem_ctx* ctx, const double* f, int32_t n_sets);
+
 /* Solve the pose set by mfem_set_pose; out_verts is host [n][3] in the caller's
  * vertex order.  stats may be NULL.  MFEM_ENOTCONV still writes x. */
 mfem_status mfem_solve(mfem_ctx* ctx, double* out_verts, mfem_stats* stats);

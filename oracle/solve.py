@@ -21,6 +21,9 @@ Newton iterations.  This driver runs Newton on E(x) for every model:
 
 Constraint C(x) (Eq. 6): "eliminate" fixes pinned vertices at x_p (k_s -> inf,
 the default); "penalty" adds k_s/2 |x_v - x_p|^2 per pin as written in Eq. 6.
+External forces (§4, "Collision response"): a per-vertex force field f adds
+-sum_v f_v . x_v to E, so the gradient gains -f and the Hessian is unchanged.
+
 Initial guess: "rest" (x = X, as in Algorithm 1), "rigid" (every vertex moved by
 the transform of the handle its position clusters to), "corot", or an explicit
 array.  "corot" (the default) starts SNH from one Newton step of the
@@ -114,9 +117,11 @@ def _pcg(K, b, tol, maxit):
 
 
 def solve(st, xf, model, constraint="eliminate", ks=0.0, newton_max=50, newton_tol=1e-12,
-          init="corot", linear="direct", cg_tol=1e-13, cg_max=100000):
-    """Solve one pose.  Returns (x (n,3), info dict)."""
+          init="corot", linear="direct", cg_tol=1e-13, cg_max=100000, f_ext=None):
+    """Solve one pose.  Returns (x (n,3), info dict).  f_ext: (n,3) external
+    vertex forces or None."""
     Q, t = rig.unpack_pose(xf)
+    fv = np.zeros((st.n, 3)) if f_ext is None else np.asarray(f_ext, dtype=np.float64).reshape(st.n, 3)
     R = Q[st.cluster]
     xp = rig.pin_targets(st.X, st.pin_verts, st.pin_handle, Q, t)
     x = initial_guess(st, Q, t, init)
@@ -143,14 +148,14 @@ def solve(st, xf, model, constraint="eliminate", ks=0.0, newton_max=50, newton_t
         return _pcg(Kff.tocsr(), -g, cg_tol, cg_max)
 
     def energy(y):
-        e = element.element_energy(y, *args).sum()
+        e = element.element_energy(y, *args).sum() - np.einsum("ij,ij->", fv, y)
         if constraint == "penalty":
             d = y[st.pin_verts] - xp
             e += 0.5 * ks * np.einsum("ij,ij->", d, d)
         return e
 
     def grad(y):
-        g = element.gradient(y, *args)
+        g = element.gradient(y, *args) - fv
         if constraint == "penalty":
             np.add.at(g, st.pin_verts, ks * (y[st.pin_verts] - xp))
         return g
@@ -161,7 +166,7 @@ def solve(st, xf, model, constraint="eliminate", ks=0.0, newton_max=50, newton_t
     g0 = float(np.linalg.norm(grad(x_ref).reshape(-1)[fidx]))
     n_pred = 0
     if isinstance(init, str) and init == "corot" and model == "snh" and newton_max > 0:
-        gc = element.gradient(x, st.T, st.G, st.vol, R, "corot", st.mu, st.lam)
+        gc = element.gradient(x, st.T, st.G, st.vol, R, "corot", st.mu, st.lam) - fv
         if constraint == "penalty":
             np.add.at(gc, st.pin_verts, ks * (x[st.pin_verts] - xp))
         df, cit = newton_direction(x, gc.reshape(-1)[fidx], "corot")

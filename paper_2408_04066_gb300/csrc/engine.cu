@@ -61,6 +61,8 @@ ElemArgs elem_args(const mfem_ctx* c) {
     a.model = c->model;
     a.constraint = c->opt.constraint;
     a.ks = c->opt.k_s;
+    a.fext = c->fext_dev;
+    a.fext_stride = c->fext_sets > 1 ? 3 * (int64_t)c->plan.n : 0;
     return a;
 }
 
@@ -780,7 +782,7 @@ void mfem_destroy(mfem_ctx* c) {
     MeshDev& M = c->mesh;
     void* ptrs[] = {M.tet, M.Dminv64, M.Dminv32, M.vol, M.cluster, M.mu, M.lam, M.X, M.vhandle, M.pin_handle_v,
                     M.vperm, M.tperm, M.slice_ptr, M.col, M.contrib_ptr, M.contrib, M.vinc_ptr, M.vinc,
-                    c->descs_dev, c->diag_dev};
+                    c->descs_dev, c->diag_dev, c->fext_dev};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     void* hp[] = {c->sc_host, c->active_host, c->alpha_host, c->alpha_ring, c->descs_host,
@@ -932,6 +934,36 @@ mfem_status mfem_set_pose(mfem_ctx* c, const double* xf, int32_t H) {
     return MFEM_OK;
 }
 
+mfem_status mfem_set_forces(mfem_ctx* c, const double* f, int32_t n_sets) {
+    if (!c) return ctx_fail(c, MFEM_EINVAL, "null context");
+    if (c->owned_by_server) return ctx_fail(c, MFEM_EINVAL, "context belongs to a server");
+    if (!f || n_sets == 0) {
+        CK(cudaStreamSynchronize(c->stream));
+        if (c->fext_dev) cudaFree(c->fext_dev);
+        c->fext_dev = nullptr;
+        c->fext_sets = 0;
+        return MFEM_OK;
+    }
+    if (n_sets < 0) return ctx_fail(c, MFEM_EINVAL, "n_sets must be >= 0");
+    const size_t n = c->plan.n, cnt = (size_t)n_sets * n * 3;
+    for (size_t i = 0; i < cnt; ++i)
+        if (!std::isfinite(f[i])) return ctx_fail(c, MFEM_EINVAL, "non-finite force");
+    std::vector<double> perm(cnt);   // caller vertex order -> internal order
+    for (size_t s = 0; s < (size_t)n_sets; ++s)
+        for (size_t o = 0; o < n; ++o)
+            for (int i = 0; i < 3; ++i) perm[(s * n + c->plan.vperm[o]) * 3 + i] = f[(s * n + o) * 3 + i];
+    CK(cudaStreamSynchronize(c->stream));
+    if (n_sets != c->fext_sets) {
+        if (c->fext_dev) cudaFree(c->fext_dev);
+        c->fext_dev = nullptr;
+        c->fext_sets = 0;
+        CK(cudaMalloc((void**)&c->fext_dev, cnt * sizeof(double)));
+    }
+    CK(cudaMemcpy(c->fext_dev, perm.data(), cnt * sizeof(double), cudaMemcpyHostToDevice));
+    c->fext_sets = n_sets;
+    return MFEM_OK;
+}
+
 static mfem_status finish_stats(mfem_ctx* c, const std::vector<ProbHost>& ph, int B, mfem_stats* stats) {
     mfem_status worst = MFEM_OK;
     for (int b = 0; b < B; ++b) {
@@ -975,6 +1007,8 @@ mfem_status mfem_solve_batch(mfem_ctx* c, const double* xf, int32_t B, double* o
     if (!c || !xf || !out) return ctx_fail(c, MFEM_EINVAL, "null argument");
     if (c->owned_by_server) return ctx_fail(c, MFEM_EINVAL, "context belongs to a server");
     if (B < 1) return ctx_fail(c, MFEM_EINVAL, "B must be >= 1");
+    if (c->fext_sets > 1 && B > c->fext_sets)
+        return ctx_fail(c, MFEM_EINVAL, "more poses than external force fields");
     if (memory != MFEM_MEM_HOST && memory != MFEM_MEM_DEVICE) return ctx_fail(c, MFEM_EINVAL, "bad memory kind");
     const int H = c->plan.H, n = c->plan.n;
     mfem_status st = ensure_slots(c, B);

@@ -72,6 +72,8 @@ struct mfem_ctx {
     int ring_pos = 0;
     void* descs_host = nullptr;
     unsigned* diag_dev = nullptr;
+    double* fext_dev = nullptr;   // external forces [fext_sets][n][3], internal order
+    int fext_sets = 0;
     unsigned* diag_host = nullptr;
     int tile_rows = 0;       // PCG rows per block
     int grid_blocks = 0;

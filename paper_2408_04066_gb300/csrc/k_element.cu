@@ -9,6 +9,8 @@
 // rig handle of the tet's cluster (§3.1).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace mfem {
@@ -329,7 +331,25 @@ __device__ __forceinline__ void blocks_quadratic(const double (&Gd)[4][3], const
         }
 }
 
+// Energy terms that live on vertex v at position y: -f_v . y for an external
+// force (§4, "Collision response") and k_s/2 |y - x_p|^2 for a pin under the
+// penalty form of Eq. 6.
+__device__ __forceinline__ double vertex_energy(const ElemArgs& A, int b, int v, const double (&y)[3]) {
+    double e = 0.0;
+    if (A.fext) {
+        const double* f = A.fext + (size_t)b * A.fext_stride + 3 * (size_t)v;
+        e -= f[0] * y[0] + f[1] * y[1] + f[2] * y[2];
+    }
+    if (A.constraint == 1 && A.mesh.pin_handle_v[v] >= 0) {
+        const double* xp = A.slot.xp + ((size_t)b * A.mesh.n + v) * 3;
+        const double d0 = y[0] - xp[0], d1 = y[1] - xp[1], d2 = y[2] - xp[2];
+        e += 0.5 * A.ks * (d0 * d0 + d1 * d1 + d2 * d2);
+    }
+    return e;
+}
+
 // ---------------------------------------------------------------------------
+// Thread k handles tet k (k < m) and the vertex terms of vertex k (k < n).
 template <typename KT, int MODEL>
 __global__ void __launch_bounds__(kTetTile) k_element(ElemArgs A) {
     const int b = blockIdx.y;
@@ -389,6 +409,11 @@ __global__ void __launch_bounds__(kTetTile) k_element(ElemArgs A) {
             blocks_quadratic<KT>(G, Q, w, mu, MODEL == 1 ? lam : 0.0, ke);
         }
     }
+    if (k < n) {
+        const double* xv = A.slot.x + ((size_t)b * n + k) * 3;
+        const double y[3] = {xv[0], xv[1], xv[2]};
+        en[0] += vertex_energy(A, b, k, y);
+    }
     double tot[1];
     double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
     if (tile_commit<1>(en, part, blockIdx.x, gridDim.x, &A.slot.sc[b].tk_e, 0, tot) && threadIdx.x == 0)
@@ -414,6 +439,15 @@ __global__ void __launch_bounds__(kTetTile) k_energy_trial(ElemArgs A) {
         load_Q(xf, M.cluster[k], Q);
         stretch(xa, G, Q, F, S);
         en[0] = M.vol[k] * psi_sigma<MODEL>(S, M.mu[k], M.lam[k], sig);
+    }
+    if (k < n) {
+        const double* xv = A.slot.x + ((size_t)b * n + k) * 3;
+        const T* dv = (const T*)A.slot.vec + (size_t)b * kVecStride * npad32(n) + kOffRec * npad32(n) +
+                      kRec * (size_t)k + kRecDX;
+        const double al = A.slot.alpha[b];
+        const double y[3] = {fma(al, (double)dv[0], xv[0]), fma(al, (double)dv[1], xv[1]),
+                             fma(al, (double)dv[2], xv[2])};
+        en[0] += vertex_energy(A, b, k, y);
     }
     double tot[1];
     double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
@@ -570,7 +604,7 @@ __global__ void k_diag(ElemArgs A, int b, unsigned* __restrict__ out3) {
 
 template <typename KT>
 void launch_element_t(const ElemArgs& a, int B, cudaStream_t s) {
-    dim3 grid((a.mesh.m + kTetTile - 1) / kTetTile, B);
+    dim3 grid((std::max(a.mesh.m, a.mesh.n) + kTetTile - 1) / kTetTile, B);
     switch (a.model) {
         case 0: k_element<KT, 0><<<grid, kTetTile, 0, s>>>(a); break;
         case 1: k_element<KT, 1><<<grid, kTetTile, 0, s>>>(a); break;
@@ -580,7 +614,7 @@ void launch_element_t(const ElemArgs& a, int B, cudaStream_t s) {
 
 template <typename T>
 void launch_trial_t(const ElemArgs& a, int B, cudaStream_t s) {
-    dim3 grid((a.mesh.m + kTetTile - 1) / kTetTile, B);
+    dim3 grid((std::max(a.mesh.m, a.mesh.n) + kTetTile - 1) / kTetTile, B);
     switch (a.model) {
         case 0: k_energy_trial<T, 0><<<grid, kTetTile, 0, s>>>(a); break;
         case 1: k_energy_trial<T, 1><<<grid, kTetTile, 0, s>>>(a); break;

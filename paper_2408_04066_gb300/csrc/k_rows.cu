@@ -8,6 +8,7 @@
 // atomics).  Pinned vertices (Eq. 6 C(x), §3.2 targets) are eliminated: their
 // rows and columns become identity/zero and their gradient entries zero, so the
 // Newton increment keeps them at x_p; the penalty form adds k_s I instead.
+// External vertex forces (§4, "Collision response") enter the gradient as -f.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -107,6 +108,12 @@ __global__ void __launch_bounds__(kRowTile) k_assemble_grad(ElemArgs A) {
             g0 += f[0];
             g1 += f[1];
             g2 += f[2];
+        }
+        if (A.fext) {  // external forces: E gains -f.x
+            const double* fv = A.fext + (size_t)b * A.fext_stride + 3 * (size_t)row;
+            g0 -= fv[0];
+            g1 -= fv[1];
+            g2 -= fv[2];
         }
         if (pin_r) {
             if (A.constraint == 0) {

@@ -59,6 +59,8 @@ struct ElemArgs {
     int model;        // mfem_model
     int constraint;   // 0 eliminate, 1 penalty
     double ks;
+    const double* fext = nullptr;  // external vertex forces [sets][n][3] (internal order) or null
+    int64_t fext_stride = 0;       // doubles between problems' force fields (0: one shared field)
 };
 
 // a0: pose -> pin targets and initial guess (init: 0 rigid, 1 rest, 2 warm)

@@ -76,6 +76,7 @@ _SIGS = [
                                 C.POINTER(Options), C.POINTER(C.c_void_p)]),
     ("mfem_set_stream", C.c_int32, [C.c_void_p, C.c_void_p]),
     ("mfem_set_pose", C.c_int32, [C.c_void_p, _dp, C.c_int32]),
+    ("mfem_set_forces", C.c_int32, [C.c_void_p, _dp, C.c_int32]),
     ("mfem_solve", C.c_int32, [C.c_void_p, _dp, C.POINTER(Stats)]),
     ("mfem_solve_batch", C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
                                      C.POINTER(Stats)]),
@@ -267,6 +268,17 @@ class Context:
     def set_pose(self, xf):
         xf = _f64(xf, (-1, 12))
         _check(self._lib.mfem_set_pose(self._ctx, _p(xf), len(xf)), self._ctx)
+
+    def set_forces(self, f):
+        """External vertex forces: (n,3) for every pose, (S,n,3) for pose b of a
+        batch taking field b, or None to remove them."""
+        if f is None:
+            _check(self._lib.mfem_set_forces(self._ctx, None, 0), self._ctx)
+            return
+        f = _f64(f)
+        sets = 1 if f.ndim == 2 else f.shape[0]
+        f = _f64(f, (sets, self.n, 3))
+        _check(self._lib.mfem_set_forces(self._ctx, _p(f), sets), self._ctx)
 
     def solve(self, out=None):
         out = np.empty((self.n, 3)) if out is None else out

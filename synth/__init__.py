@@ -9,11 +9,11 @@ CUDA library can be fed from it without sharing any of the method's code.
 from .meshes import (kuhn_voxel_mesh, bar_mesh, figure_rig, figure_mesh,
                      figure_mesh_for_tets)
 from .poses import rodrigues, figure_pose, bar_twist_pose, identity_pose, rigid_pose
-from .configs import (bar_twist_config, figure_config, lame_from_young,
-                      SNH_E, SNH_NU)
+from .configs import (bar_twist_config, bar_pull_config, face_traction_loads, figure_config,
+                      lame_from_young, SNH_E, SNH_NU)
 
 __all__ = [
     "kuhn_voxel_mesh", "bar_mesh", "figure_rig", "figure_mesh", "figure_mesh_for_tets",
     "rodrigues", "figure_pose", "bar_twist_pose", "identity_pose", "rigid_pose",
-    "bar_twist_config", "figure_config", "lame_from_young", "SNH_E", "SNH_NU",
+    "bar_twist_config", "bar_pull_config", "face_traction_loads", "figure_config", "lame_from_young", "SNH_E", "SNH_NU",
 ]

@@ -62,3 +62,42 @@ def figure_config(target_tets=200_000, model="snh", seeds=range(16), scale=1.0,
         cluster_rule="bone", pin_verts=None, pin_handle=None, pin_radius=pin_radius_cells * h,
         model=model, mu=mu, lam=lam, xfs=xfs, h=h,
     )
+
+
+def face_traction_loads(X, T, on_face, traction):
+    """Nodal loads of a uniform traction (force per area, 3-vector) on the
+    boundary triangles whose three vertices satisfy ``on_face``: each triangle
+    gives a third of traction x area to each of its vertices (the consistent
+    load of linear shape functions)."""
+    X = np.asarray(X, dtype=np.float64)
+    f = np.zeros_like(X)
+    tri = {}
+    for tet in np.asarray(T):
+        for skip in range(4):
+            face = tuple(sorted(int(v) for i, v in enumerate(tet) if i != skip))
+            tri[face] = tri.get(face, 0) + 1
+    for face, count in tri.items():
+        if count != 1 or not all(on_face[v] for v in face):
+            continue
+        a, b, c = (X[v] for v in face)
+        area = 0.5 * np.linalg.norm(np.cross(b - a, c - a))
+        for v in face:
+            f[v] += np.asarray(traction, dtype=np.float64) * area / 3.0
+    return f
+
+
+def bar_pull_config(nx=3, ny=3, nz=8, traction=0.05, model="arap", mu=1.0, lam=0.0):
+    """A bar with its z=0 face pinned to one identity handle and a uniform
+    traction along +z on its z=nz face, applied as consistent nodal loads
+    ``f_ext``.  Every tet takes the single handle."""
+    X, T = bar_mesh(nx, ny, nz)
+    joints = np.array([[nx / 2, ny / 2, 0.0]])
+    parent = np.array([-1], dtype=np.int32)
+    lo = np.where(X[:, 2] == 0.0)[0].astype(np.int32)
+    f_ext = face_traction_loads(X, T, X[:, 2] == float(nz), [0.0, 0.0, traction])
+    return dict(
+        name=f"barpull{nx}x{ny}x{nz}", X=X, T=T, joints=joints, parent=parent,
+        cluster_rule="joint", pin_verts=lo, pin_handle=np.zeros(len(lo), dtype=np.int32), pin_radius=0.0,
+        model=model, mu=mu, lam=lam, xfs=np.array([[1.0, 0, 0, 0, 0, 1, 0, 0, 0, 0, 1, 0]])[None],
+        f_ext=f_ext, traction=traction,
+    )
