@@ -160,20 +160,23 @@ def hbm_peak():
 
 
 def kernel_source_hash():
+    """Hash of the PCG kernels' sources (k_pcg.cu and the device header)."""
     import hashlib
-    src = os.path.join(ROOT, "paper_2408_04066_gb300", "csrc", "k_rows.cu")
-    return hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("k_pcg.cu", "dev.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2408_04066_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def pcg_traffic_record():
     """DRAM bytes per pose-iteration of the PCG kernels from the committed ncu
     summary (profiles/pcg_traffic.json), if it was taken on the current kernel
-    source (hash of k_rows.cu); else None."""
+    source (hash of k_pcg.cu and dev.cuh); else None."""
     rec = os.path.join(ROOT, "profiles", "pcg_traffic.json")
     try:
         with open(rec) as f:
             r = json.load(f)
-        return r if r.get("k_rows_sha256_16") == kernel_source_hash() else None
+        return r if r.get("pcg_src_sha256_16") == kernel_source_hash() else None
     except (OSError, ValueError):
         return None
 

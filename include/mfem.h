@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MFEM_ABI_VERSION 1
+#define MFEM_ABI_VERSION 2
 
 typedef enum {
     MFEM_OK = 0,
@@ -57,6 +57,7 @@ typedef enum { MFEM_ELIMINATE = 0, MFEM_PENALTY = 1 } mfem_constraint;
 typedef enum { MFEM_CLUSTER_BONE = 0, MFEM_CLUSTER_JOINT = 1, MFEM_CLUSTER_MIDPOINT = 2 } mfem_cluster_rule;
 typedef enum { MFEM_INIT_RIGID = 0, MFEM_INIT_REST = 1, MFEM_INIT_WARM = 2, MFEM_INIT_COROT = 3 } mfem_init;
 typedef enum { MFEM_MEM_HOST = 0, MFEM_MEM_DEVICE = 1 } mfem_memory;
+typedef enum { MFEM_ROT_RIG = 0, MFEM_ROT_POLAR = 1 } mfem_rotation;
 
 /* Material (§4 "A solver friendly to variant energies"; §4 "Allowing
  * heterogeneous material").  Densities, with S the element stretch:
@@ -117,6 +118,16 @@ typedef struct {
     int32_t tile_rows;   /* PCG rows per block: 64, 128 or 256; 0 = autotune (timed
                             on the first assembled system) */
     int32_t diagnostics; /* 1: fill inverted/skew/angle fields of mfem_stats (0) */
+    int32_t rotation;    /* MFEM_ROT_RIG (default): R_k is the rotation of the tet's
+                            cluster handle (§3, Eq. 3; §3.1) -- the paper's method.
+                            MFEM_ROT_POLAR: R_k is the rotation factor of F_k(x),
+                            re-evaluated at every Newton step and line-search
+                            trial (det R = +1; for det F < 0 the least stretch is
+                            negative), so E is the co-rotational FEM energy of the
+                            standard FEM model §4 compares against, with the rig
+                            coupled through the pins only.  Newton steps use the
+                            Hessian at fixed R and are line-searched on E for every
+                            model */
 } mfem_options;
 
 /* Per-pose result statistics. */

@@ -21,6 +21,13 @@ Newton iterations.  This driver runs Newton on E(x) for every model:
 
 Constraint C(x) (Eq. 6): "eliminate" fixes pinned vertices at x_p (k_s -> inf,
 the default); "penalty" adds k_s/2 |x_v - x_p|^2 per pin as written in Eq. 6.
+Rotations: "rig" (the method: R_k is the rotation of the tet's cluster handle,
+§3 Eq. 3, §3.1) or "polar" (R_k = the rotation factor of F_k(x), det +1, as a
+co-rotational FEM element takes it: E is then the energy of the standard FEM
+model §4 compares against, coupled to the rig through the pins only).  In
+"polar" mode R is re-evaluated at every iterate and line-search trial, the
+Newton step uses the Hessian at fixed R, and every model is line-searched.
+
 External forces (§4, "Collision response"): a per-vertex force field f adds
 -sum_v f_v . x_v to E, so the gradient gains -f and the Hessian is unchanged.
 
@@ -37,7 +44,7 @@ import numpy as np
 import scipy.sparse as sp
 import scipy.sparse.linalg as spla
 
-from . import element, rig
+from . import diag, element, rig
 
 LS_C = 1.0e-4
 LS_MAX = 20
@@ -117,12 +124,20 @@ def _pcg(K, b, tol, maxit):
 
 
 def solve(st, xf, model, constraint="eliminate", ks=0.0, newton_max=50, newton_tol=1e-12,
-          init="corot", linear="direct", cg_tol=1e-13, cg_max=100000, f_ext=None):
+          init="corot", linear="direct", cg_tol=1e-13, cg_max=100000, f_ext=None, rotation="rig"):
     """Solve one pose.  Returns (x (n,3), info dict).  f_ext: (n,3) external
-    vertex forces or None."""
+    vertex forces or None; rotation: "rig" or "polar"."""
+    if rotation not in ("rig", "polar"):
+        raise ValueError(rotation)
     Q, t = rig.unpack_pose(xf)
     fv = np.zeros((st.n, 3)) if f_ext is None else np.asarray(f_ext, dtype=np.float64).reshape(st.n, 3)
-    R = Q[st.cluster]
+    R_rig = Q[st.cluster]
+
+    def rot(y):
+        if rotation == "rig":
+            return R_rig
+        return diag.polar(element.deformation_gradient(y, st.T, st.G))[0]
+
     xp = rig.pin_targets(st.X, st.pin_verts, st.pin_handle, Q, t)
     x = initial_guess(st, Q, t, init)
     x[st.pin_verts] = xp
@@ -133,10 +148,9 @@ def solve(st, xf, model, constraint="eliminate", ks=0.0, newton_max=50, newton_t
     elif constraint != "penalty":
         raise ValueError(constraint)
     fidx = np.nonzero(free.reshape(-1))[0]
-    args = (st.T, st.G, st.vol, R, model, st.mu, st.lam)
 
     def newton_direction(y, g, mdl):
-        a = (st.T, st.G, st.vol, R, mdl, st.mu, st.lam)
+        a = (st.T, st.G, st.vol, rot(y), mdl, st.mu, st.lam)
         Ke = element.element_hessians(y, *a, project=True)
         K = element.assemble(Ke, st.T, n)
         if constraint == "penalty":
@@ -148,14 +162,15 @@ def solve(st, xf, model, constraint="eliminate", ks=0.0, newton_max=50, newton_t
         return _pcg(Kff.tocsr(), -g, cg_tol, cg_max)
 
     def energy(y):
-        e = element.element_energy(y, *args).sum() - np.einsum("ij,ij->", fv, y)
+        e = element.element_energy(y, st.T, st.G, st.vol, rot(y), model, st.mu, st.lam).sum() \
+            - np.einsum("ij,ij->", fv, y)
         if constraint == "penalty":
             d = y[st.pin_verts] - xp
             e += 0.5 * ks * np.einsum("ij,ij->", d, d)
         return e
 
     def grad(y):
-        g = element.gradient(y, *args) - fv
+        g = element.gradient(y, st.T, st.G, st.vol, rot(y), model, st.mu, st.lam) - fv
         if constraint == "penalty":
             np.add.at(g, st.pin_verts, ks * (y[st.pin_verts] - xp))
         return g
@@ -166,7 +181,7 @@ def solve(st, xf, model, constraint="eliminate", ks=0.0, newton_max=50, newton_t
     g0 = float(np.linalg.norm(grad(x_ref).reshape(-1)[fidx]))
     n_pred = 0
     if isinstance(init, str) and init == "corot" and model == "snh" and newton_max > 0:
-        gc = element.gradient(x, st.T, st.G, st.vol, R, "corot", st.mu, st.lam) - fv
+        gc = element.gradient(x, st.T, st.G, st.vol, rot(x), "corot", st.mu, st.lam) - fv
         if constraint == "penalty":
             np.add.at(gc, st.pin_verts, ks * (x[st.pin_verts] - xp))
         df, cit = newton_direction(x, gc.reshape(-1)[fidx], "corot")
@@ -191,7 +206,7 @@ def solve(st, xf, model, constraint="eliminate", ks=0.0, newton_max=50, newton_t
         d[fidx] = df
         d = d.reshape(n, 3)
         alpha = 1.0
-        if model == "snh":
+        if model == "snh" or rotation == "polar":
             e0 = energy(x)
             slope = float(g @ df)
             if -slope > LS_NOISE * abs(e0):
@@ -209,12 +224,12 @@ def solve(st, xf, model, constraint="eliminate", ks=0.0, newton_max=50, newton_t
     return x, info
 
 
-def element_outputs(st, xf, model, x):
+def element_outputs(st, xf, model, x, rotation="rig"):
     """s_k (Mandel 6-vector) and lambda_k (3x3, row-major 9) at x (Eq. 10-11)."""
     from .mandel import to_mandel
     Q, _ = rig.unpack_pose(xf)
-    R = Q[st.cluster]
     F = element.deformation_gradient(x, st.T, st.G)
+    R = Q[st.cluster] if rotation == "rig" else diag.polar(F)[0]
     s = to_mandel(element.stretch(R, F))
     lam = element.multiplier(x, st.T, st.G, R, model, st.mu, st.lam)
     return s, lam.reshape(-1, 9)

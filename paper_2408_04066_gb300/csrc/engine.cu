@@ -63,8 +63,13 @@ ElemArgs elem_args(const mfem_ctx* c) {
     a.ks = c->opt.k_s;
     a.fext = c->fext_dev;
     a.fext_stride = c->fext_sets > 1 ? 3 * (int64_t)c->plan.n : 0;
+    a.rot_polar = c->opt.rotation == MFEM_ROT_POLAR ? 1 : 0;
     return a;
 }
+
+// Newton steps are line-searched on E when E is not quadratic in x: SNH, and
+// every model when the rotations follow F (polar-rotation mode).
+bool line_search(const mfem_ctx* c) { return c->model == MFEM_SNH || c->opt.rotation == MFEM_ROT_POLAR; }
 
 namespace {
 
@@ -600,13 +605,14 @@ mfem_status advance(std::vector<Group>& gs) {
         }
     }
     if (!any_fin) return MFEM_OK;
-    // slope g.dx for the line search (SNH Newton steps; the predictor is quadratic)
+    // slope g.dx for the line search (SNH, or any model whose rotations follow
+    // F; the predictor step is taken whole)
     bool any_ls = false;
     std::vector<std::vector<int>> ls(gs.size());
     for (size_t gi = 0; gi < gs.size(); ++gi) {
         Group& g = gs[gi];
         ls[gi].assign(g.B, 0);
-        if (g.ctx->model != MFEM_SNH) continue;
+        if (!line_search(g.ctx)) continue;
         for (int b = 0; b < g.B; ++b) ls[gi][b] = fin[gi][b] && !g.ph[b].pred;
         if (!any_of(ls[gi])) continue;
         any_ls = true;
@@ -628,7 +634,7 @@ mfem_status advance(std::vector<Group>& gs) {
     for (size_t gi = 0; gi < gs.size(); ++gi) {
         Group& g = gs[gi];
         mfem_ctx* gc = g.ctx;
-        if (gc->model != MFEM_SNH || !any_of(ls[gi])) continue;
+        if (!line_search(gc) || !any_of(ls[gi])) continue;
         std::vector<int> testing(g.B, 0);
         std::vector<double> e0(g.B, 0.0), slope(g.B, 0.0);
         bool any = false;
@@ -742,6 +748,7 @@ void mfem_default_options(mfem_options* o) {
     o->max_batch = 16;
     o->tile_rows = 0;
     o->diagnostics = 0;
+    o->rotation = MFEM_ROT_RIG;
 }
 
 const char* mfem_status_string(mfem_status s) {
@@ -816,6 +823,7 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
     if (!(o.newton_tol >= 0.0) || !(o.cg_tol >= 0.0) || o.newton_max < 0 || o.cg_max < 1)
         return fail(MFEM_EINVAL, "bad tolerances or iteration caps");
     if (o.init < MFEM_INIT_RIGID || o.init > MFEM_INIT_COROT) return fail(MFEM_EINVAL, "bad init");
+    if (o.rotation != MFEM_ROT_RIG && o.rotation != MFEM_ROT_POLAR) return fail(MFEM_EINVAL, "bad rotation");
     if (o.tile_rows != 0 && !pcg_tile_supported(o.tile_rows))
         return fail(MFEM_EINVAL, "tile_rows must be 0, 64, 128 or 256");
     if (!mat) return fail(MFEM_EINVAL, "null material");

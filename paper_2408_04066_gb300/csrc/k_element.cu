@@ -331,6 +331,142 @@ __device__ __forceinline__ void blocks_quadratic(const double (&Gd)[4][3], const
         }
 }
 
+// Orthogonal polar factor by Higham's scaled Newton iteration
+// X <- (gamma X + X^{-T} / gamma) / 2 (N. J. Higham, "Computing the polar
+// decomposition -- with applications", SIAM J. Sci. Stat. Comput. 1986).
+template <typename RT>
+__device__ bool polar_newton(const double (&F)[3][3], RT (&R)[3][3]) {
+    RT X[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) X[i][j] = (RT)F[i][j];
+    const RT tol = sizeof(RT) == 8 ? (RT)1e-13 : (RT)1e-6;
+    for (int it = 0; it < 30; ++it) {
+        RT c00 = X[1][1] * X[2][2] - X[1][2] * X[2][1], c01 = X[1][2] * X[2][0] - X[1][0] * X[2][2],
+           c02 = X[1][0] * X[2][1] - X[1][1] * X[2][0];
+        RT c10 = X[0][2] * X[2][1] - X[0][1] * X[2][2], c11 = X[0][0] * X[2][2] - X[0][2] * X[2][0],
+           c12 = X[0][1] * X[2][0] - X[0][0] * X[2][1];
+        RT c20 = X[0][1] * X[1][2] - X[0][2] * X[1][1], c21 = X[0][2] * X[1][0] - X[0][0] * X[1][2],
+           c22 = X[0][0] * X[1][1] - X[0][1] * X[1][0];
+        RT det = X[0][0] * c00 + X[0][1] * c01 + X[0][2] * c02;
+        if (det == (RT)0) return false;
+        // X^{-T} = cof(X) / det
+        RT IT[3][3] = {{c00 / det, c01 / det, c02 / det}, {c10 / det, c11 / det, c12 / det},
+                       {c20 / det, c21 / det, c22 / det}};
+        RT nx = 0, ni = 0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                nx += X[i][j] * X[i][j];
+                ni += IT[i][j] * IT[i][j];
+            }
+        RT gam = sqrt(sqrt(ni / nx));
+        RT diff = 0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                RT y = (RT)0.5 * (gam * X[i][j] + IT[i][j] / gam);
+                diff += (y - X[i][j]) * (y - X[i][j]);
+                X[i][j] = y;
+            }
+        if (diff <= tol * tol * (RT)3) break;
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) R[i][j] = X[i][j];
+    return true;
+}
+
+// Eigenvectors of a symmetric 3x3 H by cyclic Jacobi rotations (Golub & Van
+// Loan, "Matrix Computations", symmetric Jacobi method): on return H is
+// (nearly) diagonal and the columns of V are the eigenvectors.
+__device__ void jacobi3(double (&H)[3][3], double (&V)[3][3]) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) V[i][j] = i == j ? 1.0 : 0.0;
+    for (int sweep = 0; sweep < 12; ++sweep) {
+        const double off = H[0][1] * H[0][1] + H[0][2] * H[0][2] + H[1][2] * H[1][2];
+        const double dia = H[0][0] * H[0][0] + H[1][1] * H[1][1] + H[2][2] * H[2][2];
+        if (off <= 1e-32 * dia) break;
+        for (int p = 0; p < 2; ++p)
+            for (int q = p + 1; q < 3; ++q) {
+                if (H[p][q] == 0.0) continue;
+                const double th = (H[q][q] - H[p][p]) / (2.0 * H[p][q]);
+                const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < 3; ++k) {   // H <- H J (columns p, q)
+                    const double hp = H[k][p], hq = H[k][q];
+                    H[k][p] = c * hp - s * hq;
+                    H[k][q] = s * hp + c * hq;
+                }
+                for (int k = 0; k < 3; ++k) {   // H <- J^T H (rows p, q)
+                    const double hp = H[p][k], hq = H[q][k];
+                    H[p][k] = c * hp - s * hq;
+                    H[q][k] = s * hp + c * hq;
+                }
+                for (int k = 0; k < 3; ++k) {
+                    const double vp = V[k][p], vq = V[k][q];
+                    V[k][p] = c * vp - s * vq;
+                    V[k][q] = s * vp + c * vq;
+                }
+            }
+    }
+}
+
+// Rotation factor R (det +1) of F = R P, P symmetric.  For det F < 0 the
+// eigenvalue of P of least magnitude is the negative one: the orthogonal polar
+// factor U (det -1) is reflected along the eigenvector of U^T F with the
+// smallest eigenvalue.  Returns false if F is singular.
+__device__ bool polar_rotation(const double (&F)[3][3], double (&R)[3][3]) {
+    double U[3][3];
+    if (!polar_newton<double>(F, U)) return false;
+    const double detU = U[0][0] * (U[1][1] * U[2][2] - U[1][2] * U[2][1]) -
+                        U[0][1] * (U[1][0] * U[2][2] - U[1][2] * U[2][0]) +
+                        U[0][2] * (U[1][0] * U[2][1] - U[1][1] * U[2][0]);
+    if (detU > 0.0) {
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) R[i][j] = U[i][j];
+        return true;
+    }
+    double H[3][3], V[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double hij = 0.0, hji = 0.0;
+            for (int k = 0; k < 3; ++k) {
+                hij += U[k][i] * F[k][j];
+                hji += U[k][j] * F[k][i];
+            }
+            H[i][j] = 0.5 * (hij + hji);
+        }
+    jacobi3(H, V);
+    int im = 0;
+    for (int i = 1; i < 3; ++i)
+        if (H[i][i] < H[im][im]) im = i;
+    const double v[3] = {V[0][im], V[1][im], V[2][im]};
+    for (int i = 0; i < 3; ++i) {
+        const double uv = U[i][0] * v[0] + U[i][1] * v[1] + U[i][2] * v[2];
+        for (int j = 0; j < 3; ++j) R[i][j] = U[i][j] - 2.0 * uv * v[j];
+    }
+    return true;
+}
+
+// Rotation of tet k: its rig cluster's handle rotation (§3.1), or, in the
+// polar-rotation mode, the rotation factor of its own F (the rotation a
+// co-rotational FEM element takes; the cluster rotation if F is singular).
+__device__ __forceinline__ void tet_rotation(const ElemArgs& A, const double* __restrict__ xf, int k,
+                                             const double (&xa)[4][3], const double (&G)[4][3],
+                                             double (&Q)[3][3]) {
+    if (A.rot_polar) {
+        double F[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                double f = 0.0;
+#pragma unroll
+                for (int a = 1; a < 4; ++a) f = fma(xa[a][i] - xa[0][i], G[a][j], f);
+                F[i][j] = f;
+            }
+        if (polar_rotation(F, Q)) return;
+    }
+    load_Q(xf, A.mesh.cluster[k], Q);
+}
+
 // Energy terms that live on vertex v at position y: -f_v . y for an external
 // force (§4, "Collision response") and k_s/2 |y - x_p|^2 for a pin under the
 // penalty form of Eq. 6.
@@ -365,7 +501,7 @@ __global__ void __launch_bounds__(kTetTile) k_element(ElemArgs A) {
         const int4 tv = M.tet[k];
         gather_x<float>(x, nullptr, 0.0, tv, xa);
         load_G(M.Dminv64, m, k, G);
-        load_Q(xf, M.cluster[k], Q);
+        tet_rotation(A, xf, k, xa, G, Q);
         stretch(xa, G, Q, F, S);
         const double mu = M.mu[k], lam = M.lam[k], w = M.vol[k];
         en[0] = w * psi_sigma<MODEL>(S, mu, lam, sig);
@@ -436,7 +572,7 @@ __global__ void __launch_bounds__(kTetTile) k_energy_trial(ElemArgs A) {
         double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6], sig[6];
         gather_x<T>(x, dx, A.slot.alpha[b], M.tet[k], xa, kRec);
         load_G(M.Dminv64, m, k, G);
-        load_Q(xf, M.cluster[k], Q);
+        tet_rotation(A, xf, k, xa, G, Q);
         stretch(xa, G, Q, F, S);
         en[0] = M.vol[k] * psi_sigma<MODEL>(S, M.mu[k], M.lam[k], sig);
     }
@@ -496,7 +632,7 @@ __global__ void k_elem_out(ElemArgs A, int b, double* __restrict__ s_out, double
     double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6], sig[6];
     gather_x<float>(x, nullptr, 0.0, M.tet[k], xa);
     load_G(M.Dminv64, M.m, k, G);
-    load_Q(xf, M.cluster[k], Q);
+    tet_rotation(A, xf, k, xa, G, Q);
     stretch(xa, G, Q, F, S);
     psi_sigma<MODEL>(S, M.mu[k], M.lam[k], sig);
     if (s_out)
@@ -507,48 +643,6 @@ __global__ void k_elem_out(ElemArgs A, int b, double* __restrict__ s_out, double
             for (int j = 0; j < 3; ++j)
                 lam_out[9 * (size_t)o + 3 * i + j] = Q[i][0] * sm[0][j] + Q[i][1] * sm[1][j] + Q[i][2] * sm[2][j];
     }
-}
-
-// Orthogonal polar factor by Higham's scaled Newton iteration
-// X <- (gamma X + X^{-T} / gamma) / 2 (N. J. Higham, "Computing the polar
-// decomposition -- with applications", SIAM J. Sci. Stat. Comput. 1986).
-template <typename RT>
-__device__ bool polar_newton(const double (&F)[3][3], RT (&R)[3][3]) {
-    RT X[3][3];
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) X[i][j] = (RT)F[i][j];
-    const RT tol = sizeof(RT) == 8 ? (RT)1e-13 : (RT)1e-6;
-    for (int it = 0; it < 30; ++it) {
-        RT c00 = X[1][1] * X[2][2] - X[1][2] * X[2][1], c01 = X[1][2] * X[2][0] - X[1][0] * X[2][2],
-           c02 = X[1][0] * X[2][1] - X[1][1] * X[2][0];
-        RT c10 = X[0][2] * X[2][1] - X[0][1] * X[2][2], c11 = X[0][0] * X[2][2] - X[0][2] * X[2][0],
-           c12 = X[0][1] * X[2][0] - X[0][0] * X[2][1];
-        RT c20 = X[0][1] * X[1][2] - X[0][2] * X[1][1], c21 = X[0][2] * X[1][0] - X[0][0] * X[1][2],
-           c22 = X[0][0] * X[1][1] - X[0][1] * X[1][0];
-        RT det = X[0][0] * c00 + X[0][1] * c01 + X[0][2] * c02;
-        if (det == (RT)0) return false;
-        // X^{-T} = cof(X) / det
-        RT IT[3][3] = {{c00 / det, c01 / det, c02 / det}, {c10 / det, c11 / det, c12 / det},
-                       {c20 / det, c21 / det, c22 / det}};
-        RT nx = 0, ni = 0;
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) {
-                nx += X[i][j] * X[i][j];
-                ni += IT[i][j] * IT[i][j];
-            }
-        RT gam = sqrt(sqrt(ni / nx));
-        RT diff = 0;
-        for (int i = 0; i < 3; ++i)
-            for (int j = 0; j < 3; ++j) {
-                RT y = (RT)0.5 * (gam * X[i][j] + IT[i][j] / gam);
-                diff += (y - X[i][j]) * (y - X[i][j]);
-                X[i][j] = y;
-            }
-        if (diff <= tol * tol * (RT)3) break;
-    }
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j) R[i][j] = X[i][j];
-    return true;
 }
 
 // Diagnostics: inverted tets, max |skew(Q^T F)|/|F|, max angle(Q, polar(F)).
@@ -562,7 +656,7 @@ __global__ void k_diag(ElemArgs A, int b, unsigned* __restrict__ out3) {
     double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6];
     gather_x<float>(x, nullptr, 0.0, M.tet[k], xa);
     load_G(M.Dminv64, M.m, k, G);
-    load_Q(xf, M.cluster[k], Q);
+    tet_rotation(A, xf, k, xa, G, Q);
     stretch(xa, G, Q, F, S);
     const double detF = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
                         F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +

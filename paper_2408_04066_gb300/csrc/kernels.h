@@ -61,7 +61,17 @@ struct ElemArgs {
     double ks;
     const double* fext = nullptr;  // external vertex forces [sets][n][3] (internal order) or null
     int64_t fext_stride = 0;       // doubles between problems' force fields (0: one shared field)
+    int rot_polar = 0;             // 1: R_k = rotation factor of F_k (co-rotational FEM), else the rig's
 };
+
+#ifdef __CUDACC__
+// Vector `off` of problem b in the interleaved PCG vector block of a slot.
+template <typename T>
+__device__ __forceinline__ T* vecp(const SlotDev& S, int b, int off, int n) {
+    const size_t np = npad32(n);
+    return (T*)S.vec + (size_t)b * kVecStride * np + (size_t)off * np;
+}
+#endif
 
 // a0: pose -> pin targets and initial guess (init: 0 rigid, 1 rest, 2 warm)
 void launch_pose_init(const ElemArgs& a, int B, int init, cudaStream_t s);

@@ -21,7 +21,9 @@ PRECISIONS = {"fp64": 0, "mixed": 1}
 CONSTRAINTS = {"eliminate": 0, "penalty": 1}
 CLUSTER_RULES = {"bone": 0, "joint": 1, "midpoint": 2}
 INITS = {"rigid": 0, "rest": 1, "warm": 2, "corot": 3}
+ROTATIONS = {"rig": 0, "polar": 1}
 MEM_HOST, MEM_DEVICE = 0, 1
+ABI_VERSION = 2   # MFEM_ABI_VERSION of the header these structures follow
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -41,7 +43,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("constraint", C.c_int32), ("k_s", C.c_double),
                 ("newton_tol", C.c_double), ("cg_tol", C.c_double), ("newton_max", C.c_int32),
                 ("cg_max", C.c_int32), ("init", C.c_int32), ("max_batch", C.c_int32),
-                ("tile_rows", C.c_int32), ("diagnostics", C.c_int32)]
+                ("tile_rows", C.c_int32), ("diagnostics", C.c_int32), ("rotation", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -118,6 +120,9 @@ def load(path=None):
         f = getattr(lib, name)
         f.restype = res
         f.argtypes = args
+    if lib.mfem_abi_version() != ABI_VERSION:
+        raise RuntimeError(f"{path} has ABI version {lib.mfem_abi_version()}, the binding expects "
+                           f"{ABI_VERSION}: rebuild it")
     _lib = lib
     return lib
 
@@ -158,6 +163,8 @@ def default_options(**over):
             v = CONSTRAINTS[v] if isinstance(v, str) else v
         elif k == "init":
             v = INITS[v] if isinstance(v, str) else v
+        elif k == "rotation":
+            v = ROTATIONS[v] if isinstance(v, str) else v
         setattr(o, k, v)
     return o
 
