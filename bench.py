@@ -43,6 +43,12 @@ def parse():
     p.add_argument("--fp64-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--cpu-newton-steps", type=int, default=2)
+    p.add_argument("--workload", default="figure200k", choices=["figure200k", "batched", "serve", "large"],
+                   help="figure200k: the headline batch; batched: 64+64 warm-started animation streams of "
+                        "a 200k and a 50k figure in shared launches; serve: Poisson arrivals over resident "
+                        "10k/50k/200k/800k meshes; large: one 2M-tet 40-handle character")
+    p.add_argument("--rate", type=float, default=500.0, help="serve: mean Poisson arrival rate (requests/s)")
+    p.add_argument("--duration", type=float, default=4.0, help="serve: seconds of arrivals")
     p.add_argument("--ncu-case", action="store_true",
                    help="one small solve for profiler captures: 8 poses, 3 Newton steps, 256-row tiles")
     return p.parse_args()
@@ -416,10 +422,318 @@ def run_mfem(args, dist):
             "plain_fp64": fp64,
             "newton_iters_mean": statistics.mean(newton), "pcg_iters_mean": statistics.mean(pcg_it),
             "all_converged": conv,
+            "element_updates_per_s": dist.sum(sum(p["element_updates"] for p in prof)) / (total_ms_max / 1e3),
             "roofline": roof, "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xfs_h.numel() * 8),
                     "d2h_bytes_per_step": int(out_h.numel() * 8)},
             "gpu_launches": launches, "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    ctx.close()
+
+
+def _roofline(profs, total_ms):
+    """HBM roofline of the PCG iteration from library profiles (PCG launch
+    times are recorded by the context that launched them)."""
+    pcg_ms = sum(p["pcg_ms"] for p in profs)
+    pcg_bytes = sum(p["pcg_bytes"] for p in profs)
+    pairs = max(sum(p["pcg_launches"] for p in profs) // 2, 1)
+    iters = sum(p["pcg_iters"] for p in profs)
+    peak, peak_kind = hbm_peak()
+    achieved = pcg_bytes / (pcg_ms / 1e3) / 1e9 if pcg_ms > 0 else 0.0
+    tr = pcg_traffic_record()
+    return {"kernel": "PCG iteration (k_pcg_spmv + k_pcg_update)", "bound": "hbm", "achieved": achieved,
+            "peak": peak, "peak_source": f"{peak_kind} hbm_gbs (copy, burst)", "unit": "GB/s",
+            "frac": achieved / peak,
+            "traffic": tr["dram_bytes_per_pose_iteration"] * iters / pairs if tr else None,
+            "algorithmic_bytes_per_launch_pair": pcg_bytes / pairs, "avg_launch_pair_ms": pcg_ms / pairs,
+            "launch_pairs": pairs, "pose_iterations_per_pair": iters / pairs,
+            "share_of_step": pcg_ms / total_ms if total_ms else None}
+
+
+def run_batched(args, dist):
+    """64 animation streams of the ~200k-tet figure and 64 of a half-size
+    variant (~50k tets), one frame of every stream per step, all solved in one
+    mfem_solve_multi call (shared PCG launches), each warm-started from its own
+    previous frame's solution."""
+    import numpy as np
+    import torch
+    from paper_2408_04066_gb300 import build as Bd
+    Bd.build()
+    from paper_2408_04066_gb300 import mfem
+    from synth import figure_animation, figure_config
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    nb = args.batch if args.batch != 16 else 64
+    frames = args.warmup + args.steps + 1
+    meshes = [figure_config(200000, model="snh", seeds=[]), figure_config(50000, model="snh", seeds=[], scale=0.5)]
+    ctxs, anim = [], []
+    stream = torch.cuda.current_stream(dev)
+    for mi, cfg in enumerate(meshes):
+        c = mfem.Context.from_config(cfg, precision="mixed", max_batch=nb, newton_tol=1e-6, init="warm")
+        c.set_stream(stream.cuda_stream)
+        ctxs.append(c)
+        a = np.stack([figure_animation(cfg["joints"], cfg["parent"], 100000 * (dist.rank + 1) + 1000 * mi + s,
+                                       frames) for s in range(nb)], axis=1)          # (frames, nb, H, 12)
+        anim.append(torch.tensor(a, dtype=torch.float64, device=dev))
+    infos = [c.info() for c in ctxs]
+    outs = [torch.empty((nb, i["n"], 3), dtype=torch.float64, device=dev) for i in infos]
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    f = 0
+    for _ in range(args.warmup + 1):          # frame 0 starts cold (rigid guess), then warm
+        mfem.solve_multi(ctxs, [a[f].contiguous() for a in anim], outs)
+        f += 1
+    torch.cuda.synchronize()
+    time.sleep(0.3)
+    step_ms, profs, stats = [], [], []
+    clocks.mark_start()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        dist.barrier()
+        xf = [a[f].contiguous() for a in anim]
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = mfem.solve_multi(ctxs, xf, outs)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        profs.append([c.profile() for c in ctxs])
+        stats.append(st)
+        f += 1
+    dist.barrier()
+    clocks.mark_end()
+    clk = clocks.stop()
+    clk["step_ms"] = [round(t, 3) for t in step_ms]
+    total_ms = sum(step_ms)
+    poses = dist.sum(2 * nb * args.steps)
+    value = poses / (dist.max(total_ms) / 1e3)
+    flat = [p for ps in profs for p in ps]
+    elem_updates = dist.sum(sum(p["element_updates"] for p in flat))
+    per_mesh = []
+    for mi in range(2):
+        ss = [s for st in stats for s in st[mi]]
+        per_mesh.append({"tets": infos[mi]["m"], "verts": infos[mi]["n"], "poses_per_step": nb,
+                         "newton_iters_mean": statistics.mean(s["newton_iters"] for s in ss),
+                         "pcg_iters_mean": statistics.mean(s["pcg_iters"] for s in ss),
+                         "all_converged": all(s["converged"] for s in ss)})
+    # warm start vs a cold (rigid-guess) start of the same frame, on the small mesh
+    cold = mfem.Context.from_config(meshes[1], precision="mixed", max_batch=nb, newton_tol=1e-6)
+    cold.set_stream(stream.cuda_stream)
+    _, st_cold = cold.solve_batch(anim[1][f - 1].contiguous())
+    cold.close()
+    if dist.rank == 0:
+        lat = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"batched-figure200k+figure50k-{nb}+{nb}-warm", "meshes": per_mesh,
+                       "precision": "mixed", "newton_tol": 1e-6, "init": "warm (previous frame of each stream)",
+                       "poses": "figure_animation streams at 30 frames/s",
+                       "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas x{dist.world}"},
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "note": "per step (one frame of all 2 x %d streams)" % nb},
+            "element_updates_per_s": elem_updates / (dist.max(total_ms) / 1e3),
+            "cold_start_newton_iters_mean_50k": statistics.mean(s["newton_iters"] for s in st_cold),
+            "roofline": _roofline(flat, total_ms),
+            "gpu_launches": sum(p["kernel_launches"] for p in flat), "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+    for c in ctxs:
+        c.close()
+
+
+def run_serve(args, dist):
+    """Poisson arrivals of pose solves over four resident meshes (~10k, 50k,
+    200k and 800k tets; co-rotational and neo-Hookean alternating), each request
+    the next frame of its mesh's animation, warm-started from the last solution
+    held in the slot it is admitted to; admission by device-memory budget and
+    free slots between Newton steps.  Latency is submit -> result on the host."""
+    import numpy as np
+    import torch
+    from paper_2408_04066_gb300 import build as Bd
+    Bd.build()
+    from paper_2408_04066_gb300 import mfem
+    from synth import figure_animation, figure_config
+
+    torch.cuda.set_device(dist.local)
+    specs = [(10000, "corot"), (50000, "snh"), (200000, "corot"), (800000, "snh")]
+    srv = mfem.Server(device_mem_budget=64 << 30, max_slots=64)
+    ids, anims, sizes = [], [], []
+    for mi, (tets, model) in enumerate(specs):
+        cfg = figure_config(tets, model=model, seeds=[])
+        ctx = mfem.Context.from_config(cfg, precision="mixed", newton_tol=1e-6, init="warm", tile_rows=256)
+        sizes.append({"tets": ctx.m, "verts": ctx.n, "model": model})
+        ids.append(srv.add(ctx))
+        n_frames = int(2 * args.rate * args.duration) + 8      # enough for both phases on one mesh
+        anims.append(figure_animation(cfg["joints"], cfg["parent"], 500 + 10 * dist.rank + mi, n_frames))
+    frame = [0] * len(specs)
+
+    def submit(mi):
+        t = srv.submit(ids[mi], anims[mi][frame[mi]])
+        frame[mi] += 1
+        return t
+
+    for mi in range(len(specs)):            # warm-up: two frames per mesh
+        for t in [submit(mi), submit(mi)]:
+            srv.wait(t)
+
+    def phase(rate, seconds, seed):
+        """Poisson arrivals at `rate` for `seconds`; returns per-request
+        (mesh, latency s, newton iters, converged) and the window (s)."""
+        r = np.random.default_rng(seed)
+        arr = np.cumsum(r.exponential(1.0 / rate, size=max(int(rate * seconds), 1)))
+        wh = r.integers(0, len(specs), size=len(arr))
+        res, tickets = [], []
+
+        def waiter():
+            i = 0
+            while True:
+                while i >= len(tickets):
+                    if done_submitting[0] and i >= len(tickets):
+                        return
+                    time.sleep(0.0005)
+                mi, t = tickets[i]
+                _, st, lat = srv.wait(t)
+                res.append((mi, lat, st["newton_iters"], st["converged"], time.perf_counter()))
+                i += 1
+
+        done_submitting = [False]
+        th = threading.Thread(target=waiter)
+        th.start()
+        t0 = time.perf_counter()
+        for a_, mi in zip(arr, wh):
+            d = t0 + a_ - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            tickets.append((int(mi), submit(int(mi))))
+        done_submitting[0] = True
+        th.join()
+        return res, max(x[4] for x in res) - t0
+
+    def pct(v, q):
+        return v[min(len(v) - 1, int(q * len(v)))]
+
+    def summary(res, window, rate):
+        lat = sorted(1e3 * x[1] for x in res)
+        per = []
+        for mi in range(len(specs)):
+            lm = sorted(1e3 * x[1] for x in res if x[0] == mi)
+            per.append(dict(sizes[mi], requests=len(lm), p50_ms=pct(lm, 0.5) if lm else None,
+                            p99_ms=pct(lm, 0.99) if lm else None,
+                            newton_iters_mean=statistics.mean(x[2] for x in res if x[0] == mi) if lm else None))
+        return {"offered_rate_per_s": rate, "requests": len(res), "completed_per_s": len(res) / window,
+                "p50_ms": pct(lat, 0.5), "p99_ms": pct(lat, 0.99), "max_ms": lat[-1],
+                "all_converged": all(x[3] for x in res), "meshes": per}
+
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    time.sleep(0.3)
+    clocks.mark_start()
+    c0 = srv.counters()
+    res1, win1 = phase(args.rate, args.duration, 1234 + dist.rank)        # offered load
+    cap = len(res1) / win1
+    c1 = srv.counters()
+    rate2 = 0.7 * cap
+    res2, win2 = phase(rate2, args.duration, 4321 + dist.rank)             # 70% of the measured capacity
+    clocks.mark_end()
+    clk = clocks.stop()
+    srv.close()
+    s1, s2 = summary(res1, win1, args.rate), summary(res2, win2, rate2)
+    value = dist.sum(len(res1)) / dist.max(win1)
+    if dist.rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": len(res1),
+            "warmup": 2 * len(specs), "ms_per_step": 1e3 * win1 / max(len(res1), 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
+            "data": "synthetic",
+            "config": {"workload": "serve-poisson-10k/50k/200k/800k", "meshes": sizes,
+                       "offered_rate_per_s": args.rate, "arrival_seconds": args.duration,
+                       "precision": "mixed", "newton_tol": 1e-6,
+                       "init": "warm (slot's last solve: predictor + carried correction for SNH)",
+                       "admission": "64 GiB slot budget, 64 slots, between Newton steps",
+                       "parallelism": f"replicas x{dist.world}"},
+            "latency_ms": {"p50": s2["p50_ms"], "p99": s2["p99_ms"],
+                           "note": "per request (submit to result in host memory) at 70% of the measured "
+                                   "capacity; the offered-load phase is under `offered_load`"},
+            "offered_load": s1, "at_70pct_capacity": s2,
+            "server": {"scheduling_rounds": c1["steps"] - c0["steps"],
+                       "pcg_launches": c1["pcg_launches"] - c0["pcg_launches"], "peak_slots": c1["peak_slots"]},
+            "clocks": clk,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_large(args, dist):
+    """The ~2M-tet capsule character with 40 handles (subdivided skeleton),
+    stable neo-Hookean, mixed precision, a batch of poses per step."""
+    import torch
+    from paper_2408_04066_gb300 import build as Bd
+    Bd.build()
+    from paper_2408_04066_gb300 import mfem
+    from synth import character_config
+
+    torch.cuda.set_device(dist.local)
+    dev = torch.device("cuda", dist.local)
+    nb = args.batch
+    cfg = character_config(2_000_000, 40, seeds=range(dist.rank * nb, dist.rank * nb + nb))
+    ctx = mfem.Context.from_config(cfg, precision="mixed", max_batch=nb, newton_tol=1e-6)
+    stream = torch.cuda.current_stream(dev)
+    ctx.set_stream(stream.cuda_stream)
+    info = ctx.info()
+    xfs = torch.tensor(cfg["xfs"], dtype=torch.float64, device=dev)
+    out = torch.empty((nb, info["n"], 3), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    clocks = ClockSampler(dist.local)
+    clocks.start()
+    for _ in range(args.warmup):
+        ctx.solve_batch(xfs, out)
+    torch.cuda.synchronize()
+    time.sleep(0.3)
+    step_ms, profs, stats = [], [], []
+    clocks.mark_start()
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        dist.barrier()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, st = ctx.solve_batch(xfs, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        profs.append(ctx.profile())
+        stats += st
+    dist.barrier()
+    clocks.mark_end()
+    clk = clocks.stop()
+    clk["step_ms"] = [round(t, 3) for t in step_ms]
+    total_ms = sum(step_ms)
+    value = dist.sum(nb * args.steps) / (dist.max(total_ms) / 1e3)
+    if dist.rank == 0:
+        lat = sorted(step_ms)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"character{info['m']}-h40-snh-batch{nb}", "tets": info["m"],
+                       "verts": info["n"], "handles": info["n_handles"], "pins": info["n_pins"],
+                       "batch_poses": nb, "precision": "mixed", "newton_tol": 1e-6,
+                       "device_bytes": info["device_bytes"], "parallelism": f"replicas x{dist.world}"},
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "note": "per batch step"},
+            "newton_iters_mean": statistics.mean(s["newton_iters"] for s in stats),
+            "pcg_iters_mean": statistics.mean(s["pcg_iters"] for s in stats),
+            "all_converged": all(s["converged"] for s in stats),
+            "element_updates_per_s": dist.sum(sum(p["element_updates"] for p in profs)) / (dist.max(total_ms) / 1e3),
+            "roofline": _roofline(profs, total_ms),
+            "gpu_launches": sum(p["kernel_launches"] for p in profs), "clocks": clk,
         }
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -450,6 +764,12 @@ def main():
     try:
         if args.impl == "reference":
             run_reference(args, dist)
+        elif args.workload == "batched":
+            run_batched(args, dist)
+        elif args.workload == "serve":
+            run_serve(args, dist)
+        elif args.workload == "large":
+            run_large(args, dist)
         else:
             run_mfem(args, dist)
     finally:

@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MFEM_ABI_VERSION 2
+#define MFEM_ABI_VERSION 3
 
 typedef enum {
     MFEM_OK = 0,
@@ -113,7 +113,14 @@ typedef struct {
                             counted as a Newton step; for ARAP/corot the rigid
                             guess.  RIGID moves every vertex with the handle its
                             rest position clusters to; REST uses X (Algorithm 1);
-                            WARM continues from the last solution */
+                            WARM (for animation streams): SNH takes the COROT
+                            start and then adds the correction the slot's last
+                            solve needed beyond its own predictor result, each
+                            vertex's correction turned by the rotation change of
+                            the handle its rest position clusters to; ARAP and
+                            corot take the rigid guess (their minimiser is one
+                            linear solve from any start); a state set by
+                            mfem_set_state is used as it is */
     int32_t max_batch;   /* poses per mfem_solve_batch call allocated for (16) */
     int32_t tile_rows;   /* PCG rows per block: 64, 128 or 256; 0 = autotune (timed
                             on the first assembled system) */
@@ -161,6 +168,7 @@ typedef struct {
     double total_ms;          /* first to last library event of the call */
     int32_t tile_rows;        /* PCG tile in use */
     int32_t grid_blocks;      /* PCG blocks per launch (tiles of all problems) */
+    int64_t element_updates;  /* per-tet local steps (a1) of the Newton element passes */
 } mfem_profile;
 
 typedef struct mfem_ctx mfem_ctx;
@@ -214,6 +222,20 @@ mfem_status mfem_solve(mfem_ctx* ctx, double* out_verts, mfem_stats* stats);
  * allocation if needed.  Each pose's result does not depend on the others. */
 mfem_status mfem_solve_batch(mfem_ctx* ctx, const double* xf, int32_t B, double* out,
                              int32_t memory, mfem_stats* stats);
+
+/* mfem_solve_batch over several meshes at once: B[i] poses of ctxs[i] for
+ * i < n_ctx, solved together -- every problem of every mesh moves through its
+ * own Newton steps, and each PCG iteration launch serves every problem of
+ * every mesh currently inside PCG.  xf[i] [B[i]][H_i][12], out[i] [B[i]][n_i][3]
+ * (all host or all device, as `memory` says), stats[i] host [B[i]] (stats or
+ * stats[i] may be NULL).  The contexts must be distinct and on one device; the
+ * work runs on ctxs[0]'s stream (the others' streams are synchronised first and
+ * restored after the call).  PCG tiles are ctxs[0]'s.  Each result equals the
+ * same pose solved alone.  With init = MFEM_INIT_WARM, pose b of a mesh starts
+ * from the last solution held in that mesh's slot b (see mfem_options.init). */
+mfem_status mfem_solve_multi(mfem_ctx* const* ctxs, int32_t n_ctx, const double* const* xf,
+                             const int32_t* B, double* const* out, int32_t memory,
+                             mfem_stats* const* stats);
 
 /* Element outputs of the last mfem_solve (Eq. 10-11 recovered per element):
  * s [m][6] the stretch S_k as (S00,S11,S22,S12,S02,S01) -- plain components,

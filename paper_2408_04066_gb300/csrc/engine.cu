@@ -85,7 +85,7 @@ mfem_status upload(mfem_ctx* c, U** dst, const U* src, size_t count) {
 
 void free_slots(mfem_ctx* c) {
     SlotDev& S = c->slot;
-    void* ptrs[] = {S.xf, S.x, S.xp, S.g, S.ge, S.Ke, S.val, S.dinv, S.vec, S.part, S.sc, S.active, S.alpha, S.outbuf};
+    void* ptrs[] = {S.xf, S.xf_prev, S.xpred, S.dcorr, S.x, S.xp, S.g, S.ge, S.Ke, S.val, S.dinv, S.vec, S.part, S.sc, S.active, S.alpha, S.outbuf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     int prec = S.prec;
@@ -104,7 +104,8 @@ size_t bytes_per_slot(const mfem_ctx* c) {
     const size_t kt = c->slot.prec == 1 ? 4 : 8;
     const size_t slots = (size_t)c->plan.slice_ptr.back();
     return H * 12 * 8 + 4 * n * 3 * 8 + m * 12 * 8 + m * kKe * kt + slots * 9 * kt + n * 9 * kt +
-           kVecStride * npad32((int)n) * kt + (size_t)part_tiles_for(c) * 4 * 8 + sizeof(ProbScal) + 4 + 8;
+           kVecStride * npad32((int)n) * kt + (size_t)part_tiles_for(c) * 4 * 8 + sizeof(ProbScal) + 4 + 8 +
+           H * 12 * 8 + (c->opt.init == MFEM_INIT_WARM ? 2 * n * 3 * 8 : 0);
 }
 
 mfem_status alloc_slots(mfem_ctx* c, int B) {
@@ -122,6 +123,11 @@ mfem_status alloc_slots(mfem_ctx* c, int B) {
 #define AL(ptr, bytes) \
     if ((st = al((void**)&(ptr), (bytes))) != MFEM_OK) return st;
     AL(S.xf, B * H * 12 * 8);
+    AL(S.xf_prev, B * H * 12 * 8);
+    if (c->opt.init == MFEM_INIT_WARM) {
+        AL(S.xpred, B * n * 3 * 8);
+        AL(S.dcorr, B * n * 3 * 8);
+    }
     AL(S.x, B * n * 3 * 8);
     AL(S.xp, B * n * 3 * 8);
     AL(S.g, B * n * 3 * 8);
@@ -143,7 +149,8 @@ mfem_status alloc_slots(mfem_ctx* c, int B) {
     // every slot starts at the rest shape (the WARM start without history)
     for (int b = 0; b < B; ++b)
         CK(cudaMemcpy(S.x + (size_t)b * n * 3, c->mesh.X, n * 3 * 8, cudaMemcpyDeviceToDevice));
-    c->has_state.assign(B, 0);
+    c->warm_kind.assign(B, 0);
+    c->xpred_valid.assign(B, 0);
     // pinned host staging
     if (c->sc_host) cudaFreeHost(c->sc_host);
     if (c->active_host) cudaFreeHost(c->active_host);
@@ -190,6 +197,7 @@ void end_profile(mfem_ctx* c) {
     P.element_launches = c->prof.element_launches;
     P.pcg_bytes = c->prof.pcg_bytes;
     P.element_bytes = c->prof.element_bytes;
+    P.element_updates = c->prof.element_updates;
     P.pcg_iters = c->prof.pcg_iters;
     P.tile_rows = c->tile_rows;
     P.grid_blocks = c->grid_blocks;
@@ -451,15 +459,36 @@ mfem_status advance(std::vector<Group>& gs) {
         std::vector<int> f = mask_of(g, [](const ProbHost& p) { return p.need_init != 0; });
         if (!any_of(f)) continue;
         mfem_ctx* gc = g.ctx;
-        mfem_status st = upload_active(gc, g.B, f);
+        const int oi = gc->opt.init;
+        const bool snh = gc->model == MFEM_SNH;
+        // per problem: start 0 rigid guess, 1 rest shape, 2 the state held in x
+        // (a caller's state under WARM); SNH under COROT and WARM takes the
+        // predictor step from the rigid guess; WARM then adds the correction its
+        // slot's last solve needed beyond its own predictor result
+        std::vector<int> start(g.B, 0), pred(g.B, 0), corr(g.B, 0);
+        bool need_ref = false;
+        for (int b = 0; b < g.B; ++b) {
+            if (!f[b]) continue;
+            start[b] = oi == MFEM_INIT_REST ? 1 : (oi == MFEM_INIT_WARM && gc->warm_kind[b] == 2 ? 2 : 0);
+            pred[b] = snh && start[b] == 0 && oi != MFEM_INIT_RIGID;
+            corr[b] = pred[b] && oi == MFEM_INIT_WARM && gc->warm_kind[b] == 1 && gc->xpred_valid[b];
+            need_ref |= pred[b] || start[b] != 0;
+        }
+        mfem_status st;
+        if (any_of(corr)) {
+            st = upload_active(gc, g.B, corr);
+            if (st != MFEM_OK) return st;
+            launch_warm_save(elem_args(gc), g.B, s);
+            gc->prof.launches++;
+        }
+        st = upload_active(gc, g.B, f);
         if (st != MFEM_OK) return st;
-        const bool predict = gc->opt.init == MFEM_INIT_COROT && gc->model == MFEM_SNH;
-        const int init = (gc->opt.init == MFEM_INIT_RIGID || gc->opt.init == MFEM_INIT_COROT)
-                             ? 0 : (gc->opt.init == MFEM_INIT_REST ? 1 : 2);
         std::vector<double> gref(g.B, -1.0);
-        if (predict || init != 0) {
-            const size_t xbytes = sizeof(double) * 3 * (size_t)gc->plan.n * g.B;
-            if (init == 2) CK(cudaMemcpyAsync(gc->slot.outbuf, gc->slot.x, xbytes, cudaMemcpyDeviceToDevice, s));
+        const size_t xbytes = sizeof(double) * 3 * (size_t)gc->plan.n * g.B;
+        bool parked = false;
+        if (need_ref) {   // reference gradient at the rigid guess
+            for (int b = 0; b < g.B; ++b) parked |= start[b] == 2;
+            if (parked) CK(cudaMemcpyAsync(gc->slot.outbuf, gc->slot.x, xbytes, cudaMemcpyDeviceToDevice, s));
             ElemArgs a = elem_args(gc);
             launch_pose_init(a, g.B, 0, s);
             launch_element(a, g.B, s);
@@ -471,10 +500,15 @@ mfem_status advance(std::vector<Group>& gs) {
             synced(gs);
             for (int b = 0; b < g.B; ++b)
                 if (f[b]) gref[b] = std::sqrt(gc->sc_host[b].gnorm2);
-            if (init == 2) CK(cudaMemcpyAsync(gc->slot.x, gc->slot.outbuf, xbytes, cudaMemcpyDeviceToDevice, s));
+            if (parked) CK(cudaMemcpyAsync(gc->slot.x, gc->slot.outbuf, xbytes, cudaMemcpyDeviceToDevice, s));
         }
-        if (!predict) {
-            launch_pose_init(elem_args(gc), g.B, init, s);
+        for (int code = 0; code < 3; ++code) {   // apply the starts (pins on their targets)
+            std::vector<int> m(g.B, 0);
+            for (int b = 0; b < g.B; ++b) m[b] = f[b] && start[b] == code && (code != 0 || parked || !need_ref);
+            if (!any_of(m)) continue;
+            st = upload_active(gc, g.B, m);
+            if (st != MFEM_OK) return st;
+            launch_pose_init(elem_args(gc), g.B, code, s);
             gc->prof.launches++;
         }
         for (int b = 0; b < g.B; ++b)
@@ -482,7 +516,8 @@ mfem_status advance(std::vector<Group>& gs) {
                 ProbHost& p = g.ph[b];
                 p = ProbHost();
                 p.active = 1;
-                p.pred = predict ? 1 : 0;
+                p.pred = pred[b];
+                p.corr = corr[b];
                 p.g0 = gref[b];
             }
     }
@@ -514,6 +549,7 @@ mfem_status advance(std::vector<Group>& gs) {
             int na = 0;
             for (int b = 0; b < g.B; ++b) na += f[b];
             gc->prof.element_bytes += na * element_bytes(gc);
+            gc->prof.element_updates += (int64_t)na * gc->plan.m;
         }
         if (!any) continue;
         any_elem = true;
@@ -682,6 +718,19 @@ mfem_status advance(std::vector<Group>& gs) {
         if (st != MFEM_OK) return st;
         launch_update(elem_args(gc), g.B, s);
         gc->prof.launches++;
+        if (gc->opt.init == MFEM_INIT_WARM && gc->model == MFEM_SNH) {
+            for (int apply = 0; apply < 2; ++apply) {   // after the predictor step
+                std::vector<int> m(g.B, 0);
+                for (int b = 0; b < g.B; ++b) m[b] = fin[gi][b] && g.ph[b].pred && g.ph[b].corr == apply;
+                if (!any_of(m)) continue;
+                st = upload_active(gc, g.B, m);
+                if (st != MFEM_OK) return st;
+                launch_warm_step(elem_args(gc), g.B, apply, s);
+                gc->prof.launches++;
+                for (int b = 0; b < g.B; ++b)
+                    if (m[b]) gc->xpred_valid[b] = 1;
+            }
+        }
         for (int b = 0; b < g.B; ++b)
             if (fin[gi][b]) {
                 g.ph[b].it++;
@@ -704,7 +753,10 @@ mfem_status run_batch(mfem_ctx* c, int B, std::vector<ProbHost>& ph) {
         for (int b = 0; b < B; ++b) any |= ph[b].active || ph[b].need_init;
         if (!any) break;
     }
-    for (int b = 0; b < B; ++b) c->has_state[b] = 1;
+    for (int b = 0; b < B; ++b) c->warm_kind[b] = 1;
+    // the solutions now in x belong to these poses (warm starts)
+    CK(cudaMemcpyAsync(c->slot.xf_prev, c->slot.xf, sizeof(double) * 12 * (size_t)c->plan.H * B,
+                       cudaMemcpyDeviceToDevice, c->stream));
     return MFEM_OK;
 }
 
@@ -1010,18 +1062,17 @@ mfem_status mfem_solve(mfem_ctx* c, double* out, mfem_stats* stats) {
     return finish_stats(c, ph, 1, stats);
 }
 
-mfem_status mfem_solve_batch(mfem_ctx* c, const double* xf, int32_t B, double* out, int32_t memory,
-                             mfem_stats* stats) {
+// Checks of a batch request, slot allocation, and the upload of its poses.
+static mfem_status stage_batch(mfem_ctx* c, const double* xf, int32_t B, double* out, int32_t memory) {
     if (!c || !xf || !out) return ctx_fail(c, MFEM_EINVAL, "null argument");
     if (c->owned_by_server) return ctx_fail(c, MFEM_EINVAL, "context belongs to a server");
     if (B < 1) return ctx_fail(c, MFEM_EINVAL, "B must be >= 1");
     if (c->fext_sets > 1 && B > c->fext_sets)
         return ctx_fail(c, MFEM_EINVAL, "more poses than external force fields");
     if (memory != MFEM_MEM_HOST && memory != MFEM_MEM_DEVICE) return ctx_fail(c, MFEM_EINVAL, "bad memory kind");
-    const int H = c->plan.H, n = c->plan.n;
+    const int H = c->plan.H;
     mfem_status st = ensure_slots(c, B);
     if (st != MFEM_OK) return st;
-    begin_profile(c);
     const size_t xf_bytes = sizeof(double) * 12 * (size_t)H * B;
     if (memory == MFEM_MEM_HOST) {
         st = validate_pose(c, xf, H * B);
@@ -1035,9 +1086,12 @@ mfem_status mfem_solve_batch(mfem_ctx* c, const double* xf, int32_t B, double* o
         if (st != MFEM_OK) return st;
         CK(cudaMemcpyAsync(c->slot.xf, xf, xf_bytes, cudaMemcpyDeviceToDevice, c->stream));
     }
-    std::vector<ProbHost> ph;
-    st = run_batch(c, B, ph);
-    if (st != MFEM_OK) return st;
+    return MFEM_OK;
+}
+
+// Solutions of a finished batch -> out (caller vertex order).
+static mfem_status emit_batch(mfem_ctx* c, int32_t B, double* out, int32_t memory) {
+    const int n = c->plan.n;
     if (memory == MFEM_MEM_HOST) {
         launch_unpermute(elem_args(c), B, c->slot.outbuf, c->stream);
         CK(cudaMemcpyAsync(out, c->slot.outbuf, sizeof(double) * 3 * (size_t)n * B, cudaMemcpyDeviceToHost,
@@ -1046,8 +1100,78 @@ mfem_status mfem_solve_batch(mfem_ctx* c, const double* xf, int32_t B, double* o
         launch_unpermute(elem_args(c), B, out, c->stream);
     }
     c->prof.launches++;
+    return MFEM_OK;
+}
+
+mfem_status mfem_solve_batch(mfem_ctx* c, const double* xf, int32_t B, double* out, int32_t memory,
+                             mfem_stats* stats) {
+    mfem_status st = stage_batch(c, xf, B, out, memory);
+    if (st != MFEM_OK) return st;
+    begin_profile(c);
+    std::vector<ProbHost> ph;
+    st = run_batch(c, B, ph);
+    if (st != MFEM_OK) return st;
+    st = emit_batch(c, B, out, memory);
+    if (st != MFEM_OK) return st;
     end_profile(c);
     return finish_stats(c, ph, B, stats);
+}
+
+mfem_status mfem_solve_multi(mfem_ctx* const* ctxs, int32_t n_ctx, const double* const* xf, const int32_t* B,
+                             double* const* out, int32_t memory, mfem_stats* const* stats) {
+    if (!ctxs || !xf || !B || !out || n_ctx < 1) return ctx_fail(nullptr, MFEM_EINVAL, "null argument or n_ctx < 1");
+    for (int i = 0; i < n_ctx; ++i) {
+        if (!ctxs[i]) return ctx_fail(nullptr, MFEM_EINVAL, "null context");
+        for (int j = 0; j < i; ++j)
+            if (ctxs[j] == ctxs[i]) return ctx_fail(ctxs[i], MFEM_EINVAL, "a context appears twice");
+        if (ctxs[i]->device != ctxs[0]->device) return ctx_fail(ctxs[i], MFEM_EINVAL, "contexts on different devices");
+    }
+    // every context works on the first context's stream for the call
+    std::vector<cudaStream_t> saved(n_ctx);
+    for (int i = 0; i < n_ctx; ++i) {
+        saved[i] = ctxs[i]->stream;
+        if (i > 0) {
+            cudaStreamSynchronize(ctxs[i]->stream);
+            ctxs[i]->stream = ctxs[0]->stream;
+        }
+    }
+    auto restore = [&]() {
+        for (int i = 1; i < n_ctx; ++i) ctxs[i]->stream = saved[i];
+    };
+    mfem_status st = MFEM_OK;
+    for (int i = 0; i < n_ctx && st == MFEM_OK; ++i) st = stage_batch(ctxs[i], xf[i], B[i], out[i], memory);
+    if (st != MFEM_OK) { restore(); return st; }
+    std::vector<std::vector<ProbHost>> ph(n_ctx);
+    std::vector<Group> gs;
+    for (int i = 0; i < n_ctx; ++i) {
+        begin_profile(ctxs[i]);
+        ph[i].assign(B[i], ProbHost());
+        for (int b = 0; b < B[i]; ++b) ph[i][b].need_init = 1;
+    }
+    for (int i = 0; i < n_ctx; ++i) gs.push_back(Group{ctxs[i], B[i], ph[i].data()});
+    for (int guard = 0; guard < 10000000 && st == MFEM_OK; ++guard) {
+        st = advance(gs);
+        bool any = false;
+        for (int i = 0; i < n_ctx; ++i)
+            for (int b = 0; b < B[i]; ++b) any |= ph[i][b].active || ph[i][b].need_init;
+        if (!any) break;
+    }
+    for (int i = 0; i < n_ctx && st == MFEM_OK; ++i) {
+        for (int b = 0; b < B[i]; ++b) ctxs[i]->warm_kind[b] = 1;
+        st = cuda_check(ctxs[i], cudaMemcpyAsync(ctxs[i]->slot.xf_prev, ctxs[i]->slot.xf,
+                                                 sizeof(double) * 12 * (size_t)ctxs[i]->plan.H * B[i],
+                                                 cudaMemcpyDeviceToDevice, ctxs[i]->stream), "keep poses");
+        if (st != MFEM_OK) break;
+        st = emit_batch(ctxs[i], B[i], out[i], memory);
+    }
+    mfem_status worst = st;
+    for (int i = 0; i < n_ctx && st == MFEM_OK; ++i) {
+        end_profile(ctxs[i]);
+        mfem_status si = finish_stats(ctxs[i], ph[i], B[i], stats ? stats[i] : nullptr);
+        if (si != MFEM_OK && worst == MFEM_OK) worst = si;
+    }
+    restore();
+    return worst;
 }
 
 mfem_status mfem_get_elem(mfem_ctx* c, double* s, double* lam) {
@@ -1089,7 +1213,8 @@ mfem_status mfem_set_state(mfem_ctx* c, const double* x) {
     CK(cudaMemcpyAsync(c->slot.outbuf, x, sizeof(double) * 3 * c->plan.n, cudaMemcpyHostToDevice, c->stream));
     launch_permute_in(elem_args(c), 0, c->slot.outbuf, c->stream);
     CK(cudaStreamSynchronize(c->stream));
-    c->has_state[0] = 1;
+    c->warm_kind[0] = 2;
+    c->xpred_valid[0] = 0;
     return MFEM_OK;
 }
 

@@ -23,7 +23,8 @@ struct ProbHost {
     int ran_pcg = 0;     // PCG ran in the current step
     int status = MFEM_OK;
     int converged = 0;
-    int pred = 0;        // co-rotational predictor step pending (SNH, COROT init)
+    int pred = 0;        // co-rotational predictor step pending (SNH, COROT or WARM init)
+    int corr = 0;        // after the predictor, add the last solve's rotated correction (WARM)
     double g0 = -1.0, gn = 0.0, energy = 0.0;
 };
 
@@ -36,12 +37,14 @@ struct Profiler {
     int pcg_launches = 0, element_launches = 0;
     double pcg_bytes = 0.0, element_bytes = 0.0;
     int64_t pcg_iters = 0;
+    int64_t element_updates = 0;
     cudaEvent_t start = nullptr, stop = nullptr;
     void reset() {
         used = 0;
         launches = pcg_launches = element_launches = 0;
         pcg_bytes = element_bytes = 0.0;
         pcg_iters = 0;
+        element_updates = 0;
         kind.clear();
     }
     int begin(int k, cudaStream_t s);   // returns pair index or -1
@@ -78,7 +81,11 @@ struct mfem_ctx {
     int tile_rows = 0;       // PCG rows per block
     int grid_blocks = 0;
     bool pose_set = false;
-    std::vector<int> has_state;   // per slot: x holds a previous solution
+    // per slot: 0 = x holds no start, 1 = x is the solution of the pose in
+    // slot.xf_prev (a warm start follows the handles to the new pose),
+    // 2 = x was set by the caller (a warm start uses it as it is)
+    std::vector<int> warm_kind;
+    std::vector<int> xpred_valid;   // per slot: slot.xpred holds the last solve's predictor result
     mfem::Profiler prof;
     mfem_profile last_profile{};
     std::string err;

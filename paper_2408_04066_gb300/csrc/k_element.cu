@@ -621,6 +621,45 @@ __global__ void k_pose_init(ElemArgs A, int init) {
     }
 }
 
+// Warm starts (SNH): the correction the slot's last solve needed beyond its own
+// predictor result, dcorr = x - xpred, taken before the new pose is applied.
+__global__ void k_warm_save(ElemArgs A) {
+    const int b = blockIdx.y;
+    if (!A.slot.active[b]) return;
+    const int n = A.mesh.n;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * n) return;
+    const size_t o = (size_t)b * n * 3 + i;
+    A.slot.dcorr[o] = A.slot.x[o] - A.slot.xpred[o];
+}
+
+// After the predictor step: keep x as xpred for the next solve and, with
+// apply, add the last correction turned by the rotation change of the handle
+// each free vertex's rest position clusters to, Q_h Q_h,prev^T dcorr_v.
+__global__ void k_warm_step(ElemArgs A, int apply) {
+    const int b = blockIdx.y;
+    if (!A.slot.active[b]) return;
+    const MeshDev& M = A.mesh;
+    const int v = blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= M.n) return;
+    const size_t o = ((size_t)b * M.n + v) * 3;
+    double* x = A.slot.x + o;
+    double* xp = A.slot.xpred + o;
+    xp[0] = x[0];
+    xp[1] = x[1];
+    xp[2] = x[2];
+    if (!apply || M.pin_handle_v[v] >= 0) return;
+    const int h = M.vhandle[v];
+    const double* Tn = A.slot.xf + (size_t)b * M.H * 12 + 12 * h;
+    const double* Tp = A.slot.xf_prev + (size_t)b * M.H * 12 + 12 * h;
+    const double* d = A.slot.dcorr + o;
+    double y[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) y[i] = Tp[i] * d[0] + Tp[4 + i] * d[1] + Tp[8 + i] * d[2];   // Qp^T d
+#pragma unroll
+    for (int i = 0; i < 3; ++i) x[i] += (Tn[4 * i] * y[0] + Tn[4 * i + 1] * y[1]) + Tn[4 * i + 2] * y[2];
+}
+
 template <int MODEL>
 __global__ void k_elem_out(ElemArgs A, int b, double* __restrict__ s_out, double* __restrict__ lam_out) {
     const MeshDev& M = A.mesh;
@@ -721,6 +760,16 @@ void launch_trial_t(const ElemArgs& a, int B, cudaStream_t s) {
 void launch_pose_init(const ElemArgs& a, int B, int init, cudaStream_t s) {
     dim3 grid((a.mesh.n + 255) / 256, B);
     k_pose_init<<<grid, 256, 0, s>>>(a, init);
+}
+
+void launch_warm_save(const ElemArgs& a, int B, cudaStream_t s) {
+    dim3 grid((3 * a.mesh.n + 255) / 256, B);
+    k_warm_save<<<grid, 256, 0, s>>>(a);
+}
+
+void launch_warm_step(const ElemArgs& a, int B, int apply, cudaStream_t s) {
+    dim3 grid((a.mesh.n + 255) / 256, B);
+    k_warm_step<<<grid, 256, 0, s>>>(a, apply);
 }
 
 void launch_element(const ElemArgs& a, int B, cudaStream_t s) {

@@ -37,6 +37,9 @@ struct SlotDev {
     int cap = 0;
     int prec = 1;            // 1 = mixed (float K and PCG vectors), 0 = FP64
     double* xf = nullptr;    // [B][H][12]
+    double* xf_prev = nullptr;  // [B][H][12] pose of the solution held in x (warm starts)
+    double* xpred = nullptr;    // [B][n][3] x after the predictor step of the last solve (WARM only)
+    double* dcorr = nullptr;    // [B][n][3] last solve's solution minus xpred (WARM only)
     double* x = nullptr;     // [B][n][3]
     double* xp = nullptr;    // [B][n][3] pin targets (pinned rows only)
     double* g = nullptr;     // [B][n][3] masked gradient
@@ -73,8 +76,13 @@ __device__ __forceinline__ T* vecp(const SlotDev& S, int b, int off, int n) {
 }
 #endif
 
-// a0: pose -> pin targets and initial guess (init: 0 rigid, 1 rest, 2 warm)
+// a0: pose -> pin targets and initial guess (init: 0 rigid, 1 rest, 2 the
+// state held in x)
 void launch_pose_init(const ElemArgs& a, int B, int init, cudaStream_t s);
+// warm starts (SNH): dcorr = x - xpred before the new pose is applied; after
+// the predictor step xpred = x and, with apply, x += dQ_h dcorr on free vertices
+void launch_warm_save(const ElemArgs& a, int B, cudaStream_t s);
+void launch_warm_step(const ElemArgs& a, int B, int apply, cudaStream_t s);
 // a1: element step (Ke, element forces, energy) for active problems
 void launch_element(const ElemArgs& a, int B, cudaStream_t s);
 // a6: energy at x + alpha dx for active problems (line-search trial)

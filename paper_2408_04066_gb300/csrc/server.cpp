@@ -158,6 +158,10 @@ void mfem_server::run() {
                 Request& r = reqs[me.slot_req[b]];
                 fill_stats(c, me.ph[b], &r.st);
                 r.status = e == cudaSuccess ? me.ph[b].status : MFEM_ECUDA;
+                c->warm_kind[b] = 1;   // a WARM-start mesh continues from this solution
+                const size_t H = c->plan.H;
+                cudaMemcpyAsync(c->slot.xf_prev + (size_t)b * H * 12, c->slot.xf + (size_t)b * H * 12,
+                                H * 12 * sizeof(double), cudaMemcpyDeviceToDevice, stream);
                 r.done = true;
                 r.t_done = now_s();
                 me.slot_req[b] = 0;

@@ -23,7 +23,7 @@ CLUSTER_RULES = {"bone": 0, "joint": 1, "midpoint": 2}
 INITS = {"rigid": 0, "rest": 1, "warm": 2, "corot": 3}
 ROTATIONS = {"rig": 0, "polar": 1}
 MEM_HOST, MEM_DEVICE = 0, 1
-ABI_VERSION = 2   # MFEM_ABI_VERSION of the header these structures follow
+ABI_VERSION = 3   # MFEM_ABI_VERSION of the header these structures follow
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -61,7 +61,7 @@ class Profile(C.Structure):
                 ("pcg_bytes", C.c_double), ("pcg_iters", C.c_int64), ("element_launches", C.c_int32),
                 ("element_ms", C.c_double), ("element_bytes", C.c_double), ("assemble_ms", C.c_double),
                 ("linesearch_ms", C.c_double), ("total_ms", C.c_double), ("tile_rows", C.c_int32),
-                ("grid_blocks", C.c_int32)]
+                ("grid_blocks", C.c_int32), ("element_updates", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -82,6 +82,8 @@ _SIGS = [
     ("mfem_solve", C.c_int32, [C.c_void_p, _dp, C.POINTER(Stats)]),
     ("mfem_solve_batch", C.c_int32, [C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_int32,
                                      C.POINTER(Stats)]),
+    ("mfem_solve_multi", C.c_int32, [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p), _ip,
+                                     C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
     ("mfem_get_elem", C.c_int32, [C.c_void_p, _dp, _dp]),
     ("mfem_get_elem_static", C.c_int32, [C.c_void_p, _dp, _dp]),
     ("mfem_get_state", C.c_int32, [C.c_void_p, _dp]),
@@ -352,6 +354,38 @@ class Context:
                                        C.byref(nnz), C.byref(slots), C.byref(byts)), self._ctx)
         return dict(n=n.value, m=m.value, n_handles=H.value, n_pins=npins.value, nnz_blocks=nnz.value,
                     sell_slots=slots.value, device_bytes=byts.value)
+
+
+def solve_multi(ctxs, xfs, outs=None, raise_on_notconv=False):
+    """mfem_solve_multi: xfs[i] (B_i,H_i,12) poses of Context ctxs[i] -- all numpy
+    host arrays or all torch CUDA float64 tensors.  Returns (outs, stats)."""
+    lib = load()
+    k = len(ctxs)
+    dev = hasattr(xfs[0], "is_cuda") and xfs[0].is_cuda
+    if dev:
+        import torch
+        assert all(x.dtype == torch.float64 and x.is_contiguous() for x in xfs)
+        if outs is None:
+            outs = [torch.empty((x.shape[0], c.n, 3), dtype=torch.float64, device=x.device)
+                    for c, x in zip(ctxs, xfs)]
+        xp = [x.data_ptr() for x in xfs]
+        op = [o.data_ptr() for o in outs]
+        mem = MEM_DEVICE
+    else:
+        xfs = [_f64(x, (-1, c.H, 12)) for c, x in zip(ctxs, xfs)]
+        if outs is None:
+            outs = [np.empty((x.shape[0], c.n, 3)) for c, x in zip(ctxs, xfs)]
+        xp = [x.ctypes.data for x in xfs]
+        op = [o.ctypes.data for o in outs]
+        mem = MEM_HOST
+    Bs = (C.c_int32 * k)(*[int(x.shape[0]) for x in xfs])
+    stats = [(Stats * int(x.shape[0]))() for x in xfs]
+    st_ptrs = (C.c_void_p * k)(*[C.cast(s, C.c_void_p) for s in stats])
+    cp = (C.c_void_p * k)(*[c._ctx.value for c in ctxs])
+    s = lib.mfem_solve_multi(cp, k, (C.c_void_p * k)(*xp), Bs, (C.c_void_p * k)(*op), mem, st_ptrs)
+    if s != MFEM_OK and (s != MFEM_ENOTCONV or raise_on_notconv):
+        _check(s, ctxs[0]._ctx)
+    return outs, [[st.as_dict() for st in ss] for ss in stats]
 
 
 class Server:

@@ -11,7 +11,7 @@ import functools
 
 import numpy as np
 
-from .meshes import bar_mesh, figure_mesh_for_tets
+from .meshes import bar_mesh, character_rig, figure_mesh_for_tets
 from .poses import bar_twist_pose, figure_pose
 
 # Stable neo-Hookean figure material: Young's modulus (Pa) and Poisson ratio.
@@ -59,6 +59,23 @@ def figure_config(target_tets=200_000, model="snh", seeds=range(16), scale=1.0,
         np.zeros((0, len(joints), 12))
     return dict(
         name=f"figure{len(T)}", X=X.copy(), T=T.copy(), joints=joints, parent=parent,
+        cluster_rule="bone", pin_verts=None, pin_handle=None, pin_radius=pin_radius_cells * h,
+        model=model, mu=mu, lam=lam, xfs=xfs, h=h,
+    )
+
+
+def character_config(target_tets=2_000_000, n_handles=40, model="snh", seeds=range(4), E=SNH_E, nu=SNH_NU,
+                     max_angle_deg=20.0, pin_radius_cells=1.5):
+    """The capsule character voxelised to ~target_tets with the skeleton
+    subdivided to n_handles joints (``character_rig``); FK poses turn every
+    joint by up to +-max_angle_deg (the subdivided chains compound it)."""
+    X, T, _, _, h = _figure_mesh_cached(int(target_tets), 1.0)
+    joints, parent = character_rig(n_handles)
+    mu, lam = lame_from_young(E, nu)
+    xfs = np.stack([figure_pose(joints, parent, s, max_angle_deg=max_angle_deg) for s in seeds]) \
+        if len(seeds) else np.zeros((0, len(joints), 12))
+    return dict(
+        name=f"character{len(T)}h{n_handles}", X=X.copy(), T=T.copy(), joints=joints, parent=parent,
         cluster_rule="bone", pin_verts=None, pin_handle=None, pin_radius=pin_radius_cells * h,
         model=model, mu=mu, lam=lam, xfs=xfs, h=h,
     )

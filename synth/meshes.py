@@ -98,6 +98,37 @@ def figure_rig(scale: float = 1.0):
     return _JOINTS * scale, _PARENT.copy()
 
 
+def character_rig(n_handles: int = 40, scale: float = 1.0):
+    """The stick figure's skeleton with extra joints inserted along its bones
+    (spine, neck and limb segments), n_handles joints in all, parents first.
+    The extra joints go to the bones in proportion to their lengths (largest
+    remainder), evenly spaced along each bone."""
+    J, P = _JOINTS * scale, _PARENT
+    bones = [(int(P[j]), j) for j in range(len(J)) if P[j] >= 0]
+    extra = n_handles - len(J)
+    if extra < 0:
+        raise ValueError("n_handles below the figure's 15 joints")
+    L = np.array([np.linalg.norm(J[j] - J[p]) for p, j in bones])
+    share = extra * L / L.sum()
+    k = np.floor(share).astype(int)
+    for i in np.argsort(-(share - k))[: extra - k.sum()]:
+        k[i] += 1
+    per_bone = {j: int(k[i]) for i, (_, j) in enumerate(bones)}
+    joints, parent, new_id = [], [], {}
+    for j in range(len(J)):
+        p = int(P[j])
+        up = new_id[p] if p >= 0 else -1
+        for s in range(1, per_bone.get(j, 0) + 1):      # intermediate joints of bone p -> j
+            t = s / (per_bone[j] + 1)
+            joints.append(J[p] + t * (J[j] - J[p]))
+            parent.append(up)
+            up = len(joints) - 1
+        joints.append(J[j])
+        parent.append(up)
+        new_id[j] = len(joints) - 1
+    return np.array(joints), np.array(parent, dtype=np.int32)
+
+
 def _capsule_occupancy(centers: np.ndarray, scale: float) -> np.ndarray:
     inside = np.zeros(len(centers), dtype=bool)
     for a, b, r in _CAPSULES:
@@ -131,7 +162,7 @@ def figure_mesh_for_tets(target_tets: int, scale: float = 1.0, rel_tol: float = 
     """Bisect the cell edge h until the tet count is within ``rel_tol`` of the target."""
     lo_h, hi_h = 1e-4 * scale, 0.2 * scale      # small h -> many tets
     best = None
-    for _ in range(60):
+    for it in range(60):
         h = np.sqrt(lo_h * hi_h)
         X, T, joints, parent = figure_mesh(h, scale)
         m = len(T)
@@ -142,6 +173,10 @@ def figure_mesh_for_tets(target_tets: int, scale: float = 1.0, rel_tol: float = 
         if m > target_tets:
             lo_h = h
         else:
+            if it == 0:
+                # first try already too coarse: bracket from tets ~ h^-3 instead of
+                # bisecting toward the far lower end (a grid too large to build)
+                lo_h = h * (m / target_tets) ** (1.0 / 3.0) * 0.8
             hi_h = h
     X, T, joints, parent, h = best
     return X, T, joints, parent, h

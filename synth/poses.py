@@ -66,3 +66,41 @@ def bar_twist_pose(nx=4, ny=4, nz=16, turn_deg=90.0, shift=0.5):
     Q = rodrigues([0.0, 0.0, 1.0], np.deg2rad(turn_deg))
     t = c - Q @ c + np.array([0.0, 0.0, shift])
     return np.stack([_pack(np.eye(3), np.zeros(3)), _pack(Q, t)])
+
+
+def figure_animation(joints, parent, seed, frames, fps=30.0, max_angle_deg=45.0, max_root_shift=0.1):
+    """A smooth pose sequence (one animated character) for warm-started solves.
+
+    For each joint (``numpy.random.default_rng(seed)``): a fixed axis ~
+    normalised Gaussian, amplitude ~ U(0, max_angle), frequency ~ U(0.3, 1) Hz
+    and phase ~ U(0, 2 pi); at frame f (time f / fps) the joint turns by
+    amplitude * sin(2 pi frequency t + phase) about its rest position.  The root
+    also shifts by max_root_shift * sin(...) per axis with its own frequencies
+    and phases.  Returns (frames, H, 12) forward-kinematics transforms.
+    """
+    joints = np.asarray(joints, dtype=np.float64)
+    H = len(joints)
+    rng = np.random.default_rng(seed)
+    axis = rng.normal(size=(H, 3))
+    amp = np.deg2rad(rng.uniform(0.0, max_angle_deg, size=H))
+    freq = rng.uniform(0.3, 1.0, size=H)
+    phase = rng.uniform(0.0, 2 * np.pi, size=H)
+    rfreq = rng.uniform(0.3, 1.0, size=3)
+    rphase = rng.uniform(0.0, 2 * np.pi, size=3)
+    out = np.zeros((frames, H, 12))
+    for f in range(frames):
+        t = f / fps
+        W = np.zeros((H, 4, 4))
+        for j in range(H):
+            R = rodrigues(axis[j], amp[j] * np.sin(2 * np.pi * freq[j] * t + phase[j]))
+            L = np.eye(4)
+            L[:3, :3] = R
+            L[:3, 3] = joints[j] - R @ joints[j]
+            if parent[j] < 0:
+                L[:3, 3] += max_root_shift * np.sin(2 * np.pi * rfreq * t + rphase)
+                W[j] = L
+            else:
+                assert parent[j] < j, "joints must be ordered parents-first"
+                W[j] = W[parent[j]] @ L
+        out[f] = W[:, :3, :4].reshape(H, 12)
+    return out

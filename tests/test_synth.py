@@ -85,3 +85,37 @@ def test_bar_twist_pose():
     assert np.allclose(M[1][:, :3] @ c + M[1][:, 3], c + [0, 0, 0.5])
     assert np.allclose(M[1][:, :3] @ [1, 0, 0], [0, 1, 0])
     assert len(cfg["pin_verts"]) == 50
+
+
+def test_character_rig_subdivides_bones():
+    from synth import character_rig, figure_rig
+    J, P = character_rig(40)
+    J0, P0 = figure_rig()
+    assert len(J) == 40 and all(P[j] < j for j in range(40)) and P[0] == -1
+    # every original joint survives, and every new joint lies on an original bone
+    ids = [int(np.argmin(np.linalg.norm(J - o, axis=1))) for o in J0]
+    assert all(np.allclose(J[i], o) for i, o in zip(ids, J0))
+    bones0 = [(J0[p], J0[j]) for j, p in enumerate(P0) if p >= 0]
+    for j in set(range(40)) - set(ids):
+        on = [np.linalg.norm(np.cross(J[j] - a, b - a)) / np.linalg.norm(b - a) < 1e-12 and
+              0 < np.dot(J[j] - a, b - a) < np.dot(b - a, b - a) for a, b in bones0]
+        assert any(on)
+    # chains: the original parent of each original joint is still an ancestor
+    for j, p in enumerate(P0):
+        if p < 0:
+            continue
+        a = P[ids[j]]
+        while a != ids[p]:
+            assert a > ids[p]
+            a = P[a]
+
+
+def test_figure_animation_is_smooth_and_rigid():
+    from synth import figure_animation, figure_rig
+    J, P = figure_rig()
+    A = figure_animation(J, P, 3, 20)
+    Q = A.reshape(20, 15, 3, 4)[:, :, :, :3]
+    assert np.allclose(np.einsum("fhji,fhjk->fhik", Q, Q), np.eye(3), atol=1e-12)
+    assert np.allclose(np.linalg.det(Q), 1.0)
+    step = np.abs(np.diff(A, axis=0)).max()
+    assert 0 < step < 0.3          # frame-to-frame motion at 30 frames/s
