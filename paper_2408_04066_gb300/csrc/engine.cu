@@ -85,7 +85,7 @@ mfem_status upload(mfem_ctx* c, U** dst, const U* src, size_t count) {
 
 void free_slots(mfem_ctx* c) {
     SlotDev& S = c->slot;
-    void* ptrs[] = {S.xf, S.xf_prev, S.xpred, S.dcorr, S.x, S.xp, S.g, S.ge, S.Ke, S.val, S.dinv, S.vec, S.part, S.sc, S.active, S.alpha, S.outbuf};
+    void* ptrs[] = {S.xf, S.xf_prev, S.xpred, S.dcorr, S.tol2, S.x, S.xp, S.g, S.ge, S.Ke, S.val, S.dinv, S.vec, S.part, S.sc, S.active, S.alpha, S.outbuf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     int prec = S.prec;
@@ -104,7 +104,7 @@ size_t bytes_per_slot(const mfem_ctx* c) {
     const size_t kt = c->slot.prec == 1 ? 4 : 8;
     const size_t slots = (size_t)c->plan.slice_ptr.back();
     return H * 12 * 8 + 4 * n * 3 * 8 + m * 12 * 8 + m * kKe * kt + slots * 9 * kt + n * 9 * kt +
-           kVecStride * npad32((int)n) * kt + (size_t)part_tiles_for(c) * 4 * 8 + sizeof(ProbScal) + 4 + 8 +
+           kVecStride * npad32((int)n) * kt + (size_t)part_tiles_for(c) * 4 * 8 + sizeof(ProbScal) + 4 + 8 + 8 +
            H * 12 * 8 + (c->opt.init == MFEM_INIT_WARM ? 2 * n * 3 * 8 : 0);
 }
 
@@ -141,6 +141,7 @@ mfem_status alloc_slots(mfem_ctx* c, int B) {
     AL(S.sc, B * sizeof(ProbScal));
     AL(S.active, B * sizeof(int));
     AL(S.alpha, B * sizeof(double));
+    AL(S.tol2, B * sizeof(double));
 #undef AL
     CK(cudaMemset(S.sc, 0, B * sizeof(ProbScal)));
     CK(cudaMemset(S.val, 0, B * slots * 9 * kt));   // padding slots stay zero
@@ -289,15 +290,19 @@ mfem_status upload_active(mfem_ctx* c, int B, const std::vector<int>& flags) {
     return MFEM_OK;
 }
 
-mfem_status upload_alpha(mfem_ctx* c, int B) {
+// B doubles -> device through a staging region that is not rewritten before
+// the copy has run
+mfem_status upload_doubles(mfem_ctx* c, int B, const double* v, double* dst) {
     int pos = 0;
     mfem_status st = next_stage(c, pos);
     if (st != MFEM_OK) return st;
     double* h = c->alpha_ring + (size_t)pos * c->slot.cap;
-    for (int b = 0; b < B; ++b) h[b] = c->alpha_host[b];
-    CK(cudaMemcpyAsync(c->slot.alpha, h, B * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    for (int b = 0; b < B; ++b) h[b] = v[b];
+    CK(cudaMemcpyAsync(dst, h, B * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     return MFEM_OK;
 }
+
+mfem_status upload_alpha(mfem_ctx* c, int B) { return upload_doubles(c, B, c->alpha_host, c->slot.alpha); }
 
 void synced(std::vector<Group>& gs) {
     for (auto& g : gs) g.ctx->ring_pos = 0;
@@ -401,7 +406,7 @@ mfem_status autotune_tile(mfem_ctx* c, std::vector<Group>& gs) {
     ElemArgs a = elem_args(c);
     for (int tile : kPcgTiles) {
         for (int rep = 0; rep < 2; ++rep) {
-            launch_pcg_init(a, gs[0].B, tile, 0.0, 1 << 30, c->stream);
+            launch_pcg_init(a, gs[0].B, tile, 0.0, 1 << 30, nullptr, c->stream);
             CK(cudaEventRecord(e0, c->stream));
             mfem_status st = c->slot.prec == 1 ? run_pcg<float>(c, gs, 1, tile, 20, false)
                                                : run_pcg<double>(c, gs, 0, tile, 20, false);
@@ -600,7 +605,20 @@ mfem_status advance(std::vector<Group>& gs) {
             }
             mfem_status st = upload_active(gc, g.B, start);
             if (st != MFEM_OK) return st;
-            launch_pcg_init(elem_args(gc), g.B, c->tile_rows, gc->opt.cg_tol * gc->opt.cg_tol, gc->opt.cg_max, s);
+            // PCG target of this Newton step: cg_tol, loosened when a smaller
+            // reduction already reaches newton_tol (half of what the linear model
+            // says is needed), at most 0.5
+            std::vector<double> t2(g.B, 0.0);
+            for (int b = 0; b < g.B; ++b) {
+                const ProbHost& p = g.ph[b];
+                double eta = gc->opt.cg_tol;
+                if (start[b] && !p.pred && p.g0 > 0.0 && p.gn > 0.0)
+                    eta = std::min(0.5, std::max(eta, 0.5 * gc->opt.newton_tol * p.g0 / p.gn));
+                t2[b] = eta * eta;
+            }
+            st = upload_doubles(gc, g.B, t2.data(), gc->slot.tol2);
+            if (st != MFEM_OK) return st;
+            launch_pcg_init(elem_args(gc), g.B, c->tile_rows, 0.0, gc->opt.cg_max, gc->slot.tol2, s);
             gc->prof.launches++;
             for (int b = 0; b < g.B; ++b)
                 if (start[b]) g.ph[b].in_pcg = 1;

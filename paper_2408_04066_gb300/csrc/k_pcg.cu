@@ -16,7 +16,7 @@ namespace {
 
 // r = -g, z = D^{-1} r, dx = 0, p_old = 0; rho = r.z, rr0 = r.r per problem.
 template <typename T>
-__global__ void k_pcg_init(ElemArgs A, double tol2, int maxit) {
+__global__ void k_pcg_init(ElemArgs A, double tol2, int maxit, const double* __restrict__ tol2_b) {
     const int b = blockIdx.y;
     if (!A.slot.active[b]) return;
     const int n = A.mesh.n;
@@ -54,7 +54,7 @@ __global__ void k_pcg_init(ElemArgs A, double tol2, int maxit) {
         sc->alpha_f = 0.f;
         sc->beta_f = 0.f;
         sc->iter = 0;
-        sc->tol2 = tol2;
+        sc->tol2 = tol2_b ? tol2_b[b] : tol2;
         sc->maxit = maxit;
         sc->state = (tot[1] > 0.0 && tot[0] > 0.0 && maxit > 0) ? kActive : kConverged;
     }
@@ -312,10 +312,11 @@ cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units
 
 }  // namespace
 
-void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int maxit, cudaStream_t s) {
+void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int maxit, const double* tol2_b,
+                     cudaStream_t s) {
     dim3 grid((a.mesh.n + tile_rows - 1) / tile_rows, B);
-    if (a.slot.prec == 1) k_pcg_init<float><<<grid, tile_rows, 0, s>>>(a, tol2, maxit);
-    else k_pcg_init<double><<<grid, tile_rows, 0, s>>>(a, tol2, maxit);
+    if (a.slot.prec == 1) k_pcg_init<float><<<grid, tile_rows, 0, s>>>(a, tol2, maxit, tol2_b);
+    else k_pcg_init<double><<<grid, tile_rows, 0, s>>>(a, tol2, maxit, tol2_b);
 }
 
 template <typename T>

@@ -53,6 +53,7 @@ struct SlotDev {
     ProbScal* sc = nullptr;  // [B]
     int* active = nullptr;   // [B]
     double* alpha = nullptr; // [B] step length for update / trial
+    double* tol2 = nullptr;  // [B] squared relative PCG residual target of the current Newton step
     double* outbuf = nullptr;  // [B][n][3] caller-order staging
 };
 
@@ -107,7 +108,9 @@ void launch_diag(const ElemArgs& a, int b, unsigned* out3, cudaStream_t s);
 // PCG: init (r = -g, z = D^{-1} r, rho, |r0|) and `iters` iterations (two
 // launches each) over every problem of a descriptor table; tiles of
 // tile_rows rows (64, 128 or 256), n_units = total tiles.
-void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int maxit, cudaStream_t s);
+// tol2_b: per-problem squared tolerances on the device, or null for tol2 for all.
+void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int maxit, const double* tol2_b,
+                     cudaStream_t s);
 template <typename T>
 cudaError_t launch_pcg_iters(const PcgDesc<T>* descs_dev, int n_probs, int n_units, int tile_rows, int iters,
                              cudaStream_t s);
