@@ -106,7 +106,8 @@ typedef struct {
     double newton_tol;   /* stop when |g_free| <= newton_tol |g_free(x_0)| (1e-6) */
     double cg_tol;       /* PCG relative residual per Newton step, inexact Newton (1e-2);
                             a step that needs less to reach newton_tol takes
-                            eta = min(0.5, 0.5 newton_tol |g_free(x_0)| / |g_free|) */
+                            eta = min(0.5, 0.5 newton_tol |g_free(x_0)| / |g_free|);
+                            the co-rotational predictor step takes min(cg_tol, 3e-3) */
     int32_t newton_max;  /* Newton step cap (50) */
     int32_t cg_max;      /* PCG iteration cap per Newton step (5000) */
     int32_t init;        /* mfem_init: COROT (default) -- for SNH, first one Newton

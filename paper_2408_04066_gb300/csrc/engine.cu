@@ -20,6 +20,7 @@ constexpr int kLsMax = 20;           // halvings
 constexpr double kLsNoise = 1.0e-10; // predicted decrease below this * |E|: take the step
 constexpr int kPcgTiles[3] = {64, 128, 256};   // PCG rows per block the autotuner times
 constexpr int kPcgChunk = 16;                   // PCG iterations enqueued between convergence checks
+constexpr double kPredTol = 3e-3;   // PCG target of the co-rotational predictor step (at most cg_tol)
 }  // namespace
 
 namespace mfem {
@@ -607,11 +608,14 @@ mfem_status advance(std::vector<Group>& gs) {
             if (st != MFEM_OK) return st;
             // PCG target of this Newton step: cg_tol, loosened when a smaller
             // reduction already reaches newton_tol (half of what the linear model
-            // says is needed), at most 0.5
+            // says is needed), at most 0.5.  The predictor step is solved tighter:
+            // its error, not the SNH nonlinearity, would otherwise set where the
+            // first SNH step starts (measured: 3e-3 saves ~8% of PCG iterations
+            // and a quarter of a Newton step on the 200k figure against 1e-2)
             std::vector<double> t2(g.B, 0.0);
             for (int b = 0; b < g.B; ++b) {
                 const ProbHost& p = g.ph[b];
-                double eta = gc->opt.cg_tol;
+                double eta = p.pred ? std::min(gc->opt.cg_tol, kPredTol) : gc->opt.cg_tol;
                 if (start[b] && !p.pred && p.g0 > 0.0 && p.gn > 0.0)
                     eta = std::min(0.5, std::max(eta, 0.5 * gc->opt.newton_tol * p.g0 / p.gn));
                 t2[b] = eta * eta;
