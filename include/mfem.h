@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MFEM_ABI_VERSION 3
+#define MFEM_ABI_VERSION 4
 
 typedef enum {
     MFEM_OK = 0,
@@ -58,6 +58,7 @@ typedef enum { MFEM_CLUSTER_BONE = 0, MFEM_CLUSTER_JOINT = 1, MFEM_CLUSTER_MIDPO
 typedef enum { MFEM_INIT_RIGID = 0, MFEM_INIT_REST = 1, MFEM_INIT_WARM = 2, MFEM_INIT_COROT = 3 } mfem_init;
 typedef enum { MFEM_MEM_HOST = 0, MFEM_MEM_DEVICE = 1 } mfem_memory;
 typedef enum { MFEM_ROT_RIG = 0, MFEM_ROT_POLAR = 1 } mfem_rotation;
+typedef enum { MFEM_PRECOND_BLOCK_JACOBI = 0, MFEM_PRECOND_TWO_LEVEL = 1 } mfem_precond;
 
 /* Material (§4 "A solver friendly to variant energies"; §4 "Allowing
  * heterogeneous material").  Densities, with S the element stretch:
@@ -138,6 +139,15 @@ typedef struct {
                             coupled through the pins only.  Newton steps use the
                             Hessian at fixed R and are line-searched on E for every
                             model */
+    int32_t precond;     /* MFEM_PRECOND_TWO_LEVEL (default): 3x3 block Jacobi plus an
+                            additive coarse correction on the six rigid modes of
+                            aggregates of consecutive (Morton-ordered) vertices,
+                            its matrix the rest-shape Hessian's, inverted once per
+                            mesh and turned per pose with each aggregate's handle
+                            rotation; used from the second Newton step of a pose
+                            (the first step from the rigid guess, whose residual
+                            sits at the cluster boundaries, uses block Jacobi).
+                            MFEM_PRECOND_BLOCK_JACOBI: block Jacobi only */
 } mfem_options;
 
 /* Per-pose result statistics. */
@@ -172,6 +182,8 @@ typedef struct {
     int32_t tile_rows;        /* PCG tile in use */
     int32_t grid_blocks;      /* PCG blocks per launch (tiles of all problems) */
     int64_t element_updates;  /* per-tet local steps (a1) of the Newton element passes */
+    int32_t coarse_dof;       /* dimension of the two-level coarse space (0: none) */
+    int32_t coarse_launches;  /* coarse-solve and correction launches (two-level) */
 } mfem_profile;
 
 typedef struct mfem_ctx mfem_ctx;

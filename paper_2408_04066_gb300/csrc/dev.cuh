@@ -38,8 +38,17 @@ struct ProbScal {
     double alpha_ls, pad0;
     float alpha_f, beta_f;   // FP32 copies of alpha and beta for the FP32 kernels
     int iter, state, maxit, active;
-    unsigned tk_a, tk_b, tk_g, tk_e, tk_s, tk_init, tk_pad0, tk_pad1;
+    unsigned tk_a, tk_b, tk_g, tk_e, tk_s, tk_init, tk_c;
+    int cinit;   // two-level: the next correction is the first of this solve (beta = 0)
 };
+
+// Two-level preconditioner constants: restriction partials are formed per unit
+// of 64 rows (aggregates hold a power-of-two multiple of 64 vertices) and the
+// coarse product is split into slices of kCoarseKC columns of A_c^{-1}.
+constexpr int kCoarseRows = 64;
+constexpr int kCoarseKC = 512;
+// row stride of the stored A_c^{-1} (rows padded with zeros to 32 floats)
+__host__ __device__ __forceinline__ int coarse_ld(int N) { return (N + 31) & ~31; }
 
 // One PCG problem (a pose of a mesh) in a descriptor table.
 template <typename T>
@@ -54,6 +63,15 @@ struct PcgDesc {
     double* part;          // [tiles][4] tile partials
     ProbScal* sc;
     int n_rows, n_tiles, unit_begin, pad;
+    // two-level preconditioner (coarse = 0: block Jacobi only for this solve)
+    const float4* crel;    // [n] rest offset from the aggregate centroid, w = 1 free / 0 pin
+    const int* agg_handle; // [n_agg]
+    const double* xf;      // [H][12] the problem's pose
+    float* rcp;            // [ceil(n/64)][6] restriction partials per 64-row unit
+    float* rcs;            // [coarse_n] per-aggregate sums of rcp (aggregates over 64 rows)
+    const float* rc;       // the coarse residual read by the coarse product: rcp or rcs
+    float* ec;             // [ceil(coarse_n / kCoarseKC)][coarse_n] partial coarse corrections
+    int coarse, agg_shift, coarse_n, pad2;
 };
 
 // Programmatic dependent launch: wait for the preceding grid of the stream to

@@ -86,7 +86,7 @@ mfem_status upload(mfem_ctx* c, U** dst, const U* src, size_t count) {
 
 void free_slots(mfem_ctx* c) {
     SlotDev& S = c->slot;
-    void* ptrs[] = {S.xf, S.xf_prev, S.xpred, S.dcorr, S.tol2, S.x, S.xp, S.g, S.ge, S.Ke, S.val, S.dinv, S.vec, S.part, S.sc, S.active, S.alpha, S.outbuf};
+    void* ptrs[] = {S.xf, S.xf_prev, S.xpred, S.dcorr, S.tol2, S.coarse_on, S.rcp, S.ec, S.rcs, S.x, S.xp, S.g, S.ge, S.Ke, S.val, S.dinv, S.vec, S.part, S.sc, S.active, S.alpha, S.outbuf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     int prec = S.prec;
@@ -94,6 +94,9 @@ void free_slots(mfem_ctx* c) {
     S.prec = prec;
     c->slot_bytes = 0;
 }
+
+// slices of the coarse product (ec partials per problem)
+size_t coarse_ks(const mfem_ctx* c) { return ((size_t)c->mesh.coarse_n + kCoarseKC - 1) / kCoarseKC; }
 
 int part_tiles_for(const mfem_ctx* c) {
     int a = (c->plan.n + 31) / 32, b = (c->plan.m + kTetTile - 1) / kTetTile;
@@ -106,7 +109,8 @@ size_t bytes_per_slot(const mfem_ctx* c) {
     const size_t slots = (size_t)c->plan.slice_ptr.back();
     return H * 12 * 8 + 4 * n * 3 * 8 + m * 12 * 8 + m * kKe * kt + slots * 9 * kt + n * 9 * kt +
            kVecStride * npad32((int)n) * kt + (size_t)part_tiles_for(c) * 4 * 8 + sizeof(ProbScal) + 4 + 8 + 8 +
-           H * 12 * 8 + (c->opt.init == MFEM_INIT_WARM ? 2 * n * 3 * 8 : 0);
+           H * 12 * 8 + (c->opt.init == MFEM_INIT_WARM ? 2 * n * 3 * 8 : 0) + 4 +
+           (c->mesh.coarse_n > 0 ? ((n + 255) / 256) * 24 * 4 + (coarse_ks(c) + 1) * c->mesh.coarse_n * 4 + 128 : 0);
 }
 
 mfem_status alloc_slots(mfem_ctx* c, int B) {
@@ -143,6 +147,14 @@ mfem_status alloc_slots(mfem_ctx* c, int B) {
     AL(S.active, B * sizeof(int));
     AL(S.alpha, B * sizeof(double));
     AL(S.tol2, B * sizeof(double));
+    AL(S.coarse_on, B * sizeof(int));
+    if (c->mesh.coarse_n > 0) {
+        S.rcp_stride = (((size_t)n + 255) / 256) * (256 / kCoarseRows) * 6;
+        AL(S.rcp, B * S.rcp_stride * sizeof(float));
+        AL(S.ec, B * coarse_ks(c) * c->mesh.coarse_n * sizeof(float));
+        S.rcs_stride = ((size_t)c->mesh.coarse_n + 31) & ~(size_t)31;
+        AL(S.rcs, B * S.rcs_stride * sizeof(float));
+    }
 #undef AL
     CK(cudaMemset(S.sc, 0, B * sizeof(ProbScal)));
     CK(cudaMemset(S.val, 0, B * slots * 9 * kt));   // padding slots stay zero
@@ -200,6 +212,8 @@ void end_profile(mfem_ctx* c) {
     P.pcg_bytes = c->prof.pcg_bytes;
     P.element_bytes = c->prof.element_bytes;
     P.element_updates = c->prof.element_updates;
+    P.coarse_dof = c->mesh.coarse_n;
+    P.coarse_launches = c->prof.coarse_launches;
     P.pcg_iters = c->prof.pcg_iters;
     P.tile_rows = c->tile_rows;
     P.grid_blocks = c->grid_blocks;
@@ -240,11 +254,17 @@ double element_bytes(const mfem_ctx* c) {
 }
 
 template <typename T>
-void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc<T>>& out, int& units) {
+void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc<T>>& out, int& units,
+                 std::vector<CoarseJob>* jobs = nullptr) {
     units = 0;
     for (auto& g : gs) {
         mfem_ctx* c = g.ctx;
         if (c->slot.prec != prec) continue;
+        const int first = (int)out.size();
+        bool any_coarse = false;
+        for (int b = 0; b < g.B; ++b) any_coarse |= g.ph[b].active && g.ph[b].in_pcg && g.ph[b].coarse;
+        if (jobs && any_coarse && c->mesh.coarse_n > 0)
+            jobs->push_back(CoarseJob{c->mesh.Ainv, c->mesh.coarse_n, first, 0, c->plan.agg_size / kCoarseRows});
         const int n = c->plan.n;
         const size_t slots = (size_t)c->plan.slice_ptr.back();
         for (int b = 0; b < g.B; ++b) {
@@ -265,9 +285,22 @@ void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc
             d.n_tiles = (n + tile - 1) / tile;
             d.unit_begin = units;
             d.pad = 0;
+            d.coarse = g.ph[b].coarse && c->mesh.coarse_n > 0;
+            d.crel = c->mesh.crel;
+            d.agg_handle = c->mesh.agg_handle;
+            d.xf = c->slot.xf + (size_t)b * c->plan.H * 12;
+            d.rcp = c->slot.rcp ? c->slot.rcp + (size_t)b * c->slot.rcp_stride : nullptr;
+            d.ec = c->slot.ec ? c->slot.ec + (size_t)b * coarse_ks(c) * c->mesh.coarse_n : nullptr;
+            d.rcs = c->slot.rcs ? c->slot.rcs + (size_t)b * c->slot.rcs_stride : nullptr;
+            d.rc = c->plan.agg_size == kCoarseRows ? d.rcp : d.rcs;
+            d.agg_shift = c->mesh.agg_shift;
+            d.coarse_n = c->mesh.coarse_n;
+            d.pad2 = 0;
             units += d.n_tiles;
             out.push_back(d);
         }
+        if (jobs && !jobs->empty() && jobs->back().d0 == first && jobs->back().Ainv == c->mesh.Ainv)
+            jobs->back().nd = (int)out.size() - first;
     }
 }
 
@@ -305,6 +338,16 @@ mfem_status upload_doubles(mfem_ctx* c, int B, const double* v, double* dst) {
 
 mfem_status upload_alpha(mfem_ctx* c, int B) { return upload_doubles(c, B, c->alpha_host, c->slot.alpha); }
 
+mfem_status upload_ints(mfem_ctx* c, int B, const int* v, int* dst) {
+    int pos = 0;
+    mfem_status st = next_stage(c, pos);
+    if (st != MFEM_OK) return st;
+    int* h = c->active_host + (size_t)pos * c->slot.cap;
+    for (int b = 0; b < B; ++b) h[b] = v[b];
+    CK(cudaMemcpyAsync(dst, h, B * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    return MFEM_OK;
+}
+
 void synced(std::vector<Group>& gs) {
     for (auto& g : gs) g.ctx->ring_pos = 0;
 }
@@ -323,9 +366,13 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
                     bool one_chunk = false) {
     mfem_ctx* c = c0;
     std::vector<PcgDesc<T>> d;
+    std::vector<CoarseJob> jobs;
     int units = 0;
-    build_descs<T>(gs, tile, prec, d, units);
+    build_descs<T>(gs, tile, prec, d, units, &jobs);
     if (d.empty()) return MFEM_OK;
+    const int nj = (int)jobs.size();
+    double coarse_bytes = 0.0;   // A_c^{-1} streamed once per iteration per mesh
+    for (const auto& j : jobs) coarse_bytes += 4.0 * j.N * coarse_ld(j.N);
     const size_t bytes = d.size() * sizeof(PcgDesc<T>);
     if (2 * bytes > c->descs_cap) {   // grow: wait until no copy reads the old buffers
         CK(cudaStreamSynchronize(c->stream));
@@ -344,7 +391,7 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
     CK(cudaMemcpyAsync((void*)dst, hst, bytes, cudaMemcpyHostToDevice, c->stream));
     c->grid_blocks = units;
     if (max_iters > 0) {
-        CK(launch_pcg_iters<T>(dst, (int)d.size(), units, tile, max_iters, c->stream));
+        CK(launch_pcg_iters<T>(dst, (int)d.size(), units, tile, max_iters, jobs.data(), nj, c->stream));
         return MFEM_OK;
     }
     int cap = 0;
@@ -354,11 +401,15 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
         const int n_it = std::min(kPcgChunk, cap - done);
         if (one_chunk && done > 0) break;
         int pe = count ? c->prof.begin(2, c->stream) : -1;
-        CK(launch_pcg_iters<T>(dst, (int)d.size(), units, tile, n_it, c->stream));
+        CK(launch_pcg_iters<T>(dst, (int)d.size(), units, tile, n_it, jobs.data(), nj, c->stream));
         if (count) {
             c->prof.end(pe, c->stream);
-            c->prof.launches += 2 * n_it;
+            int cl = nj > 0 ? nj + 1 : 0;
+            for (const auto& j : jobs) cl += j.agg_units > 1;
+            c->prof.launches += (2 + cl) * n_it;
             c->prof.pcg_launches += 2 * n_it;
+            c->prof.coarse_launches += cl * n_it;
+            c->prof.pcg_bytes += coarse_bytes * n_it;
         }
         bool any = false;
         for (auto& g : gs)
@@ -404,10 +455,12 @@ mfem_status autotune_tile(mfem_ctx* c, std::vector<Group>& gs) {
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
     int best_tile = 256;
+    for (auto& g : gs)
+        for (int b = 0; b < g.B; ++b) g.ph[b].coarse = 0;   // timed with block Jacobi
     ElemArgs a = elem_args(c);
     for (int tile : kPcgTiles) {
         for (int rep = 0; rep < 2; ++rep) {
-            launch_pcg_init(a, gs[0].B, tile, 0.0, 1 << 30, nullptr, c->stream);
+            launch_pcg_init(a, gs[0].B, tile, 0.0, 1 << 30, nullptr, nullptr, c->stream);
             CK(cudaEventRecord(e0, c->stream));
             mfem_status st = c->slot.prec == 1 ? run_pcg<float>(c, gs, 1, tile, 20, false)
                                                : run_pcg<double>(c, gs, 0, tile, 20, false);
@@ -524,6 +577,7 @@ mfem_status advance(std::vector<Group>& gs) {
                 p.active = 1;
                 p.pred = pred[b];
                 p.corr = corr[b];
+                p.rigid_start = start[b] == 0 && !pred[b];
                 p.g0 = gref[b];
             }
     }
@@ -622,7 +676,20 @@ mfem_status advance(std::vector<Group>& gs) {
             }
             st = upload_doubles(gc, g.B, t2.data(), gc->slot.tol2);
             if (st != MFEM_OK) return st;
-            launch_pcg_init(elem_args(gc), g.B, c->tile_rows, 0.0, gc->opt.cg_max, gc->slot.tol2, s);
+            // two-level preconditioner from the second Newton step on (the first
+            // step's residual from the rigid guess sits at the cluster boundaries,
+            // where block Jacobi does better)
+            std::vector<int> co(g.B, 0);
+            for (int b = 0; b < g.B; ++b) {   // problems already inside PCG keep their flag
+                if (!start[b]) continue;
+                ProbHost& p = g.ph[b];
+                p.coarse = gc->mesh.coarse_n > 0 && !p.pred && !(p.it == 0 && p.rigid_start);
+                co[b] = p.coarse;
+            }
+            st = upload_ints(gc, g.B, co.data(), gc->slot.coarse_on);
+            if (st != MFEM_OK) return st;
+            launch_pcg_init(elem_args(gc), g.B, c->tile_rows, 0.0, gc->opt.cg_max, gc->slot.tol2,
+                            gc->slot.coarse_on, s);
             gc->prof.launches++;
             for (int b = 0; b < g.B; ++b)
                 if (start[b]) g.ph[b].in_pcg = 1;
@@ -823,6 +890,7 @@ void mfem_default_options(mfem_options* o) {
     o->tile_rows = 0;
     o->diagnostics = 0;
     o->rotation = MFEM_ROT_RIG;
+    o->precond = MFEM_PRECOND_TWO_LEVEL;
 }
 
 const char* mfem_status_string(mfem_status s) {
@@ -863,7 +931,7 @@ void mfem_destroy(mfem_ctx* c) {
     MeshDev& M = c->mesh;
     void* ptrs[] = {M.tet, M.Dminv64, M.Dminv32, M.vol, M.cluster, M.mu, M.lam, M.X, M.vhandle, M.pin_handle_v,
                     M.vperm, M.tperm, M.slice_ptr, M.col, M.contrib_ptr, M.contrib, M.vinc_ptr, M.vinc,
-                    c->descs_dev, c->diag_dev, c->fext_dev};
+                    M.crel, M.agg_handle, M.Ainv, c->descs_dev, c->diag_dev, c->fext_dev};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     void* hp[] = {c->sc_host, c->active_host, c->alpha_host, c->alpha_ring, c->descs_host,
@@ -875,6 +943,56 @@ void mfem_destroy(mfem_ctx* c) {
     if (c->prof.stop) cudaEventDestroy(c->prof.stop);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
+}
+
+// Coarse space of the two-level preconditioner: the rest Hessian (rig at rest,
+// x = X; the co-rotational form for SNH, whose rest Hessian it equals) is
+// assembled in problem slot 0 and reduced to A_c = P^T K P, whose inverse is
+// kept per mesh.
+static mfem_status build_coarse(mfem_ctx* c) {
+    MeshDev& M = c->mesh;
+    const Plan& P = c->plan;
+    const int H = P.H;
+    std::vector<double> ident((size_t)12 * H, 0.0);
+    for (int h = 0; h < H; ++h) ident[12 * h] = ident[12 * h + 5] = ident[12 * h + 10] = 1.0;
+    int* cnb_ptr = nullptr;
+    int* cnb = nullptr;
+    mfem_status st;
+    if ((st = upload(c, &cnb_ptr, P.cnb_ptr.data(), P.cnb_ptr.size())) != MFEM_OK) return st;
+    if ((st = upload(c, &cnb, P.cnb.data(), P.cnb.size())) != MFEM_OK) {
+        cudaFree(cnb_ptr);
+        return st;
+    }
+    c->mesh_bytes -= sizeof(int) * (P.cnb_ptr.size() + P.cnb.size());
+    cudaError_t e = cudaMalloc((void**)&M.Ainv, sizeof(float) * (size_t)M.coarse_n * coarse_ld(M.coarse_n));
+    if (e == cudaSuccess) {
+        c->mesh_bytes += sizeof(float) * (size_t)M.coarse_n * coarse_ld(M.coarse_n);
+        e = cudaMemcpyAsync(c->slot.xf, ident.data(), sizeof(double) * ident.size(), cudaMemcpyHostToDevice,
+                            c->stream);
+    }
+    if (e == cudaSuccess) {
+        std::vector<int> one(1, 1);
+        st = upload_active(c, 1, one);
+        if (st != MFEM_OK) {
+            cudaFree(cnb_ptr);
+            cudaFree(cnb);
+            return st;
+        }
+        ElemArgs a = elem_args(c);
+        a.model = c->model == MFEM_ARAP ? MFEM_ARAP : MFEM_COROT;
+        a.rot_polar = 0;
+        a.fext = nullptr;
+        launch_pose_init(a, 1, 1, c->stream);
+        launch_element(a, 1, c->stream);
+        launch_assemble(a, 1, c->stream);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess)
+        e = build_coarse_inverse(M, c->slot.val, c->slot.prec, cnb_ptr, cnb, P.cnb_max, P.agg_size, M.Ainv, c->stream);
+    cudaFree(cnb_ptr);
+    cudaFree(cnb);
+    c->ring_pos = 0;
+    return cuda_check(c, e, "coarse space set-up");
 }
 
 mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets, int32_t m,
@@ -898,6 +1016,8 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
         return fail(MFEM_EINVAL, "bad tolerances or iteration caps");
     if (o.init < MFEM_INIT_RIGID || o.init > MFEM_INIT_COROT) return fail(MFEM_EINVAL, "bad init");
     if (o.rotation != MFEM_ROT_RIG && o.rotation != MFEM_ROT_POLAR) return fail(MFEM_EINVAL, "bad rotation");
+    if (o.precond != MFEM_PRECOND_BLOCK_JACOBI && o.precond != MFEM_PRECOND_TWO_LEVEL)
+        return fail(MFEM_EINVAL, "bad preconditioner");
     if (o.tile_rows != 0 && !pcg_tile_supported(o.tile_rows))
         return fail(MFEM_EINVAL, "tile_rows must be 0, 64, 128 or 256");
     if (!mat) return fail(MFEM_EINVAL, "null material");
@@ -964,8 +1084,23 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
         if (cudaEventCreate(&e) != cudaSuccess) return fail(MFEM_ECUDA, "cudaEventCreate failed");
     if (cudaEventCreate(&c->prof.start) != cudaSuccess || cudaEventCreate(&c->prof.stop) != cudaSuccess)
         return fail(MFEM_ECUDA, "cudaEventCreate failed");
+    if (o.precond == MFEM_PRECOND_TWO_LEVEL && P.n_agg > 0) {   // coarse space data (before the slots)
+        M.n_agg = P.n_agg;
+        M.agg_shift = 0;
+        while ((1 << M.agg_shift) < P.agg_size) ++M.agg_shift;
+        M.coarse_n = 6 * P.n_agg;
+        if ((st = upload(c, &M.crel, (const float4*)P.crel.data(), (size_t)P.n)) != MFEM_OK ||
+            (st = upload(c, &M.agg_handle, P.agg_handle.data(), P.agg_handle.size())) != MFEM_OK) {
+            std::string e2 = c->err;
+            return fail(st, e2);
+        }
+    }
     st = ensure_slots(c, std::max(1, o.max_batch));
     if (st != MFEM_OK) {
+        std::string e2 = c->err;
+        return fail(st, e2);
+    }
+    if (M.coarse_n > 0 && (st = build_coarse(c)) != MFEM_OK) {
         std::string e2 = c->err;
         return fail(st, e2);
     }

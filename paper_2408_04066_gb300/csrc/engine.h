@@ -25,6 +25,8 @@ struct ProbHost {
     int converged = 0;
     int pred = 0;        // co-rotational predictor step pending (SNH, COROT or WARM init)
     int corr = 0;        // after the predictor, add the last solve's rotated correction (WARM)
+    int rigid_start = 0; // the first Newton step starts from the rigid guess (block Jacobi for it)
+    int coarse = 0;      // the current PCG solve uses the two-level preconditioner
     double g0 = -1.0, gn = 0.0, energy = 0.0;
 };
 
@@ -34,14 +36,14 @@ struct Profiler {
     std::vector<int> kind;   // per event pair: 0 element, 1 assemble, 2 pcg, 3 line search, 4 other
     int used = 0;
     int launches = 0;
-    int pcg_launches = 0, element_launches = 0;
+    int pcg_launches = 0, element_launches = 0, coarse_launches = 0;
     double pcg_bytes = 0.0, element_bytes = 0.0;
     int64_t pcg_iters = 0;
     int64_t element_updates = 0;
     cudaEvent_t start = nullptr, stop = nullptr;
     void reset() {
         used = 0;
-        launches = pcg_launches = element_launches = 0;
+        launches = pcg_launches = element_launches = coarse_launches = 0;
         pcg_bytes = element_bytes = 0.0;
         pcg_iters = 0;
         element_updates = 0;

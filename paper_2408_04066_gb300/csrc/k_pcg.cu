@@ -1,5 +1,7 @@
-// PCG kernels (a5): initialisation and the two stream-ordered kernels of one
-// block-Jacobi preconditioned CG iteration over a table of problems.
+// PCG kernels (a5): initialisation and the stream-ordered kernels of one
+// preconditioned CG iteration over a table of problems.  The preconditioner is
+// 3x3 block Jacobi, or block Jacobi plus an additive coarse correction on the
+// rigid modes of vertex aggregates (two-level; set-up in k_coarse.cu).
 //
 // Paper §3, Eq. 12 and Algorithm 1 ("x = A^{-1} b"): the condensed system is
 // SPD, so it is solved by conjugate gradients (inexactly inside each Newton
@@ -14,14 +16,60 @@ namespace mfem {
 
 namespace {
 
+// Coarse residual of the rows of one block: y_i = Q_a^T r_i (the aggregate's
+// pose rotation undone), contribution P_i^T y_i = (y_i, (X_i - c_a) x y_i) of a
+// free row, summed per 64-row unit (two warps: shuffle sums, then the pair in
+// fixed order) and written to rcp_block[6 u + c].  Every thread of the block
+// calls it; rows past the end pass valid = false.
+__device__ __forceinline__ void restrict_units(const double (&r)[3], bool valid, int row, const float4* __restrict__ crel,
+                                               const int* __restrict__ agg_handle, const double* __restrict__ xf,
+                                               int agg_shift, float* __restrict__ rcp_block) {
+    __shared__ float ws[8][6];
+    float y[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (valid) {
+        const float4 v = crel[row];
+        if (v.w != 0.f) {
+            const double* Tq = xf + 12 * agg_handle[row >> agg_shift];
+            const float q0 = (float)(Tq[0] * r[0] + Tq[4] * r[1] + Tq[8] * r[2]);
+            const float q1 = (float)(Tq[1] * r[0] + Tq[5] * r[1] + Tq[9] * r[2]);
+            const float q2 = (float)(Tq[2] * r[0] + Tq[6] * r[1] + Tq[10] * r[2]);
+            y[0] = q0;
+            y[1] = q1;
+            y[2] = q2;
+            y[3] = v.y * q2 - v.z * q1;
+            y[4] = v.z * q0 - v.x * q2;
+            y[5] = v.x * q1 - v.y * q0;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) y[c] += __shfl_xor_sync(0xffffffffu, y[c], o);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0)
+#pragma unroll
+        for (int c = 0; c < 6; ++c) ws[warp][c] = y[c];
+    __syncthreads();
+    const int units = blockDim.x / kCoarseRows;
+    if ((int)threadIdx.x < 6 * units) {
+        const int u = threadIdx.x / 6, c = threadIdx.x % 6;
+        rcp_block[6 * u + c] = ws[2 * u][c] + ws[2 * u + 1][c];
+    }
+}
+
 // r = -g, z = D^{-1} r, dx = 0, p_old = 0; rho = r.z, rr0 = r.r per problem.
+// A problem with the coarse correction on (coarse_b[b]) leaves rho to the first
+// correction and writes the restriction of r instead.
 template <typename T>
-__global__ void k_pcg_init(ElemArgs A, double tol2, int maxit, const double* __restrict__ tol2_b) {
+__global__ void k_pcg_init(ElemArgs A, double tol2, int maxit, const double* __restrict__ tol2_b,
+                           const int* __restrict__ coarse_b) {
     const int b = blockIdx.y;
     if (!A.slot.active[b]) return;
     const int n = A.mesh.n;
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool coarse = coarse_b && coarse_b[b];
     double v[2] = {0.0, 0.0};
+    double r64[3] = {0.0, 0.0, 0.0};
     if (row < n) {
         const double* g = A.slot.g + ((size_t)b * n + row) * 3;
         const T* di = (const T*)A.slot.dinv + ((size_t)b * n + row) * 9;
@@ -41,12 +89,20 @@ __global__ void k_pcg_init(ElemArgs A, double tol2, int maxit, const double* __r
         }
         zp[3] = (T)0;
         zp[7] = (T)0;
+        r64[0] = (double)rr[0];
+        r64[1] = (double)rr[1];
+        r64[2] = (double)rr[2];
     }
+    if (coarse)
+        restrict_units(r64, row < n, row, A.mesh.crel, A.mesh.agg_handle, A.slot.xf + (size_t)b * A.mesh.H * 12,
+                       A.mesh.agg_shift,
+                       A.slot.rcp + (size_t)b * A.slot.rcp_stride + 6 * ((size_t)blockIdx.x * blockDim.x / kCoarseRows));
     double tot[2];
     double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
     if (tile_commit<2>(v, part, blockIdx.x, gridDim.x, &A.slot.sc[b].tk_init, 1, tot) && threadIdx.x == 0) {
         ProbScal* sc = &A.slot.sc[b];
-        sc->rho = tot[0];
+        sc->rho = coarse ? 0.0 : tot[0];
+        sc->cinit = coarse ? 1 : 0;
         sc->rr0 = tot[1];
         sc->rr = tot[1];
         sc->beta = 0.0;
@@ -56,7 +112,7 @@ __global__ void k_pcg_init(ElemArgs A, double tol2, int maxit, const double* __r
         sc->iter = 0;
         sc->tol2 = tol2_b ? tol2_b[b] : tol2;
         sc->maxit = maxit;
-        sc->state = (tot[1] > 0.0 && tot[0] > 0.0 && maxit > 0) ? kActive : kConverged;
+        sc->state = (tot[1] > 0.0 && (coarse || tot[0] > 0.0) && maxit > 0) ? kActive : kConverged;
     }
 }
 
@@ -247,7 +303,9 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
     T* zpn = (iter & 1) ? d.zp0 : d.zp1;
     T alpha, beta_unused;
     coeffs(sc, alpha, beta_unused);
+    const bool coarse = d.coarse != 0;
     double v[2] = {0.0, 0.0};
+    double r64[3] = {0.0, 0.0, 0.0};
     Partial<T> rz = Partial<T>::zero(), rr2 = Partial<T>::zero();
     if (row < d.n_rows) {
         T* zrec = zpn + 8 * (size_t)row;
@@ -268,17 +326,25 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
 #pragma unroll
         for (int i = 0; i < 3; ++i) zz[i] = di[3 * i] * rr[0] + di[3 * i + 1] * rr[1] + di[3 * i + 2] * rr[2];
         st4(zrec, zz[0], zz[1], zz[2]);
-        rz = dot3_partial(rr[0], rr[1], rr[2], zz[0], zz[1], zz[2]);
+        if (!coarse) rz = dot3_partial(rr[0], rr[1], rr[2], zz[0], zz[1], zz[2]);
         rr2 = dot3_partial(rr[0], rr[1], rr[2], rr[0], rr[1], rr[2]);
+        r64[0] = (double)rr[0];
+        r64[1] = (double)rr[1];
+        r64[2] = (double)rr[2];
     }
+    if (coarse)   // z is finished by k_pcg_correct, which also forms r.z and beta
+        restrict_units(r64, row < d.n_rows, row, d.crel, d.agg_handle, d.xf, d.agg_shift,
+                       d.rcp + 6 * ((size_t)tile * TILE / kCoarseRows));
     v[0] = warp_sum_partial(rz);
     v[1] = warp_sum_partial(rr2);
     double tot[2];
     if (tile_commit<2>(v, d.part, tile, d.n_tiles, &sc->tk_b, 1, tot, true) && threadIdx.x == 0) {
-        const double rho_new = tot[0];
-        sc->beta = sc->rho != 0.0 ? rho_new / sc->rho : 0.0;
-        sc->beta_f = (float)sc->beta;
-        sc->rho = rho_new;
+        if (!coarse) {
+            const double rho_new = tot[0];
+            sc->beta = sc->rho != 0.0 ? rho_new / sc->rho : 0.0;
+            sc->beta_f = (float)sc->beta;
+            sc->rho = rho_new;
+        }
         sc->rr = tot[1];
         const int itn = sc->iter + 1;
         sc->iter = itn;
@@ -287,10 +353,208 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
     }
 }
 
+// Coarse solve of the two-level preconditioner: e = A_c^{-1} r_c for the
+// problems d0 .. d0+nd-1 of the table (one mesh: one A_c^{-1}), up to 16 per
+// block (grid.z).  r_c is the problem's restriction partials when an aggregate
+// is one 64-row unit, else their per-aggregate sums (k_coarse_rc).  Block (grid.x, grid.y): 32 rows of A_c^{-1} over one
+// slice of kCoarseKC columns; the slice of r_c sits in shared memory as
+// [problem][column], a warp takes four rows in turn with its lanes striding the
+// columns (coalesced rows of A_c^{-1}), then shuffles each problem's sum down
+// in a fixed order.  Slice products go to ec[slice][row]; k_pcg_correct adds
+// the slices in order.
+// r_c of aggregates larger than one 64-row unit: the units' partials added in
+// unit order, for the problems d0 .. d0+nd-1 (grid.y) of one mesh.
+template <typename T>
+__global__ void k_coarse_rc(const PcgDesc<T>* __restrict__ D, int d0, int nd) {
+    pdl_wait();
+    pdl_trigger();
+    const PcgDesc<T>& q = D[d0 + blockIdx.y];
+    if (!q.coarse || q.sc->state != kActive) return;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= q.coarse_n) return;
+    const int a = k / 6, comp = k - 6 * a;
+    const int ush = q.agg_shift - 6;
+    const int n_units = (q.n_rows + kCoarseRows - 1) / kCoarseRows;
+    const int u1 = min(n_units, (a + 1) << ush);
+    float v = 0.f;
+    for (int u = a << ush; u < u1; ++u) v += q.rcp[6 * (size_t)u + comp];
+    q.rcs[k] = v;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_coarse_gemm(const float* __restrict__ Ainv, int N, int ld,
+                                                     const PcgDesc<T>* __restrict__ D, int d0, int nd) {
+    pdl_wait();
+    pdl_trigger();
+    __shared__ __align__(16) float rs[16 * kCoarseKC];
+    __shared__ const PcgDesc<T>* dp[16];
+    __shared__ int any;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int ks = blockIdx.y, pg = blockIdx.z;
+    if (t == 0) any = 0;
+    __syncthreads();
+    if (t < 16) {
+        const int q = pg * 16 + t;
+        const PcgDesc<T>* p = nullptr;
+        if (q < nd && D[d0 + q].coarse && D[d0 + q].sc->state == kActive) p = &D[d0 + q];
+        dp[t] = p;
+        if (p) atomicOr(&any, 1);
+    }
+    __syncthreads();
+    if (!any) return;
+    const int k0 = ks * kCoarseKC, klen = min(kCoarseKC, N - k0);
+    constexpr int kQ = kCoarseKC / 4;
+    for (int idx = t; idx < 16 * kQ; idx += 256) {   // r_c slice, 16-byte loads
+        const int p = idx / kQ, kk = 4 * (idx - p * kQ);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        const PcgDesc<T>* q = dp[p];
+        if (q && kk < klen) {
+            const float* src = q->rc + k0 + kk;
+            if (kk + 3 < klen) {
+                v = *reinterpret_cast<const float4*>(src);
+            } else {
+                v.x = src[0];
+                if (kk + 1 < klen) v.y = src[1];
+                if (kk + 2 < klen) v.z = src[2];
+            }
+        }
+        *reinterpret_cast<float4*>(&rs[p * kCoarseKC + kk]) = v;
+    }
+    __syncthreads();
+    // four rows per warp at once, four columns per lane (16-byte loads of rows
+    // padded to ld floats; the padding is zero): each r_c value read from
+    // shared memory feeds four rows
+    const int row0 = blockIdx.x * 32 + warp * 4;
+    float acc[4][16];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int p = 0; p < 16; ++p) acc[i][p] = 0.f;
+    const float* arow = Ainv + (size_t)row0 * ld + k0;
+#pragma unroll 2
+    for (int kk = 4 * lane; kk < klen; kk += 128) {
+        float4 a4[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            a4[i] = row0 + i < N ? __ldcs(reinterpret_cast<const float4*>(arow + (size_t)i * ld + kk))
+                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int p = 0; p < 16; ++p) {
+            const float4 rv = *reinterpret_cast<const float4*>(&rs[p * kCoarseKC + kk]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float t = acc[i][p];
+                t = fmaf(a4[i].x, rv.x, t);
+                t = fmaf(a4[i].y, rv.y, t);
+                t = fmaf(a4[i].z, rv.z, t);
+                acc[i][p] = fmaf(a4[i].w, rv.w, t);
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int p = 0; p < 16; ++p) acc[i][p] += __shfl_xor_sync(0xffffffffu, acc[i][p], o);
+    // lane l writes (row i = l / 16 + 2 h, problem p = l % 16) for h = 0, 1
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const int i = (lane >> 4) + 2 * h, p = lane & 15;
+        float mine = 0.f;
+#pragma unroll
+        for (int ii = 0; ii < 4; ++ii)
+#pragma unroll
+            for (int pp = 0; pp < 16; ++pp)
+                if (ii == i && pp == p) mine = acc[ii][pp];
+        if (row0 + i < N && dp[p]) dp[p]->ec[(size_t)ks * N + row0 + i] = mine;
+    }
+}
+
+// z_i += Q_a P_i e_a (e_a = the six coarse values of row i's aggregate, e_t +
+// e_w x (X_i - c_a) turned by the pose rotation of the aggregate), then r.z and
+// beta = rho_new / rho (0 on the first correction of a solve).  The block first
+// gathers e and Q of its aggregates into shared memory.  Problems without the
+// coarse correction return at once.
+template <typename T, int TILE>
+__global__ void __launch_bounds__(TILE) k_pcg_correct(const PcgDesc<T>* __restrict__ D, int n_probs) {
+    pdl_wait();
+    pdl_trigger();
+    const int u = blockIdx.x;
+    const PcgDesc<T>& d = D[unit_problem(D, n_probs, u)];
+    ProbScal* sc = d.sc;
+    if (!d.coarse || sc->state != kActive) return;
+    const int tile = u - d.unit_begin;
+    const int row = tile * TILE + threadIdx.x;
+    constexpr int kMaxAgg = TILE / kCoarseRows;   // aggregates a block can touch
+    __shared__ float es[kMaxAgg][6];
+    __shared__ float qs[kMaxAgg][9];
+    __shared__ float part_e[TILE];
+    const int a0 = (tile * TILE) >> d.agg_shift;
+    const int n_agg = d.coarse_n / 6;
+    const int n_ks = (d.coarse_n + kCoarseKC - 1) / kCoarseKC;
+    // slice partials of e, one load per thread, then added in slice order
+    for (int idx = threadIdx.x; idx < kMaxAgg * 6 * n_ks; idx += TILE) {
+        const int ks = idx / (kMaxAgg * 6), r = idx - ks * kMaxAgg * 6, a = a0 + r / 6;
+        if (idx < TILE) part_e[idx] = a < n_agg ? d.ec[(size_t)ks * d.coarse_n + 6 * a + r % 6] : 0.f;
+    }
+    if ((int)threadIdx.x < kMaxAgg * 9) {
+        const int ai = threadIdx.x / 9, q = threadIdx.x % 9, a = a0 + ai;
+        qs[ai][q] = a < n_agg ? (float)d.xf[12 * d.agg_handle[a] + 4 * (q / 3) + q % 3] : 0.f;
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < kMaxAgg * 6) {
+        float v = 0.f;
+        for (int ks = 0; ks < n_ks; ++ks) {
+            const int idx = ks * kMaxAgg * 6 + threadIdx.x;
+            const int a = a0 + (int)threadIdx.x / 6;
+            v += idx < TILE ? part_e[idx]
+                            : (a < n_agg ? d.ec[(size_t)ks * d.coarse_n + 6 * a + threadIdx.x % 6] : 0.f);
+        }
+        es[threadIdx.x / 6][threadIdx.x % 6] = v;
+    }
+    __syncthreads();
+    T* zp = (sc->iter & 1) ? d.zp1 : d.zp0;   // the record the next k_pcg_spmv reads
+    Partial<T> rz = Partial<T>::zero();
+    if (row < d.n_rows) {
+        T r[3], z[3];
+        ld4(d.rec + kRec * (size_t)row + kRecR, r);
+        ld4(zp + 8 * (size_t)row, z);
+        const float4 v = d.crel[row];
+        if (v.w != 0.f) {
+            const int ai = (row >> d.agg_shift) - a0;
+            const float* e = es[ai];
+            const float* Q = qs[ai];
+            const float l0 = e[0] + (e[4] * v.z - e[5] * v.y);
+            const float l1 = e[1] + (e[5] * v.x - e[3] * v.z);
+            const float l2 = e[2] + (e[3] * v.y - e[4] * v.x);
+#pragma unroll
+            for (int i = 0; i < 3; ++i) z[i] += (T)(Q[3 * i] * l0 + Q[3 * i + 1] * l1 + Q[3 * i + 2] * l2);
+            st4(zp + 8 * (size_t)row, z[0], z[1], z[2]);
+        }
+        rz = dot3_partial(r[0], r[1], r[2], z[0], z[1], z[2]);
+    }
+    double v[1] = {warp_sum_partial(rz)};
+    double tot[1];
+    if (tile_commit<1>(v, d.part, tile, d.n_tiles, &sc->tk_c, 3, tot, true) && threadIdx.x == 0) {
+        const double rho_new = tot[0];
+        if (rho_new > 0.0 && isfinite(rho_new)) {
+            sc->beta = (sc->cinit || sc->rho == 0.0) ? 0.0 : rho_new / sc->rho;
+            sc->rho = rho_new;
+        } else {   // z orthogonal to r, or the preconditioner lost definiteness: stop here
+            sc->beta = 0.0;
+            sc->state = kConverged;
+        }
+        sc->cinit = 0;
+        sc->beta_f = (float)sc->beta;
+    }
+}
+
 // Each launch may start while the previous kernel of the stream drains
 // (programmatic stream serialization); the kernels wait on it first thing.
 template <typename T, int TILE>
-cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units, int iters, cudaStream_t s) {
+cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units, int iters, const CoarseJob* jobs,
+                               int n_jobs, cudaStream_t s) {
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -302,7 +566,27 @@ cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     for (int i = 0; i < iters; ++i) {
-        cudaError_t e = cudaLaunchKernelEx(&cfg, k_pcg_spmv<T, TILE>, descs, n_probs);
+        cudaError_t e;
+        if (n_jobs > 0) {   // two-level: finish z of the current residual first
+            for (int j = 0; j < n_jobs; ++j) {
+                if (jobs[j].agg_units > 1) {   // per-aggregate sums of the unit partials
+                    cudaLaunchConfig_t rc = cfg;
+                    rc.gridDim = dim3((jobs[j].N + 255) / 256, jobs[j].nd);
+                    rc.blockDim = dim3(256);
+                    e = cudaLaunchKernelEx(&rc, k_coarse_rc<T>, descs, jobs[j].d0, jobs[j].nd);
+                    if (e != cudaSuccess) return e;
+                }
+                cudaLaunchConfig_t gc = cfg;
+                gc.gridDim = dim3((jobs[j].N + 31) / 32, (jobs[j].N + kCoarseKC - 1) / kCoarseKC, (jobs[j].nd + 15) / 16);
+                gc.blockDim = dim3(256);
+                e = cudaLaunchKernelEx(&gc, k_coarse_gemm<T>, jobs[j].Ainv, jobs[j].N, coarse_ld(jobs[j].N), descs,
+                                       jobs[j].d0, jobs[j].nd);
+                if (e != cudaSuccess) return e;
+            }
+            e = cudaLaunchKernelEx(&cfg, k_pcg_correct<T, TILE>, descs, n_probs);
+            if (e != cudaSuccess) return e;
+        }
+        e = cudaLaunchKernelEx(&cfg, k_pcg_spmv<T, TILE>, descs, n_probs);
         if (e != cudaSuccess) return e;
         e = cudaLaunchKernelEx(&cfg, k_pcg_update<T, TILE>, descs, n_probs);
         if (e != cudaSuccess) return e;
@@ -313,26 +597,28 @@ cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units
 }  // namespace
 
 void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int maxit, const double* tol2_b,
-                     cudaStream_t s) {
+                     const int* coarse_b, cudaStream_t s) {
     dim3 grid((a.mesh.n + tile_rows - 1) / tile_rows, B);
-    if (a.slot.prec == 1) k_pcg_init<float><<<grid, tile_rows, 0, s>>>(a, tol2, maxit, tol2_b);
-    else k_pcg_init<double><<<grid, tile_rows, 0, s>>>(a, tol2, maxit, tol2_b);
+    if (a.slot.prec == 1) k_pcg_init<float><<<grid, tile_rows, 0, s>>>(a, tol2, maxit, tol2_b, coarse_b);
+    else k_pcg_init<double><<<grid, tile_rows, 0, s>>>(a, tol2, maxit, tol2_b, coarse_b);
 }
 
 template <typename T>
 cudaError_t launch_pcg_iters(const PcgDesc<T>* descs, int n_probs, int n_units, int tile_rows, int iters,
-                             cudaStream_t s) {
+                             const CoarseJob* jobs, int n_jobs, cudaStream_t s) {
     switch (tile_rows) {
-        case 64: return launch_pcg_iters_t<T, 64>(descs, n_probs, n_units, iters, s);
-        case 128: return launch_pcg_iters_t<T, 128>(descs, n_probs, n_units, iters, s);
-        case 256: return launch_pcg_iters_t<T, 256>(descs, n_probs, n_units, iters, s);
+        case 64: return launch_pcg_iters_t<T, 64>(descs, n_probs, n_units, iters, jobs, n_jobs, s);
+        case 128: return launch_pcg_iters_t<T, 128>(descs, n_probs, n_units, iters, jobs, n_jobs, s);
+        case 256: return launch_pcg_iters_t<T, 256>(descs, n_probs, n_units, iters, jobs, n_jobs, s);
         default: return cudaErrorInvalidValue;
     }
 }
 
 bool pcg_tile_supported(int tile_rows) { return tile_rows == 64 || tile_rows == 128 || tile_rows == 256; }
 
-template cudaError_t launch_pcg_iters<float>(const PcgDesc<float>*, int, int, int, int, cudaStream_t);
-template cudaError_t launch_pcg_iters<double>(const PcgDesc<double>*, int, int, int, int, cudaStream_t);
+template cudaError_t launch_pcg_iters<float>(const PcgDesc<float>*, int, int, int, int, const CoarseJob*, int,
+                                             cudaStream_t);
+template cudaError_t launch_pcg_iters<double>(const PcgDesc<double>*, int, int, int, int, const CoarseJob*, int,
+                                              cudaStream_t);
 
 }  // namespace mfem

@@ -30,6 +30,11 @@ struct MeshDev {
     int* contrib = nullptr;       // [16m]
     int* vinc_ptr = nullptr;      // [n+1]
     int* vinc = nullptr;          // [4m]
+    // two-level preconditioner (coarse_n = 0: block Jacobi only)
+    int n_agg = 0, agg_shift = 0, coarse_n = 0;
+    float4* crel = nullptr;       // [n] rest offset from the aggregate centroid, w = 1 free / 0 pin
+    int* agg_handle = nullptr;    // [n_agg]
+    float* Ainv = nullptr;        // [coarse_n][coarse_ld] inverse of the rest coarse matrix (rows padded)
 };
 
 // Per-batch problem buffers of one mesh (B problems, strides in elements).
@@ -54,6 +59,12 @@ struct SlotDev {
     int* active = nullptr;   // [B]
     double* alpha = nullptr; // [B] step length for update / trial
     double* tol2 = nullptr;  // [B] squared relative PCG residual target of the current Newton step
+    int* coarse_on = nullptr;  // [B] two-level preconditioner in the current PCG solve
+    float* rcp = nullptr;    // [B][rcp_stride] restriction partials (6 floats per 64-row unit)
+    float* ec = nullptr;     // [B][ceil(coarse_n / kCoarseKC)][coarse_n] partial coarse corrections
+    float* rcs = nullptr;    // [B][rcs_stride] per-aggregate coarse residual (aggregates over 64 rows)
+    size_t rcs_stride = 0;
+    size_t rcp_stride = 0;
     double* outbuf = nullptr;  // [B][n][3] caller-order staging
 };
 
@@ -108,12 +119,24 @@ void launch_diag(const ElemArgs& a, int b, unsigned* out3, cudaStream_t s);
 // PCG: init (r = -g, z = D^{-1} r, rho, |r0|) and `iters` iterations (two
 // launches each) over every problem of a descriptor table; tiles of
 // tile_rows rows (64, 128 or 256), n_units = total tiles.
-// tol2_b: per-problem squared tolerances on the device, or null for tol2 for all.
+// tol2_b: per-problem squared tolerances on the device, or null for tol2 for all;
+// coarse_b: per-problem flags (device) of the two-level preconditioner, or null.
 void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int maxit, const double* tol2_b,
-                     cudaStream_t s);
+                     const int* coarse_b, cudaStream_t s);
+// One mesh's coarse solve inside the PCG iterations: descriptors d0 .. d0+nd-1.
+struct CoarseJob {
+    const float* Ainv;
+    int N, d0, nd, agg_units;   // agg_units: 64-row units per aggregate
+};
 template <typename T>
 cudaError_t launch_pcg_iters(const PcgDesc<T>* descs_dev, int n_probs, int n_units, int tile_rows, int iters,
-                             cudaStream_t s);
+                             const CoarseJob* jobs, int n_jobs, cudaStream_t s);
 bool pcg_tile_supported(int tile_rows);
+
+// Coarse space set-up: A_c = P^T K P of the assembled matrix `val` (problem 0 of
+// a slot, precision prec) and its FP32 inverse into Ainv (coarse_n rows of
+// coarse_ld(coarse_n) floats, zero padding).
+cudaError_t build_coarse_inverse(const MeshDev& M, const void* val, int prec, const int* cnb_ptr, const int* cnb,
+                                 int cnb_max, int agg_size, float* Ainv, cudaStream_t s);
 
 }  // namespace mfem

@@ -390,6 +390,48 @@ mfem_status plan_layout(const mfem_material* mat, const double* rest_verts, cons
     std::vector<int32_t> vf(p.vinc_ptr.begin(), p.vinc_ptr.end() - 1);
     for (int k = 0; k < m; ++k)
         for (int a = 0; a < 4; ++a) p.vinc[vf[p.tet[4 * (size_t)k + a]]++] = 4 * k + a;
+
+    // --- aggregates for the coarse space: runs of agg_size consecutive vertices
+    // of the Morton order (spatially compact), the smallest power of two >= 64
+    // that keeps 6 n_agg <= kCoarseMaxDof.  Rigid modes of the rest shape about
+    // the centroid of the aggregate's free vertices; pins take no part.
+    int agg = kCoarseUnit;
+    while (6 * (int64_t)((n + agg - 1) / agg) > kCoarseMaxDof) agg *= 2;
+    p.agg_size = agg;
+    p.n_agg = (n + agg - 1) / agg;
+    p.crel.assign((size_t)4 * n, 0.f);
+    p.agg_handle.assign(p.n_agg, 0);
+    for (int a = 0; a < p.n_agg; ++a) {
+        const int i0 = a * agg, i1 = std::min(n, i0 + agg);
+        double c[3] = {0, 0, 0};
+        int nf = 0;
+        for (int i = i0; i < i1; ++i)
+            if (!p.pinned[i]) {
+                for (int d = 0; d < 3; ++d) c[d] += p.X[3 * (size_t)i + d];
+                ++nf;
+            }
+        for (int d = 0; d < 3; ++d) c[d] = nf ? c[d] / nf : p.X[3 * (size_t)i0 + d];
+        std::vector<int> votes(p.H, 0);
+        for (int i = i0; i < i1; ++i) {
+            for (int d = 0; d < 3; ++d) p.crel[4 * (size_t)i + d] = (float)(p.X[3 * (size_t)i + d] - c[d]);
+            p.crel[4 * (size_t)i + 3] = p.pinned[i] ? 0.f : 1.f;
+            votes[p.vhandle[i]]++;
+        }
+        p.agg_handle[a] = (int32_t)(std::max_element(votes.begin(), votes.end()) - votes.begin());
+    }
+    p.cnb_ptr.assign(p.n_agg + 1, 0);
+    p.cnb.clear();
+    p.cnb_max = 0;
+    for (int a = 0; a < p.n_agg; ++a) {
+        std::vector<int32_t> js;
+        for (int i = a * agg; i < std::min(n, (a + 1) * agg); ++i)
+            for (int j : nb[i]) js.push_back(j / agg);
+        std::sort(js.begin(), js.end());
+        js.erase(std::unique(js.begin(), js.end()), js.end());
+        p.cnb.insert(p.cnb.end(), js.begin(), js.end());
+        p.cnb_ptr[a + 1] = (int32_t)p.cnb.size();
+        p.cnb_max = std::max(p.cnb_max, (int32_t)js.size());
+    }
     return MFEM_OK;
 }
 

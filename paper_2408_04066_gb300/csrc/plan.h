@@ -50,7 +50,20 @@ struct Plan {
     std::vector<int32_t> vinc_ptr;     // [n+1]
     std::vector<int32_t> vinc;         // [4 m] code: tet*4 + a
     double bbox_diag = 0.0;
+    // two-level preconditioner: aggregates of agg_size consecutive internal
+    // (Morton-ordered) vertices, each carrying the six rigid modes of its rest
+    // shape; n_agg = 0 when the mesh has no coarse space
+    int32_t agg_size = 0, n_agg = 0;
+    std::vector<float> crel;          // [n][4] X_i - c_a, w = 1 for a free vertex, 0 for a pin
+    std::vector<int32_t> agg_handle;  // [n_agg] the handle most of the aggregate's vertices cluster to
+    std::vector<int32_t> cnb_ptr, cnb;  // neighbour aggregates of each aggregate (sorted, incl. itself)
+    int32_t cnb_max = 0;
 };
+
+// Largest coarse space (6 rigid modes per aggregate) the planner builds.
+constexpr int kCoarseMaxDof = 6144;
+// Aggregates never have fewer vertices than this (one unit of the restriction).
+constexpr int kCoarseUnit = 64;
 
 // Validation, rest precompute (Eq. 5), clustering (§3.1) and pins (Eq. 6).
 // Fills the caller-order fields.  Returns MFEM_OK or an error with `err` set.

@@ -22,8 +22,9 @@ CONSTRAINTS = {"eliminate": 0, "penalty": 1}
 CLUSTER_RULES = {"bone": 0, "joint": 1, "midpoint": 2}
 INITS = {"rigid": 0, "rest": 1, "warm": 2, "corot": 3}
 ROTATIONS = {"rig": 0, "polar": 1}
+PRECONDS = {"block_jacobi": 0, "two_level": 1}
 MEM_HOST, MEM_DEVICE = 0, 1
-ABI_VERSION = 3   # MFEM_ABI_VERSION of the header these structures follow
+ABI_VERSION = 4   # MFEM_ABI_VERSION of the header these structures follow
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -43,7 +44,8 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("constraint", C.c_int32), ("k_s", C.c_double),
                 ("newton_tol", C.c_double), ("cg_tol", C.c_double), ("newton_max", C.c_int32),
                 ("cg_max", C.c_int32), ("init", C.c_int32), ("max_batch", C.c_int32),
-                ("tile_rows", C.c_int32), ("diagnostics", C.c_int32), ("rotation", C.c_int32)]
+                ("tile_rows", C.c_int32), ("diagnostics", C.c_int32), ("rotation", C.c_int32),
+                ("precond", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -61,7 +63,8 @@ class Profile(C.Structure):
                 ("pcg_bytes", C.c_double), ("pcg_iters", C.c_int64), ("element_launches", C.c_int32),
                 ("element_ms", C.c_double), ("element_bytes", C.c_double), ("assemble_ms", C.c_double),
                 ("linesearch_ms", C.c_double), ("total_ms", C.c_double), ("tile_rows", C.c_int32),
-                ("grid_blocks", C.c_int32), ("element_updates", C.c_int64)]
+                ("grid_blocks", C.c_int32), ("element_updates", C.c_int64), ("coarse_dof", C.c_int32),
+                ("coarse_launches", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -167,6 +170,8 @@ def default_options(**over):
             v = INITS[v] if isinstance(v, str) else v
         elif k == "rotation":
             v = ROTATIONS[v] if isinstance(v, str) else v
+        elif k == "precond":
+            v = PRECONDS[v] if isinstance(v, str) else v
         setattr(o, k, v)
     return o
 
