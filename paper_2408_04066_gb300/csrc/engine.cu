@@ -240,10 +240,15 @@ namespace {
 // HBM once, 3-vectors counted as 3 elements): matrix values and column ids;
 // k_pcg_spmv reads the row's z and p_old and writes p_new and q; k_pcg_update
 // reads p_new, q, dx, r and the 9-element D^-1 and writes dx, r, z.
-double pcg_bytes_per_iter(const mfem_ctx* c) {
+// With the two-level preconditioner the update also reads the aggregate offset
+// (16) and the correction reads r, z, the offset and writes z (per row); the
+// coarse product's A_c^{-1} is counted per launch in run_pcg.
+double pcg_bytes_per_iter(const mfem_ctx* c, bool coarse) {
     const double kt = c->slot.prec == 1 ? 4.0 : 8.0;
     const double nnzb = (double)c->plan.nnz_blocks, n = c->plan.n;
-    return nnzb * (9.0 * kt + 4.0) + n * (4.0 * 3.0 * kt) + n * (4.0 * 3.0 * kt + 9.0 * kt + 3.0 * 3.0 * kt);
+    double b = nnzb * (9.0 * kt + 4.0) + n * (4.0 * 3.0 * kt) + n * (4.0 * 3.0 * kt + 9.0 * kt + 3.0 * 3.0 * kt);
+    if (coarse) b += n * (16.0 + 3.0 * 3.0 * kt + 16.0);
+    return b;
 }
 
 // Element kernel: static tet data (idx 16, D_m^-1 72, W 8, cluster 4, mu/lam 16),
@@ -724,7 +729,7 @@ mfem_status advance(std::vector<Group>& gs) {
                 any_fin = true;
                 p.pcg_iters += g.ctx->sc_host[b].iter;
                 g.ctx->prof.pcg_iters += g.ctx->sc_host[b].iter;
-                g.ctx->prof.pcg_bytes += g.ctx->sc_host[b].iter * pcg_bytes_per_iter(g.ctx);
+                g.ctx->prof.pcg_bytes += g.ctx->sc_host[b].iter * pcg_bytes_per_iter(g.ctx, p.coarse);
                 g.ctx->alpha_host[b] = 1.0;
             }
         }

@@ -424,50 +424,53 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(const float* __restrict__ A
     // four rows per warp at once, four columns per lane (16-byte loads of rows
     // padded to ld floats; the padding is zero): each r_c value read from
     // shared memory feeds four rows
-    const int row0 = blockIdx.x * 32 + warp * 4;
-    float acc[4][16];
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-        for (int p = 0; p < 16; ++p) acc[i][p] = 0.f;
-    const float* arow = Ainv + (size_t)row0 * ld + k0;
-#pragma unroll 2
-    for (int kk = 4 * lane; kk < klen; kk += 128) {
-        float4 a4[4];
+    for (int pass = 0; pass < kCoarseRowPasses; ++pass) {
+        const int row0 = (blockIdx.x * kCoarseRowPasses + pass) * 32 + warp * 4;
+        if (row0 >= N) break;
+        float acc[4][16];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
-            a4[i] = row0 + i < N ? __ldcs(reinterpret_cast<const float4*>(arow + (size_t)i * ld + kk))
-                                 : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-        for (int p = 0; p < 16; ++p) {
-            const float4 rv = *reinterpret_cast<const float4*>(&rs[p * kCoarseKC + kk]);
+            for (int p = 0; p < 16; ++p) acc[i][p] = 0.f;
+        const float* arow = Ainv + (size_t)row0 * ld + k0;
+#pragma unroll 2
+        for (int kk = 4 * lane; kk < klen; kk += 128) {
+            float4 a4[4];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                float t = acc[i][p];
-                t = fmaf(a4[i].x, rv.x, t);
-                t = fmaf(a4[i].y, rv.y, t);
-                t = fmaf(a4[i].z, rv.z, t);
-                acc[i][p] = fmaf(a4[i].w, rv.w, t);
+            for (int i = 0; i < 4; ++i)
+                a4[i] = row0 + i < N ? __ldcs(reinterpret_cast<const float4*>(arow + (size_t)i * ld + kk))
+                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int p = 0; p < 16; ++p) {
+                const float4 rv = *reinterpret_cast<const float4*>(&rs[p * kCoarseKC + kk]);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    float t = acc[i][p];
+                    t = fmaf(a4[i].x, rv.x, t);
+                    t = fmaf(a4[i].y, rv.y, t);
+                    t = fmaf(a4[i].z, rv.z, t);
+                    acc[i][p] = fmaf(a4[i].w, rv.w, t);
+                }
             }
         }
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
+        for (int o = 16; o > 0; o >>= 1)
 #pragma unroll
-        for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int p = 0; p < 16; ++p) acc[i][p] += __shfl_xor_sync(0xffffffffu, acc[i][p], o);
-    // lane l writes (row i = l / 16 + 2 h, problem p = l % 16) for h = 0, 1
+                for (int p = 0; p < 16; ++p) acc[i][p] += __shfl_xor_sync(0xffffffffu, acc[i][p], o);
+        // lane l writes (row i = l / 16 + 2 h, problem p = l % 16) for h = 0, 1
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const int i = (lane >> 4) + 2 * h, p = lane & 15;
-        float mine = 0.f;
+        for (int h = 0; h < 2; ++h) {
+            const int i = (lane >> 4) + 2 * h, p = lane & 15;
+            float mine = 0.f;
 #pragma unroll
-        for (int ii = 0; ii < 4; ++ii)
+            for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-            for (int pp = 0; pp < 16; ++pp)
-                if (ii == i && pp == p) mine = acc[ii][pp];
-        if (row0 + i < N && dp[p]) dp[p]->ec[(size_t)ks * N + row0 + i] = mine;
+                for (int pp = 0; pp < 16; ++pp)
+                    if (ii == i && pp == p) mine = acc[ii][pp];
+            if (row0 + i < N && dp[p]) dp[p]->ec[(size_t)ks * N + row0 + i] = mine;
+        }
     }
 }
 
@@ -577,7 +580,8 @@ cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units
                     if (e != cudaSuccess) return e;
                 }
                 cudaLaunchConfig_t gc = cfg;
-                gc.gridDim = dim3((jobs[j].N + 31) / 32, (jobs[j].N + kCoarseKC - 1) / kCoarseKC, (jobs[j].nd + 15) / 16);
+                gc.gridDim = dim3((jobs[j].N + 32 * kCoarseRowPasses - 1) / (32 * kCoarseRowPasses),
+                                  (jobs[j].N + kCoarseKC - 1) / kCoarseKC, (jobs[j].nd + 15) / 16);
                 gc.blockDim = dim3(256);
                 e = cudaLaunchKernelEx(&gc, k_coarse_gemm<T>, jobs[j].Ainv, jobs[j].N, coarse_ld(jobs[j].N), descs,
                                        jobs[j].d0, jobs[j].nd);
