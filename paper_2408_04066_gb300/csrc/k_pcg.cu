@@ -354,8 +354,8 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
 }
 
 // Coarse solve of the two-level preconditioner: e = A_c^{-1} r_c for the
-// problems d0 .. d0+nd-1 of the table (one mesh: one A_c^{-1}), up to 16 per
-// block (grid.z).  r_c is the problem's restriction partials when an aggregate
+// problems d0 .. d0+nd-1 of the table (one mesh: one A_c^{-1}), NP (8 or 16,
+// the smallest that holds them, 16 per grid.z slice beyond) per block.  r_c is the problem's restriction partials when an aggregate
 // is one 64-row unit, else their per-aggregate sums (k_coarse_rc).  Block (grid.x, grid.y): 32 rows of A_c^{-1} over one
 // slice of kCoarseKC columns; the slice of r_c sits in shared memory as
 // [problem][column], a warp takes four rows in turn with its lanes striding the
@@ -381,20 +381,20 @@ __global__ void k_coarse_rc(const PcgDesc<T>* __restrict__ D, int d0, int nd) {
     q.rcs[k] = v;
 }
 
-template <typename T>
+template <typename T, int NP>
 __global__ void __launch_bounds__(256) k_coarse_gemm(const float* __restrict__ Ainv, int N, int ld,
                                                      const PcgDesc<T>* __restrict__ D, int d0, int nd) {
     pdl_wait();
     pdl_trigger();
-    __shared__ __align__(16) float rs[16 * kCoarseKC];
-    __shared__ const PcgDesc<T>* dp[16];
+    __shared__ __align__(16) float rs[NP * kCoarseKC];
+    __shared__ const PcgDesc<T>* dp[NP];
     __shared__ int any;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int ks = blockIdx.y, pg = blockIdx.z;
     if (t == 0) any = 0;
     __syncthreads();
-    if (t < 16) {
-        const int q = pg * 16 + t;
+    if (t < NP) {
+        const int q = pg * NP + t;
         const PcgDesc<T>* p = nullptr;
         if (q < nd && D[d0 + q].coarse && D[d0 + q].sc->state == kActive) p = &D[d0 + q];
         dp[t] = p;
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(const float* __restrict__ A
     if (!any) return;
     const int k0 = ks * kCoarseKC, klen = min(kCoarseKC, N - k0);
     constexpr int kQ = kCoarseKC / 4;
-    for (int idx = t; idx < 16 * kQ; idx += 256) {   // r_c slice, 16-byte loads
+    for (int idx = t; idx < NP * kQ; idx += 256) {   // r_c slice, 16-byte loads
         const int p = idx / kQ, kk = 4 * (idx - p * kQ);
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         const PcgDesc<T>* q = dp[p];
@@ -427,11 +427,11 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(const float* __restrict__ A
     for (int pass = 0; pass < kCoarseRowPasses; ++pass) {
         const int row0 = (blockIdx.x * kCoarseRowPasses + pass) * 32 + warp * 4;
         if (row0 >= N) break;
-        float acc[4][16];
+        float acc[4][NP];
 #pragma unroll
         for (int i = 0; i < 4; ++i)
 #pragma unroll
-            for (int p = 0; p < 16; ++p) acc[i][p] = 0.f;
+            for (int p = 0; p < NP; ++p) acc[i][p] = 0.f;
         const float* arow = Ainv + (size_t)row0 * ld + k0;
 #pragma unroll 2
         for (int kk = 4 * lane; kk < klen; kk += 128) {
@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(const float* __restrict__ A
                 a4[i] = row0 + i < N ? __ldcs(reinterpret_cast<const float4*>(arow + (size_t)i * ld + kk))
                                      : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-            for (int p = 0; p < 16; ++p) {
+            for (int p = 0; p < NP; ++p) {
                 const float4 rv = *reinterpret_cast<const float4*>(&rs[p * kCoarseKC + kk]);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
@@ -458,16 +458,16 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(const float* __restrict__ A
 #pragma unroll
             for (int i = 0; i < 4; ++i)
 #pragma unroll
-                for (int p = 0; p < 16; ++p) acc[i][p] += __shfl_xor_sync(0xffffffffu, acc[i][p], o);
-        // lane l writes (row i = l / 16 + 2 h, problem p = l % 16) for h = 0, 1
+                for (int p = 0; p < NP; ++p) acc[i][p] += __shfl_xor_sync(0xffffffffu, acc[i][p], o);
+        // lane l writes (row i, problem p) = (l / NP, l % NP) + 32 / NP rows per step
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int i = (lane >> 4) + 2 * h, p = lane & 15;
+        for (int h = 0; h < 4 * NP / 32; ++h) {
+            const int e = lane + 32 * h, i = e / NP, p = e % NP;
             float mine = 0.f;
 #pragma unroll
             for (int ii = 0; ii < 4; ++ii)
 #pragma unroll
-                for (int pp = 0; pp < 16; ++pp)
+                for (int pp = 0; pp < NP; ++pp)
                     if (ii == i && pp == p) mine = acc[ii][pp];
             if (row0 + i < N && dp[p]) dp[p]->ec[(size_t)ks * N + row0 + i] = mine;
         }
@@ -580,11 +580,16 @@ cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units
                     if (e != cudaSuccess) return e;
                 }
                 cudaLaunchConfig_t gc = cfg;
+                const int np = jobs[j].nd <= 8 ? 8 : 16;
                 gc.gridDim = dim3((jobs[j].N + 32 * kCoarseRowPasses - 1) / (32 * kCoarseRowPasses),
-                                  (jobs[j].N + kCoarseKC - 1) / kCoarseKC, (jobs[j].nd + 15) / 16);
+                                  (jobs[j].N + kCoarseKC - 1) / kCoarseKC, (jobs[j].nd + np - 1) / np);
                 gc.blockDim = dim3(256);
-                e = cudaLaunchKernelEx(&gc, k_coarse_gemm<T>, jobs[j].Ainv, jobs[j].N, coarse_ld(jobs[j].N), descs,
-                                       jobs[j].d0, jobs[j].nd);
+                if (np == 8)
+                    e = cudaLaunchKernelEx(&gc, k_coarse_gemm<T, 8>, jobs[j].Ainv, jobs[j].N, coarse_ld(jobs[j].N),
+                                           descs, jobs[j].d0, jobs[j].nd);
+                else
+                    e = cudaLaunchKernelEx(&gc, k_coarse_gemm<T, 16>, jobs[j].Ainv, jobs[j].N, coarse_ld(jobs[j].N),
+                                           descs, jobs[j].d0, jobs[j].nd);
                 if (e != cudaSuccess) return e;
             }
             e = cudaLaunchKernelEx(&cfg, k_pcg_correct<T, TILE>, descs, n_probs);
