@@ -344,7 +344,7 @@ def run_mfem(args, dist):
     peak, peak_kind = hbm_peak()
     achieved = pcg_bytes / (pcg_ms / 1e3) / 1e9 if pcg_ms > 0 else 0.0
     tr = pcg_traffic_record()
-    roof = {"kernel": "PCG iteration (k_pcg_spmv + k_pcg_update)", "bound": "hbm", "achieved": achieved,
+    roof = {"kernel": "PCG iteration (k_pcg_spmv + k_pcg_update, + k_coarse_gemm + k_pcg_correct on two-level steps)", "bound": "hbm", "achieved": achieved,
             "peak": peak, "peak_source": f"{peak_kind} hbm_gbs (copy, burst)", "unit": "GB/s",
             "frac": achieved / peak,
             "traffic": (tr["dram_bytes_per_pose_iteration"] * pcg_pose_iters / pairs if tr else None),
@@ -442,7 +442,7 @@ def _roofline(profs, total_ms):
     peak, peak_kind = hbm_peak()
     achieved = pcg_bytes / (pcg_ms / 1e3) / 1e9 if pcg_ms > 0 else 0.0
     tr = pcg_traffic_record()
-    return {"kernel": "PCG iteration (k_pcg_spmv + k_pcg_update)", "bound": "hbm", "achieved": achieved,
+    return {"kernel": "PCG iteration (k_pcg_spmv + k_pcg_update, + k_coarse_gemm + k_pcg_correct on two-level steps)", "bound": "hbm", "achieved": achieved,
             "peak": peak, "peak_source": f"{peak_kind} hbm_gbs (copy, burst)", "unit": "GB/s",
             "frac": achieved / peak,
             "traffic": tr["dram_bytes_per_pose_iteration"] * iters / pairs if tr else None,
