@@ -45,6 +45,11 @@ struct MeshEntry {
     int cap = 0;
     std::vector<ProbHost> ph;
     std::vector<uint64_t> slot_req;  // 0 = free
+    // WARM meshes: the mesh's most recent solution (x [n][3], its predictor
+    // result [n][3] and its pose [H][12]), copied into the slot of each admitted
+    // request, so every request continues from the latest frame solved
+    double* bank = nullptr;
+    int bank_state = 0;   // 0 none, 1 x and pose, 2 also the predictor result
 };
 
 }  // namespace
@@ -113,6 +118,19 @@ void mfem_server::run() {
                 peak = std::max(peak, in_use);
                 admitted.emplace_back(r.mesh, slot);
                 const size_t H = me.ctx->plan.H;
+                if (me.bank_state > 0) {
+                    mfem_ctx* c = me.ctx;
+                    const size_t n3 = (size_t)c->plan.n * 3;
+                    cudaMemcpyAsync(c->slot.x + slot * n3, me.bank, n3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    stream);
+                    if (me.bank_state == 2)
+                        cudaMemcpyAsync(c->slot.xpred + slot * n3, me.bank + n3, n3 * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, stream);
+                    cudaMemcpyAsync(c->slot.xf_prev + (size_t)slot * H * 12, me.bank + 2 * n3, H * 12 * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, stream);
+                    c->warm_kind[slot] = 1;
+                    c->xpred_valid[slot] = me.bank_state == 2;
+                }
                 cudaMemcpyAsync(me.ctx->slot.xf + (size_t)slot * H * 12, r.xf.data(), H * 12 * sizeof(double),
                                 cudaMemcpyHostToDevice, stream);
                 it = queue.erase(it);
@@ -162,6 +180,16 @@ void mfem_server::run() {
                 const size_t H = c->plan.H;
                 cudaMemcpyAsync(c->slot.xf_prev + (size_t)b * H * 12, c->slot.xf + (size_t)b * H * 12,
                                 H * 12 * sizeof(double), cudaMemcpyDeviceToDevice, stream);
+                if (me.bank && me.ph[b].status == MFEM_OK) {   // the mesh's latest frame
+                    cudaMemcpyAsync(me.bank, c->slot.x + b * n * 3, n * 3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                                    stream);
+                    if (c->xpred_valid[b])
+                        cudaMemcpyAsync(me.bank + n * 3, c->slot.xpred + b * n * 3, n * 3 * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, stream);
+                    cudaMemcpyAsync(me.bank + 2 * n * 3, c->slot.xf + (size_t)b * H * 12, H * 12 * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, stream);
+                    me.bank_state = c->xpred_valid[b] ? 2 : 1;
+                }
                 r.done = true;
                 r.t_done = now_s();
                 me.slot_req[b] = 0;
@@ -213,6 +241,9 @@ mfem_status mfem_server_add(mfem_server* s, mfem_ctx* c, int32_t* mesh_id) {
     MeshEntry me;
     me.ctx = c;
     me.cap = cap;
+    if (c->opt.init == MFEM_INIT_WARM &&
+        cudaMalloc((void**)&me.bank, sizeof(double) * ((size_t)c->plan.n * 6 + (size_t)c->plan.H * 12)) != cudaSuccess)
+        return ctx_fail(c, MFEM_ENOMEM, "warm-start bank");
     me.ph.assign(cap, ProbHost());
     me.slot_req.assign(cap, 0);
     s->used += per * cap;
@@ -292,6 +323,7 @@ void mfem_server_destroy(mfem_server* s) {
     s->cv_work.notify_all();
     if (s->worker.joinable()) s->worker.join();
     for (auto& me : s->meshes) {
+        if (me.bank) cudaFree(me.bank);
         me.ctx->owned_by_server = false;
         me.ctx->stream = me.ctx->own_stream;
         mfem_destroy(me.ctx);

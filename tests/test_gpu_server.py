@@ -70,3 +70,30 @@ def test_server_budget_refuses_too_large_mesh(mfem):
         srv.add(mfem.Context.from_config(cfg, precision="mixed"))
     assert e.value.status == mfem.MFEM_ENOMEM
     srv.close()
+
+
+def test_served_animation_continues_from_the_latest_frame(mfem):
+    """WARM meshes keep their latest solution resident: frames of one animation
+    submitted one after another reach the oracle's solutions, and after the
+    first frame take fewer Newton steps than frames started cold."""
+    from oracle import solve as S
+    from synth import figure_animation
+    cfg = dict(figure_config(3000, seeds=[]), model="snh")
+    anim = figure_animation(cfg["joints"], cfg["parent"], 21, 6)
+    so = S.Setup.from_config(cfg)
+    srv = mfem.Server(max_slots=4)
+    mid = srv.add(mfem.Context.from_config(cfg, precision="fp64", init="warm", newton_tol=1e-10, cg_tol=1e-8))
+    cold = mfem.Context.from_config(cfg, precision="fp64", newton_tol=1e-10, cg_tol=1e-8)
+    warm_it, cold_it = [], []
+    for f in range(6):
+        out, st, _ = srv.wait(srv.submit(mid, anim[f]), timeout_ms=120000)
+        xo, _ = S.solve(so, anim[f], "snh", newton_tol=1e-12)
+        assert st["converged"] == 1
+        assert np.abs(out - xo).max() / so.bbox_diag <= 1e-8, f
+        cold.set_pose(anim[f])
+        _, sc = cold.solve()
+        if f > 0:
+            warm_it.append(st["newton_iters"])
+            cold_it.append(sc["newton_iters"])
+    assert sum(warm_it) < sum(cold_it), (warm_it, cold_it)
+    srv.close()
