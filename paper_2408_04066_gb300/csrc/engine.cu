@@ -555,8 +555,8 @@ mfem_status advance(std::vector<Group>& gs) {
             if (parked) CK(cudaMemcpyAsync(gc->slot.outbuf, gc->slot.x, xbytes, cudaMemcpyDeviceToDevice, s));
             ElemArgs a = elem_args(gc);
             launch_pose_init(a, g.B, 0, s);
-            launch_element(a, g.B, s);
-            launch_assemble(a, g.B, s);
+            launch_element(a, g.B, s, false);   // forces only: the reference needs no Hessian
+            launch_gradient(a, g.B, s);
             gc->prof.launches += 3;
             st = read_scalars(gc, g.B);
             if (st != MFEM_OK) return st;
@@ -593,10 +593,16 @@ mfem_status advance(std::vector<Group>& gs) {
     for (auto& g : gs) {
         mfem_ctx* gc = g.ctx;
         bool any = false;
-        for (int pass = 0; pass < 2; ++pass) {
+        // pass 0: Newton steps (element blocks and matrix), 1: the co-rotational
+        // predictor, 2: iterates expected to meet newton_tol (forces only)
+        for (int pass = 0; pass < 3; ++pass) {
             std::vector<int> f(g.B, 0);
-            for (int b = 0; b < g.B; ++b)
-                f[b] = (g.ph[b].active && !g.ph[b].in_pcg && g.ph[b].pred == pass) ? 1 : 0;
+            for (int b = 0; b < g.B; ++b) {
+                const ProbHost& p = g.ph[b];
+                if (!p.active || p.in_pcg) continue;
+                const bool fo = !p.pred && p.expect_conv && !p.need_hess;
+                f[b] = pass == 0 ? (!p.pred && !fo) : (pass == 1 ? p.pred : fo);
+            }
             if (!any_of(f)) continue;
             any = true;
             mfem_status st = upload_active(gc, g.B, f);
@@ -604,10 +610,11 @@ mfem_status advance(std::vector<Group>& gs) {
             ElemArgs a = elem_args(gc);
             if (pass == 1) a.model = MFEM_COROT;
             int pe = gc->prof.begin(0, s);
-            launch_element(a, g.B, s);
+            launch_element(a, g.B, s, pass != 2);
             gc->prof.end(pe, s);
             int pa = gc->prof.begin(1, s);
-            launch_assemble(a, g.B, s);
+            if (pass == 2) launch_gradient(a, g.B, s);
+            else launch_assemble(a, g.B, s);
             gc->prof.end(pa, s);
             gc->prof.launches += 2;
             gc->prof.element_launches++;
@@ -651,7 +658,13 @@ mfem_status advance(std::vector<Group>& gs) {
                         p.status = MFEM_ENOTCONV;
                         continue;
                     }
+                    if (p.expect_conv && !p.need_hess) {   // tested with forces only: form the Hessian next
+                        p.need_hess = 1;
+                        continue;
+                    }
                 }
+                p.expect_conv = 0;
+                p.need_hess = 0;
                 start[b] = 1;
             }
             if (!any_of(start)) continue;
@@ -678,6 +691,7 @@ mfem_status advance(std::vector<Group>& gs) {
                 if (start[b] && !p.pred && p.g0 > 0.0 && p.gn > 0.0)
                     eta = std::min(0.5, std::max(eta, 0.5 * gc->opt.newton_tol * p.g0 / p.gn));
                 t2[b] = eta * eta;
+                if (start[b]) g.ph[b].expect_conv = !p.pred && eta > gc->opt.cg_tol;
             }
             st = upload_doubles(gc, g.B, t2.data(), gc->slot.tol2);
             if (st != MFEM_OK) return st;

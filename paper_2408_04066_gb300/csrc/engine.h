@@ -27,6 +27,9 @@ struct ProbHost {
     int corr = 0;        // after the predictor, add the last solve's rotated correction (WARM)
     int rigid_start = 0; // the first Newton step starts from the rigid guess (block Jacobi for it)
     int coarse = 0;      // the current PCG solve uses the two-level preconditioner
+    int expect_conv = 0; // the current step was solved to just reach newton_tol: test the next
+                         // iterate with forces only (no element Hessian, no matrix)
+    int need_hess = 0;   // that test failed: the next element pass forms the Hessian
     double g0 = -1.0, gn = 0.0, energy = 0.0;
 };
 

@@ -486,7 +486,8 @@ __device__ __forceinline__ double vertex_energy(const ElemArgs& A, int b, int v,
 
 // ---------------------------------------------------------------------------
 // Thread k handles tet k (k < m) and the vertex terms of vertex k (k < n).
-template <typename KT, int MODEL>
+// HESS = false: energy and forces only (a gradient test needs no Hessian).
+template <typename KT, int MODEL, bool HESS>
 __global__ void __launch_bounds__(kTetTile) k_element(ElemArgs A) {
     const int b = blockIdx.y;
     if (!A.slot.active[b]) return;
@@ -518,7 +519,8 @@ __global__ void __launch_bounds__(kTetTile) k_element(ElemArgs A) {
 #pragma unroll
             for (int i = 0; i < 3; ++i) ge[3 * a + i] = P[i][0] * G[a][0] + P[i][1] * G[a][1] + P[i][2] * G[a][2];
         KT* ke = (KT*)A.slot.Ke + ((size_t)b * m + k) * kKe;
-        if (MODEL == 2) {
+        if (!HESS) {
+        } else if (MODEL == 2) {
             bool fp64 = sizeof(KT) == 8;
             if (!fp64) {  // near-degenerate or inverted stretch: FP64 Hessian
                 const double J = S[0] * (S[1] * S[2] - S[3] * S[3]) + S[5] * (S[4] * S[3] - S[2] * S[5]) +
@@ -736,12 +738,20 @@ __global__ void k_diag(ElemArgs A, int b, unsigned* __restrict__ out3) {
 }
 
 template <typename KT>
-void launch_element_t(const ElemArgs& a, int B, cudaStream_t s) {
+void launch_element_t(const ElemArgs& a, int B, bool hess, cudaStream_t s) {
     dim3 grid((std::max(a.mesh.m, a.mesh.n) + kTetTile - 1) / kTetTile, B);
-    switch (a.model) {
-        case 0: k_element<KT, 0><<<grid, kTetTile, 0, s>>>(a); break;
-        case 1: k_element<KT, 1><<<grid, kTetTile, 0, s>>>(a); break;
-        default: k_element<KT, 2><<<grid, kTetTile, 0, s>>>(a); break;
+    if (hess) {
+        switch (a.model) {
+            case 0: k_element<KT, 0, true><<<grid, kTetTile, 0, s>>>(a); break;
+            case 1: k_element<KT, 1, true><<<grid, kTetTile, 0, s>>>(a); break;
+            default: k_element<KT, 2, true><<<grid, kTetTile, 0, s>>>(a); break;
+        }
+    } else {
+        switch (a.model) {
+            case 0: k_element<KT, 0, false><<<grid, kTetTile, 0, s>>>(a); break;
+            case 1: k_element<KT, 1, false><<<grid, kTetTile, 0, s>>>(a); break;
+            default: k_element<KT, 2, false><<<grid, kTetTile, 0, s>>>(a); break;
+        }
     }
 }
 
@@ -772,9 +782,9 @@ void launch_warm_step(const ElemArgs& a, int B, int apply, cudaStream_t s) {
     k_warm_step<<<grid, 256, 0, s>>>(a, apply);
 }
 
-void launch_element(const ElemArgs& a, int B, cudaStream_t s) {
-    if (a.slot.prec == 1) launch_element_t<float>(a, B, s);
-    else launch_element_t<double>(a, B, s);
+void launch_element(const ElemArgs& a, int B, cudaStream_t s, bool hess) {
+    if (a.slot.prec == 1) launch_element_t<float>(a, B, hess, s);
+    else launch_element_t<double>(a, B, hess, s);
 }
 
 void launch_energy_trial(const ElemArgs& a, int B, cudaStream_t s) {

@@ -19,6 +19,46 @@ namespace {
 
 __device__ __forceinline__ int pair_index(int a, int b) { return a * 4 - (a * (a - 1)) / 2 + (b - a); }
 
+// Gradient of row `row` of problem b: the element forces of its tets in fixed
+// incidence order, the external force, and the pin term (zero under
+// elimination, k_s (x - x_p) under the penalty form).  Writes g, returns |g|^2.
+__device__ __forceinline__ double row_gradient(const ElemArgs& A, int b, int row, bool pin_r) {
+    const MeshDev& M = A.mesh;
+    const int n = M.n;
+    // gradient of row: sum of element forces in fixed incidence order
+    const double* ge = A.slot.ge + (size_t)b * M.m * 12;
+    double g0 = 0, g1 = 0, g2 = 0;
+    for (int ii = M.vinc_ptr[row]; ii < M.vinc_ptr[row + 1]; ++ii) {
+        const int code = M.vinc[ii];
+        const double* f = ge + (size_t)(code >> 2) * 12 + 3 * (code & 3);
+        g0 += f[0];
+        g1 += f[1];
+        g2 += f[2];
+    }
+    if (A.fext) {  // external forces: E gains -f.x
+        const double* fv = A.fext + (size_t)b * A.fext_stride + 3 * (size_t)row;
+        g0 -= fv[0];
+        g1 -= fv[1];
+        g2 -= fv[2];
+    }
+    if (pin_r) {
+        if (A.constraint == 0) {
+            g0 = g1 = g2 = 0.0;
+        } else {
+            const double* x = A.slot.x + ((size_t)b * n + row) * 3;
+            const double* xp = A.slot.xp + ((size_t)b * n + row) * 3;
+            g0 += A.ks * (x[0] - xp[0]);
+            g1 += A.ks * (x[1] - xp[1]);
+            g2 += A.ks * (x[2] - xp[2]);
+        }
+    }
+    double* gout = A.slot.g + ((size_t)b * n + row) * 3;
+    gout[0] = g0;
+    gout[1] = g1;
+    gout[2] = g2;
+    return g0 * g0 + g1 * g1 + g2 * g2;
+}
+
 // One thread per block row: the row's matrix blocks, its inverse diagonal
 // block, and its gradient entry; |g_free|^2 per problem.
 template <typename KT>
@@ -93,39 +133,21 @@ __global__ void __launch_bounds__(kRowTile) k_assemble_grad(ElemArgs A) {
                 di[8] = (KT)((a[0] * a[4] - a[1] * a[3]) * id);
             }
         }
-        // gradient of row: sum of element forces in fixed incidence order
-        const double* ge = A.slot.ge + (size_t)b * M.m * 12;
-        double g0 = 0, g1 = 0, g2 = 0;
-        for (int ii = M.vinc_ptr[row]; ii < M.vinc_ptr[row + 1]; ++ii) {
-            const int code = M.vinc[ii];
-            const double* f = ge + (size_t)(code >> 2) * 12 + 3 * (code & 3);
-            g0 += f[0];
-            g1 += f[1];
-            g2 += f[2];
-        }
-        if (A.fext) {  // external forces: E gains -f.x
-            const double* fv = A.fext + (size_t)b * A.fext_stride + 3 * (size_t)row;
-            g0 -= fv[0];
-            g1 -= fv[1];
-            g2 -= fv[2];
-        }
-        if (pin_r) {
-            if (A.constraint == 0) {
-                g0 = g1 = g2 = 0.0;
-            } else {
-                const double* x = A.slot.x + ((size_t)b * n + row) * 3;
-                const double* xp = A.slot.xp + ((size_t)b * n + row) * 3;
-                g0 += A.ks * (x[0] - xp[0]);
-                g1 += A.ks * (x[1] - xp[1]);
-                g2 += A.ks * (x[2] - xp[2]);
-            }
-        }
-        double* gout = A.slot.g + ((size_t)b * n + row) * 3;
-        gout[0] = g0;
-        gout[1] = g1;
-        gout[2] = g2;
-        gn[0] = g0 * g0 + g1 * g1 + g2 * g2;
+        gn[0] = row_gradient(A, b, row, pin_r);
     }
+    double tot[1];
+    double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
+    if (tile_commit<1>(gn, part, blockIdx.x, gridDim.x, &A.slot.sc[b].tk_g, 0, tot) && threadIdx.x == 0)
+        A.slot.sc[b].gnorm2 = tot[0];
+}
+
+// Gradient only (a convergence test that needs no matrix): |g_free|^2 per problem.
+__global__ void __launch_bounds__(kRowTile) k_gradient(ElemArgs A) {
+    const int b = blockIdx.y;
+    if (!A.slot.active[b]) return;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    double gn[1] = {0.0};
+    if (row < A.mesh.n) gn[0] = row_gradient(A, b, row, A.mesh.pin_handle_v[row] >= 0);
     double tot[1];
     double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
     if (tile_commit<1>(gn, part, blockIdx.x, gridDim.x, &A.slot.sc[b].tk_g, 0, tot) && threadIdx.x == 0)
@@ -194,7 +216,10 @@ void launch_assemble(const ElemArgs& a, int B, cudaStream_t s) {
     else k_assemble_grad<double><<<grid, kRowTile, 0, s>>>(a);
 }
 
-void launch_gradient(const ElemArgs& a, int B, cudaStream_t s) { launch_assemble(a, B, s); }
+void launch_gradient(const ElemArgs& a, int B, cudaStream_t s) {
+    dim3 grid((a.mesh.n + kRowTile - 1) / kRowTile, B);
+    k_gradient<<<grid, kRowTile, 0, s>>>(a);
+}
 
 void launch_slope(const ElemArgs& a, int B, cudaStream_t s) {
     dim3 grid((a.mesh.n + kRowTile - 1) / kRowTile, B);

@@ -96,7 +96,8 @@ void launch_pose_init(const ElemArgs& a, int B, int init, cudaStream_t s);
 void launch_warm_save(const ElemArgs& a, int B, cudaStream_t s);
 void launch_warm_step(const ElemArgs& a, int B, int apply, cudaStream_t s);
 // a1: element step (Ke, element forces, energy) for active problems
-void launch_element(const ElemArgs& a, int B, cudaStream_t s);
+// hess = false: energy and forces only (no element blocks)
+void launch_element(const ElemArgs& a, int B, cudaStream_t s, bool hess = true);
 // a6: energy at x + alpha dx for active problems (line-search trial)
 void launch_energy_trial(const ElemArgs& a, int B, cudaStream_t s);
 // a2/a3/a4: gather matrix blocks with pin elimination, block-Jacobi inverse
