@@ -21,18 +21,21 @@ namespace {
 // free row, summed per 64-row unit (two warps: shuffle sums, then the pair in
 // fixed order) and written to rcp_block[6 u + c].  Every thread of the block
 // calls it; rows past the end pass valid = false.
-__device__ __forceinline__ void restrict_units(const double (&r)[3], bool valid, int row, const float4* __restrict__ crel,
+__device__ __forceinline__ void restrict_units(const float (&r)[3], bool valid, int row, const float4* __restrict__ crel,
                                                const int* __restrict__ agg_handle, const double* __restrict__ xf,
                                                int agg_shift, float* __restrict__ rcp_block) {
     __shared__ float ws[8][6];
     float y[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (valid) {
         const float4 v = crel[row];
-        if (v.w != 0.f) {
+        if (v.w != 0.f) {   // FP32 throughout (the coarse correction is a preconditioner)
             const double* Tq = xf + 12 * agg_handle[row >> agg_shift];
-            const float q0 = (float)(Tq[0] * r[0] + Tq[4] * r[1] + Tq[8] * r[2]);
-            const float q1 = (float)(Tq[1] * r[0] + Tq[5] * r[1] + Tq[9] * r[2]);
-            const float q2 = (float)(Tq[2] * r[0] + Tq[6] * r[1] + Tq[10] * r[2]);
+            float Qt[9];
+#pragma unroll
+            for (int e = 0; e < 9; ++e) Qt[e] = (float)Tq[4 * (e / 3) + e % 3];
+            const float q0 = Qt[0] * r[0] + Qt[3] * r[1] + Qt[6] * r[2];
+            const float q1 = Qt[1] * r[0] + Qt[4] * r[1] + Qt[7] * r[2];
+            const float q2 = Qt[2] * r[0] + Qt[5] * r[1] + Qt[8] * r[2];
             y[0] = q0;
             y[1] = q1;
             y[2] = q2;
@@ -69,7 +72,7 @@ __global__ void k_pcg_init(ElemArgs A, double tol2, int maxit, const double* __r
     const int row = blockIdx.x * blockDim.x + threadIdx.x;
     const bool coarse = coarse_b && coarse_b[b];
     double v[2] = {0.0, 0.0};
-    double r64[3] = {0.0, 0.0, 0.0};
+    float r32[3] = {0.f, 0.f, 0.f};
     if (row < n) {
         const double* g = A.slot.g + ((size_t)b * n + row) * 3;
         const T* di = (const T*)A.slot.dinv + ((size_t)b * n + row) * 9;
@@ -89,12 +92,12 @@ __global__ void k_pcg_init(ElemArgs A, double tol2, int maxit, const double* __r
         }
         zp[3] = (T)0;
         zp[7] = (T)0;
-        r64[0] = (double)rr[0];
-        r64[1] = (double)rr[1];
-        r64[2] = (double)rr[2];
+        r32[0] = (float)rr[0];
+        r32[1] = (float)rr[1];
+        r32[2] = (float)rr[2];
     }
     if (coarse)
-        restrict_units(r64, row < n, row, A.mesh.crel, A.mesh.agg_handle, A.slot.xf + (size_t)b * A.mesh.H * 12,
+        restrict_units(r32, row < n, row, A.mesh.crel, A.mesh.agg_handle, A.slot.xf + (size_t)b * A.mesh.H * 12,
                        A.mesh.agg_shift,
                        A.slot.rcp + (size_t)b * A.slot.rcp_stride + 6 * ((size_t)blockIdx.x * blockDim.x / kCoarseRows));
     double tot[2];
@@ -305,7 +308,7 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
     coeffs(sc, alpha, beta_unused);
     const bool coarse = d.coarse != 0;
     double v[2] = {0.0, 0.0};
-    double r64[3] = {0.0, 0.0, 0.0};
+    float r32[3] = {0.f, 0.f, 0.f};
     Partial<T> rz = Partial<T>::zero(), rr2 = Partial<T>::zero();
     if (row < d.n_rows) {
         T* zrec = zpn + 8 * (size_t)row;
@@ -328,12 +331,12 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
         st4(zrec, zz[0], zz[1], zz[2]);
         if (!coarse) rz = dot3_partial(rr[0], rr[1], rr[2], zz[0], zz[1], zz[2]);
         rr2 = dot3_partial(rr[0], rr[1], rr[2], rr[0], rr[1], rr[2]);
-        r64[0] = (double)rr[0];
-        r64[1] = (double)rr[1];
-        r64[2] = (double)rr[2];
+        r32[0] = (float)rr[0];
+        r32[1] = (float)rr[1];
+        r32[2] = (float)rr[2];
     }
     if (coarse)   // z is finished by k_pcg_correct, which also forms r.z and beta
-        restrict_units(r64, row < d.n_rows, row, d.crel, d.agg_handle, d.xf, d.agg_shift,
+        restrict_units(r32, row < d.n_rows, row, d.crel, d.agg_handle, d.xf, d.agg_shift,
                        d.rcp + 6 * ((size_t)tile * TILE / kCoarseRows));
     v[0] = warp_sum_partial(rz);
     v[1] = warp_sum_partial(rr2);
