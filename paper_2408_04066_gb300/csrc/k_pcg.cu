@@ -21,18 +21,23 @@ namespace {
 // free row, summed per 64-row unit (two warps: shuffle sums, then the pair in
 // fixed order) and written to rcp_block[6 u + c].  Every thread of the block
 // calls it; rows past the end pass valid = false.
-__device__ __forceinline__ void restrict_units(const float (&r)[3], bool valid, int row, const float4* __restrict__ crel,
-                                               const int* __restrict__ agg_handle, const double* __restrict__ xf,
-                                               int agg_shift, float* __restrict__ rcp_block) {
+__device__ __forceinline__ void restrict_units(const float (&r)[3], bool valid, int row, int row0,
+                                               const float4* __restrict__ crel, const int* __restrict__ agg_handle,
+                                               const double* __restrict__ xf, int agg_shift, int n_agg,
+                                               float* __restrict__ rcp_block) {
     __shared__ float ws[8][6];
+    __shared__ float qs[4][9];   // pose rotations of the block's aggregates (blocks hold <= 256 rows)
+    const int a0 = row0 >> agg_shift;   // row0: the block's first row
+    if (threadIdx.x < 36) {
+        const int ai = threadIdx.x / 9, e = threadIdx.x % 9, a = a0 + ai;
+        qs[ai][e] = a < n_agg ? (float)xf[12 * agg_handle[a] + 4 * (e / 3) + e % 3] : 0.f;
+    }
+    __syncthreads();
     float y[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (valid) {
         const float4 v = crel[row];
         if (v.w != 0.f) {   // FP32 throughout (the coarse correction is a preconditioner)
-            const double* Tq = xf + 12 * agg_handle[row >> agg_shift];
-            float Qt[9];
-#pragma unroll
-            for (int e = 0; e < 9; ++e) Qt[e] = (float)Tq[4 * (e / 3) + e % 3];
+            const float* Qt = qs[(row >> agg_shift) - a0];
             const float q0 = Qt[0] * r[0] + Qt[3] * r[1] + Qt[6] * r[2];
             const float q1 = Qt[1] * r[0] + Qt[4] * r[1] + Qt[7] * r[2];
             const float q2 = Qt[2] * r[0] + Qt[5] * r[1] + Qt[8] * r[2];
@@ -97,8 +102,8 @@ __global__ void k_pcg_init(ElemArgs A, double tol2, int maxit, const double* __r
         r32[2] = (float)rr[2];
     }
     if (coarse)
-        restrict_units(r32, row < n, row, A.mesh.crel, A.mesh.agg_handle, A.slot.xf + (size_t)b * A.mesh.H * 12,
-                       A.mesh.agg_shift,
+        restrict_units(r32, row < n, row, (int)(blockIdx.x * blockDim.x), A.mesh.crel, A.mesh.agg_handle,
+                       A.slot.xf + (size_t)b * A.mesh.H * 12, A.mesh.agg_shift, A.mesh.n_agg,
                        A.slot.rcp + (size_t)b * A.slot.rcp_stride + 6 * ((size_t)blockIdx.x * blockDim.x / kCoarseRows));
     double tot[2];
     double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
@@ -336,8 +341,8 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
         r32[2] = (float)rr[2];
     }
     if (coarse)   // z is finished by k_pcg_correct, which also forms r.z and beta
-        restrict_units(r32, row < d.n_rows, row, d.crel, d.agg_handle, d.xf, d.agg_shift,
-                       d.rcp + 6 * ((size_t)tile * TILE / kCoarseRows));
+        restrict_units(r32, row < d.n_rows, row, tile * TILE, d.crel, d.agg_handle, d.xf, d.agg_shift,
+                       d.coarse_n / 6, d.rcp + 6 * ((size_t)tile * TILE / kCoarseRows));
     v[0] = warp_sum_partial(rz);
     v[1] = warp_sum_partial(rr2);
     double tot[2];
@@ -499,6 +504,15 @@ __global__ void __launch_bounds__(TILE) k_pcg_correct(const PcgDesc<T>* __restri
     const int a0 = (tile * TILE) >> d.agg_shift;
     const int n_agg = d.coarse_n / 6;
     const int n_ks = (d.coarse_n + kCoarseKC - 1) / kCoarseKC;
+    // the row's own loads go out first, so their latency overlaps the staging
+    T* zp = (sc->iter & 1) ? d.zp1 : d.zp0;   // the record the next k_pcg_spmv reads
+    T r[3] = {(T)0, (T)0, (T)0}, z[3] = {(T)0, (T)0, (T)0};
+    float4 off = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (row < d.n_rows) {
+        ld4(d.rec + kRec * (size_t)row + kRecR, r);
+        ld4(zp + 8 * (size_t)row, z);
+        off = d.crel[row];
+    }
     // slice partials of e, one load per thread, then added in slice order
     for (int idx = threadIdx.x; idx < kMaxAgg * 6 * n_ks; idx += TILE) {
         const int ks = idx / (kMaxAgg * 6), r = idx - ks * kMaxAgg * 6, a = a0 + r / 6;
@@ -520,20 +534,15 @@ __global__ void __launch_bounds__(TILE) k_pcg_correct(const PcgDesc<T>* __restri
         es[threadIdx.x / 6][threadIdx.x % 6] = v;
     }
     __syncthreads();
-    T* zp = (sc->iter & 1) ? d.zp1 : d.zp0;   // the record the next k_pcg_spmv reads
     Partial<T> rz = Partial<T>::zero();
     if (row < d.n_rows) {
-        T r[3], z[3];
-        ld4(d.rec + kRec * (size_t)row + kRecR, r);
-        ld4(zp + 8 * (size_t)row, z);
-        const float4 v = d.crel[row];
-        if (v.w != 0.f) {
+        if (off.w != 0.f) {
             const int ai = (row >> d.agg_shift) - a0;
             const float* e = es[ai];
             const float* Q = qs[ai];
-            const float l0 = e[0] + (e[4] * v.z - e[5] * v.y);
-            const float l1 = e[1] + (e[5] * v.x - e[3] * v.z);
-            const float l2 = e[2] + (e[3] * v.y - e[4] * v.x);
+            const float l0 = e[0] + (e[4] * off.z - e[5] * off.y);
+            const float l1 = e[1] + (e[5] * off.x - e[3] * off.z);
+            const float l2 = e[2] + (e[3] * off.y - e[4] * off.x);
 #pragma unroll
             for (int i = 0; i < 3; ++i) z[i] += (T)(Q[3 * i] * l0 + Q[3 * i + 1] * l1 + Q[3 * i + 2] * l2);
             st4(zp + 8 * (size_t)row, z[0], z[1], z[2]);
