@@ -293,7 +293,8 @@ def run_mfem(args, dist):
     cfg = figure_config(args.tets, model=args.model, seeds=range(dist.rank * nb, dist.rank * nb + nb))
     opts = dict(precision=args.precision, max_batch=nb, newton_tol=1e-6)
     ctx = mfem.Context.from_config(cfg, **opts)
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)      # a created stream (CUDA graphs cannot capture the legacy one)
+    torch.cuda.set_stream(stream)
     ctx.set_stream(stream.cuda_stream)
     info = ctx.info()
     xfs = torch.tensor(cfg["xfs"], dtype=torch.float64, device=dev)
@@ -469,7 +470,8 @@ def run_batched(args, dist):
     frames = args.warmup + args.steps + 1
     meshes = [figure_config(200000, model="snh", seeds=[]), figure_config(50000, model="snh", seeds=[], scale=0.5)]
     ctxs, anim = [], []
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)      # a created stream (CUDA graphs cannot capture the legacy one)
+    torch.cuda.set_stream(stream)
     for mi, cfg in enumerate(meshes):
         c = mfem.Context.from_config(cfg, precision="mixed", max_batch=nb, newton_tol=1e-6, init="warm")
         c.set_stream(stream.cuda_stream)
@@ -683,7 +685,8 @@ def run_large(args, dist):
     nb = args.batch
     cfg = character_config(2_000_000, 40, seeds=range(dist.rank * nb, dist.rank * nb + nb))
     ctx = mfem.Context.from_config(cfg, precision="mixed", max_batch=nb, newton_tol=1e-6)
-    stream = torch.cuda.current_stream(dev)
+    stream = torch.cuda.Stream(dev)      # a created stream (CUDA graphs cannot capture the legacy one)
+    torch.cuda.set_stream(stream)
     ctx.set_stream(stream.cuda_stream)
     info = ctx.info()
     xfs = torch.tensor(cfg["xfs"], dtype=torch.float64, device=dev)

@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MFEM_ABI_VERSION 4
+#define MFEM_ABI_VERSION 5
 
 typedef enum {
     MFEM_OK = 0,
@@ -59,6 +59,7 @@ typedef enum { MFEM_INIT_RIGID = 0, MFEM_INIT_REST = 1, MFEM_INIT_WARM = 2, MFEM
 typedef enum { MFEM_MEM_HOST = 0, MFEM_MEM_DEVICE = 1 } mfem_memory;
 typedef enum { MFEM_ROT_RIG = 0, MFEM_ROT_POLAR = 1 } mfem_rotation;
 typedef enum { MFEM_PRECOND_BLOCK_JACOBI = 0, MFEM_PRECOND_TWO_LEVEL = 1 } mfem_precond;
+typedef enum { MFEM_LAUNCH_GRAPH = 0, MFEM_LAUNCH_DIRECT = 1 } mfem_launch;
 
 /* Material (§4 "A solver friendly to variant energies"; §4 "Allowing
  * heterogeneous material").  Densities, with S the element stretch:
@@ -148,6 +149,11 @@ typedef struct {
                             (the first step from the rigid guess, whose residual
                             sits at the cluster boundaries, uses block Jacobi).
                             MFEM_PRECOND_BLOCK_JACOBI: block Jacobi only */
+    int32_t launch;      /* MFEM_LAUNCH_GRAPH (default): each chunk of PCG iterations
+                            is captured once per set of launch parameters as a CUDA
+                            graph and replayed (up to 256 graphs per context; a
+                            stream that cannot capture falls back to direct
+                            launches); MFEM_LAUNCH_DIRECT: launches every kernel */
 } mfem_options;
 
 /* Per-pose result statistics. */

@@ -366,6 +366,51 @@ mfem_status read_scalars(mfem_ctx* c, int B) {
 // descriptor table is uploaded once, then chunks of kPcgChunk iterations are
 // enqueued and the problem states read back after each chunk (max_iters > 0:
 // exactly that many iterations, no checks -- used by the autotuner).
+// One chunk of PCG iterations: replayed from a CUDA graph captured the first
+// time these launch parameters occur (the descriptor table lives at a fixed
+// device address; only its contents change), else launched directly.
+template <typename T>
+mfem_status launch_chunk(mfem_ctx* c, const PcgDesc<T>* dst, int nd, int units, int tile, int n_it,
+                         const std::vector<CoarseJob>& jobs) {
+    const int nj = (int)jobs.size();
+    if (c->opt.launch == MFEM_LAUNCH_GRAPH && !c->graphs_off) {
+        char buf[96];
+        snprintf(buf, sizeof buf, "%d %p %d %d %d %d", (int)sizeof(T), (const void*)dst, nd, units, tile, n_it);
+        std::string key(buf);
+        for (const auto& j : jobs) {
+            snprintf(buf, sizeof buf, " %p %d %d %d %d", (const void*)j.Ainv, j.N, j.d0, j.nd, j.agg_units);
+            key += buf;
+        }
+        auto it = c->graphs.find(key);
+        if (it == c->graphs.end()) {
+            if (c->graphs.size() >= 256) {   // bounded cache
+                for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+                c->graphs.clear();
+            }
+            cudaGraph_t g = nullptr;
+            cudaGraphExec_t ex = nullptr;
+            bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            if (ok) {
+                const cudaError_t e1 = launch_pcg_iters<T>(dst, nd, units, tile, n_it, jobs.data(), nj, c->stream);
+                const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
+                ok = e1 == cudaSuccess && e2 == cudaSuccess && g && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
+            }
+            if (g) cudaGraphDestroy(g);
+            if (!ok) {   // keep to direct launches from now on
+                cudaGetLastError();
+                c->graphs_off = true;
+                CK(launch_pcg_iters<T>(dst, nd, units, tile, n_it, jobs.data(), nj, c->stream));
+                return MFEM_OK;
+            }
+            it = c->graphs.emplace(key, ex).first;
+        }
+        CK(cudaGraphLaunch(it->second, c->stream));
+        return MFEM_OK;
+    }
+    CK(launch_pcg_iters<T>(dst, nd, units, tile, n_it, jobs.data(), nj, c->stream));
+    return MFEM_OK;
+}
+
 template <typename T>
 mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, int max_iters, bool count,
                     bool one_chunk = false) {
@@ -406,7 +451,8 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
         const int n_it = std::min(kPcgChunk, cap - done);
         if (one_chunk && done > 0) break;
         int pe = count ? c->prof.begin(2, c->stream) : -1;
-        CK(launch_pcg_iters<T>(dst, (int)d.size(), units, tile, n_it, jobs.data(), nj, c->stream));
+        mfem_status lst = launch_chunk<T>(c, dst, (int)d.size(), units, tile, n_it, jobs);
+        if (lst != MFEM_OK) return lst;
         if (count) {
             c->prof.end(pe, c->stream);
             int cl = nj > 0 ? nj + 1 : 0;
@@ -910,6 +956,7 @@ void mfem_default_options(mfem_options* o) {
     o->diagnostics = 0;
     o->rotation = MFEM_ROT_RIG;
     o->precond = MFEM_PRECOND_TWO_LEVEL;
+    o->launch = MFEM_LAUNCH_GRAPH;
 }
 
 const char* mfem_status_string(mfem_status s) {
@@ -957,6 +1004,7 @@ void mfem_destroy(mfem_ctx* c) {
                   c->diag_host};
     for (void* p : hp)
         if (p) cudaFreeHost(p);
+    for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
     for (auto e : c->prof.ev) cudaEventDestroy(e);
     if (c->prof.start) cudaEventDestroy(c->prof.start);
     if (c->prof.stop) cudaEventDestroy(c->prof.stop);
@@ -1037,6 +1085,7 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
     if (o.rotation != MFEM_ROT_RIG && o.rotation != MFEM_ROT_POLAR) return fail(MFEM_EINVAL, "bad rotation");
     if (o.precond != MFEM_PRECOND_BLOCK_JACOBI && o.precond != MFEM_PRECOND_TWO_LEVEL)
         return fail(MFEM_EINVAL, "bad preconditioner");
+    if (o.launch != MFEM_LAUNCH_GRAPH && o.launch != MFEM_LAUNCH_DIRECT) return fail(MFEM_EINVAL, "bad launch mode");
     if (o.tile_rows != 0 && !pcg_tile_supported(o.tile_rows))
         return fail(MFEM_EINVAL, "tile_rows must be 0, 64, 128 or 256");
     if (!mat) return fail(MFEM_EINVAL, "null material");

@@ -4,6 +4,7 @@
 
 #include <cuda_runtime.h>
 
+#include <map>
 #include <string>
 #include <vector>
 
@@ -92,6 +93,9 @@ struct mfem_ctx {
     std::vector<int> warm_kind;
     std::vector<int> xpred_valid;   // per slot: slot.xpred holds the last solve's predictor result
     mfem::Profiler prof;
+    // PCG chunks captured as CUDA graphs, keyed by the launch parameters
+    std::map<std::string, cudaGraphExec_t> graphs;
+    bool graphs_off = false;   // capture failed once (e.g. a stream that cannot capture)
     mfem_profile last_profile{};
     std::string err;
     bool owned_by_server = false;

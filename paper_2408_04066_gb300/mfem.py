@@ -23,8 +23,9 @@ CLUSTER_RULES = {"bone": 0, "joint": 1, "midpoint": 2}
 INITS = {"rigid": 0, "rest": 1, "warm": 2, "corot": 3}
 ROTATIONS = {"rig": 0, "polar": 1}
 PRECONDS = {"block_jacobi": 0, "two_level": 1}
+LAUNCHES = {"graph": 0, "direct": 1}
 MEM_HOST, MEM_DEVICE = 0, 1
-ABI_VERSION = 4   # MFEM_ABI_VERSION of the header these structures follow
+ABI_VERSION = 5   # MFEM_ABI_VERSION of the header these structures follow
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -45,7 +46,7 @@ class Options(C.Structure):
                 ("newton_tol", C.c_double), ("cg_tol", C.c_double), ("newton_max", C.c_int32),
                 ("cg_max", C.c_int32), ("init", C.c_int32), ("max_batch", C.c_int32),
                 ("tile_rows", C.c_int32), ("diagnostics", C.c_int32), ("rotation", C.c_int32),
-                ("precond", C.c_int32)]
+                ("precond", C.c_int32), ("launch", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -172,6 +173,8 @@ def default_options(**over):
             v = ROTATIONS[v] if isinstance(v, str) else v
         elif k == "precond":
             v = PRECONDS[v] if isinstance(v, str) else v
+        elif k == "launch":
+            v = LAUNCHES[v] if isinstance(v, str) else v
         setattr(o, k, v)
     return o
 

@@ -80,3 +80,15 @@ def test_two_level_penalty_mode(mfem, fig10k):
     xo, _ = S.solve(so, fig10k["xfs"][2], "snh", constraint="penalty", ks=ks, newton_tol=1e-12, newton_max=80)
     assert st["converged"] == 1
     assert np.abs(x - xo).max() / so.bbox_diag <= 1e-9
+
+
+def test_graph_replay_equals_direct_launches(mfem, fig10k):
+    """PCG chunks replayed from captured CUDA graphs give the same bits as
+    launching every kernel."""
+    g = mfem.Context.from_config(fig10k, precision="mixed", max_batch=4, launch="graph")
+    d = mfem.Context.from_config(fig10k, precision="mixed", max_batch=4, launch="direct")
+    for _ in range(2):   # the second solve replays cached graphs
+        xg, sg = g.solve_batch(fig10k["xfs"])
+        xd, sd = d.solve_batch(fig10k["xfs"])
+        assert np.array_equal(xg, xd)
+        assert [s["pcg_iters"] for s in sg] == [s["pcg_iters"] for s in sd]
