@@ -488,7 +488,7 @@ __device__ __forceinline__ double vertex_energy(const ElemArgs& A, int b, int v,
 // Thread k handles tet k (k < m) and the vertex terms of vertex k (k < n).
 // HESS = false: energy and forces only (a gradient test needs no Hessian).
 template <typename KT, int MODEL, bool HESS>
-__global__ void __launch_bounds__(kTetTile) k_element(ElemArgs A) {
+__global__ void __launch_bounds__(kTetTile, 4) k_element(ElemArgs A) {
     const int b = blockIdx.y;
     if (!A.slot.active[b]) return;
     const MeshDev& M = A.mesh;
@@ -528,14 +528,17 @@ __global__ void __launch_bounds__(kTetTile) k_element(ElemArgs A) {
                 fp64 = J < kFallbackJ;
             }
             if (fp64) {
+                // the Hessian of a strongly strained tet in FP64 (its terms cancel);
+                // the SPD filter of the result in the kernel's precision (GB300 runs
+                // FP64 at a small fraction of FP32, and the filter needs no more)
                 double C[6][6];
                 snh_hessian<double>(S, mu, lam, C);
-                if (!chol_shifted_ok<double>(C, kSpdEps * mu)) filter_spd<double>(C, kSpdEps * mu);
                 KT Ck[6][6];
 #pragma unroll
                 for (int p = 0; p < 6; ++p)
 #pragma unroll
                     for (int q = 0; q < 6; ++q) Ck[p][q] = (KT)C[p][q];
+                if (!chol_shifted_ok<KT>(Ck, (KT)(kSpdEps * mu))) filter_spd<KT>(Ck, (KT)(kSpdEps * mu));
                 blocks_generic<KT>(Ck, G, Q, w, ke);
             } else {
                 KT C[6][6];
