@@ -171,13 +171,14 @@ typedef struct {
 } mfem_stats;
 
 /* Device-side profile of the last solve call, timed with CUDA events on the
- * context's stream.  The dominant work is the PCG iteration: one SpMV+dot
- * kernel and one update kernel per iteration, enqueued in chunks. */
+ * context's stream.  The dominant work is the PCG iteration: an SpMV+dot
+ * kernel and an update kernel per iteration, plus the coarse product and
+ * correction kernels on two-level iterations, enqueued in chunks. */
 typedef struct {
     int32_t kernel_launches;  /* all library kernels launched in the call */
-    int32_t pcg_launches;     /* PCG kernel launches (two per iteration) */
-    double pcg_ms;            /* summed time of the PCG iteration kernels */
-    double pcg_bytes;         /* algorithmic bytes moved by those kernels */
+    int32_t pcg_launches;     /* SpMV and update launches (two per iteration) */
+    double pcg_ms;            /* summed time of the PCG iteration chunks (all their kernels) */
+    double pcg_bytes;         /* algorithmic bytes moved by those chunks */
     int64_t pcg_iters;        /* PCG iterations summed over poses */
     int32_t element_launches;
     double element_ms;

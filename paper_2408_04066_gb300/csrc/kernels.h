@@ -117,9 +117,10 @@ void launch_elem_out(const ElemArgs& a, int b, double* s_out, double* lam_out, c
 // diagnostics: inverted count, max rel skew, max angle for problem b
 void launch_diag(const ElemArgs& a, int b, unsigned* out3, cudaStream_t s);
 
-// PCG: init (r = -g, z = D^{-1} r, rho, |r0|) and `iters` iterations (two
-// launches each) over every problem of a descriptor table; tiles of
-// tile_rows rows (64, 128 or 256), n_units = total tiles.
+// PCG: init (r = -g, z = D^{-1} r, rho, |r0|) and `iters` iterations over
+// every problem of a descriptor table (spmv + update; with coarse jobs, the
+// coarse product per mesh and the correction first); tiles of tile_rows rows
+// (64, 128 or 256), n_units = total tiles.
 // tol2_b: per-problem squared tolerances on the device, or null for tol2 for all;
 // coarse_b: per-problem flags (device) of the two-level preconditioner, or null.
 void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int maxit, const double* tol2_b,
