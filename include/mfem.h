@@ -106,7 +106,7 @@ typedef struct {
                             MFEM_PENALTY: k_s/2 |x_v - x_p|^2 per pin (Eq. 6) */
     double k_s;          /* penalty stiffness (PENALTY only) */
     double newton_tol;   /* stop when |g_free| <= newton_tol |g_free(x_0)| (1e-6) */
-    double cg_tol;       /* PCG relative residual per Newton step, inexact Newton (1e-2);
+    double cg_tol;       /* PCG relative residual per Newton step, inexact Newton (3e-2);
                             a step that needs less to reach newton_tol takes
                             eta = min(0.5, 0.5 newton_tol |g_free(x_0)| / |g_free|);
                             the co-rotational predictor step takes min(cg_tol, 3e-3) */

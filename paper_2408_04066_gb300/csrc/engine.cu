@@ -947,7 +947,7 @@ void mfem_default_options(mfem_options* o) {
     o->constraint = MFEM_ELIMINATE;
     o->k_s = 0.0;
     o->newton_tol = 1e-6;
-    o->cg_tol = 1e-2;
+    o->cg_tol = 3e-2;
     o->newton_max = 50;
     o->cg_max = 5000;
     o->init = MFEM_INIT_COROT;

@@ -16,22 +16,29 @@ namespace mfem {
 
 namespace {
 
-// Coarse residual of the rows of one block: y_i = Q_a^T r_i (the aggregate's
-// pose rotation undone), contribution P_i^T y_i = (y_i, (X_i - c_a) x y_i) of a
-// free row, summed per 64-row unit (two warps: shuffle sums, then the pair in
-// fixed order) and written to rcp_block[6 u + c].  Every thread of the block
-// calls it; rows past the end pass valid = false.
-__device__ __forceinline__ void restrict_units(const float (&r)[3], bool valid, int row, int row0,
-                                               const float4* __restrict__ crel, const int* __restrict__ agg_handle,
-                                               const double* __restrict__ xf, int agg_shift, int n_agg,
-                                               float* __restrict__ rcp_block) {
-    __shared__ float ws[8][6];
-    __shared__ float qs[4][9];   // pose rotations of the block's aggregates (blocks hold <= 256 rows)
-    const int a0 = row0 >> agg_shift;   // row0: the block's first row
+// Pose rotations of the aggregates a block of rows from row0 touches (blocks
+// hold <= 256 rows, so <= 4 aggregates) into qs; threads 0..35 load, the caller
+// synchronises (restrict_units does).
+__device__ __forceinline__ void stage_rotations(float (*qs)[9], int row0, const int* __restrict__ agg_handle,
+                                                const double* __restrict__ xf, int agg_shift, int n_agg) {
+    const int a0 = row0 >> agg_shift;
     if (threadIdx.x < 36) {
         const int ai = threadIdx.x / 9, e = threadIdx.x % 9, a = a0 + ai;
         qs[ai][e] = a < n_agg ? (float)xf[12 * agg_handle[a] + 4 * (e / 3) + e % 3] : 0.f;
     }
+}
+
+// Coarse residual of the rows of one block: y_i = Q_a^T r_i (the aggregate's
+// pose rotation undone, Q staged by stage_rotations), contribution
+// P_i^T y_i = (y_i, (X_i - c_a) x y_i) of a free row, summed per 64-row unit
+// (two warps: shuffle sums, then the pair in fixed order) and written to
+// rcp_block[6 u + c].  Every thread of the block calls it; rows past the end
+// pass valid = false.
+__device__ __forceinline__ void restrict_units(const float (&r)[3], bool valid, int row, int row0,
+                                               const float4* __restrict__ crel, const float (*qs)[9], int agg_shift,
+                                               float* __restrict__ rcp_block) {
+    __shared__ float ws[8][6];
+    const int a0 = row0 >> agg_shift;   // row0: the block's first row
     __syncthreads();
     float y[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (valid) {
@@ -101,10 +108,14 @@ __global__ void k_pcg_init(ElemArgs A, double tol2, int maxit, const double* __r
         r32[1] = (float)rr[1];
         r32[2] = (float)rr[2];
     }
-    if (coarse)
-        restrict_units(r32, row < n, row, (int)(blockIdx.x * blockDim.x), A.mesh.crel, A.mesh.agg_handle,
-                       A.slot.xf + (size_t)b * A.mesh.H * 12, A.mesh.agg_shift, A.mesh.n_agg,
-                       A.slot.rcp + (size_t)b * A.slot.rcp_stride + 6 * ((size_t)blockIdx.x * blockDim.x / kCoarseRows));
+    if (coarse) {
+        __shared__ float qs[4][9];
+        const int row0 = (int)(blockIdx.x * blockDim.x);
+        stage_rotations(qs, row0, A.mesh.agg_handle, A.slot.xf + (size_t)b * A.mesh.H * 12, A.mesh.agg_shift,
+                        A.mesh.n_agg);
+        restrict_units(r32, row < n, row, row0, A.mesh.crel, qs, A.mesh.agg_shift,
+                       A.slot.rcp + (size_t)b * A.slot.rcp_stride + 6 * ((size_t)row0 / kCoarseRows));
+    }
     double tot[2];
     double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
     if (tile_commit<2>(v, part, blockIdx.x, gridDim.x, &A.slot.sc[b].tk_init, 1, tot) && threadIdx.x == 0) {
@@ -239,14 +250,22 @@ __device__ __forceinline__ int unit_problem(const PcgDesc<T>* __restrict__ D, in
 // kernel is latency-bound on its dependent col -> gather loads.
 template <typename T, int TILE>
 __global__ void __launch_bounds__(TILE, 2048 / TILE) k_pcg_spmv(const PcgDesc<T>* __restrict__ D, int n_probs) {
-    pdl_wait();
-    pdl_trigger();
+    // prologue on data no kernel of the iteration writes (the descriptor table
+    // and the matrix structure), overlapping the previous kernel's drain
     const int u = blockIdx.x;
     const PcgDesc<T>& d = D[unit_problem(D, n_probs, u)];
     ProbScal* sc = d.sc;
-    if (sc->state != kActive) return;
     const int tile = u - d.unit_begin;
     const int row = tile * TILE + threadIdx.x;
+    int base = 0, w = 0;
+    if (row < d.n_rows) {
+        const int s = row >> 5;
+        base = __ldg(d.slice_ptr + s);
+        w = (__ldg(d.slice_ptr + s + 1) - base) >> 5;
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (sc->state != kActive) return;
     const int iter = sc->iter;
     const T* zpo = (iter & 1) ? d.zp1 : d.zp0;
     T* zpn = (iter & 1) ? d.zp0 : d.zp1;
@@ -255,8 +274,7 @@ __global__ void __launch_bounds__(TILE, 2048 / TILE) k_pcg_spmv(const PcgDesc<T>
     double v[1] = {0.0};
     Partial<T> pq = Partial<T>::zero();
     if (row < d.n_rows) {
-        const int s = row >> 5, lane = row & 31;
-        const int base = __ldg(d.slice_ptr + s), w = (__ldg(d.slice_ptr + s + 1) - base) >> 5;
+        const int lane = row & 31;
         T a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll 4
         for (int k = 0; k < w; ++k) {
@@ -299,19 +317,21 @@ __global__ void __launch_bounds__(TILE, 2048 / TILE) k_pcg_spmv(const PcgDesc<T>
 
 template <typename T, int TILE>
 __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restrict__ D, int n_probs) {
-    pdl_wait();
-    pdl_trigger();
-    const int u = blockIdx.x;
+    __shared__ float qs[4][9];
+    const int u = blockIdx.x;   // prologue: descriptor and pose rotations (fixed during the solve)
     const PcgDesc<T>& d = D[unit_problem(D, n_probs, u)];
     ProbScal* sc = d.sc;
-    if (sc->state != kActive) return;
     const int tile = u - d.unit_begin;
     const int row = tile * TILE + threadIdx.x;
+    const bool coarse = d.coarse != 0;
+    if (coarse) stage_rotations(qs, tile * TILE, d.agg_handle, d.xf, d.agg_shift, d.coarse_n / 6);
+    pdl_wait();
+    pdl_trigger();
+    if (sc->state != kActive) return;
     const int iter = sc->iter;
     T* zpn = (iter & 1) ? d.zp0 : d.zp1;
     T alpha, beta_unused;
     coeffs(sc, alpha, beta_unused);
-    const bool coarse = d.coarse != 0;
     double v[2] = {0.0, 0.0};
     float r32[3] = {0.f, 0.f, 0.f};
     Partial<T> rz = Partial<T>::zero(), rr2 = Partial<T>::zero();
@@ -341,8 +361,8 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
         r32[2] = (float)rr[2];
     }
     if (coarse)   // z is finished by k_pcg_correct, which also forms r.z and beta
-        restrict_units(r32, row < d.n_rows, row, tile * TILE, d.crel, d.agg_handle, d.xf, d.agg_shift,
-                       d.coarse_n / 6, d.rcp + 6 * ((size_t)tile * TILE / kCoarseRows));
+        restrict_units(r32, row < d.n_rows, row, tile * TILE, d.crel, qs, d.agg_shift,
+                       d.rcp + 6 * ((size_t)tile * TILE / kCoarseRows));
     v[0] = warp_sum_partial(rz);
     v[1] = warp_sum_partial(rr2);
     double tot[2];
@@ -374,10 +394,12 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
 // unit order, for the problems d0 .. d0+nd-1 (grid.y) of one mesh.
 template <typename T>
 __global__ void k_coarse_rc(const PcgDesc<T>* __restrict__ D, int d0, int nd) {
+    const PcgDesc<T>& q = D[d0 + blockIdx.y];
+    const bool coarse = q.coarse != 0;
+    ProbScal* sc = q.sc;
     pdl_wait();
     pdl_trigger();
-    const PcgDesc<T>& q = D[d0 + blockIdx.y];
-    if (!q.coarse || q.sc->state != kActive) return;
+    if (!coarse || sc->state != kActive) return;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= q.coarse_n) return;
     const int a = k / 6, comp = k - 6 * a;
@@ -392,19 +414,24 @@ __global__ void k_coarse_rc(const PcgDesc<T>* __restrict__ D, int d0, int nd) {
 template <typename T, int NP>
 __global__ void __launch_bounds__(256) k_coarse_gemm(const float* __restrict__ Ainv, int N, int ld,
                                                      const PcgDesc<T>* __restrict__ D, int d0, int nd) {
-    pdl_wait();
-    pdl_trigger();
     __shared__ __align__(16) float rs[NP * kCoarseKC];
     __shared__ const PcgDesc<T>* dp[NP];
     __shared__ int any;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int ks = blockIdx.y, pg = blockIdx.z;
+    const PcgDesc<T>* mine = nullptr;   // prologue: descriptors are fixed during the solve
+    ProbScal* msc = nullptr;
+    if (t < NP && pg * NP + t < nd && D[d0 + pg * NP + t].coarse) {
+        mine = &D[d0 + pg * NP + t];
+        msc = mine->sc;
+    }
     if (t == 0) any = 0;
+    pdl_wait();
+    pdl_trigger();
     __syncthreads();
     if (t < NP) {
-        const int q = pg * NP + t;
         const PcgDesc<T>* p = nullptr;
-        if (q < nd && D[d0 + q].coarse && D[d0 + q].sc->state == kActive) p = &D[d0 + q];
+        if (mine && msc->state == kActive) p = mine;
         dp[t] = p;
         if (p) atomicOr(&any, 1);
     }
@@ -489,38 +516,41 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(const float* __restrict__ A
 // coarse correction return at once.
 template <typename T, int TILE>
 __global__ void __launch_bounds__(TILE) k_pcg_correct(const PcgDesc<T>* __restrict__ D, int n_probs) {
-    pdl_wait();
-    pdl_trigger();
-    const int u = blockIdx.x;
-    const PcgDesc<T>& d = D[unit_problem(D, n_probs, u)];
-    ProbScal* sc = d.sc;
-    if (!d.coarse || sc->state != kActive) return;
-    const int tile = u - d.unit_begin;
-    const int row = tile * TILE + threadIdx.x;
     constexpr int kMaxAgg = TILE / kCoarseRows;   // aggregates a block can touch
     __shared__ float es[kMaxAgg][6];
     __shared__ float qs[kMaxAgg][9];
     __shared__ float part_e[TILE];
+    // prologue on data fixed during the solve (descriptor, rest offsets, pose
+    // rotations), overlapping the previous kernel's drain
+    const int u = blockIdx.x;
+    const PcgDesc<T>& d = D[unit_problem(D, n_probs, u)];
+    if (!d.coarse) return;
+    ProbScal* sc = d.sc;
+    const int tile = u - d.unit_begin;
+    const int row = tile * TILE + threadIdx.x;
     const int a0 = (tile * TILE) >> d.agg_shift;
     const int n_agg = d.coarse_n / 6;
     const int n_ks = (d.coarse_n + kCoarseKC - 1) / kCoarseKC;
+    float4 off = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (row < d.n_rows) off = d.crel[row];
+    if ((int)threadIdx.x < kMaxAgg * 9) {
+        const int ai = threadIdx.x / 9, q = threadIdx.x % 9, a = a0 + ai;
+        qs[ai][q] = a < n_agg ? (float)d.xf[12 * d.agg_handle[a] + 4 * (q / 3) + q % 3] : 0.f;
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (sc->state != kActive) return;   // block-uniform: before any barrier
     // the row's own loads go out first, so their latency overlaps the staging
     T* zp = (sc->iter & 1) ? d.zp1 : d.zp0;   // the record the next k_pcg_spmv reads
     T r[3] = {(T)0, (T)0, (T)0}, z[3] = {(T)0, (T)0, (T)0};
-    float4 off = make_float4(0.f, 0.f, 0.f, 0.f);
     if (row < d.n_rows) {
         ld4(d.rec + kRec * (size_t)row + kRecR, r);
         ld4(zp + 8 * (size_t)row, z);
-        off = d.crel[row];
     }
     // slice partials of e, one load per thread, then added in slice order
     for (int idx = threadIdx.x; idx < kMaxAgg * 6 * n_ks; idx += TILE) {
         const int ks = idx / (kMaxAgg * 6), r = idx - ks * kMaxAgg * 6, a = a0 + r / 6;
         if (idx < TILE) part_e[idx] = a < n_agg ? d.ec[(size_t)ks * d.coarse_n + 6 * a + r % 6] : 0.f;
-    }
-    if ((int)threadIdx.x < kMaxAgg * 9) {
-        const int ai = threadIdx.x / 9, q = threadIdx.x % 9, a = a0 + ai;
-        qs[ai][q] = a < n_agg ? (float)d.xf[12 * d.agg_handle[a] + 4 * (q / 3) + q % 3] : 0.f;
     }
     __syncthreads();
     if ((int)threadIdx.x < kMaxAgg * 6) {
