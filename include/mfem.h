@@ -81,7 +81,8 @@ typedef struct {
  * with no bones, the nearest joint); MFEM_CLUSTER_JOINT takes the nearest
  * joint; MFEM_CLUSTER_MIDPOINT the bone whose midpoint is nearest (the
  * variants compared in §4, "Exploring different rotation clustering");
- * tet_cluster [m] (handle indices) overrides all (§4, user-defined clusters).  Pins (Eq. 6 "pin vertices along the skeleton"): pin_verts /
+ * tet_cluster [m] (handle indices) overrides all (§4, user-defined clusters).
+ * Pins (Eq. 6; vertices held along the skeleton): pin_verts /
  * pin_handle [n_pins] if given, else every vertex within pin_radius of a joint
  * or a bone midpoint, following the handle its position clusters to.  Ties in
  * nearest-X searches go to the lowest index (a 1e-10 * bbox_diag^2 margin). */
