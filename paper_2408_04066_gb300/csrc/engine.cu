@@ -21,6 +21,8 @@ constexpr double kLsNoise = 1.0e-10; // predicted decrease below this * |E|: tak
 constexpr int kPcgTiles[3] = {64, 128, 256};   // PCG rows per block the autotuner times
 constexpr int kPcgChunk = 16;                   // PCG iterations enqueued between convergence checks
 constexpr double kPredTol = 3e-3;   // PCG target of the co-rotational predictor step (at most cg_tol)
+constexpr double kEwGamma = 0.9;    // forcing rule where the Newton model is trusted (see advance)
+constexpr double kEwMin = 1e-4;     // tightest PCG target that rule sets (well above FP32 PCG's floor)
 }  // namespace
 
 namespace mfem {
@@ -724,20 +726,49 @@ mfem_status advance(std::vector<Group>& gs) {
             }
             mfem_status st = upload_active(gc, g.B, start);
             if (st != MFEM_OK) return st;
-            // PCG target of this Newton step: cg_tol, loosened when a smaller
-            // reduction already reaches newton_tol (half of what the linear model
-            // says is needed), at most 0.5.  The predictor step is solved tighter:
-            // its error, not the SNH nonlinearity, would otherwise set where the
-            // first SNH step starts (measured: 3e-3 saves ~8% of PCG iterations
-            // and a quarter of a Newton step on the 200k figure against 1e-2)
+            // PCG target of this Newton step: cg_tol; where the Newton model is
+            // trusted -- a quadratic energy (ARAP or corot with rig rotations:
+            // Newton is iterative refinement of one linear solve) or a warm start
+            // (near the solution) -- tightened after each step to
+            // 0.9 (|g_k| / |g_k-1|)^2 (Eisenstat-Walker's second choice, with
+            // their safeguard, at least kEwMin), so that a step the model
+            // predicts well is followed by a more accurate one; loosened when a
+            // smaller reduction already reaches newton_tol (half of what the
+            // linear model says is needed), at most 0.5.  The predictor step is
+            // solved tighter: its error, not the SNH nonlinearity, would otherwise
+            // set where the first SNH step starts (measured: 3e-3 saves ~8% of
+            // PCG iterations and a quarter of a Newton step on the 200k figure
+            // against 1e-2).  Measured on the 200k figure, batch of 16: the
+            // tightening takes corot from 4 to 3 Newton steps (297 -> 340
+            // frames/s) and warm-started SNH streams from 3.6 to 3.1 (+14%), but
+            // costs cold SNH poses 1.3%, which therefore keep the fixed target.
+            const bool quadratic = gc->model != MFEM_SNH && gc->opt.rotation == MFEM_ROT_RIG;
+            const bool trusted = quadratic || gc->opt.init == MFEM_INIT_WARM;
             std::vector<double> t2(g.B, 0.0);
             for (int b = 0; b < g.B; ++b) {
-                const ProbHost& p = g.ph[b];
+                ProbHost& p = g.ph[b];
                 double eta = p.pred ? std::min(gc->opt.cg_tol, kPredTol) : gc->opt.cg_tol;
-                if (start[b] && !p.pred && p.g0 > 0.0 && p.gn > 0.0)
-                    eta = std::min(0.5, std::max(eta, 0.5 * gc->opt.newton_tol * p.g0 / p.gn));
+                if (start[b] && trusted && !p.pred && p.gprev > 0.0 && p.gn > 0.0) {
+                    const double rho = p.gn / p.gprev;
+                    double ew = kEwGamma * rho * rho;
+                    const double guard = kEwGamma * p.eta_prev * p.eta_prev;
+                    if (guard > 0.1) ew = std::max(ew, guard);
+                    eta = std::min(eta, std::max(ew, kEwMin));
+                }
+                bool last = false;   // solved to just reach newton_tol
+                if (start[b] && !p.pred && p.g0 > 0.0 && p.gn > 0.0) {
+                    const double need = 0.5 * gc->opt.newton_tol * p.g0 / p.gn;
+                    last = need > eta;
+                    eta = std::min(0.5, std::max(eta, need));
+                }
                 t2[b] = eta * eta;
-                if (start[b]) g.ph[b].expect_conv = !p.pred && eta > gc->opt.cg_tol;
+                if (start[b]) {
+                    p.expect_conv = last;
+                    if (!p.pred) {
+                        p.gprev = p.gn;
+                        p.eta_prev = eta;
+                    }
+                }
             }
             st = upload_doubles(gc, g.B, t2.data(), gc->slot.tol2);
             if (st != MFEM_OK) return st;

@@ -32,6 +32,8 @@ struct ProbHost {
                          // iterate with forces only (no element Hessian, no matrix)
     int need_hess = 0;   // that test failed: the next element pass forms the Hessian
     double g0 = -1.0, gn = 0.0, energy = 0.0;
+    double gprev = -1.0;   // |g_free| before the last Newton step (not the predictor), for the forcing rule
+    double eta_prev = 0.0; // that step's PCG target
 };
 
 // Profile accumulator with a pool of CUDA events on the context stream.
