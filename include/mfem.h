@@ -108,7 +108,11 @@ typedef struct {
     double k_s;          /* penalty stiffness (PENALTY only) */
     double newton_tol;   /* stop when |g_free| <= newton_tol |g_free(x_0)| (1e-6) */
     double cg_tol;       /* PCG relative residual per Newton step, inexact Newton (3e-2);
-                            a step that needs less to reach newton_tol takes
+                            for quadratic energies (ARAP, corot with rig rotations)
+                            and WARM starts each step after the first takes
+                            min(cg_tol, max(1e-4, 0.9 (|g_k| / |g_k-1|)^2)),
+                            safeguarded (Eisenstat-Walker); a step that needs less
+                            to reach newton_tol takes
                             eta = min(0.5, 0.5 newton_tol |g_free(x_0)| / |g_free|);
                             the co-rotational predictor step takes min(cg_tol, 3e-3) */
     int32_t newton_max;  /* Newton step cap (50) */
