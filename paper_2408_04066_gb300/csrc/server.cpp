@@ -97,12 +97,14 @@ void mfem_server::run() {
     cudaSetDevice(device);
     for (;;) {
         std::vector<std::pair<int, int>> admitted;
-        size_t nm = 0;
+        // the meshes known at this step, taken under the lock: mfem_server_add
+        // may append to the deque meanwhile (element addresses stay valid)
+        std::vector<MeshEntry*> ms;
         {
             std::unique_lock<std::mutex> lk(mu);
-            nm = meshes.size();
             cv_work.wait(lk, [&] { return stop || !queue.empty() || in_use > 0; });
             if (stop && in_use == 0) break;
+            for (auto& m : meshes) ms.push_back(&m);
             // admission: FIFO scan, a full mesh does not block other meshes
             for (auto it = queue.begin(); it != queue.end() && in_use < max_slots;) {
                 Request& r = reqs[*it];
@@ -137,8 +139,8 @@ void mfem_server::run() {
             }
         }
         std::vector<Group> gs;
-        for (size_t mi = 0; mi < nm; ++mi) {
-            MeshEntry& me = meshes[mi];
+        for (MeshEntry* mp : ms) {
+            MeshEntry& me = *mp;
             bool busy = false;
             for (int b = 0; b < me.cap; ++b) busy |= me.slot_req[b] != 0;
             if (busy) {
@@ -156,8 +158,8 @@ void mfem_server::run() {
             continue;
         }
         // completion
-        for (size_t mi = 0; mi < nm; ++mi) {
-            MeshEntry& me = meshes[mi];
+        for (MeshEntry* mp : ms) {
+            MeshEntry& me = *mp;
             for (int b = 0; b < me.cap; ++b) {
                 if (!me.slot_req[b] || me.ph[b].active || me.ph[b].need_init) continue;
                 mfem_ctx* c = me.ctx;
