@@ -94,3 +94,33 @@ def test_host_plan_other_cluster_rules_match_oracle(lib, rule):
     st = S.Setup.from_config(dict(cfg, cluster_rule=rule))
     assert np.array_equal(tc, st.cluster)
     assert np.array_equal(np.nonzero(pinned)[0], np.sort(st.pin_verts))
+
+
+@pytest.mark.parametrize("rule", ["bone", "joint", "midpoint"])
+@pytest.mark.parametrize("seed", range(4))
+def test_host_plan_matches_oracle_on_grid_rigs_with_ties(lib, rule, seed):
+    """Random voxel blobs with joints on the half-integer grid: many tet
+    barycenters and vertices sit at exactly equal distances from two joints,
+    bones or midpoints, so the tie rule (lowest index within the margin) is
+    exercised, and the host planner must still agree with the oracle."""
+    rng = np.random.default_rng(100 + seed)
+    from synth.meshes import kuhn_voxel_mesh
+    occ = rng.random((5, 4, 6)) < 0.6
+    occ[2, 2, :] = True                                  # a spine through the blob
+    X, T = kuhn_voxel_mesh(occ, 1.0)
+    H = int(rng.integers(2, 7))
+    joints = rng.integers(0, 11, size=(H, 3)) * 0.5
+    joints[:, 0] = np.minimum(joints[:, 0], 5.0)
+    joints[:, 1] = np.minimum(joints[:, 1], 4.0)
+    parent = np.array([-1] + [int(rng.integers(0, j)) for j in range(1, H)], dtype=np.int32)
+    for j in range(1, H):                                # no zero-length bones
+        if np.allclose(joints[j], joints[parent[j]]):
+            joints[j, 2] += 0.5
+    cfg = dict(X=X, T=T, joints=joints, parent=parent, cluster_rule=rule, pin_verts=None, pin_handle=None,
+               pin_radius=0.75, model="arap", mu=1.0, lam=0.0)
+    tc, pinned, ph = mfem.plan(X, T, joints, parent, rule, None, None, cfg["pin_radius"])
+    st = S.Setup.from_config(cfg)
+    assert np.array_equal(tc, st.cluster)
+    assert np.array_equal(np.nonzero(pinned)[0], np.sort(st.pin_verts))
+    order = np.argsort(st.pin_verts)
+    assert np.array_equal(ph[pinned], st.pin_handle[order])
