@@ -124,3 +124,29 @@ def test_host_plan_matches_oracle_on_grid_rigs_with_ties(lib, rule, seed):
     assert np.array_equal(np.nonzero(pinned)[0], np.sort(st.pin_verts))
     order = np.argsort(st.pin_verts)
     assert np.array_equal(ph[pinned], st.pin_handle[order])
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """No silent fallback: loading a library that is not there raises."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = ("from paper_2408_04066_gb300 import mfem\n"
+            "try:\n"
+            f"    mfem.load({str(tmp_path / 'libmfem.so')!r})\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n")
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and "raised:" in r.stdout and "is missing" in r.stdout
+
+
+def test_context_without_a_gpu_is_an_error(lib):
+    """Without a CUDA device, creating a context returns MFEM_ECUDA: the
+    product path has no CPU fallback."""
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    cfg = bar_twist_config()
+    with pytest.raises(mfem.MfemError) as e:
+        mfem.Context.from_config(cfg, precision="fp64")
+    assert e.value.status == mfem.MFEM_ECUDA
