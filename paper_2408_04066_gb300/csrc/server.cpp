@@ -150,10 +150,13 @@ void mfem_server::run() {
         }
         if (gs.empty()) continue;
         mfem_status st = advance(gs);
-        steps++;
-        for (auto& g : gs) pcg_launches += g.ctx->prof.pcg_launches;
+        {
+            std::lock_guard<std::mutex> lk(mu);   // counters and err are read by other threads
+            steps++;
+            for (auto& g : gs) pcg_launches += g.ctx->prof.pcg_launches;
+            if (st != MFEM_OK) err = gs[0].ctx->err;
+        }
         if (st != MFEM_OK) {
-            err = gs[0].ctx->err;
             fail_all_busy(st);
             continue;
         }
