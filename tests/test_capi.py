@@ -150,3 +150,42 @@ def test_context_without_a_gpu_is_an_error(lib):
     with pytest.raises(mfem.MfemError) as e:
         mfem.Context.from_config(cfg, precision="fp64")
     assert e.value.status == mfem.MFEM_ECUDA
+
+
+def _header_struct_fields(name):
+    """Field names and C types of `typedef struct { ... } name;` in the header,
+    in declaration order (comments stripped; `double a, b;` gives two fields)."""
+    text = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*" + name + r"\s*;", text).group(1)
+    fields = []
+    for decl in body.split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        m = re.match(r"((?:const )?[A-Za-z_0-9]+\s*\**)\s*(.*)", decl)
+        ctype, names = m.group(1).replace(" ", ""), m.group(2)
+        for n in names.split(","):
+            n = n.strip()
+            stars = len(n) - len(n.lstrip("*"))
+            fields.append((n.lstrip("*"), ctype + "*" * stars))
+    return fields
+
+
+_CTYPE = {"int32_t": "c_int", "double": "c_double", "int64_t": "c_long", "size_t": "c_ulong"}
+
+
+@pytest.mark.parametrize("cname,pyname", [("mfem_material", "Material"), ("mfem_handles", "Handles"),
+                                          ("mfem_options", "Options"), ("mfem_stats", "Stats"),
+                                          ("mfem_profile", "Profile")])
+def test_binding_structs_match_the_header(cname, pyname):
+    """The ctypes structures declare the header's fields in the same order with
+    the same widths, so no field is read at a shifted offset."""
+    import ctypes as C
+    hdr = _header_struct_fields(cname)
+    py = getattr(mfem, pyname)._fields_
+    assert [n.rstrip("_") for n, _ in py] == [n for n, _ in hdr]   # lambda_: a Python keyword
+    for (n, t), (_, pt) in zip(hdr, py):
+        if t.endswith("*"):
+            assert C.sizeof(pt) == C.sizeof(C.c_void_p), n
+        else:
+            assert C.sizeof(pt) == C.sizeof(getattr(C, _CTYPE[t])), (n, t)
