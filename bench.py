@@ -231,6 +231,74 @@ def oracle_step_times(tets, model, seed, nsteps):
     return times
 
 
+def _oracle_concurrent_step(tets, model, seed, barrier, q):
+    os.environ["OMP_NUM_THREADS"] = "1"
+    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    sys.path.insert(0, ROOT)
+    from oracle import solve as S
+    from synth import figure_config
+    try:
+        cfg = figure_config(tets, model=model, seeds=[seed])
+        st = S.Setup.from_config(cfg)
+        kw = dict(newton_tol=1e-6, linear="cg", cg_tol=1e-2)
+        barrier.wait(timeout=600)          # every process times its step at the same time
+        t0 = time.perf_counter()
+        S.solve(st, cfg["xfs"][0], model, newton_max=1, **kw)
+        t1 = time.perf_counter()
+        S.solve(st, cfg["xfs"][0], model, newton_max=0, **kw)
+        t2 = time.perf_counter()
+        q.put(max((t1 - t0) - (t2 - t1), 1e-9))
+    except Exception as e:                 # reported, not raised: the parent waits on the queue
+        q.put(repr(e))
+
+
+def oracle_concurrent_step_times(tets, model, nprocs, timeout_s=180.0):
+    """One oracle Newton step (CG mode) in each of `nprocs` spawned processes
+    (poses 0 .. nprocs-1), started together; returns their step times."""
+    import multiprocessing as mp
+    import queue
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    barrier = ctx.Barrier(nprocs)
+    ps = [ctx.Process(target=_oracle_concurrent_step, args=(tets, model, k, barrier, q)) for k in range(nprocs)]
+    for p in ps:
+        p.start()
+    deadline = time.time() + timeout_s
+    out = []
+    try:
+        for _ in range(nprocs):
+            out.append(q.get(timeout=max(1.0, deadline - time.time())))
+    except queue.Empty:
+        out.append("timed out")
+    finally:
+        for p in ps:
+            p.join(timeout=10)
+            if p.is_alive():
+                p.terminate()
+                p.join(timeout=10)
+    bad = [o for o in out if not isinstance(o, float)]
+    if bad:
+        raise RuntimeError(f"oracle processes failed: {bad[0]}")
+    return out
+
+
+def cpu_baseline_all_cores(args, steps_frame):
+    """The oracle on every host core: one pose per core, all timing one Newton
+    step at the same time (threads per process = 1)."""
+    try:
+        nprocs = len(os.sched_getaffinity(0))     # the cores this process may run on
+    except AttributeError:
+        nprocs = os.cpu_count() or 1
+    times = oracle_concurrent_step_times(args.tets, args.model, nprocs)
+    spf, _ = newton_steps_per_frame()
+    spf = spf or steps_frame
+    t = max(times)
+    return {"value": nprocs / (t * spf), "unit": UNIT, "cores": nprocs, "kind": "oracle",
+            "sample": (f"{nprocs} processes, one oracle Newton step (FP64, Jacobi-PCG to 1e-2) of poses 0-{nprocs - 1} "
+                       f"each on the {args.tets // 1000}k-tet figure, started together; slowest {t:.2f} s "
+                       f"(mean {statistics.mean(times):.2f} s), x {spf:.2f} Newton steps per frame")}
+
+
 def cpu_baseline(args, steps_frame):
     times = oracle_step_times(args.tets, args.model, 0, args.cpu_newton_steps)
     t = statistics.mean(times)
@@ -405,9 +473,13 @@ def run_mfem(args, dist):
         fp64["mixed_vs_fp64_max_err_over_bbox"] = float((xm - x64).abs().max().item() / bbox)
         ctx64.close()
 
-    cpu = None
+    cpu = cpu_all = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args, statistics.mean(newton))
+        try:
+            cpu_all = cpu_baseline_all_cores(args, statistics.mean(newton))
+        except Exception as e:     # context only: the line is printed without it
+            cpu_all = {"unavailable": str(e)[:200]}
 
     if dist.rank == 0:
         lat = sorted(step_ms)
@@ -424,7 +496,7 @@ def run_mfem(args, dist):
             "newton_iters_mean": statistics.mean(newton), "pcg_iters_mean": statistics.mean(pcg_it),
             "all_converged": conv,
             "element_updates_per_s": dist.sum(sum(p["element_updates"] for p in prof)) / (total_ms_max / 1e3),
-            "roofline": roof, "cpu_baseline": cpu,
+            "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xfs_h.numel() * 8),
                     "d2h_bytes_per_step": int(out_h.numel() * 8)},
             "gpu_launches": launches, "clocks": clk,

@@ -87,3 +87,13 @@ def test_reference_arm_under_torchrun_prints_on_rank_zero_only():
     assert r.returncode == 0, r.stderr[-2000:]
     lines = _json_lines(r.stdout)
     assert len(lines) == 1 and lines[0]["impl"] == "reference" and lines[0]["n_gpus"] == 2
+
+
+def test_oracle_on_all_cores_runs_one_pose_per_process():
+    """The all-core CPU baseline: spawned oracle processes time one Newton step
+    each, started together; a failing process is reported, not waited on."""
+    import bench
+    times = bench.oracle_concurrent_step_times(3000, "snh", 2)
+    assert len(times) == 2 and all(isinstance(t, float) and t > 0 for t in times)
+    with pytest.raises(RuntimeError):
+        bench.oracle_concurrent_step_times(3000, "no-such-model", 2)
