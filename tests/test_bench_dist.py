@@ -97,3 +97,25 @@ def test_oracle_on_all_cores_runs_one_pose_per_process():
     assert len(times) == 2 and all(isinstance(t, float) and t > 0 for t in times)
     with pytest.raises(RuntimeError):
         bench.oracle_concurrent_step_times(3000, "no-such-model", 2)
+
+
+def test_roofline_arithmetic():
+    """`roofline` of the JSON line: achieved = algorithmic bytes / PCG time,
+    frac = achieved / peak, traffic = the ncu record's bytes per
+    pose-iteration x pose-iterations per launch pair (or None without a record
+    for the current kernel source)."""
+    import bench
+    profs = [dict(pcg_ms=2.0, pcg_bytes=8e9, pcg_launches=40, pcg_iters=100),
+             dict(pcg_ms=3.0, pcg_bytes=12e9, pcg_launches=60, pcg_iters=140)]
+    r = bench._roofline(profs, total_ms=10.0)
+    peak, kind = bench.hbm_peak()
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == peak
+    assert r["achieved"] == pytest.approx(20e9 / 5e-3 / 1e9)           # 4000 GB/s
+    assert r["frac"] == pytest.approx(r["achieved"] / peak)
+    assert r["launch_pairs"] == 50 and r["pose_iterations_per_pair"] == pytest.approx(240 / 50)
+    assert r["share_of_step"] == pytest.approx(0.5)
+    rec = bench.pcg_traffic_record()
+    if rec is None:
+        assert r["traffic"] is None
+    else:
+        assert r["traffic"] == pytest.approx(rec["dram_bytes_per_pose_iteration"] * 240 / 50)
