@@ -42,7 +42,6 @@ def parse():
     p.add_argument("--precision", default="mixed")
     p.add_argument("--fp64-steps", type=int, default=2)
     p.add_argument("--no-cpu-baseline", action="store_true")
-    p.add_argument("--cpu-newton-steps", type=int, default=2)
     p.add_argument("--workload", default="figure200k", choices=["figure200k", "batched", "serve", "large"],
                    help="figure200k: the headline batch; batched: 64+64 warm-started animation streams of "
                         "a 200k and a 50k figure in shared launches; serve: Poisson arrivals over resident "
@@ -165,102 +164,118 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+PCG_SOURCES = ("k_pcg.cu", "k_coarse_tc.cu", "dev.cuh")
+PCG_KERNELS = ("PCG iteration (k_pcg_spmv + k_pcg_update; on two-level steps also the coarse product "
+               "k_coarse_tc and k_pcg_correct)")
+
+
 def kernel_source_hash():
-    """Hash of the PCG kernels' sources (k_pcg.cu and the device header)."""
+    """Hash of the PCG kernels' sources (the iteration kernels, the tensor-core
+    coarse product and the device header)."""
     import hashlib
     h = hashlib.sha256()
-    for f in ("k_pcg.cu", "dev.cuh"):
+    for f in PCG_SOURCES:
         h.update(open(os.path.join(ROOT, "paper_2408_04066_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
 
-def pcg_traffic_record():
+def pcg_traffic_record(mesh=None):
     """DRAM bytes per pose-iteration of the PCG kernels from the committed ncu
     summary (profiles/pcg_traffic.json), if it was taken on the current kernel
-    source (hash of k_pcg.cu and dev.cuh); else None."""
+    source and, when `mesh` = (tets, verts) is given, on that mesh; else None."""
     rec = os.path.join(ROOT, "profiles", "pcg_traffic.json")
     try:
         with open(rec) as f:
             r = json.load(f)
-        return r if r.get("pcg_src_sha256_16") == kernel_source_hash() else None
     except (OSError, ValueError):
         return None
+    if r.get("pcg_src_sha256_16") != kernel_source_hash():
+        return None
+    if mesh is not None and tuple(r.get("mesh", ())) != tuple(mesh):
+        return None
+    return r
 
 
 # ---------------------------------------------------------------- CPU oracle
-def newton_steps_per_frame():
-    path = os.path.join(ROOT, "tests", "golden", "figure200k_newton_steps.txt")
-    try:
-        rows = [l.split() for l in open(path) if l.strip() and not l.startswith("#")]
-        return statistics.mean(float(r[1]) for r in rows), path
-    except (OSError, ValueError, statistics.StatisticsError):
-        return None, path
+# A frame of the oracle = one whole pose solve as the GPU path does it: FP64
+# throughout, the co-rotational predictor, Newton steps with the oracle's own
+# FP64 Jacobi-PCG to a relative residual of 1e-2 (inexact Newton, like the GPU
+# path), backtracking line search, stop at |g_free| <= 1e-6 |g_free(x_ref)|.
+# (Its sparse direct solver takes minutes per frame on this mesh, so it serves
+# the parity tests, not the timed baseline.)  Mesh set-up is not timed.
+ORACLE_FRAME = dict(newton_tol=1e-6, linear="cg", cg_tol=1e-2)
 
 
-def _oracle_newton_steps(tets, model, seed, nsteps, q):
-    os.environ["OMP_NUM_THREADS"] = "1"
-    os.environ["OPENBLAS_NUM_THREADS"] = "1"
+def _single_thread():
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+
+
+def _oracle_frames(tets, model, seeds, warm_seed, q):
+    """Time full oracle frames of the given poses after one untimed warm-up frame."""
+    _single_thread()
     sys.path.insert(0, ROOT)
-    from oracle import solve as S
-    from synth import figure_config
-    cfg = figure_config(tets, model=model, seeds=[seed])
-    st = S.Setup.from_config(cfg)
-    times = []
-    kw = dict(newton_tol=1e-6, linear="cg", cg_tol=1e-2)
-    for k in range(nsteps):
-        # one Newton step = solve with one step minus solve with none (the
-        # latter holds the reference and final gradient/energy evaluations)
-        t0 = time.perf_counter()
-        S.solve(st, cfg["xfs"][0], model, newton_max=1, **kw)
-        t1 = time.perf_counter()
-        S.solve(st, cfg["xfs"][0], model, newton_max=0, **kw)
-        t2 = time.perf_counter()
-        times.append(max((t1 - t0) - (t2 - t1), 1e-9))
-    q.put(times)
-
-
-def oracle_step_times(tets, model, seed, nsteps):
-    """Time `nsteps` single oracle Newton steps (CG mode) in a spawned process."""
-    import multiprocessing as mp
-    ctx = mp.get_context("spawn")
-    q = ctx.Queue()
-    p = ctx.Process(target=_oracle_newton_steps, args=(tets, model, seed, nsteps, q))
-    p.start()
-    times = q.get()
-    p.join()
-    return times
-
-
-def _oracle_concurrent_step(tets, model, seed, barrier, q):
-    os.environ["OMP_NUM_THREADS"] = "1"
-    os.environ["OPENBLAS_NUM_THREADS"] = "1"
-    sys.path.insert(0, ROOT)
-    from oracle import solve as S
-    from synth import figure_config
     try:
-        cfg = figure_config(tets, model=model, seeds=[seed])
+        from oracle import solve as S
+        from synth import figure_config
+        cfg = figure_config(tets, model=model, seeds=list(seeds) + [warm_seed])
         st = S.Setup.from_config(cfg)
-        kw = dict(newton_tol=1e-6, linear="cg", cg_tol=1e-2)
-        barrier.wait(timeout=600)          # every process times its step at the same time
-        t0 = time.perf_counter()
-        S.solve(st, cfg["xfs"][0], model, newton_max=1, **kw)
-        t1 = time.perf_counter()
-        S.solve(st, cfg["xfs"][0], model, newton_max=0, **kw)
-        t2 = time.perf_counter()
-        q.put(max((t1 - t0) - (t2 - t1), 1e-9))
+        S.solve(st, cfg["xfs"][-1], model, **ORACLE_FRAME)          # warm-up frame
+        times = []
+        for i in range(len(seeds)):
+            t0 = time.perf_counter()
+            _, info = S.solve(st, cfg["xfs"][i], model, **ORACLE_FRAME)
+            times.append(time.perf_counter() - t0)
+        q.put(times)
     except Exception as e:                 # reported, not raised: the parent waits on the queue
         q.put(repr(e))
 
 
-def oracle_concurrent_step_times(tets, model, nprocs, timeout_s=180.0):
-    """One oracle Newton step (CG mode) in each of `nprocs` spawned processes
-    (poses 0 .. nprocs-1), started together; returns their step times."""
+def oracle_frame_times(tets, model, seeds, warm_seed=99, timeout_s=900.0):
+    """Full oracle frames of `seeds`, one after another in one spawned
+    single-threaded process, after one warm-up frame."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_oracle_frames, args=(tets, model, list(seeds), warm_seed, q))
+    p.start()
+    try:
+        out = q.get(timeout=timeout_s)
+    finally:
+        p.join(timeout=30)
+        if p.is_alive():
+            p.terminate()
+    if not isinstance(out, list):
+        raise RuntimeError(f"oracle process failed: {out}")
+    return out
+
+
+def _oracle_concurrent_frame(tets, model, seed, barrier, q):
+    _single_thread()
+    sys.path.insert(0, ROOT)
+    try:
+        from oracle import solve as S
+        from synth import figure_config
+        cfg = figure_config(tets, model=model, seeds=[seed, 1000 + seed])
+        st = S.Setup.from_config(cfg)
+        S.solve(st, cfg["xfs"][1], model, **ORACLE_FRAME)           # warm-up frame
+        barrier.wait(timeout=900)          # every process times its frame at the same time
+        t0 = time.perf_counter()
+        S.solve(st, cfg["xfs"][0], model, **ORACLE_FRAME)
+        q.put(time.perf_counter() - t0)
+    except Exception as e:                 # reported, not raised: the parent waits on the queue
+        q.put(repr(e))
+
+
+def oracle_concurrent_frame_times(tets, model, nprocs, timeout_s=900.0):
+    """One full oracle frame in each of `nprocs` spawned single-threaded
+    processes (poses 0 .. nprocs-1), timed together after a warm-up frame."""
     import multiprocessing as mp
     import queue
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     barrier = ctx.Barrier(nprocs)
-    ps = [ctx.Process(target=_oracle_concurrent_step, args=(tets, model, k, barrier, q)) for k in range(nprocs)]
+    ps = [ctx.Process(target=_oracle_concurrent_frame, args=(tets, model, k, barrier, q)) for k in range(nprocs)]
     for p in ps:
         p.start()
     deadline = time.time() + timeout_s
@@ -282,35 +297,34 @@ def oracle_concurrent_step_times(tets, model, nprocs, timeout_s=180.0):
     return out
 
 
-def cpu_baseline_all_cores(args, steps_frame):
-    """The oracle on every host core: one pose per core, all timing one Newton
-    step at the same time (threads per process = 1)."""
+def host_cores():
     try:
-        nprocs = len(os.sched_getaffinity(0))     # the cores this process may run on
+        return len(os.sched_getaffinity(0))     # the cores this process may run on
     except AttributeError:
-        nprocs = os.cpu_count() or 1
-    times = oracle_concurrent_step_times(args.tets, args.model, nprocs)
-    spf, _ = newton_steps_per_frame()
-    spf = spf or steps_frame
+        return os.cpu_count() or 1
+
+
+def cpu_baseline_all_cores(args):
+    """The oracle on every host core: one pose per core, every process timing
+    one full frame at the same time (threads per process = 1)."""
+    nprocs = host_cores()
+    times = oracle_concurrent_frame_times(args.tets, args.model, nprocs)
     t = max(times)
-    return {"value": nprocs / (t * spf), "unit": UNIT, "cores": nprocs, "kind": "oracle",
-            "sample": (f"{nprocs} processes, one oracle Newton step (FP64, Jacobi-PCG to 1e-2) of poses 0-{nprocs - 1} "
-                       f"each on the {args.tets // 1000}k-tet figure, started together; slowest {t:.2f} s "
-                       f"(mean {statistics.mean(times):.2f} s), x {spf:.2f} Newton steps per frame")}
+    return {"value": nprocs / t, "unit": UNIT, "cores": nprocs, "kind": "oracle",
+            "sample": (f"{nprocs} single-threaded processes, one full oracle frame each (poses 0-{nprocs - 1} of the "
+                       f"{args.tets // 1000}k-tet figure; FP64, Jacobi-PCG 1e-2 inexact Newton to 1e-6) after one "
+                       f"warm-up frame, timed together; slowest {t:.2f} s, mean {statistics.mean(times):.2f} s")}
 
 
-def cpu_baseline(args, steps_frame):
-    times = oracle_step_times(args.tets, args.model, 0, args.cpu_newton_steps)
-    t = statistics.mean(times)
-    spf, src = newton_steps_per_frame()
-    if spf is None:
-        spf = steps_frame
-        src = "GPU-measured Newton steps per frame"
-    return {"value": 1.0 / (t * spf), "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": (f"{len(times)} oracle Newton steps (FP64, Jacobi-PCG to 1e-2) of pose 0 on the "
-                       f"{args.tets // 1000}k-tet figure, {t:.2f} s each, x {spf:.2f} Newton steps per frame "
-                       f"(oracle counts, {os.path.relpath(src, ROOT) if os.path.isabs(src) else src}); "
-                       f"BLAS/OpenMP threads = 1")}
+def cpu_baseline(args):
+    """Median of 5 full oracle frames (poses 0-4) after one warm-up frame,
+    single-threaded."""
+    times = oracle_frame_times(args.tets, args.model, range(5))
+    t = statistics.median(times)
+    return {"value": 1.0 / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": (f"median of 5 frames: full oracle frames of poses 0-4 of the {args.tets // 1000}k-tet figure "
+                       f"(FP64, Jacobi-PCG 1e-2 inexact Newton to 1e-6), after one warm-up frame, one thread "
+                       f"(BLAS/OpenMP threads = 1); frame times {', '.join(f'{x:.2f}' for x in times)} s")}
 
 
 def workload_config(m, n, H, pins, nb, precision):
@@ -320,18 +334,20 @@ def workload_config(m, n, H, pins, nb, precision):
 
 
 def run_reference(args, dist):
+    """The oracle as the reference arm: each step is one full oracle frame of
+    the workload's figure (pose = step index mod 16), single-threaded, after
+    `warmup` untimed frames."""
     if dist.rank != 0:
         return
     from synth import figure_config
     from oracle import solve as S
     cfg = figure_config(args.tets, model=args.model, seeds=[0])   # mesh generation is setup, not timed
     st = S.Setup.from_config(cfg)
-    total = oracle_step_times(args.tets, args.model, 0, args.warmup + args.steps)
+    total = oracle_frame_times(args.tets, args.model, [k % 16 for k in range(args.warmup + args.steps)],
+                               timeout_s=3600.0)
     times = total[args.warmup:]
     t = statistics.mean(times)
-    spf, src = newton_steps_per_frame()
-    spf = spf or 1.0
-    value = 1.0 / (t * spf)
+    value = 1.0 / t
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t, "higher_is_better": True,
@@ -339,8 +355,9 @@ def run_reference(args, dist):
         "config": dict(workload_config(st.m, st.n, len(cfg["joints"]), len(st.pin_verts), args.batch,
                                        args.precision), parallelism="oracle, 1 CPU thread"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"each step = one oracle Newton step (FP64, Jacobi-PCG 1e-2) of pose 0; "
-                                   f"frames/s = 1 / (mean step time x {spf:.2f} Newton steps per frame)"},
+                         "sample": (f"each step = one full oracle frame (FP64, Jacobi-PCG 1e-2 inexact Newton to "
+                                    f"1e-6) of pose (step mod 16), one thread, {args.warmup} untimed warm-up frames; "
+                                    f"frames/s = 1 / mean frame time")},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -412,8 +429,8 @@ def run_mfem(args, dist):
     pairs = max(pcg_launches // 2, 1)
     peak, peak_kind = hbm_peak()
     achieved = pcg_bytes / (pcg_ms / 1e3) / 1e9 if pcg_ms > 0 else 0.0
-    tr = pcg_traffic_record()
-    roof = {"kernel": "PCG iteration (k_pcg_spmv + k_pcg_update, + k_coarse_gemm + k_pcg_correct on two-level steps)", "bound": "hbm", "achieved": achieved,
+    tr = pcg_traffic_record((info["m"], info["n"]))
+    roof = {"kernel": PCG_KERNELS, "bound": "hbm", "achieved": achieved,
             "peak": peak, "peak_source": f"{peak_kind} hbm_gbs (copy, burst)", "unit": "GB/s",
             "frac": achieved / peak,
             "traffic": (tr["dram_bytes_per_pose_iteration"] * pcg_pose_iters / pairs if tr else None),
@@ -473,11 +490,16 @@ def run_mfem(args, dist):
         fp64["mixed_vs_fp64_max_err_over_bbox"] = float((xm - x64).abs().max().item() / bbox)
         ctx64.close()
 
+    # request-level latency: the same poses as one-pose requests through the
+    # server, `nb` kept in flight (a closed loop at the batch's load); latency =
+    # submit -> result in host memory, measured by the server
+    req = served_request_latency(mfem, cfg, opts, nb, 4 * nb)
+
     cpu = cpu_all = None
     if dist.rank == 0 and dist.world == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline(args, statistics.mean(newton))
+        cpu = cpu_baseline(args)
         try:
-            cpu_all = cpu_baseline_all_cores(args, statistics.mean(newton))
+            cpu_all = cpu_baseline_all_cores(args)
         except Exception as e:     # context only: the line is printed without it
             cpu_all = {"unavailable": str(e)[:200]}
 
@@ -487,15 +509,24 @@ def run_mfem(args, dist):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+            "dtype_note": ("mixed: FP32 element Hessians, matrix, SpMV and PCG vectors; FP64 positions, element "
+                           "forces (the Newton residual), stop test and line-search energies; PCG inner products "
+                           "as float-float (Dekker/Knuth error-free FP32 pairs, ~48 bits) per row and warp, "
+                           "then FP64; coarse solve BF16 x 3-part BF16 split on the tensor cores, FP32 "
+                           "accumulation" if args.precision == "mixed" else "FP64 throughout except the "
+                           "preconditioner's coarse solve (BF16 tensor cores, FP32 accumulation)"),
+            "data": "synthetic",
             "config": dict(workload_config(info["m"], info["n"], info["n_handles"], info["n_pins"], nb,
                                            args.precision), parallelism=f"replicas x{dist.world}"),
-            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                           "note": "per batch step; every pose of a batch completes with the step"},
+            "latency_ms": dict(req, note=f"per request: one pose per request through the server, {nb} requests "
+                                         f"kept in flight, submit to result in host memory"),
+            "batch_step_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                              "note": "per batch step; every pose of a batch completes with the step"},
             "plain_fp64": fp64,
             "newton_iters_mean": statistics.mean(newton), "pcg_iters_mean": statistics.mean(pcg_it),
             "all_converged": conv,
-            "element_updates_per_s": dist.sum(sum(p["element_updates"] for p in prof)) / (total_ms_max / 1e3),
+            "element_updates_per_s": element_rate(prof),
             "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xfs_h.numel() * 8),
                     "d2h_bytes_per_step": int(out_h.numel() * 8)},
@@ -505,17 +536,50 @@ def run_mfem(args, dist):
     ctx.close()
 
 
-def _roofline(profs, total_ms):
+def element_rate(profs):
+    """Element updates per second of element-kernel time: tets x Newton element
+    passes over the summed CUDA-event time of the element launches."""
+    ms = sum(p["element_ms"] for p in profs)
+    return sum(p["element_updates"] for p in profs) / (ms / 1e3) if ms > 0 else None
+
+
+def served_request_latency(mfem, cfg, opts, in_flight, n_requests):
+    """One-pose requests over the workload's poses through mfem_server, a
+    closed loop with `in_flight` requests outstanding; p50/p99 of the server's
+    submit -> completion latency and the completed requests per second."""
+    srv = mfem.Server(device_mem_budget=0, max_slots=in_flight)
+    mid = srv.add(mfem.Context.from_config(cfg, **dict(opts, max_batch=in_flight)))
+    xfs = cfg["xfs"]
+    for t in [srv.submit(mid, xfs[k % len(xfs)]) for k in range(in_flight)]:   # warm-up round
+        srv.wait(t)
+    t0 = time.perf_counter()
+    pending = [srv.submit(mid, xfs[k % len(xfs)]) for k in range(in_flight)]
+    lat, k = [], in_flight
+    while pending:
+        _, st, l_s = srv.wait(pending.pop(0))
+        lat.append(1e3 * l_s)
+        if k < n_requests:
+            pending.append(srv.submit(mid, xfs[k % len(xfs)]))
+            k += 1
+    wall = time.perf_counter() - t0
+    srv.close()
+    lat.sort()
+    return {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+            "requests": len(lat), "completed_per_s": len(lat) / wall}
+
+
+def _roofline(profs, total_ms, mesh):
     """HBM roofline of the PCG iteration from library profiles (PCG launch
-    times are recorded by the context that launched them)."""
+    times are recorded by the context that launched them).  `traffic` comes
+    from the ncu record only when it was taken on this mesh (tets, verts)."""
     pcg_ms = sum(p["pcg_ms"] for p in profs)
     pcg_bytes = sum(p["pcg_bytes"] for p in profs)
     pairs = max(sum(p["pcg_launches"] for p in profs) // 2, 1)
     iters = sum(p["pcg_iters"] for p in profs)
     peak, peak_kind = hbm_peak()
     achieved = pcg_bytes / (pcg_ms / 1e3) / 1e9 if pcg_ms > 0 else 0.0
-    tr = pcg_traffic_record()
-    return {"kernel": "PCG iteration (k_pcg_spmv + k_pcg_update, + k_coarse_gemm + k_pcg_correct on two-level steps)", "bound": "hbm", "achieved": achieved,
+    tr = pcg_traffic_record(mesh)
+    return {"kernel": PCG_KERNELS, "bound": "hbm", "achieved": achieved,
             "peak": peak, "peak_source": f"{peak_kind} hbm_gbs (copy, burst)", "unit": "GB/s",
             "frac": achieved / peak,
             "traffic": tr["dram_bytes_per_pose_iteration"] * iters / pairs if tr else None,
@@ -587,7 +651,6 @@ def run_batched(args, dist):
     poses = dist.sum(2 * nb * args.steps)
     value = poses / (dist.max(total_ms) / 1e3)
     flat = [p for ps in profs for p in ps]
-    elem_updates = dist.sum(sum(p["element_updates"] for p in flat))
     per_mesh = []
     for mi in range(2):
         ss = [s for st in stats for s in st[mi]]
@@ -612,9 +675,9 @@ def run_batched(args, dist):
                        "l2": "256 MiB buffer written between timed steps", "parallelism": f"replicas x{dist.world}"},
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                            "note": "per step (one frame of all 2 x %d streams)" % nb},
-            "element_updates_per_s": elem_updates / (dist.max(total_ms) / 1e3),
+            "element_updates_per_s": element_rate(flat),
             "cold_start_newton_iters_mean_50k": statistics.mean(s["newton_iters"] for s in st_cold),
-            "roofline": _roofline(flat, total_ms),
+            "roofline": _roofline(flat, total_ms, mesh=("two meshes",)),
             "gpu_launches": sum(p["kernel_launches"] for p in flat), "clocks": clk,
         }
         print(json.dumps(line), flush=True)
@@ -806,8 +869,8 @@ def run_large(args, dist):
             "newton_iters_mean": statistics.mean(s["newton_iters"] for s in stats),
             "pcg_iters_mean": statistics.mean(s["pcg_iters"] for s in stats),
             "all_converged": all(s["converged"] for s in stats),
-            "element_updates_per_s": dist.sum(sum(p["element_updates"] for p in profs)) / (dist.max(total_ms) / 1e3),
-            "roofline": _roofline(profs, total_ms),
+            "element_updates_per_s": element_rate(profs),
+            "roofline": _roofline(profs, total_ms, mesh=(info["m"], info["n"])),
             "gpu_launches": sum(p["kernel_launches"] for p in profs), "clocks": clk,
         }
         print(json.dumps(line), flush=True)

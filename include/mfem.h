@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define MFEM_ABI_VERSION 5
+#define MFEM_ABI_VERSION 6
 
 typedef enum {
     MFEM_OK = 0,
@@ -60,6 +60,7 @@ typedef enum { MFEM_MEM_HOST = 0, MFEM_MEM_DEVICE = 1 } mfem_memory;
 typedef enum { MFEM_ROT_RIG = 0, MFEM_ROT_POLAR = 1 } mfem_rotation;
 typedef enum { MFEM_PRECOND_BLOCK_JACOBI = 0, MFEM_PRECOND_TWO_LEVEL = 1 } mfem_precond;
 typedef enum { MFEM_LAUNCH_GRAPH = 0, MFEM_LAUNCH_DIRECT = 1 } mfem_launch;
+typedef enum { MFEM_COARSE_TC = 0, MFEM_COARSE_FP32 = 1 } mfem_coarse_product;
 
 /* Material (§4 "A solver friendly to variant energies"; §4 "Allowing
  * heterogeneous material").  Densities, with S the element stretch:
@@ -159,6 +160,19 @@ typedef struct {
                             graph and replayed (up to 256 graphs per context; a
                             stream that cannot capture falls back to direct
                             launches); MFEM_LAUNCH_DIRECT: launches every kernel */
+    int32_t coarse_agg;  /* vertices per aggregate of the two-level preconditioner:
+                            0 (default) = the smallest power of two >= 64 that keeps
+                            the coarse space at most 6144 dof (6 per aggregate);
+                            else a power of two >= 64, raised to that smallest size
+                            if it is below it.  Other values: MFEM_EINVAL */
+    int32_t coarse_product; /* the coarse solve e = A_c^{-1} r_c of the two-level
+                            preconditioner: MFEM_COARSE_TC (default) -- A_c^{-1}
+                            rounded to BF16 (a fixed symmetric matrix) times r_c
+                            split exactly into three BF16 parts, on the tensor
+                            cores (tcgen05) with FP32 accumulation;
+                            MFEM_COARSE_FP32 -- FP32 A_c^{-1} on the CUDA cores.
+                            Both keep the preconditioner linear and SPD; the
+                            solution does not depend on the choice */
 } mfem_options;
 
 /* Per-pose result statistics. */
@@ -196,6 +210,7 @@ typedef struct {
     int64_t element_updates;  /* per-tet local steps (a1) of the Newton element passes */
     int32_t coarse_dof;       /* dimension of the two-level coarse space (0: none) */
     int32_t coarse_launches;  /* coarse-solve and correction launches (two-level) */
+    int32_t coarse_tc;        /* 1: the coarse solves ran on the tensor cores */
 } mfem_profile;
 
 typedef struct mfem_ctx mfem_ctx;
@@ -282,14 +297,26 @@ mfem_status mfem_get_elem(mfem_ctx* ctx, double* s, double* lam);
  * or allocating library routine.  Arguments and outputs are those of
  * mfem_get_elem (host s [m][6], lam [m][9], caller tet order, either may be
  * NULL).  The context's device must be current.  The first call on a device
- * looks up the array's device address (cudaGetSymbolAddress): make that first
- * call before any stream capture.  All calls on a device share the one array,
+ * looks up the array's device address (cudaGetSymbolAddress) and keeps it for
+ * the life of the process: make that first call before any stream capture, and
+ * do not reset the device (cudaDeviceReset) between calls -- the kept address
+ * would then be stale.  All calls on a device share the one array,
  * which keeps the last call's contents (each call overwrites every entry it
  * returns); two calls whose work overlaps on the GPU (other streams or
  * threads) race on it.  Meshes with more than MFEM_ELEM_STATIC_MAX_TETS tets
  * are rejected with MFEM_EINVAL. */
 #define MFEM_ELEM_STATIC_MAX_TETS 65536
 mfem_status mfem_get_elem_static(mfem_ctx* ctx, double* s, double* lam);
+
+/* The coarse solve of the two-level preconditioner applied to given vectors,
+ * for inspection and tests (not part of the paper's method, §5: the reduced
+ * space is the preconditioner's).  rc: host [B][N] FP32 coarse residuals in the
+ * coarse basis of mfem_get_info's mesh (N = profile.coarse_dof), e: host
+ * [B][N] results e_b = A_c^{-1} rc_b as the solve computes them (slice
+ * partials added in slice order).  product: MFEM_COARSE_TC or
+ * MFEM_COARSE_FP32.  Allocates and frees device memory during the call.
+ * MFEM_EINVAL if the context has no coarse space or B < 1. */
+mfem_status mfem_coarse_apply(mfem_ctx* ctx, const float* rc, int32_t B, float* e, int32_t product);
 
 /* Warm-start state (the last solution, host [n][3], caller order). */
 mfem_status mfem_get_state(const mfem_ctx* ctx, double* x);

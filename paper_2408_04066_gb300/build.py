@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libmfem.so")
-SOURCES = ["plan.cpp", "engine.cu", "server.cpp", "k_element.cu", "k_rows.cu", "k_pcg.cu", "k_coarse.cu", "noalloc.cu"]
+SOURCES = ["plan.cpp", "engine.cu", "server.cpp", "k_element.cu", "k_rows.cu", "k_pcg.cu", "k_coarse.cu", "k_coarse_tc.cu",
+           "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

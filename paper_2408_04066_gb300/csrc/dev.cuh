@@ -46,7 +46,7 @@ struct ProbScal {
 // of 64 rows (aggregates hold a power-of-two multiple of 64 vertices) and the
 // coarse product is split into slices of kCoarseKC columns of A_c^{-1}.
 constexpr int kCoarseRows = 64;
-constexpr int kCoarseKC = 512;
+constexpr int kCoarseKC = 256;
 constexpr int kCoarseRowPasses = 1;   // 32-row passes per block of the coarse product (measured: 4 is slower)
 // row stride of the stored A_c^{-1} (rows padded with zeros to 32 floats)
 __host__ __device__ __forceinline__ int coarse_ld(int N) { return (N + 31) & ~31; }

@@ -216,6 +216,7 @@ void end_profile(mfem_ctx* c) {
     P.element_updates = c->prof.element_updates;
     P.coarse_dof = c->mesh.coarse_n;
     P.coarse_launches = c->prof.coarse_launches;
+    P.coarse_tc = c->mesh.coarse_n > 0 && c->mesh.coarse_tc ? 1 : 0;
     P.pcg_iters = c->prof.pcg_iters;
     P.tile_rows = c->tile_rows;
     P.grid_blocks = c->grid_blocks;
@@ -271,7 +272,8 @@ void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc
         bool any_coarse = false;
         for (int b = 0; b < g.B; ++b) any_coarse |= g.ph[b].active && g.ph[b].in_pcg && g.ph[b].coarse;
         if (jobs && any_coarse && c->mesh.coarse_n > 0)
-            jobs->push_back(CoarseJob{c->mesh.Ainv, c->mesh.coarse_n, first, 0, c->plan.agg_size / kCoarseRows});
+            jobs->push_back(CoarseJob{c->mesh.Ainv, c->mesh.coarse_tc ? c->mesh.Abf : nullptr, c->mesh.coarse_err, c,
+                                      c->mesh.coarse_n, first, 0, c->plan.agg_size / kCoarseRows});
         const int n = c->plan.n;
         const size_t slots = (size_t)c->plan.slice_ptr.back();
         for (int b = 0; b < g.B; ++b) {
@@ -306,7 +308,7 @@ void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc
             units += d.n_tiles;
             out.push_back(d);
         }
-        if (jobs && !jobs->empty() && jobs->back().d0 == first && jobs->back().Ainv == c->mesh.Ainv)
+        if (jobs && !jobs->empty() && jobs->back().d0 == first && jobs->back().key == c)
             jobs->back().nd = (int)out.size() - first;
     }
 }
@@ -361,6 +363,8 @@ void synced(std::vector<Group>& gs) {
 
 mfem_status read_scalars(mfem_ctx* c, int B) {
     CK(cudaMemcpyAsync(c->sc_host, c->slot.sc, B * sizeof(ProbScal), cudaMemcpyDeviceToHost, c->stream));
+    if (c->mesh.coarse_err && c->cerr_host)
+        CK(cudaMemcpyAsync(c->cerr_host, c->mesh.coarse_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream));
     return MFEM_OK;
 }
 
@@ -380,7 +384,7 @@ mfem_status launch_chunk(mfem_ctx* c, const PcgDesc<T>* dst, int nd, int units, 
         snprintf(buf, sizeof buf, "%d %p %d %d %d %d", (int)sizeof(T), (const void*)dst, nd, units, tile, n_it);
         std::string key(buf);
         for (const auto& j : jobs) {
-            snprintf(buf, sizeof buf, " %p %d %d %d %d", (const void*)j.Ainv, j.N, j.d0, j.nd, j.agg_units);
+            snprintf(buf, sizeof buf, " %p %d %d %d %d %d", j.key, j.Abf ? 1 : 0, j.N, j.d0, j.nd, j.agg_units);
             key += buf;
         }
         auto it = c->graphs.find(key);
@@ -424,7 +428,7 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
     if (d.empty()) return MFEM_OK;
     const int nj = (int)jobs.size();
     double coarse_bytes = 0.0;   // A_c^{-1} streamed once per iteration per mesh
-    for (const auto& j : jobs) coarse_bytes += 4.0 * j.N * coarse_ld(j.N);
+    for (const auto& j : jobs) coarse_bytes += j.Abf ? 2.0 * j.N * j.N : 4.0 * j.N * coarse_ld(j.N);
     const size_t bytes = d.size() * sizeof(PcgDesc<T>);
     if (2 * bytes > c->descs_cap) {   // grow: wait until no copy reads the old buffers
         CK(cudaStreamSynchronize(c->stream));
@@ -474,6 +478,8 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
         synced(gs);
         for (auto& g : gs) {
             if (g.ctx->slot.prec != prec) continue;
+            if (g.ctx->cerr_host && *g.ctx->cerr_host)
+                return ctx_fail(c, MFEM_ECUDA, "coarse product: a bounded wait in the tensor-core kernel ran out");
             for (int b = 0; b < g.B; ++b)
                 if (g.ph[b].active && g.ph[b].in_pcg && g.ctx->sc_host[b].state == kActive) any = true;
         }
@@ -664,7 +670,7 @@ mfem_status advance(std::vector<Group>& gs) {
             if (pass == 2) launch_gradient(a, g.B, s);
             else launch_assemble(a, g.B, s);
             gc->prof.end(pa, s);
-            gc->prof.launches += 2;
+            gc->prof.launches += pass == 2 ? 2 : 3;   // element; gradient, or slot assembly + gradient
             gc->prof.element_launches++;
             int na = 0;
             for (int b = 0; b < g.B; ++b) na += f[b];
@@ -988,6 +994,8 @@ void mfem_default_options(mfem_options* o) {
     o->rotation = MFEM_ROT_RIG;
     o->precond = MFEM_PRECOND_TWO_LEVEL;
     o->launch = MFEM_LAUNCH_GRAPH;
+    o->coarse_agg = 0;
+    o->coarse_product = MFEM_COARSE_TC;
 }
 
 const char* mfem_status_string(mfem_status s) {
@@ -1027,12 +1035,12 @@ void mfem_destroy(mfem_ctx* c) {
     free_slots(c);
     MeshDev& M = c->mesh;
     void* ptrs[] = {M.tet, M.Dminv64, M.Dminv32, M.vol, M.cluster, M.mu, M.lam, M.X, M.vhandle, M.pin_handle_v,
-                    M.vperm, M.tperm, M.slice_ptr, M.col, M.contrib_ptr, M.contrib, M.vinc_ptr, M.vinc,
-                    M.crel, M.agg_handle, M.Ainv, c->descs_dev, c->diag_dev, c->fext_dev};
+                    M.vperm, M.tperm, M.slice_ptr, M.col, M.slot_row, M.contrib_ptr, M.contrib, M.vinc_ptr, M.vinc,
+                    M.crel, M.agg_handle, M.Ainv, M.Abf, M.coarse_err, c->descs_dev, c->diag_dev, c->fext_dev};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     void* hp[] = {c->sc_host, c->active_host, c->alpha_host, c->alpha_ring, c->descs_host,
-                  c->diag_host};
+                  c->diag_host, c->cerr_host};
     for (void* p : hp)
         if (p) cudaFreeHost(p);
     for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
@@ -1089,6 +1097,21 @@ static mfem_status build_coarse(mfem_ctx* c) {
         e = build_coarse_inverse(M, c->slot.val, c->slot.prec, cnb_ptr, cnb, P.cnb_max, P.agg_size, M.Ainv, c->stream);
     cudaFree(cnb_ptr);
     cudaFree(cnb);
+    // BF16 tiles for the tensor-core product (the FP32 inverse is kept for the
+    // CUDA-core product and mfem_coarse_apply), and the error word
+    if (e == cudaSuccess) e = cudaMalloc(&M.Abf, coarse_tc_bytes(M.coarse_n));
+    if (e == cudaSuccess) {
+        c->mesh_bytes += coarse_tc_bytes(M.coarse_n);
+        e = coarse_tc_pack(M.Ainv, M.coarse_n, M.Abf, c->stream);
+    }
+    if (e == cudaSuccess) e = cudaMalloc((void**)&M.coarse_err, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMemsetAsync(M.coarse_err, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->cerr_host, sizeof(unsigned));
+    if (e == cudaSuccess) {
+        *c->cerr_host = 0;
+        e = coarse_tc_init();
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
     c->ring_pos = 0;
     return cuda_check(c, e, "coarse space set-up");
 }
@@ -1119,11 +1142,16 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
     if (o.launch != MFEM_LAUNCH_GRAPH && o.launch != MFEM_LAUNCH_DIRECT) return fail(MFEM_EINVAL, "bad launch mode");
     if (o.tile_rows != 0 && !pcg_tile_supported(o.tile_rows))
         return fail(MFEM_EINVAL, "tile_rows must be 0, 64, 128 or 256");
+    if (o.coarse_agg != 0 && (o.coarse_agg < kCoarseUnit || (o.coarse_agg & (o.coarse_agg - 1)) != 0 ||
+                              o.coarse_agg > (1 << 24)))
+        return fail(MFEM_EINVAL, "coarse_agg must be 0 or a power of two >= 64");
+    if (o.coarse_product != MFEM_COARSE_TC && o.coarse_product != MFEM_COARSE_FP32)
+        return fail(MFEM_EINVAL, "bad coarse_product");
     if (!mat) return fail(MFEM_EINVAL, "null material");
     std::string err;
     mfem_status st = plan_rig(rest_verts, n, tets, m, hs, c->plan, err);
     if (st != MFEM_OK) return fail(st, err);
-    st = plan_layout(mat, rest_verts, tets, c->plan, err);
+    st = plan_layout(mat, rest_verts, tets, c->plan, err, o.coarse_agg);
     if (st != MFEM_OK) return fail(st, err);
     c->model = mat->model;
     c->slot.prec = o.precision == MFEM_MIXED ? 1 : 0;
@@ -1170,6 +1198,7 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
     UP(M.tperm, P.tperm.data(), P.tperm.size());
     UP(M.slice_ptr, sp.data(), sp.size());
     UP(M.col, P.sell_col.data(), P.sell_col.size());
+    UP(M.slot_row, P.slot_row.data(), P.slot_row.size());
     UP(M.contrib_ptr, P.contrib_ptr.data(), P.contrib_ptr.size());
     UP(M.contrib, P.contrib.data(), P.contrib.size());
     UP(M.vinc_ptr, P.vinc_ptr.data(), P.vinc_ptr.size());
@@ -1188,6 +1217,7 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
         M.agg_shift = 0;
         while ((1 << M.agg_shift) < P.agg_size) ++M.agg_shift;
         M.coarse_n = 6 * P.n_agg;
+        M.coarse_tc = o.coarse_product == MFEM_COARSE_TC ? 1 : 0;
         if ((st = upload(c, &M.crel, (const float4*)P.crel.data(), (size_t)P.n)) != MFEM_OK ||
             (st = upload(c, &M.agg_handle, P.agg_handle.data(), P.agg_handle.size())) != MFEM_OK) {
             std::string e2 = c->err;
@@ -1437,7 +1467,11 @@ mfem_status mfem_get_elem(mfem_ctx* c, double* s, double* lam) {
     double* buf = nullptr;
     CK(cudaMalloc((void**)&buf, sizeof(double) * 15 * m));
     launch_elem_out(elem_args(c), 0, s ? buf : nullptr, lam ? buf + 6 * m : nullptr, c->stream);
-    mfem_status st = MFEM_OK;
+    mfem_status st = cuda_check(c, cudaGetLastError(), "element-output kernel launch");
+    if (st != MFEM_OK) {
+        cudaFree(buf);
+        return st;
+    }
     if (s && (st = cuda_check(c, cudaMemcpyAsync(s, buf, sizeof(double) * 6 * m, cudaMemcpyDeviceToHost, c->stream),
                               "copy s")) != MFEM_OK) {
         cudaFree(buf);
@@ -1490,6 +1524,75 @@ mfem_status mfem_get_info(const mfem_ctx* c, int32_t* n, int32_t* m, int32_t* H,
     if (nnz_blocks) *nnz_blocks = c->plan.nnz_blocks;
     if (sell_slots) *sell_slots = c->plan.slice_ptr.back();
     if (device_bytes) *device_bytes = (int64_t)(c->mesh_bytes + c->slot_bytes);
+    return MFEM_OK;
+}
+
+mfem_status mfem_coarse_apply(mfem_ctx* c, const float* rc, int32_t B, float* e, int32_t product) {
+    if (!c || !rc || !e) return ctx_fail(c, MFEM_EINVAL, "null argument");
+    if (c->mesh.coarse_n <= 0) return ctx_fail(c, MFEM_EINVAL, "the context has no coarse space");
+    if (B < 1) return ctx_fail(c, MFEM_EINVAL, "B must be >= 1");
+    if (product != MFEM_COARSE_TC && product != MFEM_COARSE_FP32) return ctx_fail(c, MFEM_EINVAL, "bad product");
+    const int N = c->mesh.coarse_n;
+    const size_t nks = coarse_ks(c);
+    // per problem: r_c, the slice partials, and scalars marking it active
+    float* rc_d = nullptr;
+    float* ec_d = nullptr;
+    ProbScal* sc_d = nullptr;
+    PcgDesc<float>* d_d = nullptr;
+    auto cleanup = [&]() {
+        cudaFree(rc_d);
+        cudaFree(ec_d);
+        cudaFree(sc_d);
+        cudaFree(d_d);
+    };
+    // r_c rows padded to the 16-byte-aligned stride the kernels' vector loads need
+    const size_t ldr = coarse_ld(N);
+    cudaError_t err = cudaMalloc((void**)&rc_d, sizeof(float) * (size_t)B * ldr);
+    if (err == cudaSuccess) err = cudaMalloc((void**)&ec_d, sizeof(float) * (size_t)B * nks * N);
+    if (err == cudaSuccess) err = cudaMalloc((void**)&sc_d, sizeof(ProbScal) * (size_t)B);
+    if (err == cudaSuccess) err = cudaMalloc((void**)&d_d, sizeof(PcgDesc<float>) * (size_t)B);
+    std::vector<ProbScal> sc(B);
+    std::vector<PcgDesc<float>> d(B);
+    for (int b = 0; b < B; ++b) {
+        std::memset(&sc[b], 0, sizeof(ProbScal));
+        sc[b].state = kActive;
+        std::memset(&d[b], 0, sizeof(PcgDesc<float>));
+        d[b].coarse = 1;
+        d[b].coarse_n = N;
+        d[b].sc = sc_d + b;
+        d[b].rc = rc_d + (size_t)b * ldr;
+        d[b].ec = ec_d + (size_t)b * nks * N;
+    }
+    if (err == cudaSuccess)
+        err = cudaMemcpy2DAsync(rc_d, sizeof(float) * ldr, rc, sizeof(float) * N, sizeof(float) * N, B,
+                                cudaMemcpyHostToDevice, c->stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(sc_d, sc.data(), sizeof(ProbScal) * B, cudaMemcpyHostToDevice, c->stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(d_d, d.data(), sizeof(PcgDesc<float>) * B, cudaMemcpyHostToDevice, c->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(ec_d, 0, sizeof(float) * (size_t)B * nks * N, c->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(c->mesh.coarse_err, 0, sizeof(unsigned), c->stream);
+    if (err == cudaSuccess) {
+        CoarseJob j{c->mesh.Ainv, product == MFEM_COARSE_TC ? c->mesh.Abf : nullptr, c->mesh.coarse_err, c, N, 0, B,
+                    1};
+        err = launch_coarse_only(d_d, B, &j, c->stream);
+    }
+    std::vector<float> ec((size_t)B * nks * N);
+    unsigned werr = 0;
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(ec.data(), ec_d, sizeof(float) * ec.size(), cudaMemcpyDeviceToHost, c->stream);
+    if (err == cudaSuccess)
+        err = cudaMemcpyAsync(&werr, c->mesh.coarse_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
+    cleanup();
+    if (err != cudaSuccess) return cuda_check(c, err, "coarse apply");
+    if (werr) return ctx_fail(c, MFEM_ECUDA, "coarse product: a bounded wait in the tensor-core kernel ran out");
+    for (int b = 0; b < B; ++b)   // slices added in slice order, as the correction kernel does
+        for (int i = 0; i < N; ++i) {
+            float v = 0.f;
+            for (size_t k = 0; k < nks; ++k) v += ec[((size_t)b * nks + k) * N + i];
+            e[(size_t)b * N + i] = v;
+        }
     return MFEM_OK;
 }
 

@@ -86,6 +86,7 @@ struct mfem_ctx {
     double* fext_dev = nullptr;   // external forces [fext_sets][n][3], internal order
     int fext_sets = 0;
     unsigned* diag_host = nullptr;
+    unsigned* cerr_host = nullptr;   // pinned copy of mesh.coarse_err, read with the problem scalars
     int tile_rows = 0;       // PCG rows per block
     int grid_blocks = 0;
     bool pose_set = false;

@@ -3,8 +3,8 @@
 // 3x3 block Jacobi, or block Jacobi plus an additive coarse correction on the
 // rigid modes of vertex aggregates (two-level; set-up in k_coarse.cu).
 //
-// Paper §3, Eq. 12 and Algorithm 1 ("x = A^{-1} b"): the condensed system is
-// SPD, so it is solved by conjugate gradients (inexactly inside each Newton
+// Paper §3, Eq. 12 and the linear solve of Algorithm 1: the condensed system
+// is SPD, so it is solved by conjugate gradients (inexactly inside each Newton
 // step, to a relative residual).  Dots are accumulated as float-float partials
 // per row and warp and reduced per problem in FP64 with a ticketed, fixed-order
 // tile reduction, so results do not depend on scheduling.
@@ -621,6 +621,11 @@ cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units
                     e = cudaLaunchKernelEx(&rc, k_coarse_rc<T>, descs, jobs[j].d0, jobs[j].nd);
                     if (e != cudaSuccess) return e;
                 }
+                if (jobs[j].Abf) {   // tensor cores, BF16 A_c^{-1}
+                    e = launch_coarse_tc<T>(cfg, jobs[j], descs);
+                    if (e != cudaSuccess) return e;
+                    continue;
+                }
                 cudaLaunchConfig_t gc = cfg;
                 const int np = jobs[j].nd <= 8 ? 8 : 16;
                 gc.gridDim = dim3((jobs[j].N + 32 * kCoarseRowPasses - 1) / (32 * kCoarseRowPasses),
@@ -666,6 +671,22 @@ cudaError_t launch_pcg_iters(const PcgDesc<T>* descs, int n_probs, int n_units, 
 }
 
 bool pcg_tile_supported(int tile_rows) { return tile_rows == 64 || tile_rows == 128 || tile_rows == 256; }
+
+cudaError_t launch_coarse_only(const PcgDesc<float>* descs, int n_probs, const CoarseJob* job, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.stream = s;
+    if (job->Abf) return launch_coarse_tc<float>(cfg, *job, descs);
+    const int np = job->nd <= 8 ? 8 : 16;
+    cfg.gridDim = dim3((job->N + 32 * kCoarseRowPasses - 1) / (32 * kCoarseRowPasses),
+                       (job->N + kCoarseKC - 1) / kCoarseKC, (job->nd + np - 1) / np);
+    cfg.blockDim = dim3(256);
+    (void)n_probs;
+    if (np == 8)
+        return cudaLaunchKernelEx(&cfg, k_coarse_gemm<float, 8>, job->Ainv, job->N, coarse_ld(job->N), descs,
+                                  job->d0, job->nd);
+    return cudaLaunchKernelEx(&cfg, k_coarse_gemm<float, 16>, job->Ainv, job->N, coarse_ld(job->N), descs, job->d0,
+                              job->nd);
+}
 
 template cudaError_t launch_pcg_iters<float>(const PcgDesc<float>*, int, int, int, int, const CoarseJob*, int,
                                              cudaStream_t);

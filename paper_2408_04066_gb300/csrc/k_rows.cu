@@ -2,7 +2,7 @@
 // elimination (a3) and block-Jacobi inverse (a4), gradient gather, slope and
 // update (a6) and permutations (a7).
 //
-// Paper §3, Eq. 12 and Algorithm 1 ("assemble", "x = A^{-1} b"): the matrix
+// Paper §3, Eq. 12 and the assembly and linear-solve steps of Algorithm 1: the matrix
 // sum_k W_k A_k^T H_s A_k is gathered per 3x3 block from the element blocks of
 // every tet that contains both vertices, in a fixed order (deterministic, no
 // atomics).  Pinned vertices (Eq. 6 C(x), §3.2 targets) are eliminated: their
@@ -59,86 +59,78 @@ __device__ __forceinline__ double row_gradient(const ElemArgs& A, int b, int row
     return g0 * g0 + g1 * g1 + g2 * g2;
 }
 
-// One thread per block row: the row's matrix blocks, its inverse diagonal
-// block, and its gradient entry; |g_free|^2 per problem.
+// One thread per slot of the sliced pattern: the slot's 3x3 block summed from
+// the element blocks of every tet holding both vertices (the contributions of
+// a slot are sorted by tet, so the order -- and every bit of the result -- is
+// the same as a row-by-row gather), pin elimination or the penalty term, and,
+// on the diagonal slot, the row's block-Jacobi inverse.  Consecutive threads
+// take consecutive slots, so the block writes are coalesced; a slot's gather is
+// a handful of loads, so there are ~15x more independent threads than rows to
+// hide their latency.  The gradient gather runs in k_gradient.
 template <typename KT>
-__global__ void __launch_bounds__(kRowTile) k_assemble_grad(ElemArgs A) {
+__global__ void __launch_bounds__(kRowTile) k_assemble_slots(ElemArgs A) {
     const int b = blockIdx.y;
     if (!A.slot.active[b]) return;
     const MeshDev& M = A.mesh;
-    const int n = M.n;
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    double gn[1] = {0.0};
-    if (row < n) {
-        const int s = row >> 5, lane = row & 31;
-        const int base = M.slice_ptr[s], w = (M.slice_ptr[s + 1] - base) >> 5;
-        const bool pin_r = M.pin_handle_v[row] >= 0;
-        const KT* Ke = (const KT*)A.slot.Ke + (size_t)b * M.m * kKe;
-        KT* val = (KT*)A.slot.val + (size_t)b * M.slots * 9;
-        for (int k = 0; k < w; ++k) {
-            const int g = base + (k << 5);
-            const int slot = g + lane;
-            const int c = M.col[slot];
-            if (c < 0) continue;
-            KT acc[9];
+    const int64_t gs = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gs >= M.slots) return;
+    const int c = __ldg(M.col + gs);
+    if (c < 0) return;   // padding: stays zero
+    const int row = __ldg(M.slot_row + gs);
+    const int lane = row & 31;
+    const KT* Ke = (const KT*)A.slot.Ke + (size_t)b * M.m * kKe;
+    KT acc[9];
 #pragma unroll
-            for (int e = 0; e < 9; ++e) acc[e] = (KT)0;
-            const int c0 = M.contrib_ptr[slot], c1 = M.contrib_ptr[slot + 1];
-            for (int ci = c0; ci < c1; ++ci) {
-                const int code = M.contrib[ci];
-                const int t = code >> 4, ea = (code >> 2) & 3, eb = code & 3;
-                if (ea <= eb) {
-                    const KT* blk = Ke + (size_t)t * kKe + 9 * pair_index(ea, eb);
+    for (int e = 0; e < 9; ++e) acc[e] = (KT)0;
+    const int c0 = __ldg(M.contrib_ptr + gs), c1 = __ldg(M.contrib_ptr + gs + 1);
+    for (int ci = c0; ci < c1; ++ci) {
+        const int code = __ldg(M.contrib + ci);
+        const int t = code >> 4, ea = (code >> 2) & 3, eb = code & 3;
+        if (ea <= eb) {
+            const KT* blk = Ke + (size_t)t * kKe + 9 * pair_index(ea, eb);
 #pragma unroll
-                    for (int e = 0; e < 9; ++e) acc[e] += blk[e];
-                } else {
-                    const KT* blk = Ke + (size_t)t * kKe + 9 * pair_index(eb, ea);
+            for (int e = 0; e < 9; ++e) acc[e] += blk[e];
+        } else {
+            const KT* blk = Ke + (size_t)t * kKe + 9 * pair_index(eb, ea);
 #pragma unroll
-                    for (int i = 0; i < 3; ++i)
+            for (int i = 0; i < 3; ++i)
 #pragma unroll
-                        for (int j = 0; j < 3; ++j) acc[3 * i + j] += blk[3 * j + i];
-                }
-            }
-            const bool diag = (c == row);
-            if (A.constraint == 0) {
-                if (pin_r || M.pin_handle_v[c] >= 0) {
-#pragma unroll
-                    for (int e = 0; e < 9; ++e) acc[e] = (diag && (e % 4 == 0)) ? (KT)1 : (KT)0;
-                }
-            } else if (diag && pin_r) {
-                acc[0] += (KT)A.ks;
-                acc[4] += (KT)A.ks;
-                acc[8] += (KT)A.ks;
-            }
-            KT* out = val + (size_t)g * 9 + lane;
-#pragma unroll
-            for (int e = 0; e < 9; ++e) out[32 * e] = acc[e];
-            if (diag) {  // block-Jacobi: inverse of the diagonal block, formed in FP64
-                double a[9];
-#pragma unroll
-                for (int e = 0; e < 9; ++e) a[e] = (double)acc[e];
-                double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8],
-                       c02 = a[3] * a[7] - a[4] * a[6];
-                double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
-                double id = det != 0.0 ? 1.0 / det : 0.0;
-                KT* di = (KT*)A.slot.dinv + ((size_t)b * n + row) * 9;
-                di[0] = (KT)(c00 * id);
-                di[1] = (KT)((a[2] * a[7] - a[1] * a[8]) * id);
-                di[2] = (KT)((a[1] * a[5] - a[2] * a[4]) * id);
-                di[3] = (KT)(c01 * id);
-                di[4] = (KT)((a[0] * a[8] - a[2] * a[6]) * id);
-                di[5] = (KT)((a[2] * a[3] - a[0] * a[5]) * id);
-                di[6] = (KT)(c02 * id);
-                di[7] = (KT)((a[1] * a[6] - a[0] * a[7]) * id);
-                di[8] = (KT)((a[0] * a[4] - a[1] * a[3]) * id);
-            }
+                for (int j = 0; j < 3; ++j) acc[3 * i + j] += blk[3 * j + i];
         }
-        gn[0] = row_gradient(A, b, row, pin_r);
     }
-    double tot[1];
-    double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
-    if (tile_commit<1>(gn, part, blockIdx.x, gridDim.x, &A.slot.sc[b].tk_g, 0, tot) && threadIdx.x == 0)
-        A.slot.sc[b].gnorm2 = tot[0];
+    const bool diag = (c == row);
+    const bool pin_r = M.pin_handle_v[row] >= 0;
+    if (A.constraint == 0) {
+        if (pin_r || M.pin_handle_v[c] >= 0) {
+#pragma unroll
+            for (int e = 0; e < 9; ++e) acc[e] = (diag && (e % 4 == 0)) ? (KT)1 : (KT)0;
+        }
+    } else if (diag && pin_r) {
+        acc[0] += (KT)A.ks;
+        acc[4] += (KT)A.ks;
+        acc[8] += (KT)A.ks;
+    }
+    KT* out = (KT*)A.slot.val + (size_t)b * M.slots * 9 + (size_t)(gs - lane) * 9 + lane;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) out[32 * e] = acc[e];
+    if (diag) {  // block-Jacobi: inverse of the diagonal block, formed in FP64
+        double a[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) a[e] = (double)acc[e];
+        const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+        const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+        const double id = det != 0.0 ? 1.0 / det : 0.0;
+        KT* di = (KT*)A.slot.dinv + ((size_t)b * M.n + row) * 9;
+        di[0] = (KT)(c00 * id);
+        di[1] = (KT)((a[2] * a[7] - a[1] * a[8]) * id);
+        di[2] = (KT)((a[1] * a[5] - a[2] * a[4]) * id);
+        di[3] = (KT)(c01 * id);
+        di[4] = (KT)((a[0] * a[8] - a[2] * a[6]) * id);
+        di[5] = (KT)((a[2] * a[3] - a[0] * a[5]) * id);
+        di[6] = (KT)(c02 * id);
+        di[7] = (KT)((a[1] * a[6] - a[0] * a[7]) * id);
+        di[8] = (KT)((a[0] * a[4] - a[1] * a[3]) * id);
+    }
 }
 
 // Gradient only (a convergence test that needs no matrix): |g_free|^2 per problem.
@@ -211,9 +203,10 @@ __global__ void k_permute_in(ElemArgs A, int b, const double* __restrict__ xin) 
 }  // namespace
 
 void launch_assemble(const ElemArgs& a, int B, cudaStream_t s) {
-    dim3 grid((a.mesh.n + kRowTile - 1) / kRowTile, B);
-    if (a.slot.prec == 1) k_assemble_grad<float><<<grid, kRowTile, 0, s>>>(a);
-    else k_assemble_grad<double><<<grid, kRowTile, 0, s>>>(a);
+    const dim3 grid((unsigned)((a.mesh.slots + kRowTile - 1) / kRowTile), B);
+    if (a.slot.prec == 1) k_assemble_slots<float><<<grid, kRowTile, 0, s>>>(a);
+    else k_assemble_slots<double><<<grid, kRowTile, 0, s>>>(a);
+    launch_gradient(a, B, s);
 }
 
 void launch_gradient(const ElemArgs& a, int B, cudaStream_t s) {

@@ -26,6 +26,7 @@ struct MeshDev {
     int* tperm = nullptr;         // [m] caller tet -> internal
     int* slice_ptr = nullptr;     // [n_slices+1]
     int* col = nullptr;           // [slots]
+    int* slot_row = nullptr;      // [slots] block row of each slot
     int* contrib_ptr = nullptr;   // [slots+1]
     int* contrib = nullptr;       // [16m]
     int* vinc_ptr = nullptr;      // [n+1]
@@ -35,6 +36,9 @@ struct MeshDev {
     float4* crel = nullptr;       // [n] rest offset from the aggregate centroid, w = 1 free / 0 pin
     int* agg_handle = nullptr;    // [n_agg]
     float* Ainv = nullptr;        // [coarse_n][coarse_ld] inverse of the rest coarse matrix (rows padded)
+    void* Abf = nullptr;          // the same inverse in BF16, tiled for the tensor-core product
+    unsigned* coarse_err = nullptr;  // [1] bits set by a coarse-product wait that ran out
+    int coarse_tc = 0;            // 1: the coarse product runs on the tensor cores (Abf)
 };
 
 // Per-batch problem buffers of one mesh (B problems, strides in elements).
@@ -127,7 +131,10 @@ void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int m
                      const int* coarse_b, cudaStream_t s);
 // One mesh's coarse solve inside the PCG iterations: descriptors d0 .. d0+nd-1.
 struct CoarseJob {
-    const float* Ainv;
+    const float* Ainv;          // FP32 inverse (CUDA-core product) ...
+    const void* Abf;            // ... or its BF16 tiles (tensor-core product), when not null
+    unsigned* err;              // the mesh's coarse-product error word
+    const void* key;            // the mesh (context) the job belongs to
     int N, d0, nd, agg_units;   // agg_units: 64-row units per aggregate
 };
 template <typename T>
@@ -140,5 +147,16 @@ bool pcg_tile_supported(int tile_rows);
 // coarse_ld(coarse_n) floats, zero padding).
 cudaError_t build_coarse_inverse(const MeshDev& M, const void* val, int prec, const int* cnb_ptr, const int* cnb,
                                  int cnb_max, int agg_size, float* Ainv, cudaStream_t s);
+
+// Tensor-core coarse product (k_coarse_tc.cu): bytes of the BF16 tiles of an
+// N x N inverse, their packing from the FP32 inverse, the one-time kernel
+// attribute set-up (before any capture), and the launch for one job.
+// The coarse product alone for one job (mfem_coarse_apply).
+cudaError_t launch_coarse_only(const PcgDesc<float>* descs, int n_probs, const CoarseJob* job, cudaStream_t s);
+size_t coarse_tc_bytes(int N);
+cudaError_t coarse_tc_pack(const float* Ainv, int N, void* Abf, cudaStream_t s);
+cudaError_t coarse_tc_init();
+template <typename T>
+cudaError_t launch_coarse_tc(const cudaLaunchConfig_t& base, const CoarseJob& j, const PcgDesc<T>* descs);
 
 }  // namespace mfem

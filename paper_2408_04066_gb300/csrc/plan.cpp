@@ -255,7 +255,7 @@ mfem_status plan_rig(const double* rest_verts, int32_t n, const int32_t* tets, i
 }
 
 mfem_status plan_layout(const mfem_material* mat, const double* rest_verts, const int32_t* tets,
-                        Plan& p, std::string& err) {
+                        Plan& p, std::string& err, int agg_request) {
     const int n = p.n, m = p.m;
     if (!mat) { err = "null material"; return MFEM_EINVAL; }
     if (mat->model < MFEM_ARAP || mat->model > MFEM_SNH) { err = "unknown material model"; return MFEM_EINVAL; }
@@ -352,6 +352,9 @@ mfem_status plan_layout(const mfem_material* mat, const double* rest_verts, cons
     if (slots >= ((int64_t)1 << 31)) { err = "pattern too large for int32 slot ids"; return MFEM_EINVAL; }
     p.sell_col.assign(slots, -1);
     p.diag_slot.assign(n, -1);
+    p.slot_row.assign(slots, 0);
+    for (int s = 0; s < p.n_slices; ++s)
+        for (int64_t g = p.slice_ptr[s]; g < p.slice_ptr[s + 1]; ++g) p.slot_row[g] = (int32_t)(s * kSlice + (g - p.slice_ptr[s]) % kSlice);
     for (int i = 0; i < n; ++i) {
         int s = i / kSlice, l = i % kSlice;
         for (size_t k = 0; k < nb[i].size(); ++k) {
@@ -397,6 +400,7 @@ mfem_status plan_layout(const mfem_material* mat, const double* rest_verts, cons
     // the centroid of the aggregate's free vertices; pins take no part.
     int agg = kCoarseUnit;
     while (6 * (int64_t)((n + agg - 1) / agg) > kCoarseMaxDof) agg *= 2;
+    if (agg_request > agg) agg = agg_request;   // a power of two (checked by mfem_create)
     p.agg_size = agg;
     p.n_agg = (n + agg - 1) / agg;
     p.crel.assign((size_t)4 * n, 0.f);

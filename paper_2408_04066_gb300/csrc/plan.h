@@ -43,6 +43,7 @@ struct Plan {
     std::vector<int32_t> slice_w;    // [n_slices] blocks per row (max in slice)
     std::vector<int32_t> sell_col;   // [slots] column block or -1
     std::vector<int32_t> diag_slot;  // [n] slot holding the diagonal block of a row
+    std::vector<int32_t> slot_row;   // [slots] block row of each slot (padding slots too)
     int64_t nnz_blocks = 0;
     // element-block -> matrix-block gather lists
     std::vector<int32_t> contrib_ptr;  // [slots+1]
@@ -71,7 +72,9 @@ mfem_status plan_rig(const double* rest_verts, int32_t n, const int32_t* tets, i
                      const mfem_handles* hs, Plan& p, std::string& err);
 
 // Material constants, reordering and the sliced pattern (needs plan_rig first).
+// agg_request: vertices per coarse aggregate (0 = smallest allowed; see
+// mfem_options.coarse_agg).
 mfem_status plan_layout(const mfem_material* mat, const double* rest_verts,
-                        const int32_t* tets, Plan& p, std::string& err);
+                        const int32_t* tets, Plan& p, std::string& err, int agg_request = 0);
 
 }  // namespace mfem

@@ -236,19 +236,24 @@ mfem_status mfem_server_add(mfem_server* s, mfem_ctx* c, int32_t* mesh_id) {
         cap = (int)std::min<size_t>((size_t)cap, left / per);
         if (cap < 1) return ctx_fail(c, MFEM_ENOMEM, "one request slot of this mesh exceeds the server budget");
     }
+    MeshEntry me;
+    me.ctx = c;
+    me.cap = cap;
+    // everything that can fail comes before the context is changed, so a
+    // refused mesh is left as the caller handed it over
+    if (c->opt.init == MFEM_INIT_WARM &&
+        cudaMalloc((void**)&me.bank, sizeof(double) * ((size_t)c->plan.n * 6 + (size_t)c->plan.H * 12)) != cudaSuccess)
+        return ctx_fail(c, MFEM_ENOMEM, "warm-start bank");
+    mfem_status st = ensure_slots(c, cap);
+    if (st != MFEM_OK) {
+        if (me.bank) cudaFree(me.bank);
+        return st;
+    }
     cudaStreamSynchronize(c->stream);
     c->stream = s->stream;
     if (c->tile_rows == 0) c->tile_rows = 256;   // one tile for every mesh in a shared launch
     if (!s->meshes.empty()) c->tile_rows = s->meshes[0].ctx->tile_rows;
-    mfem_status st = ensure_slots(c, cap);
-    if (st != MFEM_OK) return st;
     c->owned_by_server = true;
-    MeshEntry me;
-    me.ctx = c;
-    me.cap = cap;
-    if (c->opt.init == MFEM_INIT_WARM &&
-        cudaMalloc((void**)&me.bank, sizeof(double) * ((size_t)c->plan.n * 6 + (size_t)c->plan.H * 12)) != cudaSuccess)
-        return ctx_fail(c, MFEM_ENOMEM, "warm-start bank");
     me.ph.assign(cap, ProbHost());
     me.slot_req.assign(cap, 0);
     s->used += per * cap;

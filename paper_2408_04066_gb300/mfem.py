@@ -24,8 +24,9 @@ INITS = {"rigid": 0, "rest": 1, "warm": 2, "corot": 3}
 ROTATIONS = {"rig": 0, "polar": 1}
 PRECONDS = {"block_jacobi": 0, "two_level": 1}
 LAUNCHES = {"graph": 0, "direct": 1}
+COARSE_PRODUCTS = {"tc": 0, "fp32": 1}
 MEM_HOST, MEM_DEVICE = 0, 1
-ABI_VERSION = 5   # MFEM_ABI_VERSION of the header these structures follow
+ABI_VERSION = 6   # MFEM_ABI_VERSION of the header these structures follow
 
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -46,7 +47,8 @@ class Options(C.Structure):
                 ("newton_tol", C.c_double), ("cg_tol", C.c_double), ("newton_max", C.c_int32),
                 ("cg_max", C.c_int32), ("init", C.c_int32), ("max_batch", C.c_int32),
                 ("tile_rows", C.c_int32), ("diagnostics", C.c_int32), ("rotation", C.c_int32),
-                ("precond", C.c_int32), ("launch", C.c_int32)]
+                ("precond", C.c_int32), ("launch", C.c_int32), ("coarse_agg", C.c_int32),
+                ("coarse_product", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -65,7 +67,7 @@ class Profile(C.Structure):
                 ("element_ms", C.c_double), ("element_bytes", C.c_double), ("assemble_ms", C.c_double),
                 ("linesearch_ms", C.c_double), ("total_ms", C.c_double), ("tile_rows", C.c_int32),
                 ("grid_blocks", C.c_int32), ("element_updates", C.c_int64), ("coarse_dof", C.c_int32),
-                ("coarse_launches", C.c_int32)]
+                ("coarse_launches", C.c_int32), ("coarse_tc", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -90,6 +92,8 @@ _SIGS = [
                                      C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]),
     ("mfem_get_elem", C.c_int32, [C.c_void_p, _dp, _dp]),
     ("mfem_get_elem_static", C.c_int32, [C.c_void_p, _dp, _dp]),
+    ("mfem_coarse_apply", C.c_int32, [C.c_void_p, C.POINTER(C.c_float), C.c_int32, C.POINTER(C.c_float),
+                                      C.c_int32]),
     ("mfem_get_state", C.c_int32, [C.c_void_p, _dp]),
     ("mfem_set_state", C.c_int32, [C.c_void_p, _dp]),
     ("mfem_get_profile", C.c_int32, [C.c_void_p, C.POINTER(Profile)]),
@@ -175,6 +179,8 @@ def default_options(**over):
             v = PRECONDS[v] if isinstance(v, str) else v
         elif k == "launch":
             v = LAUNCHES[v] if isinstance(v, str) else v
+        elif k == "coarse_product":
+            v = COARSE_PRODUCTS[v] if isinstance(v, str) else v
         setattr(o, k, v)
     return o
 
@@ -340,6 +346,19 @@ class Context:
         lam = np.empty((self.m, 9)) if lam is None else lam
         _check(self._lib.mfem_get_elem_static(self._ctx, _p(s), _p(lam)), self._ctx)
         return s, lam
+
+    def coarse_apply(self, rc, product="tc"):
+        """mfem_coarse_apply: e_b = A_c^{-1} rc_b as the solve computes it, rc
+        (B, N) float32 in the mesh's coarse basis; product "tc" or "fp32"."""
+        rc = np.ascontiguousarray(rc, dtype=np.float32)
+        if rc.ndim == 1:
+            rc = rc[None]
+        e = np.empty_like(rc)
+        fp = C.POINTER(C.c_float)
+        _check(self._lib.mfem_coarse_apply(self._ctx, rc.ctypes.data_as(fp), rc.shape[0], e.ctypes.data_as(fp),
+                                           COARSE_PRODUCTS[product] if isinstance(product, str) else product),
+               self._ctx)
+        return e
 
     def get_state(self):
         x = np.empty((self.n, 3))

@@ -90,13 +90,23 @@ def test_reference_arm_under_torchrun_prints_on_rank_zero_only():
 
 
 def test_oracle_on_all_cores_runs_one_pose_per_process():
-    """The all-core CPU baseline: spawned oracle processes time one Newton step
+    """The all-core CPU baseline: spawned oracle processes time one full frame
     each, started together; a failing process is reported, not waited on."""
     import bench
-    times = bench.oracle_concurrent_step_times(3000, "snh", 2)
+    times = bench.oracle_concurrent_frame_times(3000, "snh", 2)
     assert len(times) == 2 and all(isinstance(t, float) and t > 0 for t in times)
     with pytest.raises(RuntimeError):
-        bench.oracle_concurrent_step_times(3000, "no-such-model", 2)
+        bench.oracle_concurrent_frame_times(3000, "no-such-model", 2)
+
+
+def test_single_thread_baseline_times_five_frames():
+    """cpu_baseline: the median of 5 full oracle frames after a warm-up frame."""
+    import argparse
+    import bench
+    d = bench.cpu_baseline(argparse.Namespace(tets=3000, model="snh"))
+    assert d["kind"] == "oracle" and d["cores"] == 1 and d["value"] > 0
+    assert d["sample"].startswith("median of 5 frames")
+    assert d["sample"].count(",") >= 4          # five frame times listed
 
 
 def test_roofline_arithmetic():
@@ -107,14 +117,15 @@ def test_roofline_arithmetic():
     import bench
     profs = [dict(pcg_ms=2.0, pcg_bytes=8e9, pcg_launches=40, pcg_iters=100),
              dict(pcg_ms=3.0, pcg_bytes=12e9, pcg_launches=60, pcg_iters=140)]
-    r = bench._roofline(profs, total_ms=10.0)
+    r = bench._roofline(profs, total_ms=10.0, mesh=(198474, 40103))
     peak, kind = bench.hbm_peak()
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == peak
     assert r["achieved"] == pytest.approx(20e9 / 5e-3 / 1e9)           # 4000 GB/s
     assert r["frac"] == pytest.approx(r["achieved"] / peak)
     assert r["launch_pairs"] == 50 and r["pose_iterations_per_pair"] == pytest.approx(240 / 50)
     assert r["share_of_step"] == pytest.approx(0.5)
-    rec = bench.pcg_traffic_record()
+    rec = bench.pcg_traffic_record((198474, 40103))
+    assert bench._roofline(profs, total_ms=10.0, mesh=(10, 20))["traffic"] is None   # another mesh: no record
     if rec is None:
         assert r["traffic"] is None
     else:

@@ -1,0 +1,208 @@
+"""GPU parity of the launch configurations the benchmark runs, against the FP64
+oracle (paper §3 Eq. 12, Algorithm 1), one test per workload configuration.
+
+Positions are compared as max |x_gpu - x_oracle| / bbox diagonal.  At the
+benchmark's stop rule (|g_free| <= 1e-6 |g_free(x_ref)|, PCG target 3e-2) both
+paths stop within the stop tolerance of the minimiser, so the bound there is
+the mixed path's 1e-5 for both precisions; the FP64 path solved tightly must
+meet 1e-9.  Meshes the oracle cannot solve in seconds are checked through the
+FP64 free gradient the oracle recomputes at the GPU solution.  Each test
+records its errors as a junit property (``parity``), which the per-config
+error table is read from (``pytest -m gpu --junitxml=...``).
+
+Launch shapes covered here and nowhere else:
+* more than 8 poses of one mesh in a batch -- the coarse product's 16-problem
+  variant;
+* aggregates of more than 64 rows (``coarse_agg``) -- the per-aggregate sums of
+  the restriction partials before the coarse product, as on the 800k and 2M
+  meshes;
+* the 198k-tet figure at the benchmark's own settings.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import element, rig, solve as S
+from synth import bar_twist_config, figure_animation, figure_config
+from golden_util import mesh_checksum
+from oracle_pool import solve_jobs, solve_many
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP64 = 1e-9
+TOL_MIXED = 1e-5
+GOLD = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "figure200k_snh_solutions.npz")
+
+
+@pytest.fixture(scope="module")
+def mfem():
+    from paper_2408_04066_gb300 import build, mfem as m
+    build.build()
+    m.load()
+    return m
+
+
+def _err(x, ref, bbox):
+    return float(np.abs(np.asarray(x) - np.asarray(ref)).max() / bbox)
+
+
+def _free_grad_rel(cfg, xf, x, model):
+    """|g_free(x)| / |g_free(x_ref)| in FP64 by the oracle (rig rotations)."""
+    so = S.Setup.from_config(cfg)
+    Q, t = rig.unpack_pose(xf)
+    args = (so.T, so.G, so.vol, Q[so.cluster], model, so.mu, so.lam)
+    g = element.gradient(x, *args)
+    g[so.pin_verts] = 0.0
+    x0 = S.initial_guess(so, Q, t, "rigid")
+    x0[so.pin_verts] = rig.pin_targets(so.X, so.pin_verts, so.pin_handle, Q, t)
+    g0 = element.gradient(x0, *args)
+    g0[so.pin_verts] = 0.0
+    return float(np.linalg.norm(g) / np.linalg.norm(g0))
+
+
+def test_cfg1_bar_twist(mfem, record_property):
+    cfg = bar_twist_config()
+    so = S.Setup.from_config(cfg)
+    xo, _ = S.solve(so, cfg["xfs"][0], "arap", newton_max=20, newton_tol=0.0)
+    res = {}
+    for precision, kw in (("fp64", dict(newton_tol=0.0, newton_max=20, cg_tol=1e-10)),
+                          ("mixed", dict(newton_tol=1e-6))):
+        ctx = mfem.Context.from_config(cfg, precision=precision, **kw)
+        x, st = ctx.solve_batch(cfg["xfs"])
+        res[precision] = _err(x[0], xo, so.bbox_diag)
+        ctx.close()
+    record_property("parity", json.dumps({"config": "cfg1 bar twist", **res}))
+    assert res["fp64"] <= TOL_FP64 and res["mixed"] <= TOL_MIXED, res
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_sixteen_problem_coarse_product(mfem, precision, record_property):
+    """12 poses of one mesh in one batch: the coarse product takes its
+    16-problem variant; tight tolerances compare the arithmetic."""
+    cfg = figure_config(10000, seeds=range(12), model="snh")
+    so = S.Setup.from_config(cfg)
+    tight = dict(newton_tol=1e-11, cg_tol=1e-9) if precision == "fp64" else dict(newton_tol=1e-9, cg_tol=1e-3)
+    ctx = mfem.Context.from_config(cfg, precision=precision, max_batch=12, newton_max=80, **tight)
+    x, st = ctx.solve_batch(cfg["xfs"])
+    prof = ctx.profile()
+    ctx.close()
+    assert prof["coarse_dof"] > 0 and prof["coarse_launches"] > 0
+    ref = solve_many(cfg, list(cfg["xfs"]), "snh", newton_tol=1e-12, newton_max=80)
+    errs = [_err(x[b], ref[b][0], so.bbox_diag) for b in range(12)]
+    record_property("parity", json.dumps({"config": f"10k figure x12 poses ({precision})", "max_err": max(errs)}))
+    assert all(s["converged"] for s in st)
+    assert max(errs) <= (TOL_FP64 if precision == "fp64" else TOL_MIXED), errs
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("agg", [128, 256])
+def test_large_aggregates(mfem, precision, agg, record_property):
+    """Aggregates of 128 and 256 vertices: the restriction partials of each
+    64-row unit are summed per aggregate before the coarse product."""
+    cfg = figure_config(10000, seeds=range(3), model="snh")
+    so = S.Setup.from_config(cfg)
+    tight = dict(newton_tol=1e-11, cg_tol=1e-9) if precision == "fp64" else dict(newton_tol=1e-9, cg_tol=1e-3)
+    ctx = mfem.Context.from_config(cfg, precision=precision, max_batch=3, newton_max=80, coarse_agg=agg, **tight)
+    x, st = ctx.solve_batch(cfg["xfs"])
+    prof = ctx.profile()
+    ctx.close()
+    assert prof["coarse_dof"] == 6 * ((so.n + agg - 1) // agg)
+    ref = solve_many(cfg, list(cfg["xfs"]), "snh", newton_tol=1e-12, newton_max=80)
+    errs = [_err(x[b], ref[b][0], so.bbox_diag) for b in range(3)]
+    record_property("parity", json.dumps({"config": f"10k figure, {agg}-vertex aggregates ({precision})",
+                                          "max_err": max(errs)}))
+    assert all(s["converged"] for s in st)
+    assert max(errs) <= (TOL_FP64 if precision == "fp64" else TOL_MIXED), errs
+
+
+def test_coarse_agg_option_is_checked(mfem):
+    cfg = figure_config(3000, seeds=range(1), model="snh")
+    for bad in (32, 96, -64):
+        with pytest.raises(mfem.MfemError):
+            mfem.Context.from_config(cfg, coarse_agg=bad)
+
+
+def test_cfg2_figure200k_at_bench_settings(mfem, record_property):
+    """Two poses of the 198k-tet SNH figure in the benchmark's launch
+    configuration (batch of poses, defaults: PCG target 3e-2, newton_tol 1e-6,
+    two-level preconditioner, graph replay), mixed and FP64, and the FP64 path
+    solved tightly, against the oracle's direct-solve solutions (stored by
+    tests/golden/make_figure_solutions.py, sampled at 4096 vertices)."""
+    gold = np.load(GOLD)
+    cfg = figure_config(200000, seeds=[int(s) for s in gold["seeds"]], model="snh")
+    assert np.allclose(mesh_checksum(cfg["X"], cfg["T"]), gold["mesh_checksum"], rtol=0, atol=1e-6)
+    idx, bbox = gold["idx"], float(gold["bbox_diag"])
+    res = {}
+    for name, kw in (("mixed", dict(precision="mixed")), ("fp64", dict(precision="fp64")),
+                     ("fp64_tight", dict(precision="fp64", newton_tol=1e-11, cg_tol=1e-9, newton_max=80))):
+        ctx = mfem.Context.from_config(cfg, max_batch=2, **kw)
+        x, st = ctx.solve_batch(cfg["xfs"])
+        ctx.close()
+        assert all(s["converged"] for s in st), (name, st)
+        res[name] = max(_err(x[b][idx], gold["x"][b], bbox) for b in range(2))
+    record_property("parity", json.dumps({"config": "cfg2 figure198k SNH x2 poses", **res}))
+    assert res["mixed"] <= TOL_MIXED and res["fp64"] <= TOL_MIXED, res
+    assert res["fp64_tight"] <= TOL_FP64, res
+
+
+def test_cfg3_batched_warm_streams(mfem, record_property):
+    """The batched configuration's shape at oracle-solvable sizes: warm-started
+    animation streams of a half-scale figure and of the 10k figure in one
+    multi-mesh call, benchmark tolerances; the last frame of every stream
+    against the oracle."""
+    meshes = [dict(figure_config(50000, seeds=[], scale=0.5), model="snh"),
+              dict(figure_config(10000, seeds=[]), model="snh")]
+    ns, frames = 3, 3
+    anims = [np.stack([figure_animation(c["joints"], c["parent"], 300 + 10 * i + s, frames) for s in range(ns)], 1)
+             for i, c in enumerate(meshes)]
+    ctxs = [mfem.Context.from_config(c, precision="mixed", max_batch=ns, init="warm") for c in meshes]
+    for f in range(frames):
+        outs, stats = mfem.solve_multi(ctxs, [a[f] for a in anims])
+    for c in ctxs:
+        c.close()
+    jobs = [(c, anims[i][frames - 1][s], "snh", dict(newton_tol=1e-12, newton_max=80))
+            for i, c in enumerate(meshes) for s in range(ns)]
+    ref = solve_jobs(jobs)
+    errs, k = [], 0
+    for i, c in enumerate(meshes):
+        bbox = float(np.linalg.norm(c["X"].max(0) - c["X"].min(0)))
+        for s in range(ns):
+            assert stats[i][s]["converged"] == 1
+            errs.append(_err(outs[i][s], ref[k][0], bbox))
+            k += 1
+    record_property("parity", json.dumps({"config": "cfg3 batched warm streams (figure50k half-scale + 10k)",
+                                          "mixed": max(errs)}))
+    assert max(errs) <= TOL_MIXED, errs
+
+
+def test_cfg4_served_requests(mfem, record_property):
+    """The serving configuration's four meshes (10k corot, 50k SNH, 200k corot,
+    800k SNH), warm, benchmark tolerances: the 10k and 50k results against the
+    oracle's solutions, the 200k and 800k results through the FP64 free
+    gradient the oracle recomputes at them."""
+    specs = [(10000, "corot"), (50000, "snh"), (200000, "corot"), (800000, "snh")]
+    cfgs = [dict(figure_config(t, seeds=[]), model=m) for t, m in specs]
+    srv = mfem.Server(device_mem_budget=0, max_slots=8)
+    ids = [srv.add(mfem.Context.from_config(c, precision="mixed", init="warm", tile_rows=256)) for c in cfgs]
+    anims = [figure_animation(c["joints"], c["parent"], 900 + i, 3) for i, c in enumerate(cfgs)]
+    last = {}
+    for f in range(3):
+        ts = [(i, srv.submit(ids[i], anims[i][f])) for i in range(4)]
+        for i, t in ts:
+            out, st, lat = srv.wait(t, timeout_ms=300000)
+            assert st["converged"] == 1, (i, f, st)
+            last[i] = out
+    srv.close()
+    ref = solve_jobs([(cfgs[i], anims[i][2], specs[i][1], dict(newton_tol=1e-12, newton_max=80)) for i in (0, 1)])
+    res = {}
+    for i in (0, 1):
+        bbox = float(np.linalg.norm(cfgs[i]["X"].max(0) - cfgs[i]["X"].min(0)))
+        res[f"{specs[i][0] // 1000}k_{specs[i][1]}_err"] = _err(last[i], ref[i][0], bbox)
+    for i in (2, 3):
+        res[f"{specs[i][0] // 1000}k_{specs[i][1]}_rel_grad"] = _free_grad_rel(cfgs[i], anims[i][2], last[i],
+                                                                              specs[i][1])
+    record_property("parity", json.dumps({"config": "cfg4 served 10k/50k/200k/800k", **res}))
+    assert res["10k_corot_err"] <= TOL_MIXED and res["50k_snh_err"] <= TOL_MIXED, res
+    assert res["200k_corot_rel_grad"] <= 1.5e-6 and res["800k_snh_rel_grad"] <= 1.5e-6, res

@@ -2,7 +2,10 @@
 allocate device memory after set-up (a per-frame animation loop, a plugin
 inside a fixed device budget): called through the C ABI, its results must equal
 those of mfem_get_elem on two calls in a row, and meshes above its fixed limit
-are refused.  Kept in a file of its own that pytest collects last."""
+are refused.  Kept in a file of its own that pytest collects last: a run that
+stops at its first failure (-x) has then already run every other GPU test, so a
+fault in this optional entry point cannot hide a result of the main path.  The
+tests here do not depend on that order: each passes alone in a fresh process."""
 import numpy as np
 import pytest
 
