@@ -47,7 +47,7 @@ def parse():
                         "a 200k and a 50k figure in shared launches; serve: Poisson arrivals over resident "
                         "10k/50k/200k/800k meshes; large: one 2M-tet 40-handle character")
     p.add_argument("--rate", type=float, default=500.0, help="serve: mean Poisson arrival rate (requests/s)")
-    p.add_argument("--duration", type=float, default=4.0, help="serve: seconds of arrivals")
+    p.add_argument("--duration", type=float, default=20.0, help="serve: seconds of arrivals per phase")
     p.add_argument("--ncu-case", action="store_true",
                    help="one small solve for profiler captures: 8 poses, 3 Newton steps, 256-row tiles")
     return p.parse_args()
@@ -211,8 +211,10 @@ def _single_thread():
         os.environ[k] = "1"
 
 
-def _oracle_frames(tets, model, seeds, warm_seed, q):
-    """Time full oracle frames of the given poses after one untimed warm-up frame."""
+def _oracle_frames(tets, model, seeds, warm_seed, warm_frames, warm_tets, q):
+    """Time full oracle frames of the given poses after untimed warm-up frames
+    (`warm_frames` of them, on a `warm_tets` figure when given, else one on the
+    timed mesh)."""
     _single_thread()
     sys.path.insert(0, ROOT)
     try:
@@ -220,7 +222,13 @@ def _oracle_frames(tets, model, seeds, warm_seed, q):
         from synth import figure_config
         cfg = figure_config(tets, model=model, seeds=list(seeds) + [warm_seed])
         st = S.Setup.from_config(cfg)
-        S.solve(st, cfg["xfs"][-1], model, **ORACLE_FRAME)          # warm-up frame
+        if warm_tets:
+            wcfg = figure_config(warm_tets, model=model, seeds=range(max(warm_frames, 1)))
+            wst = S.Setup.from_config(wcfg)
+            for xf in wcfg["xfs"][:warm_frames]:
+                S.solve(wst, xf, model, **ORACLE_FRAME)             # warm-up frames (code paths)
+        else:
+            S.solve(st, cfg["xfs"][-1], model, **ORACLE_FRAME)      # warm-up frame
         times = []
         for i in range(len(seeds)):
             t0 = time.perf_counter()
@@ -231,13 +239,13 @@ def _oracle_frames(tets, model, seeds, warm_seed, q):
         q.put(repr(e))
 
 
-def oracle_frame_times(tets, model, seeds, warm_seed=99, timeout_s=900.0):
+def oracle_frame_times(tets, model, seeds, warm_seed=99, timeout_s=900.0, warm_frames=1, warm_tets=0):
     """Full oracle frames of `seeds`, one after another in one spawned
-    single-threaded process, after one warm-up frame."""
+    single-threaded process, after warm-up frames (see _oracle_frames)."""
     import multiprocessing as mp
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
-    p = ctx.Process(target=_oracle_frames, args=(tets, model, list(seeds), warm_seed, q))
+    p = ctx.Process(target=_oracle_frames, args=(tets, model, list(seeds), warm_seed, warm_frames, warm_tets, q))
     p.start()
     try:
         out = q.get(timeout=timeout_s)
@@ -343,9 +351,10 @@ def run_reference(args, dist):
     from oracle import solve as S
     cfg = figure_config(args.tets, model=args.model, seeds=[0])   # mesh generation is setup, not timed
     st = S.Setup.from_config(cfg)
-    total = oracle_frame_times(args.tets, args.model, [k % 16 for k in range(args.warmup + args.steps)],
-                               timeout_s=3600.0)
-    times = total[args.warmup:]
+    # warm-up steps: full frames of a small figure (the same code paths), so the
+    # run stays within minutes; timed steps: full frames of the workload's mesh
+    times = oracle_frame_times(args.tets, args.model, [k % 16 for k in range(args.steps)], timeout_s=3600.0,
+                               warm_frames=args.warmup, warm_tets=3000)
     t = statistics.mean(times)
     value = 1.0 / t
     line = {
@@ -356,7 +365,8 @@ def run_reference(args, dist):
                                        args.precision), parallelism="oracle, 1 CPU thread"),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
                          "sample": (f"each step = one full oracle frame (FP64, Jacobi-PCG 1e-2 inexact Newton to "
-                                    f"1e-6) of pose (step mod 16), one thread, {args.warmup} untimed warm-up frames; "
+                                    f"1e-6) of pose (step mod 16), one thread, after {args.warmup} untimed warm-up "
+                                    f"frames of the 3k-tet figure; "
                                     f"frames/s = 1 / mean frame time")},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -793,14 +803,19 @@ def run_serve(args, dist):
                        "offered_rate_per_s": args.rate, "arrival_seconds": args.duration,
                        "precision": "mixed", "newton_tol": 1e-6,
                        "init": "warm (slot's last solve: predictor + carried correction for SNH)",
-                       "admission": "64 GiB slot budget, 64 slots, between Newton steps",
+                       "admission": ("device memory: 64 GiB budget for request slots and warm state, at most 64 "
+                                     "requests admitted at once; each mesh's slot pools (8 slots each) grow while "
+                                     "the budget has room and idle pools are released; admitted between Newton "
+                                     "steps"),
                        "parallelism": f"replicas x{dist.world}"},
             "latency_ms": {"p50": s2["p50_ms"], "p99": s2["p99_ms"],
                            "note": "per request (submit to result in host memory) at 70% of the measured "
                                    "capacity; the offered-load phase is under `offered_load`"},
             "offered_load": s1, "at_70pct_capacity": s2,
             "server": {"scheduling_rounds": c1["steps"] - c0["steps"],
-                       "pcg_launches": c1["pcg_launches"] - c0["pcg_launches"], "peak_slots": c1["peak_slots"]},
+                       "pcg_launches": c1["pcg_launches"] - c0["pcg_launches"], "peak_slots": c1["peak_slots"],
+                       "pools_added": c1["pools_added"], "pools_released": c1["pools_released"],
+                       "device_bytes_after_offered_phase": c1["device_bytes"]},
             "clocks": clk,
         }
         print(json.dumps(line), flush=True)

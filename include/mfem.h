@@ -352,15 +352,21 @@ const char* mfem_last_error(const mfem_ctx* ctx);
  * together (each PCG iteration launch serves every admitted request).
  * Each request's result equals the same pose solved alone by mfem_solve_batch. */
 
-/* device_mem_budget: bytes the server may hold for request slots (0 = no
- * limit); max_slots: requests admitted at once across meshes. */
+/* device_mem_budget: bytes the server may hold for request slots and warm
+ * state (0 = no limit); max_slots: requests admitted at once across meshes.
+ * Admission is by device memory: each mesh starts with one pool of up to 8
+ * request slots; a request that finds every slot of its mesh busy gets a new
+ * pool of up to 8 slots (sharing the mesh's device data) when the budget has
+ * room for it -- pools of other meshes idle at that moment are released to make
+ * room -- and otherwise waits in the queue; pools idle for 0.5 s are
+ * released. */
 mfem_status mfem_server_create(size_t device_mem_budget, int32_t max_slots, mfem_server** out);
 
 /* Hand a context to the server (ownership transfers; do not use or destroy
  * ctx afterwards).  *mesh_id receives its id.  The mesh's resident state
- * (pattern, static element data) stays on the device until the server is
- * destroyed.  Fails with MFEM_ENOMEM if one slot of this mesh cannot fit the
- * budget. */
+ * (pattern, static element data, preconditioner) stays on the device until the
+ * server is destroyed.  Fails with MFEM_ENOMEM if one slot of this mesh cannot
+ * fit the budget; the context is then left with the caller. */
 mfem_status mfem_server_add(mfem_server* srv, mfem_ctx* mesh, int32_t* mesh_id);
 
 /* Queue one pose solve: xf host [H][12] (copied now), out_verts host [n][3]
@@ -376,9 +382,12 @@ mfem_status mfem_server_submit(mfem_server* srv, int32_t mesh_id, const double* 
 mfem_status mfem_server_wait(mfem_server* srv, uint64_t ticket, int32_t timeout_ms,
                              mfem_stats* stats, double* latency_s);
 
-/* Counters: requests completed, Newton steps run, PCG launches, peak slots in use. */
+/* Counters: requests completed, scheduling rounds run, PCG launches, peak
+ * slots in use, slot pools added and released, device bytes held for slots and
+ * warm state.  Any output may be NULL. */
 mfem_status mfem_server_counters(mfem_server* srv, int64_t* completed, int64_t* steps,
-                                 int64_t* pcg_launches, int32_t* peak_slots);
+                                 int64_t* pcg_launches, int32_t* peak_slots, int64_t* pools_added,
+                                 int64_t* pools_released, int64_t* device_bytes);
 
 void mfem_server_destroy(mfem_server* srv);
 

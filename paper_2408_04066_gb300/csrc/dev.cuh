@@ -16,7 +16,17 @@ constexpr int kWarp = 32;
 constexpr int kSliceRows = 32;       // rows per SELL slice (one warp)
 constexpr int kTetTile = 128;        // tets per element-kernel block
 constexpr int kRowTile = 256;        // rows per block in row kernels other than PCG
-constexpr int kKe = 90;              // 10 upper 3x3 blocks of a symmetric 12x12
+constexpr int kRowTileU = 256;       // rows per block of the PCG update and correction kernels
+// Element blocks of one tet: the upper 3x3 blocks K_ab (a <= b) of the
+// symmetric 12x12 element matrix in the order (0,0) (0,1) (0,2) (0,3) (1,1)
+// (1,2) (1,3) (2,2) (2,3) (3,3); a diagonal block is symmetric and keeps its six
+// upper entries (xx, yy, zz, yz, xz, xy), an off-diagonal block its nine
+// (row-major): 78 values per tet.
+constexpr int kKe = 78;
+__host__ __device__ __forceinline__ int ke_offset(int a, int b) {   // a <= b
+    const int p = a * 4 - (a * (a - 1)) / 2 + (b - a);              // block index
+    return 9 * p - 3 * (a + (b > a ? 1 : 0));                        // minus the diagonal blocks' 3 saved
+}
 
 // Per-problem PCG vector area, in elements of the PCG type, rows padded to 32:
 // two ping-pong records zp[n][8] = (z.xyz, 0, p.xyz, 0) so a neighbour's z and
@@ -63,7 +73,8 @@ struct PcgDesc {
     T* rec;                // [n][12] (dx, r, q) records
     double* part;          // [tiles][4] tile partials
     ProbScal* sc;
-    int n_rows, n_tiles, unit_begin, pad;
+    int n_rows, n_tiles, unit_begin;   // the SpMV's tiles (autotuned rows per block)
+    int n_tiles_u;                     // the row-local kernels' tiles (kRowTileU rows per block)
     // two-level preconditioner (coarse = 0: block Jacobi only for this solve)
     const float4* crel;    // [n] rest offset from the aggregate centroid, w = 1 free / 0 pin
     const int* agg_handle; // [n_agg]
@@ -72,7 +83,8 @@ struct PcgDesc {
     float* rcs;            // [coarse_n] per-aggregate sums of rcp (aggregates over 64 rows)
     const float* rc;       // the coarse residual read by the coarse product: rcp or rcs
     float* ec;             // [ceil(coarse_n / kCoarseKC)][coarse_n] partial coarse corrections
-    int coarse, agg_shift, coarse_n, pad2;
+    int coarse, agg_shift, coarse_n;
+    int unit_begin_u;
 };
 
 // Programmatic dependent launch: wait for the preceding grid of the stream to

@@ -88,7 +88,8 @@ mfem_status upload(mfem_ctx* c, U** dst, const U* src, size_t count) {
 
 void free_slots(mfem_ctx* c) {
     SlotDev& S = c->slot;
-    void* ptrs[] = {S.xf, S.xf_prev, S.xpred, S.dcorr, S.tol2, S.coarse_on, S.rcp, S.ec, S.rcs, S.x, S.xp, S.g, S.ge, S.Ke, S.val, S.dinv, S.vec, S.part, S.sc, S.active, S.alpha, S.outbuf};
+    void* ptrs[] = {S.xf, S.xf_prev, S.xpred, S.dcorr, S.tol2, S.coarse_on, S.rcp, S.ec, S.rcs, S.x, S.xprev, S.xp,
+                    S.g, S.ge, S.Ke, S.val, S.dinv, S.vec, S.part, S.sc, S.active, S.alpha, S.outbuf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     int prec = S.prec;
@@ -111,7 +112,7 @@ size_t bytes_per_slot(const mfem_ctx* c) {
     const size_t slots = (size_t)c->plan.slice_ptr.back();
     return H * 12 * 8 + 4 * n * 3 * 8 + m * 12 * 8 + m * kKe * kt + slots * 9 * kt + n * 9 * kt +
            kVecStride * npad32((int)n) * kt + (size_t)part_tiles_for(c) * 4 * 8 + sizeof(ProbScal) + 4 + 8 + 8 +
-           H * 12 * 8 + (c->opt.init == MFEM_INIT_WARM ? 2 * n * 3 * 8 : 0) + 4 +
+           H * 12 * 8 + (c->opt.init == MFEM_INIT_WARM ? 2 * n * 3 * 8 : 0) + 4 + (line_search(c) ? n * 3 * 8 : 0) +
            (c->mesh.coarse_n > 0 ? ((n + 255) / 256) * 24 * 4 + (coarse_ks(c) + 1) * c->mesh.coarse_n * 4 + 128 : 0);
 }
 
@@ -136,6 +137,7 @@ mfem_status alloc_slots(mfem_ctx* c, int B) {
         AL(S.dcorr, B * n * 3 * 8);
     }
     AL(S.x, B * n * 3 * 8);
+    if (line_search(c)) AL(S.xprev, B * n * 3 * 8);
     AL(S.xp, B * n * 3 * 8);
     AL(S.g, B * n * 3 * 8);
     AL(S.outbuf, B * n * 3 * 8);
@@ -262,9 +264,10 @@ double element_bytes(const mfem_ctx* c) {
 }
 
 template <typename T>
-void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc<T>>& out, int& units,
+void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc<T>>& out, int& units, int& units_u,
                  std::vector<CoarseJob>* jobs = nullptr) {
     units = 0;
+    units_u = 0;
     for (auto& g : gs) {
         mfem_ctx* c = g.ctx;
         if (c->slot.prec != prec) continue;
@@ -293,7 +296,8 @@ void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc
             d.n_rows = n;
             d.n_tiles = (n + tile - 1) / tile;
             d.unit_begin = units;
-            d.pad = 0;
+            d.n_tiles_u = (n + kRowTileU - 1) / kRowTileU;
+            d.unit_begin_u = units_u;
             d.coarse = g.ph[b].coarse && c->mesh.coarse_n > 0;
             d.crel = c->mesh.crel;
             d.agg_handle = c->mesh.agg_handle;
@@ -304,8 +308,8 @@ void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc
             d.rc = c->plan.agg_size == kCoarseRows ? d.rcp : d.rcs;
             d.agg_shift = c->mesh.agg_shift;
             d.coarse_n = c->mesh.coarse_n;
-            d.pad2 = 0;
             units += d.n_tiles;
+            units_u += d.n_tiles_u;
             out.push_back(d);
         }
         if (jobs && !jobs->empty() && jobs->back().d0 == first && jobs->back().key == c)
@@ -376,12 +380,13 @@ mfem_status read_scalars(mfem_ctx* c, int B) {
 // time these launch parameters occur (the descriptor table lives at a fixed
 // device address; only its contents change), else launched directly.
 template <typename T>
-mfem_status launch_chunk(mfem_ctx* c, const PcgDesc<T>* dst, int nd, int units, int tile, int n_it,
+mfem_status launch_chunk(mfem_ctx* c, const PcgDesc<T>* dst, int nd, int units, int units_u, int tile, int n_it,
                          const std::vector<CoarseJob>& jobs) {
     const int nj = (int)jobs.size();
     if (c->opt.launch == MFEM_LAUNCH_GRAPH && !c->graphs_off) {
         char buf[96];
-        snprintf(buf, sizeof buf, "%d %p %d %d %d %d", (int)sizeof(T), (const void*)dst, nd, units, tile, n_it);
+        snprintf(buf, sizeof buf, "%d %p %d %d %d %d %d", (int)sizeof(T), (const void*)dst, nd, units, units_u, tile,
+                 n_it);
         std::string key(buf);
         for (const auto& j : jobs) {
             snprintf(buf, sizeof buf, " %p %d %d %d %d %d", j.key, j.Abf ? 1 : 0, j.N, j.d0, j.nd, j.agg_units);
@@ -397,7 +402,7 @@ mfem_status launch_chunk(mfem_ctx* c, const PcgDesc<T>* dst, int nd, int units, 
             cudaGraphExec_t ex = nullptr;
             bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
-                const cudaError_t e1 = launch_pcg_iters<T>(dst, nd, units, tile, n_it, jobs.data(), nj, c->stream);
+                const cudaError_t e1 = launch_pcg_iters<T>(dst, nd, units, units_u, tile, n_it, jobs.data(), nj, c->stream);
                 const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
                 ok = e1 == cudaSuccess && e2 == cudaSuccess && g && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
             }
@@ -405,7 +410,7 @@ mfem_status launch_chunk(mfem_ctx* c, const PcgDesc<T>* dst, int nd, int units, 
             if (!ok) {   // keep to direct launches from now on
                 cudaGetLastError();
                 c->graphs_off = true;
-                CK(launch_pcg_iters<T>(dst, nd, units, tile, n_it, jobs.data(), nj, c->stream));
+                CK(launch_pcg_iters<T>(dst, nd, units, units_u, tile, n_it, jobs.data(), nj, c->stream));
                 return MFEM_OK;
             }
             it = c->graphs.emplace(key, ex).first;
@@ -413,7 +418,7 @@ mfem_status launch_chunk(mfem_ctx* c, const PcgDesc<T>* dst, int nd, int units, 
         CK(cudaGraphLaunch(it->second, c->stream));
         return MFEM_OK;
     }
-    CK(launch_pcg_iters<T>(dst, nd, units, tile, n_it, jobs.data(), nj, c->stream));
+    CK(launch_pcg_iters<T>(dst, nd, units, units_u, tile, n_it, jobs.data(), nj, c->stream));
     return MFEM_OK;
 }
 
@@ -423,8 +428,8 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
     mfem_ctx* c = c0;
     std::vector<PcgDesc<T>> d;
     std::vector<CoarseJob> jobs;
-    int units = 0;
-    build_descs<T>(gs, tile, prec, d, units, &jobs);
+    int units = 0, units_u = 0;
+    build_descs<T>(gs, tile, prec, d, units, units_u, &jobs);
     if (d.empty()) return MFEM_OK;
     const int nj = (int)jobs.size();
     double coarse_bytes = 0.0;   // A_c^{-1} streamed once per iteration per mesh
@@ -447,7 +452,7 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
     CK(cudaMemcpyAsync((void*)dst, hst, bytes, cudaMemcpyHostToDevice, c->stream));
     c->grid_blocks = units;
     if (max_iters > 0) {
-        CK(launch_pcg_iters<T>(dst, (int)d.size(), units, tile, max_iters, jobs.data(), nj, c->stream));
+        CK(launch_pcg_iters<T>(dst, (int)d.size(), units, units_u, tile, max_iters, jobs.data(), nj, c->stream));
         return MFEM_OK;
     }
     int cap = 0;
@@ -457,7 +462,7 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
         const int n_it = std::min(kPcgChunk, cap - done);
         if (one_chunk && done > 0) break;
         int pe = count ? c->prof.begin(2, c->stream) : -1;
-        mfem_status lst = launch_chunk<T>(c, dst, (int)d.size(), units, tile, n_it, jobs);
+        mfem_status lst = launch_chunk<T>(c, dst, (int)d.size(), units, units_u, tile, n_it, jobs);
         if (lst != MFEM_OK) return lst;
         if (count) {
             c->prof.end(pe, c->stream);
@@ -561,6 +566,86 @@ bool any_of(const std::vector<int>& f) {
     for (int v : f)
         if (v) return true;
     return false;
+}
+
+}  // namespace
+
+namespace {
+
+// Backtracking on E for the problems in `testing` (step lengths in alpha_host,
+// halved after each failed Armijo test; attempt k_first, k_first + 1, ...; at
+// attempt kLsMax the step is taken as it is), energy trials at x + alpha dx.
+mfem_status backtrack(std::vector<Group>& gs, Group& g, std::vector<int> testing, const std::vector<double>& e0,
+                      const std::vector<double>& slope, int k_first) {
+    mfem_ctx* gc = g.ctx;
+    mfem_ctx* c = gc;   // for CK
+    cudaStream_t s = gc->stream;
+    bool any = any_of(testing);
+    for (int k = k_first; any && k <= kLsMax; ++k) {
+        mfem_status st = upload_active(gc, g.B, testing);
+        if (st != MFEM_OK) return st;
+        st = upload_alpha(gc, g.B);
+        if (st != MFEM_OK) return st;
+        int pl = gc->prof.begin(3, s);
+        launch_energy_trial(elem_args(gc), g.B, s);
+        gc->prof.end(pl, s);
+        gc->prof.launches++;
+        st = read_scalars(gc, g.B);
+        if (st != MFEM_OK) return st;
+        CK(cudaStreamSynchronize(s));
+        synced(gs);
+        any = false;
+        for (int b = 0; b < g.B; ++b) {
+            if (!testing[b]) continue;
+            const double a = gc->alpha_host[b];
+            const double et = gc->sc_host[b].energy_trial;
+            if (et <= e0[b] + kLsC * a * slope[b] || k == kLsMax) {
+                testing[b] = 0;
+            } else {
+                gc->alpha_host[b] = 0.5 * a;
+                any = true;
+            }
+        }
+    }
+    return MFEM_OK;
+}
+
+// Armijo's test of the speculative full steps whose element pass just ran
+// (energies in sc_host).  A rejected step goes back to x_prev, backtracks from
+// alpha = 1/2 with energy trials, takes the accepted step, and needs another
+// element pass (the caller leaves such problems out of this round's PCG).
+// Returns the rejected problems in `rejected`.
+mfem_status check_speculative(std::vector<Group>& gs, Group& g, std::vector<int>& rejected) {
+    mfem_ctx* gc = g.ctx;
+    mfem_ctx* c = gc;   // for CK
+    rejected.assign(g.B, 0);
+    std::vector<double> e0(g.B, 0.0), slope(g.B, 0.0);
+    bool any = false;
+    for (int b = 0; b < g.B; ++b) {
+        ProbHost& p = g.ph[b];
+        if (!p.active || p.in_pcg || !p.spec) continue;
+        p.spec = 0;
+        const double et = gc->sc_host[b].energy;
+        if (et <= p.spec_e0 + kLsC * 1.0 * p.spec_slope) continue;   // attempt 0 (alpha = 1) passes
+        rejected[b] = 1;
+        e0[b] = p.spec_e0;
+        slope[b] = p.spec_slope;
+        gc->alpha_host[b] = 0.5;
+        any = true;
+        const size_t xb = sizeof(double) * 3 * (size_t)gc->plan.n;
+        CK(cudaMemcpyAsync(gc->slot.x + (size_t)b * 3 * gc->plan.n, gc->slot.xprev + (size_t)b * 3 * gc->plan.n, xb,
+                           cudaMemcpyDeviceToDevice, gc->stream));
+    }
+    if (!any) return MFEM_OK;
+    mfem_status st = backtrack(gs, g, rejected, e0, slope, 1);
+    if (st != MFEM_OK) return st;
+    st = upload_active(gc, g.B, rejected);
+    if (st != MFEM_OK) return st;
+    st = upload_alpha(gc, g.B);
+    if (st != MFEM_OK) return st;
+    launch_update(elem_args(gc), g.B, gc->stream);
+    gc->prof.launches++;
+    return MFEM_OK;
 }
 
 }  // namespace
@@ -687,10 +772,12 @@ mfem_status advance(std::vector<Group>& gs) {
         synced(gs);
         for (auto& g : gs) {
             mfem_ctx* gc = g.ctx;
-            std::vector<int> start(g.B, 0);
+            std::vector<int> start(g.B, 0), redo;
+            mfem_status sst = check_speculative(gs, g, redo);
+            if (sst != MFEM_OK) return sst;
             for (int b = 0; b < g.B; ++b) {
                 ProbHost& p = g.ph[b];
-                if (!p.active || p.in_pcg) continue;
+                if (!p.active || p.in_pcg || redo[b]) continue;   // a rejected full step: element pass again
                 if (!p.pred) {   // the predictor's gradient is not the SNH residual
                     const ProbScal& sc = gc->sc_host[b];
                     p.gn = std::sqrt(sc.gnorm2);
@@ -857,45 +944,26 @@ mfem_status advance(std::vector<Group>& gs) {
         CK(cudaStreamSynchronize(s));
         synced(gs);
     }
-    // backtracking line search on E (SNH)
+    // backtracking line search on E (SNH, polar rotations): attempt 0 (the full
+    // step) is taken speculatively -- x_prev is kept, x moves to x_prev + dx, and
+    // the problem's next element pass, which evaluates E there anyway, decides
+    // Armijo's test (check_speculative); a step whose predicted decrease is
+    // below rounding noise is taken untested
     for (size_t gi = 0; gi < gs.size(); ++gi) {
         Group& g = gs[gi];
         mfem_ctx* gc = g.ctx;
         if (!line_search(gc) || !any_of(ls[gi])) continue;
-        std::vector<int> testing(g.B, 0);
-        std::vector<double> e0(g.B, 0.0), slope(g.B, 0.0);
-        bool any = false;
+        const size_t xb = sizeof(double) * 3 * (size_t)gc->plan.n;
         for (int b = 0; b < g.B; ++b) {
             if (!ls[gi][b]) continue;
-            e0[b] = g.ph[b].energy;
-            slope[b] = gc->sc_host[b].slope;
-            if (-slope[b] > kLsNoise * std::fabs(e0[b])) { testing[b] = 1; any = true; }
-        }
-        for (int k = 0; any && k <= kLsMax; ++k) {
-            mfem_status st = upload_active(gc, g.B, testing);
-            if (st != MFEM_OK) return st;
-            st = upload_alpha(gc, g.B);
-            if (st != MFEM_OK) return st;
-            int pl = gc->prof.begin(3, s);
-            launch_energy_trial(elem_args(gc), g.B, s);
-            gc->prof.end(pl, s);
-            gc->prof.launches++;
-            st = read_scalars(gc, g.B);
-            if (st != MFEM_OK) return st;
-            CK(cudaStreamSynchronize(s));
-            synced(gs);
-            any = false;
-            for (int b = 0; b < g.B; ++b) {
-                if (!testing[b]) continue;
-                const double a = gc->alpha_host[b];
-                const double et = gc->sc_host[b].energy_trial;
-                if (et <= e0[b] + kLsC * a * slope[b] || k == kLsMax) {
-                    testing[b] = 0;
-                } else {
-                    gc->alpha_host[b] = 0.5 * a;
-                    any = true;
-                }
-            }
+            ProbHost& p = g.ph[b];
+            const double e0 = p.energy, slope = gc->sc_host[b].slope;
+            if (!(-slope > kLsNoise * std::fabs(e0))) continue;
+            p.spec = 1;
+            p.spec_e0 = e0;
+            p.spec_slope = slope;
+            CK(cudaMemcpyAsync(gc->slot.xprev + (size_t)b * 3 * gc->plan.n, gc->slot.x + (size_t)b * 3 * gc->plan.n,
+                               xb, cudaMemcpyDeviceToDevice, s));
         }
     }
     // x <- x + alpha dx; the problem's next step starts with its element pass
@@ -968,6 +1036,51 @@ void fill_stats(const mfem_ctx* c, const ProbHost& p, mfem_stats* st) {
 
 }  // namespace mfem
 
+namespace mfem {
+
+mfem_ctx* ctx_slot_clone(mfem_ctx* src, int cap, cudaStream_t stream, mfem_status* st) {
+    mfem_ctx* c = new mfem_ctx();
+    // what a solve needs of the plan after creation: sizes, the pattern's slot
+    // count, pins (count) and the aggregate size
+    Plan& P = c->plan;
+    const Plan& S = src->plan;
+    P.n = S.n;
+    P.m = S.m;
+    P.H = S.H;
+    P.nnz_blocks = S.nnz_blocks;
+    P.n_slices = S.n_slices;
+    P.slice_ptr = S.slice_ptr;
+    P.pin_vert = S.pin_vert;
+    P.pin_handle = S.pin_handle;
+    P.vperm = S.vperm;
+    P.agg_size = S.agg_size;
+    P.n_agg = S.n_agg;
+    c->model = src->model;
+    c->opt = src->opt;
+    c->device = src->device;
+    c->stream = stream;
+    c->mesh = src->mesh;
+    c->mesh_shared = true;
+    c->slot.prec = src->slot.prec;
+    c->tile_rows = src->tile_rows;
+    c->owned_by_server = true;
+    mfem_status s = MFEM_OK;
+    if (cudaMallocHost((void**)&c->cerr_host, sizeof(unsigned)) != cudaSuccess) s = MFEM_ENOMEM;
+    if (s == MFEM_OK) {
+        *c->cerr_host = 0;
+        s = ensure_slots(c, cap);
+    }
+    if (s != MFEM_OK) {
+        if (st) *st = s;
+        mfem_destroy(c);
+        return nullptr;
+    }
+    if (st) *st = MFEM_OK;
+    return c;
+}
+
+}  // namespace mfem
+
 using namespace mfem;
 
 // ============================================================================
@@ -1033,6 +1146,7 @@ void mfem_destroy(mfem_ctx* c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     free_slots(c);
+    if (c->mesh_shared) c->mesh = MeshDev();   // the owner frees the mesh data
     MeshDev& M = c->mesh;
     void* ptrs[] = {M.tet, M.Dminv64, M.Dminv32, M.vol, M.cluster, M.mu, M.lam, M.X, M.vhandle, M.pin_handle_v,
                     M.vperm, M.tperm, M.slice_ptr, M.col, M.slot_row, M.contrib_ptr, M.contrib, M.vinc_ptr, M.vinc,

@@ -34,6 +34,11 @@ struct ProbHost {
     double g0 = -1.0, gn = 0.0, energy = 0.0;
     double gprev = -1.0;   // |g_free| before the last Newton step (not the predictor), for the forcing rule
     double eta_prev = 0.0; // that step's PCG target
+    // speculative full step of a line-searched Newton step: x holds x_prev + dx
+    // (x_prev kept in slot.xprev) and the next element pass, which computes
+    // E(x_prev + dx) anyway, decides Armijo's test at alpha = 1
+    int spec = 0;
+    double spec_e0 = 0.0, spec_slope = 0.0;
 };
 
 // Profile accumulator with a pool of CUDA events on the context stream.
@@ -102,6 +107,7 @@ struct mfem_ctx {
     mfem_profile last_profile{};
     std::string err;
     bool owned_by_server = false;
+    bool mesh_shared = false;   // a server slot pool: the mesh's device data belongs to another context
 };
 
 namespace mfem {
@@ -116,6 +122,10 @@ struct Group {
 };
 
 mfem_status ctx_fail(mfem_ctx* c, mfem_status s, const std::string& msg);
+// A context that shares src's device mesh data (and preconditioner) but owns
+// `cap` request slots of its own, working on `stream` (server slot pools).
+// Returns null and sets *st on failure.  Destroy it before src.
+mfem_ctx* ctx_slot_clone(mfem_ctx* src, int cap, cudaStream_t stream, mfem_status* st);
 mfem_status cuda_check(mfem_ctx* c, cudaError_t e, const char* what);
 mfem_status ensure_slots(mfem_ctx* c, int B);
 size_t slot_bytes_for(const mfem_ctx* c, int B);

@@ -60,6 +60,8 @@ constexpr uint64_t kTcWaitNs = 200ull * 1000ull * 1000ull;   // 0.2 s per bounde
 
 static_assert(kTcKS % (16 * kTcChunks) == 0, "K slice must split into whole MMA steps per chunk");
 static_assert(kTcChunkBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
+static_assert((kTcProbs & (kTcProbs - 1)) == 0 && (kTcProbs * kTcKS / 8) % 128 == 0,
+              "B build: whole work items per thread, problem index in the low bits");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -188,10 +190,13 @@ __global__ void __launch_bounds__(128) k_coarse_tc(const __nv_bfloat16* __restri
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kTcABytes + kTcBBytes);   // chunks, then MMA done
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kTcChunks + 1);
     __shared__ const PcgDesc<T>* dp[kTcProbs];
+    __shared__ const float* rcs[kTcProbs];
     __shared__ int any, s_ok;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int mt = blockIdx.x, ks = blockIdx.y, pg = blockIdx.z;
-    // prologue on data fixed during the solve, overlapping the previous kernel
+    // prologue on data fixed during the solve, overlapping the previous kernel:
+    // the descriptors, and the tile of A_c^{-1} itself (four bulk copies, one
+    // barrier each) -- it does not depend on the previous kernel
     const PcgDesc<T>* mine = nullptr;
     if (t < kTcProbs && pg * kTcProbs + t < nd && D[d0 + pg * kTcProbs + t].coarse) mine = &D[d0 + pg * kTcProbs + t];
     if (t == 0) {
@@ -200,6 +205,12 @@ __global__ void __launch_bounds__(128) k_coarse_tc(const __nv_bfloat16* __restri
         for (int c = 0; c <= kTcChunks; ++c) mbar_init(&bars[c], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const unsigned char* gA =
+            reinterpret_cast<const unsigned char*>(Abf + ((size_t)mt * nks + ks) * (size_t)(kTcM * kTcKS));
+        for (int c = 0; c < kTcChunks; ++c) {
+            mbar_expect_tx(&bars[c], kTcChunkBytes);
+            bulk_g2s(sA + c * kTcChunkBytes, gA + (size_t)c * kTcChunkBytes, kTcChunkBytes, &bars[c]);
+        }
     }
     pdl_wait();
     pdl_trigger();
@@ -207,18 +218,14 @@ __global__ void __launch_bounds__(128) k_coarse_tc(const __nv_bfloat16* __restri
     if (t < kTcProbs) {
         const PcgDesc<T>* p = (mine && mine->sc->state == kActive) ? mine : nullptr;
         dp[t] = p;
+        rcs[t] = p ? p->rc : nullptr;
         if (p) atomicOr(&any, 1);
     }
     __syncthreads();
-    if (!any) return;   // block-uniform: no copy issued, no tensor memory held
-
-    if (t == 0) {   // the tile: four bulk copies, one barrier each
-        const unsigned char* gA =
-            reinterpret_cast<const unsigned char*>(Abf + ((size_t)mt * nks + ks) * (size_t)(kTcM * kTcKS));
-        for (int c = 0; c < kTcChunks; ++c) {
-            mbar_expect_tx(&bars[c], kTcChunkBytes);
-            bulk_g2s(sA + c * kTcChunkBytes, gA + (size_t)c * kTcChunkBytes, kTcChunkBytes, &bars[c]);
-        }
+    if (!any) {   // block-uniform: nothing to compute; let the prefetch land before the memory is released
+        if (t == 0)
+            for (int c = 0; c < kTcChunks; ++c) mbar_wait(&bars[c], 0);
+        return;
     }
     if (warp == 0) {   // tensor memory for the 128 x 48 FP32 accumulator
         __syncwarp();
@@ -228,23 +235,46 @@ __global__ void __launch_bounds__(128) k_coarse_tc(const __nv_bfloat16* __restri
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     // B operand: each problem's r_c slice as three BF16 parts (rows p, 16 + p,
-    // 32 + p of the N = 48 operand), zero for absent problems and past N
+    // 32 + p of the N = 48 operand), zero for absent problems and past N.  A
+    // work item is 8 consecutive columns of one problem: two 16-byte loads, and
+    // each part is one 16-byte row of a core matrix; the problem index varies
+    // fastest over the threads, so a warp's stores fill consecutive rows.
     const int k0 = ks * kTcKS;
-    for (int idx = t; idx < kTcProbs * kTcKS; idx += blockDim.x) {
-        const int p = idx / kTcKS, kk = idx - p * kTcKS, k = k0 + kk;
-        const PcgDesc<T>* q = dp[p];
-        const float r = (q && k < N) ? q->rc[k] : 0.f;
-        const __nv_bfloat16 hi = __float2bfloat16_rn(r);
-        const float r1 = r - __bfloat162float(hi);
-        const __nv_bfloat16 mid = __float2bfloat16_rn(r1);
-        const __nv_bfloat16 lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
-        __nv_bfloat16* bs = reinterpret_cast<__nv_bfloat16*>(sB);
-        const int s = kk >> 4, j2 = (kk >> 3) & 1, c = kk & 7;
-        const size_t base = (size_t)s * (kTcN * 16) + j2 * 64 + c;
+#pragma unroll
+    for (int it = 0; it < (kTcProbs * kTcKS / 8) / 128; ++it) {
+        const int item = t + 128 * it;
+        const int p = item & (kTcProbs - 1), kk0 = 8 * (item / kTcProbs), k = k0 + kk0;
+        const float* src = rcs[p];
+        float v[8];
+        if (src && k + 7 < N) {
+            const float4 a = *reinterpret_cast<const float4*>(src + k);
+            const float4 c = *reinterpret_cast<const float4*>(src + k + 4);
+            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = c.x; v[5] = c.y; v[6] = c.z; v[7] = c.w;
+        } else {
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = (src && k + e < N) ? src[k + e] : 0.f;
+        }
+        uint32_t hi[4], mid[4], lo[4];
+#pragma unroll
+        for (int e = 0; e < 8; e += 2) {
+            __nv_bfloat16 h[2], m[2], l[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float r = v[e + q];
+                h[q] = __float2bfloat16_rn(r);
+                const float r1 = r - __bfloat162float(h[q]);
+                m[q] = __float2bfloat16_rn(r1);
+                l[q] = __float2bfloat16_rn(r1 - __bfloat162float(m[q]));
+            }
+            hi[e / 2] = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
+            mid[e / 2] = (uint32_t)__bfloat16_as_ushort(m[0]) | ((uint32_t)__bfloat16_as_ushort(m[1]) << 16);
+            lo[e / 2] = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
+        }
+        unsigned char* step = sB + (kk0 >> 4) * kTcStepB + ((kk0 >> 3) & 1) * 128;
         const int n0 = p, n1 = kTcProbs + p, n2 = 2 * kTcProbs + p;
-        bs[base + (n0 >> 3) * 128 + (n0 & 7) * 8] = hi;
-        bs[base + (n1 >> 3) * 128 + (n1 & 7) * 8] = mid;
-        bs[base + (n2 >> 3) * 128 + (n2 & 7) * 8] = lo;
+        *reinterpret_cast<uint4*>(step + (n0 >> 3) * 256 + (n0 & 7) * 16) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(step + (n1 >> 3) * 256 + (n1 & 7) * 16) = make_uint4(mid[0], mid[1], mid[2], mid[3]);
+        *reinterpret_cast<uint4*>(step + (n2 >> 3) * 256 + (n2 & 7) * 16) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B visible to the tensor cores
     tc_fence_before();

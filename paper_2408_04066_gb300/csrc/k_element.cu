@@ -22,9 +22,7 @@ constexpr double kInvSqrt2 = 0.7071067811865476;
 constexpr double kSpdEps = 1.0e-6;     // Hessian eigenvalue floor, times mu
 constexpr double kFallbackJ = 0.25;    // mixed path: det S below this -> FP64 Hessian
 
-__device__ __forceinline__ int pair_index(int a, int b) {  // a <= b
-    return a * 4 - (a * (a - 1)) / 2 + (b - a);
-}
+constexpr int kMaxStagedHandles = 64;   // pose rotations staged in shared memory up to this many handles
 
 // Gather the four vertex positions of tet k of problem b (optionally x + alpha dx).
 // dx, if given, is read with a stride of dx_stride elements per vertex.
@@ -251,20 +249,11 @@ __device__ __forceinline__ void Ecol(const KT (&g)[3], const KT (&u)[3], KT (&e)
     e[5] = (u[0] * g[1] + u[1] * g[0]) * is2;
 }
 
-// Element blocks K_ab = W E_a^T C E_b for a <= b, generic 6x6 C.
+// Element blocks K_ab = W E_a^T C E_b for a <= b, generic 6x6 C, in the
+// 78-value layout (diagonal blocks: upper entries only).
 template <typename KT>
-__device__ __forceinline__ void blocks_generic(const KT (&C)[6][6], const double (&Gd)[4][3],
-                                               const double (&Qd)[3][3], double w, KT* __restrict__ out) {
-    KT G[4][3], Q[3][3];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int i = 0; i < 3; ++i) G[a][i] = (KT)Gd[a][i];
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) Q[i][j] = (KT)Qd[i][j];
-    const KT W = (KT)w;
+__device__ __forceinline__ void blocks_generic(const KT (&C)[6][6], const KT (&G)[4][3], const KT (&Q)[3][3],
+                                               KT W, KT* __restrict__ out) {
 #pragma unroll
     for (int b = 0; b < 4; ++b) {
         KT CE[3][6];  // (C E_b) columns
@@ -283,7 +272,8 @@ __device__ __forceinline__ void blocks_generic(const KT (&C)[6][6], const double
         }
 #pragma unroll
         for (int a = 0; a <= b; ++a) {
-            KT* o = out + 9 * pair_index(a, b);
+            KT* o = out + ke_offset(a, b);
+            KT blk[3][3];
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 KT e[6];
@@ -291,43 +281,58 @@ __device__ __forceinline__ void blocks_generic(const KT (&C)[6][6], const double
                 Ecol<KT>(G[a], u, e);
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
+                    if (a == b && j < i) continue;   // diagonal block: upper entries
                     KT s = 0;
 #pragma unroll
                     for (int p = 0; p < 6; ++p) s += e[p] * CE[j][p];
-                    o[3 * i + j] = s;
+                    blk[i][j] = s;
                 }
+            }
+            if (a == b) {
+                o[0] = blk[0][0]; o[1] = blk[1][1]; o[2] = blk[2][2];
+                o[3] = blk[1][2]; o[4] = blk[0][2]; o[5] = blk[0][1];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) o[3 * i + j] = blk[i][j];
             }
         }
     }
 }
 
 // ARAP / co-rotational blocks in closed form:
-// K_ab = W [mu (G_a.G_b) I + mu h_b h_a^T + lam h_a h_b^T], h_a = Q G_a.
+// K_ab = W [mu (G_a.G_b) I + mu h_b h_a^T + lam h_a h_b^T], h_a = Q G_a,
+// in the 78-value layout.
 template <typename KT>
-__device__ __forceinline__ void blocks_quadratic(const double (&Gd)[4][3], const double (&Qd)[3][3],
-                                                 double w, double mu, double lam, KT* __restrict__ out) {
-    KT G[4][3], h[4][3];
+__device__ __forceinline__ void blocks_quadratic(const KT (&G)[4][3], const KT (&Q)[3][3], KT wm, KT wl,
+                                                 KT* __restrict__ out) {
+    KT h[4][3];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) G[a][i] = (KT)Gd[a][i];
-#pragma unroll
-    for (int a = 0; a < 4; ++a)
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-            h[a][i] = (KT)Qd[i][0] * G[a][0] + (KT)Qd[i][1] * G[a][1] + (KT)Qd[i][2] * G[a][2];
-    const KT wm = (KT)(w * mu), wl = (KT)(w * lam);
+        for (int i = 0; i < 3; ++i) h[a][i] = Q[i][0] * G[a][0] + Q[i][1] * G[a][1] + Q[i][2] * G[a][2];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
         for (int b = a; b < 4; ++b) {
-            KT* o = out + 9 * pair_index(a, b);
+            KT* o = out + ke_offset(a, b);
             const KT gg = wm * (G[a][0] * G[b][0] + G[a][1] * G[b][1] + G[a][2] * G[b][2]);
+            KT blk[3][3];
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll
                 for (int j = 0; j < 3; ++j)
-                    o[3 * i + j] = (i == j ? gg : (KT)0) + wm * h[b][i] * h[a][j] + wl * h[a][i] * h[b][j];
+                    blk[i][j] = (i == j ? gg : (KT)0) + wm * h[b][i] * h[a][j] + wl * h[a][i] * h[b][j];
+            if (a == b) {
+                o[0] = blk[0][0]; o[1] = blk[1][1]; o[2] = blk[2][2];
+                o[3] = blk[1][2]; o[4] = blk[0][2]; o[5] = blk[0][1];
+            } else {
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+#pragma unroll
+                    for (int j = 0; j < 3; ++j) o[3 * i + j] = blk[i][j];
+            }
         }
 }
 
@@ -448,9 +453,10 @@ __device__ bool polar_rotation(const double (&F)[3][3], double (&R)[3][3]) {
 // Rotation of tet k: its rig cluster's handle rotation (§3.1), or, in the
 // polar-rotation mode, the rotation factor of its own F (the rotation a
 // co-rotational FEM element takes; the cluster rotation if F is singular).
-__device__ __forceinline__ void tet_rotation(const ElemArgs& A, const double* __restrict__ xf, int k,
-                                             const double (&xa)[4][3], const double (&G)[4][3],
-                                             double (&Q)[3][3]) {
+// qs: the problem's handle rotations staged in shared memory, or null.
+__device__ __forceinline__ void tet_rotation(const ElemArgs& A, const double* __restrict__ xf,
+                                             const double (*qs)[9], int k, const double (&xa)[4][3],
+                                             const double (&G)[4][3], double (&Q)[3][3]) {
     if (A.rot_polar) {
         double F[3][3];
 #pragma unroll
@@ -464,7 +470,28 @@ __device__ __forceinline__ void tet_rotation(const ElemArgs& A, const double* __
             }
         if (polar_rotation(F, Q)) return;
     }
-    load_Q(xf, A.mesh.cluster[k], Q);
+    const int h = A.mesh.cluster[k];
+    if (qs) {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) Q[i][j] = qs[h][3 * i + j];
+    } else {
+        load_Q(xf, h, Q);
+    }
+}
+
+// The problem's handle rotations into shared memory (every thread calls it;
+// returns qs, or null when the rig has more handles than are staged).
+__device__ __forceinline__ const double (*stage_pose(double (*qs)[9], const double* __restrict__ xf,
+                                                     int H))[9] {
+    if (H > kMaxStagedHandles) return nullptr;
+    for (int i = threadIdx.x; i < 9 * H; i += blockDim.x) {
+        const int h = i / 9, e = i - 9 * h;
+        qs[h][e] = xf[12 * h + 4 * (e / 3) + e % 3];
+    }
+    __syncthreads();
+    return qs;
 }
 
 // Energy terms that live on vertex v at position y: -f_v . y for an external
@@ -487,68 +514,118 @@ __device__ __forceinline__ double vertex_energy(const ElemArgs& A, int b, int v,
 // ---------------------------------------------------------------------------
 // Thread k handles tet k (k < m) and the vertex terms of vertex k (k < n).
 // HESS = false: energy and forces only (a gradient test needs no Hessian).
+//
+// Stores: each warp's 32 tets write contiguous records (12 FP64 forces, 78
+// element-block values), so a thread's record is first built in the warp's
+// shared-memory area and the warp then copies the area out with consecutive
+// lanes on consecutive words; forces first, then the blocks in the same area.
+// FP64 Hessians (KT = double) are written directly.
+constexpr int kStageWords = 2560;   // floats per warp: 32 x 78 blocks, or 32 x 12 doubles of forces
+
 template <typename KT, int MODEL, bool HESS>
 __global__ void __launch_bounds__(kTetTile, 4) k_element(ElemArgs A) {
+    __shared__ double qsh[kMaxStagedHandles][9];
+    __shared__ __align__(16) float stage[kTetTile / 32][kStageWords];
     const int b = blockIdx.y;
-    if (!A.slot.active[b]) return;
+    if (!A.slot.active[b]) return;   // block-uniform
     const MeshDev& M = A.mesh;
     const int m = M.m, n = M.n;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k0 = k - lane;                         // the warp's first tet
+    const int nvalid = max(0, min(32, m - k0));      // tets of this warp
+    const double* xf = A.slot.xf + (size_t)b * M.H * 12;
+    const double(*qs)[9] = stage_pose(qsh, xf, M.H);
     double en[1] = {0.0};
+    double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6], sig[6];
+    double mu = 0.0, lam = 0.0, w = 0.0;
+    double* gs = reinterpret_cast<double*>(stage[warp]);   // [32][12] forces
     if (k < m) {
         const double* x = A.slot.x + (size_t)b * n * 3;
-        const double* xf = A.slot.xf + (size_t)b * M.H * 12;
-        double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6], sig[6];
         const int4 tv = M.tet[k];
         gather_x<float>(x, nullptr, 0.0, tv, xa);
         load_G(M.Dminv64, m, k, G);
-        tet_rotation(A, xf, k, xa, G, Q);
+        tet_rotation(A, xf, qs, k, xa, G, Q);
         stretch(xa, G, Q, F, S);
-        const double mu = M.mu[k], lam = M.lam[k], w = M.vol[k];
+        mu = M.mu[k];
+        lam = M.lam[k];
+        w = M.vol[k];
         en[0] = w * psi_sigma<MODEL>(S, mu, lam, sig);
-        // Lambda = Q sigma; forces f_a = W Lambda G_a
-        const double sm[3][3] = {{sig[0], sig[5], sig[4]}, {sig[5], sig[1], sig[3]}, {sig[4], sig[3], sig[2]}};
+        // forces f_a = W Lambda G_a, Lambda = Q sigma (a = 1..3), f_0 = -(f_1 + f_2 + f_3)
+        const double sw[3][3] = {{w * sig[0], w * sig[5], w * sig[4]},
+                                 {w * sig[5], w * sig[1], w * sig[3]},
+                                 {w * sig[4], w * sig[3], w * sig[2]}};
         double P[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
 #pragma unroll
-            for (int j = 0; j < 3; ++j) P[i][j] = w * (Q[i][0] * sm[0][j] + Q[i][1] * sm[1][j] + Q[i][2] * sm[2][j]);
-        double* ge = A.slot.ge + ((size_t)b * m + k) * 12;
+            for (int j = 0; j < 3; ++j) P[i][j] = Q[i][0] * sw[0][j] + Q[i][1] * sw[1][j] + Q[i][2] * sw[2][j];
+        double f0[3] = {0.0, 0.0, 0.0};
+        double* gl = gs + 12 * lane;
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
+        for (int a = 1; a < 4; ++a)
 #pragma unroll
-            for (int i = 0; i < 3; ++i) ge[3 * a + i] = P[i][0] * G[a][0] + P[i][1] * G[a][1] + P[i][2] * G[a][2];
-        KT* ke = (KT*)A.slot.Ke + ((size_t)b * m + k) * kKe;
-        if (!HESS) {
-        } else if (MODEL == 2) {
+            for (int i = 0; i < 3; ++i) {
+                const double f = P[i][0] * G[a][0] + P[i][1] * G[a][1] + P[i][2] * G[a][2];
+                gl[3 * a + i] = f;
+                f0[i] -= f;
+            }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gl[i] = f0[i];
+    }
+    __syncwarp();
+    {   // forces out: the warp's 32 contiguous 96-byte records
+        double* ge = A.slot.ge + ((size_t)b * m + k0) * 12;
+        for (int i = lane; i < 12 * nvalid; i += 32) ge[i] = gs[i];
+    }
+    __syncwarp();
+    if (HESS && k < m) {
+        KT* ke = sizeof(KT) == 4 ? reinterpret_cast<KT*>(stage[warp]) + kKe * lane
+                                 : (KT*)A.slot.Ke + ((size_t)b * m + k) * kKe;
+        // FP32 copies of the shape gradients and the rotation (the Hessian's precision)
+        KT Gk[4][3], Qk[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                Gk[r + 1][c] = sizeof(KT) == 4 ? (KT)M.Dminv32[(size_t)(3 * r + c) * m + k] : (KT)G[r + 1][c];
+                Qk[r][c] = (KT)Q[r][c];
+            }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Gk[0][c] = -(Gk[1][c] + Gk[2][c] + Gk[3][c]);
+        if (MODEL == 2) {
             bool fp64 = sizeof(KT) == 8;
             if (!fp64) {  // near-degenerate or inverted stretch: FP64 Hessian
-                const double J = S[0] * (S[1] * S[2] - S[3] * S[3]) + S[5] * (S[4] * S[3] - S[2] * S[5]) +
-                                 S[4] * (S[5] * S[3] - S[1] * S[4]);
-                fp64 = J < kFallbackJ;
+                const float s0 = (float)S[0], s1 = (float)S[1], s2 = (float)S[2];
+                const float s3 = (float)S[3], s4 = (float)S[4], s5 = (float)S[5];
+                const float J = s0 * (s1 * s2 - s3 * s3) + s5 * (s4 * s3 - s2 * s5) + s4 * (s5 * s3 - s1 * s4);
+                fp64 = J < (float)kFallbackJ;
             }
+            KT C[6][6];
             if (fp64) {
                 // the Hessian of a strongly strained tet in FP64 (its terms cancel);
                 // the SPD filter of the result in the kernel's precision (GB300 runs
                 // FP64 at a small fraction of FP32, and the filter needs no more)
-                double C[6][6];
-                snh_hessian<double>(S, mu, lam, C);
-                KT Ck[6][6];
+                double Cd[6][6];
+                snh_hessian<double>(S, mu, lam, Cd);
 #pragma unroll
                 for (int p = 0; p < 6; ++p)
 #pragma unroll
-                    for (int q = 0; q < 6; ++q) Ck[p][q] = (KT)C[p][q];
-                if (!chol_shifted_ok<KT>(Ck, (KT)(kSpdEps * mu))) filter_spd<KT>(Ck, (KT)(kSpdEps * mu));
-                blocks_generic<KT>(Ck, G, Q, w, ke);
+                    for (int q = 0; q < 6; ++q) C[p][q] = (KT)Cd[p][q];
             } else {
-                KT C[6][6];
                 snh_hessian<KT>(S, mu, lam, C);
-                if (!chol_shifted_ok<KT>(C, (KT)(kSpdEps * mu))) filter_spd<KT>(C, (KT)(kSpdEps * mu));
-                blocks_generic<KT>(C, G, Q, w, ke);
             }
+            if (!chol_shifted_ok<KT>(C, (KT)(kSpdEps * mu))) filter_spd<KT>(C, (KT)(kSpdEps * mu));
+            blocks_generic<KT>(C, Gk, Qk, (KT)w, ke);
         } else {
-            blocks_quadratic<KT>(G, Q, w, mu, MODEL == 1 ? lam : 0.0, ke);
+            blocks_quadratic<KT>(Gk, Qk, (KT)(w * mu), (KT)(w * (MODEL == 1 ? lam : 0.0)), ke);
         }
+    }
+    if (HESS && sizeof(KT) == 4) {   // element blocks out: 32 contiguous 312-byte records
+        __syncwarp();
+        const float2* src = reinterpret_cast<const float2*>(stage[warp]);
+        float2* dst = reinterpret_cast<float2*>((float*)A.slot.Ke + ((size_t)b * m + k0) * kKe);
+        for (int i = lane; i < (kKe / 2) * nvalid; i += 32) dst[i] = src[i];
     }
     if (k < n) {
         const double* xv = A.slot.x + ((size_t)b * n + k) * 3;
@@ -564,20 +641,22 @@ __global__ void __launch_bounds__(kTetTile, 4) k_element(ElemArgs A) {
 // Energy at x + alpha_b dx_b (line search trial, a6).
 template <typename T, int MODEL>
 __global__ void __launch_bounds__(kTetTile) k_energy_trial(ElemArgs A) {
+    __shared__ double qsh[kMaxStagedHandles][9];
     const int b = blockIdx.y;
-    if (!A.slot.active[b]) return;
+    if (!A.slot.active[b]) return;   // block-uniform
     const MeshDev& M = A.mesh;
     const int m = M.m, n = M.n;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const double* xf = A.slot.xf + (size_t)b * M.H * 12;
+    const double(*qs)[9] = stage_pose(qsh, xf, M.H);
     double en[1] = {0.0};
     if (k < m) {
         const double* x = A.slot.x + (size_t)b * n * 3;
         const T* dx = (const T*)A.slot.vec + (size_t)b * kVecStride * npad32(n) + kOffRec * npad32(n) + kRecDX;
-        const double* xf = A.slot.xf + (size_t)b * M.H * 12;
         double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6], sig[6];
         gather_x<T>(x, dx, A.slot.alpha[b], M.tet[k], xa, kRec);
         load_G(M.Dminv64, m, k, G);
-        tet_rotation(A, xf, k, xa, G, Q);
+        tet_rotation(A, xf, qs, k, xa, G, Q);
         stretch(xa, G, Q, F, S);
         en[0] = M.vol[k] * psi_sigma<MODEL>(S, M.mu[k], M.lam[k], sig);
     }
@@ -676,7 +755,7 @@ __global__ void k_elem_out(ElemArgs A, int b, double* __restrict__ s_out, double
     double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6], sig[6];
     gather_x<float>(x, nullptr, 0.0, M.tet[k], xa);
     load_G(M.Dminv64, M.m, k, G);
-    tet_rotation(A, xf, k, xa, G, Q);
+    tet_rotation(A, xf, nullptr, k, xa, G, Q);
     stretch(xa, G, Q, F, S);
     psi_sigma<MODEL>(S, M.mu[k], M.lam[k], sig);
     if (s_out)
@@ -700,7 +779,7 @@ __global__ void k_diag(ElemArgs A, int b, unsigned* __restrict__ out3) {
     double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6];
     gather_x<float>(x, nullptr, 0.0, M.tet[k], xa);
     load_G(M.Dminv64, M.m, k, G);
-    tet_rotation(A, xf, k, xa, G, Q);
+    tet_rotation(A, xf, nullptr, k, xa, G, Q);
     stretch(xa, G, Q, F, S);
     const double detF = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
                         F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +

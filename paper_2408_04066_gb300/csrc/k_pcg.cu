@@ -234,13 +234,14 @@ __device__ __forceinline__ void coeffs(const ProbScal* sc, double& a, double& b)
     b = sc->beta;
 }
 
-// problem of unit u: last descriptor whose unit_begin <= u
-template <typename T>
+// problem of unit u: last descriptor whose unit_begin (SpMV tiles) or
+// unit_begin_u (row-local kernels' tiles, ROWU) is <= u
+template <bool ROWU = false, typename T>
 __device__ __forceinline__ int unit_problem(const PcgDesc<T>* __restrict__ D, int n_probs, int u) {
     int lo = 0, hi = n_probs - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (D[mid].unit_begin <= u) lo = mid;
+        if ((ROWU ? D[mid].unit_begin_u : D[mid].unit_begin) <= u) lo = mid;
         else hi = mid - 1;
     }
     return lo;
@@ -319,9 +320,9 @@ template <typename T, int TILE>
 __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restrict__ D, int n_probs) {
     __shared__ float qs[4][9];
     const int u = blockIdx.x;   // prologue: descriptor and pose rotations (fixed during the solve)
-    const PcgDesc<T>& d = D[unit_problem(D, n_probs, u)];
+    const PcgDesc<T>& d = D[unit_problem<true>(D, n_probs, u)];
     ProbScal* sc = d.sc;
-    const int tile = u - d.unit_begin;
+    const int tile = u - d.unit_begin_u;
     const int row = tile * TILE + threadIdx.x;
     const bool coarse = d.coarse != 0;
     if (coarse) stage_rotations(qs, tile * TILE, d.agg_handle, d.xf, d.agg_shift, d.coarse_n / 6);
@@ -366,7 +367,7 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
     v[0] = warp_sum_partial(rz);
     v[1] = warp_sum_partial(rr2);
     double tot[2];
-    if (tile_commit<2>(v, d.part, tile, d.n_tiles, &sc->tk_b, 1, tot, true) && threadIdx.x == 0) {
+    if (tile_commit<2>(v, d.part, tile, d.n_tiles_u, &sc->tk_b, 1, tot, true) && threadIdx.x == 0) {
         if (!coarse) {
             const double rho_new = tot[0];
             sc->beta = sc->rho != 0.0 ? rho_new / sc->rho : 0.0;
@@ -523,10 +524,10 @@ __global__ void __launch_bounds__(TILE) k_pcg_correct(const PcgDesc<T>* __restri
     // prologue on data fixed during the solve (descriptor, rest offsets, pose
     // rotations), overlapping the previous kernel's drain
     const int u = blockIdx.x;
-    const PcgDesc<T>& d = D[unit_problem(D, n_probs, u)];
+    const PcgDesc<T>& d = D[unit_problem<true>(D, n_probs, u)];
     if (!d.coarse) return;
     ProbScal* sc = d.sc;
-    const int tile = u - d.unit_begin;
+    const int tile = u - d.unit_begin_u;
     const int row = tile * TILE + threadIdx.x;
     const int a0 = (tile * TILE) >> d.agg_shift;
     const int n_agg = d.coarse_n / 6;
@@ -581,7 +582,7 @@ __global__ void __launch_bounds__(TILE) k_pcg_correct(const PcgDesc<T>* __restri
     }
     double v[1] = {warp_sum_partial(rz)};
     double tot[1];
-    if (tile_commit<1>(v, d.part, tile, d.n_tiles, &sc->tk_c, 3, tot, true) && threadIdx.x == 0) {
+    if (tile_commit<1>(v, d.part, tile, d.n_tiles_u, &sc->tk_c, 3, tot, true) && threadIdx.x == 0) {
         const double rho_new = tot[0];
         if (rho_new > 0.0 && isfinite(rho_new)) {
             sc->beta = (sc->cinit || sc->rho == 0.0) ? 0.0 : rho_new / sc->rho;
@@ -598,8 +599,8 @@ __global__ void __launch_bounds__(TILE) k_pcg_correct(const PcgDesc<T>* __restri
 // Each launch may start while the previous kernel of the stream drains
 // (programmatic stream serialization); the kernels wait on it first thing.
 template <typename T, int TILE>
-cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units, int iters, const CoarseJob* jobs,
-                               int n_jobs, cudaStream_t s) {
+cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units, int n_units_u, int iters,
+                               const CoarseJob* jobs, int n_jobs, cudaStream_t s) {
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
@@ -610,6 +611,9 @@ cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units
     cfg.stream = s;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    cudaLaunchConfig_t cfg_u = cfg;   // row-local kernels: their own fixed tile
+    cfg_u.gridDim = dim3(n_units_u);
+    cfg_u.blockDim = dim3(kRowTileU);
     for (int i = 0; i < iters; ++i) {
         cudaError_t e;
         if (n_jobs > 0) {   // two-level: finish z of the current residual first
@@ -639,12 +643,12 @@ cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units
                                            descs, jobs[j].d0, jobs[j].nd);
                 if (e != cudaSuccess) return e;
             }
-            e = cudaLaunchKernelEx(&cfg, k_pcg_correct<T, TILE>, descs, n_probs);
+            e = cudaLaunchKernelEx(&cfg_u, k_pcg_correct<T, kRowTileU>, descs, n_probs);
             if (e != cudaSuccess) return e;
         }
         e = cudaLaunchKernelEx(&cfg, k_pcg_spmv<T, TILE>, descs, n_probs);
         if (e != cudaSuccess) return e;
-        e = cudaLaunchKernelEx(&cfg, k_pcg_update<T, TILE>, descs, n_probs);
+        e = cudaLaunchKernelEx(&cfg_u, k_pcg_update<T, kRowTileU>, descs, n_probs);
         if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
@@ -660,12 +664,12 @@ void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int m
 }
 
 template <typename T>
-cudaError_t launch_pcg_iters(const PcgDesc<T>* descs, int n_probs, int n_units, int tile_rows, int iters,
-                             const CoarseJob* jobs, int n_jobs, cudaStream_t s) {
+cudaError_t launch_pcg_iters(const PcgDesc<T>* descs, int n_probs, int n_units, int n_units_u, int tile_rows,
+                             int iters, const CoarseJob* jobs, int n_jobs, cudaStream_t s) {
     switch (tile_rows) {
-        case 64: return launch_pcg_iters_t<T, 64>(descs, n_probs, n_units, iters, jobs, n_jobs, s);
-        case 128: return launch_pcg_iters_t<T, 128>(descs, n_probs, n_units, iters, jobs, n_jobs, s);
-        case 256: return launch_pcg_iters_t<T, 256>(descs, n_probs, n_units, iters, jobs, n_jobs, s);
+        case 64: return launch_pcg_iters_t<T, 64>(descs, n_probs, n_units, n_units_u, iters, jobs, n_jobs, s);
+        case 128: return launch_pcg_iters_t<T, 128>(descs, n_probs, n_units, n_units_u, iters, jobs, n_jobs, s);
+        case 256: return launch_pcg_iters_t<T, 256>(descs, n_probs, n_units, n_units_u, iters, jobs, n_jobs, s);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -688,9 +692,9 @@ cudaError_t launch_coarse_only(const PcgDesc<float>* descs, int n_probs, const C
                               job->nd);
 }
 
-template cudaError_t launch_pcg_iters<float>(const PcgDesc<float>*, int, int, int, int, const CoarseJob*, int,
-                                             cudaStream_t);
-template cudaError_t launch_pcg_iters<double>(const PcgDesc<double>*, int, int, int, int, const CoarseJob*, int,
-                                              cudaStream_t);
+template cudaError_t launch_pcg_iters<float>(const PcgDesc<float>*, int, int, int, int, int, const CoarseJob*,
+                                             int, cudaStream_t);
+template cudaError_t launch_pcg_iters<double>(const PcgDesc<double>*, int, int, int, int, int, const CoarseJob*,
+                                              int, cudaStream_t);
 
 }  // namespace mfem

@@ -17,8 +17,6 @@ namespace mfem {
 
 namespace {
 
-__device__ __forceinline__ int pair_index(int a, int b) { return a * 4 - (a * (a - 1)) / 2 + (b - a); }
-
 // Gradient of row `row` of problem b: the element forces of its tets in fixed
 // incidence order, the external force, and the pin term (zero under
 // elimination, k_s (x - x_p) under the penalty form).  Writes g, returns |g|^2.
@@ -86,12 +84,18 @@ __global__ void __launch_bounds__(kRowTile) k_assemble_slots(ElemArgs A) {
     for (int ci = c0; ci < c1; ++ci) {
         const int code = __ldg(M.contrib + ci);
         const int t = code >> 4, ea = (code >> 2) & 3, eb = code & 3;
-        if (ea <= eb) {
-            const KT* blk = Ke + (size_t)t * kKe + 9 * pair_index(ea, eb);
+        if (ea == eb) {   // symmetric diagonal block: six stored entries
+            const KT* blk = Ke + (size_t)t * kKe + ke_offset(ea, ea);
+            const KT xx = blk[0], yy = blk[1], zz = blk[2], yz = blk[3], xz = blk[4], xy = blk[5];
+            acc[0] += xx; acc[1] += xy; acc[2] += xz;
+            acc[3] += xy; acc[4] += yy; acc[5] += yz;
+            acc[6] += xz; acc[7] += yz; acc[8] += zz;
+        } else if (ea < eb) {
+            const KT* blk = Ke + (size_t)t * kKe + ke_offset(ea, eb);
 #pragma unroll
             for (int e = 0; e < 9; ++e) acc[e] += blk[e];
         } else {
-            const KT* blk = Ke + (size_t)t * kKe + 9 * pair_index(eb, ea);
+            const KT* blk = Ke + (size_t)t * kKe + ke_offset(eb, ea);
 #pragma unroll
             for (int i = 0; i < 3; ++i)
 #pragma unroll

@@ -50,6 +50,7 @@ struct SlotDev {
     double* xpred = nullptr;    // [B][n][3] x after the predictor step of the last solve (WARM only)
     double* dcorr = nullptr;    // [B][n][3] last solve's solution minus xpred (WARM only)
     double* x = nullptr;     // [B][n][3]
+    double* xprev = nullptr; // [B][n][3] x before a speculative full Newton step (line-searched models)
     double* xp = nullptr;    // [B][n][3] pin targets (pinned rows only)
     double* g = nullptr;     // [B][n][3] masked gradient
     double* ge = nullptr;    // [B][m][12] element forces
@@ -137,9 +138,11 @@ struct CoarseJob {
     const void* key;            // the mesh (context) the job belongs to
     int N, d0, nd, agg_units;   // agg_units: 64-row units per aggregate
 };
+// n_units: SpMV tiles (tile_rows rows) over all problems; n_units_u: the
+// update and correction kernels' tiles (kRowTileU rows).
 template <typename T>
-cudaError_t launch_pcg_iters(const PcgDesc<T>* descs_dev, int n_probs, int n_units, int tile_rows, int iters,
-                             const CoarseJob* jobs, int n_jobs, cudaStream_t s);
+cudaError_t launch_pcg_iters(const PcgDesc<T>* descs_dev, int n_probs, int n_units, int n_units_u, int tile_rows,
+                             int iters, const CoarseJob* jobs, int n_jobs, cudaStream_t s);
 bool pcg_tile_supported(int tile_rows);
 
 // Coarse space set-up: A_c = P^T K P of the assembled matrix `val` (problem 0 of

@@ -1,20 +1,29 @@
 // Serving: continuous batching of pose solves over resident meshes.
 //
 // A worker thread owns the GPU work.  Between Newton steps it admits queued
-// requests into free slots (per-mesh slot sets sized by the device-memory
-// budget at mfem_server_add), then advances every admitted request of every
-// mesh by one Newton step together -- the element and assembly kernels per
-// mesh and one sequence of PCG iteration launches for all of them -- and hands finished
+// requests, then advances every admitted request of every mesh by one Newton
+// step together -- the element and assembly kernels per slot pool and one
+// sequence of PCG iteration launches for all of them -- and hands finished
 // requests back.  A request's arithmetic never depends on the others in the
 // step (per-problem deterministic reductions), so its result equals the same
 // pose solved alone.
+//
+// Admission by device memory: a mesh's requests run in slot pools -- its own
+// context (the first pool, made when the mesh is added) and further contexts
+// that share the mesh's device data but own request slots of their own.  A
+// request that finds every slot of its mesh busy gets a new pool when the
+// device-memory budget has room for it (pools idle for a while are released
+// first when it does not), else it waits in the queue; pools that stay idle
+// are released, so memory flows to the meshes that have requests.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <condition_variable>
 #include <cstring>
 #include <deque>
+#include <memory>
 #include <mutex>
 #include <thread>
 #include <unordered_map>
@@ -25,6 +34,9 @@
 using namespace mfem;
 
 namespace {
+
+constexpr int kPoolSlots = 8;           // request slots per pool
+constexpr double kPoolIdleRelease = 0.5;   // seconds a pool other than the first stays idle before release
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -40,16 +52,24 @@ struct Request {
     bool done = false;
 };
 
-struct MeshEntry {
-    mfem_ctx* ctx = nullptr;
+struct Pool {
+    mfem_ctx* ctx = nullptr;   // the mesh's context (first pool) or a slot clone of it
     int cap = 0;
+    size_t bytes = 0;          // charged to the budget
     std::vector<ProbHost> ph;
     std::vector<uint64_t> slot_req;  // 0 = free
+    int busy = 0;
+    double idle_since = 0.0;
+};
+
+struct MeshEntry {
+    std::vector<std::unique_ptr<Pool>> pools;   // pools[0] is the context handed to mfem_server_add
     // WARM meshes: the mesh's most recent solution (x [n][3], its predictor
     // result [n][3] and its pose [H][12]), copied into the slot of each admitted
     // request, so every request continues from the latest frame solved
     double* bank = nullptr;
     int bank_state = 0;   // 0 none, 1 x and pose, 2 also the predictor result
+    mfem_ctx* owner() const { return pools[0]->ctx; }
 };
 
 }  // namespace
@@ -63,7 +83,7 @@ struct mfem_server {
     size_t budget = 0, used = 0;
     int max_slots = 0, in_use = 0, peak = 0;
     uint64_t next_ticket = 1;
-    int64_t completed = 0, steps = 0, pcg_launches = 0;
+    int64_t completed = 0, steps = 0, pcg_launches = 0, pools_added = 0, pools_released = 0;
     bool stop = false;
     bool started = false;
     int device = 0;
@@ -73,55 +93,110 @@ struct mfem_server {
 
     void run();
     void fail_all_busy(int status);
+    bool grow(MeshEntry& me);           // under mu
+    bool release_idle(double older_than, const MeshEntry* keep);   // under mu
 };
+
+// A new slot pool for `me` if the budget has room (after releasing idle pools
+// of other meshes when it has not).  Called under mu by the worker.
+bool mfem_server::grow(MeshEntry& me) {
+    const int cap = std::min(kPoolSlots, max_slots - in_use);
+    if (cap < 1) return false;
+    mfem_ctx* owner = me.owner();
+    const size_t bytes = slot_bytes_for(owner, cap);
+    if (budget && used + bytes > budget && !(release_idle(0.0, &me) && used + bytes <= budget)) return false;
+    mfem_status st;
+    mfem_ctx* c = ctx_slot_clone(owner, cap, stream, &st);
+    if (!c) return false;
+    auto p = std::make_unique<Pool>();
+    p->ctx = c;
+    p->cap = cap;
+    p->bytes = bytes;
+    p->ph.assign(cap, ProbHost());
+    p->slot_req.assign(cap, 0);
+    p->idle_since = now_s();
+    me.pools.push_back(std::move(p));
+    used += bytes;
+    pools_added++;
+    return true;
+}
+
+// Release pools (never a mesh's first) that have been idle at least
+// `older_than` seconds; `keep`'s pools are spared.  Returns true if any was.
+bool mfem_server::release_idle(double older_than, const MeshEntry* keep) {
+    const double t = now_s();
+    bool any = false;
+    for (auto& me : meshes) {
+        if (&me == keep) continue;
+        for (size_t i = me.pools.size(); i-- > 1;) {
+            Pool& p = *me.pools[i];
+            if (p.busy || t - p.idle_since < older_than) continue;
+            mfem_destroy(p.ctx);
+            used -= p.bytes;
+            me.pools.erase(me.pools.begin() + i);
+            pools_released++;
+            any = true;
+        }
+    }
+    return any;
+}
 
 void mfem_server::fail_all_busy(int status) {
     std::lock_guard<std::mutex> lk(mu);
     for (auto& me : meshes)
-        for (int b = 0; b < me.cap; ++b)
-            if (me.slot_req[b]) {
-                auto it = reqs.find(me.slot_req[b]);
-                if (it != reqs.end()) {
-                    it->second.status = status;
-                    it->second.done = true;
-                    it->second.t_done = now_s();
+        for (auto& pp : me.pools) {
+            Pool& p = *pp;
+            for (int b = 0; b < p.cap; ++b)
+                if (p.slot_req[b]) {
+                    auto it = reqs.find(p.slot_req[b]);
+                    if (it != reqs.end()) {
+                        it->second.status = status;
+                        it->second.done = true;
+                        it->second.t_done = now_s();
+                    }
+                    p.slot_req[b] = 0;
+                    p.ph[b] = ProbHost();
+                    in_use--;
                 }
-                me.slot_req[b] = 0;
-                me.ph[b] = ProbHost();
-                in_use--;
-            }
+            p.busy = 0;
+            p.idle_since = now_s();
+        }
     cv_done.notify_all();
 }
 
 void mfem_server::run() {
     cudaSetDevice(device);
     for (;;) {
-        std::vector<std::pair<int, int>> admitted;
-        // the meshes known at this step, taken under the lock: mfem_server_add
-        // may append to the deque meanwhile (element addresses stay valid)
-        std::vector<MeshEntry*> ms;
+        std::vector<Pool*> ps;   // every pool, taken under the lock
         {
             std::unique_lock<std::mutex> lk(mu);
             cv_work.wait(lk, [&] { return stop || !queue.empty() || in_use > 0; });
             if (stop && in_use == 0) break;
-            for (auto& m : meshes) ms.push_back(&m);
-            // admission: FIFO scan, a full mesh does not block other meshes
+            // admission: FIFO scan; a mesh that cannot take a request does not block others
             for (auto it = queue.begin(); it != queue.end() && in_use < max_slots;) {
                 Request& r = reqs[*it];
                 MeshEntry& me = meshes[r.mesh];
+                Pool* pool = nullptr;
                 int slot = -1;
-                for (int b = 0; b < me.cap; ++b)
-                    if (!me.slot_req[b]) { slot = b; break; }
-                if (slot < 0) { ++it; continue; }
-                me.slot_req[slot] = *it;
-                me.ph[slot] = ProbHost();
-                me.ph[slot].need_init = 1;
+                for (auto& pp : me.pools) {
+                    for (int b = 0; b < pp->cap && slot < 0; ++b)
+                        if (!pp->slot_req[b]) slot = b;
+                    if (slot >= 0) { pool = pp.get(); break; }
+                }
+                if (!pool && grow(me)) {
+                    pool = me.pools.back().get();
+                    slot = 0;
+                }
+                if (!pool) { ++it; continue; }
+                mfem_ctx* c = pool->ctx;
+                pool->slot_req[slot] = *it;
+                pool->ph[slot] = ProbHost();
+                pool->ph[slot].need_init = 1;
+                pool->busy++;
                 in_use++;
                 peak = std::max(peak, in_use);
-                admitted.emplace_back(r.mesh, slot);
-                const size_t H = me.ctx->plan.H;
+                const size_t H = c->plan.H;
                 if (me.bank_state > 0) {
-                    mfem_ctx* c = me.ctx;
                     const size_t n3 = (size_t)c->plan.n * 3;
                     cudaMemcpyAsync(c->slot.x + slot * n3, me.bank, n3 * sizeof(double), cudaMemcpyDeviceToDevice,
                                     stream);
@@ -133,21 +208,20 @@ void mfem_server::run() {
                     c->warm_kind[slot] = 1;
                     c->xpred_valid[slot] = me.bank_state == 2;
                 }
-                cudaMemcpyAsync(me.ctx->slot.xf + (size_t)slot * H * 12, r.xf.data(), H * 12 * sizeof(double),
+                cudaMemcpyAsync(c->slot.xf + (size_t)slot * H * 12, r.xf.data(), H * 12 * sizeof(double),
                                 cudaMemcpyHostToDevice, stream);
                 it = queue.erase(it);
             }
+            release_idle(kPoolIdleRelease, nullptr);
+            for (auto& m : meshes)
+                for (auto& pp : m.pools) ps.push_back(pp.get());
         }
         std::vector<Group> gs;
-        for (MeshEntry* mp : ms) {
-            MeshEntry& me = *mp;
-            bool busy = false;
-            for (int b = 0; b < me.cap; ++b) busy |= me.slot_req[b] != 0;
-            if (busy) {
-                me.ctx->prof.reset();
-                gs.push_back(Group{me.ctx, me.cap, me.ph.data()});
+        for (Pool* p : ps)
+            if (p->busy) {
+                p->ctx->prof.reset();
+                gs.push_back(Group{p->ctx, p->cap, p->ph.data()});
             }
-        }
         if (gs.empty()) continue;
         mfem_status st = advance(gs);
         {
@@ -161,43 +235,49 @@ void mfem_server::run() {
             continue;
         }
         // completion
-        for (MeshEntry* mp : ms) {
-            MeshEntry& me = *mp;
-            for (int b = 0; b < me.cap; ++b) {
-                if (!me.slot_req[b] || me.ph[b].active || me.ph[b].need_init) continue;
-                mfem_ctx* c = me.ctx;
+        for (Pool* pp : ps) {
+            Pool& pool = *pp;
+            if (!pool.busy) continue;
+            for (int b = 0; b < pool.cap; ++b) {
+                if (!pool.slot_req[b] || pool.ph[b].active || pool.ph[b].need_init) continue;
+                mfem_ctx* c = pool.ctx;
                 ElemArgs a = elem_args(c);
                 const size_t n = c->plan.n;
                 a.slot.x += (size_t)b * n * 3;
                 double* out = nullptr;
+                MeshEntry* me = nullptr;
                 {
                     std::lock_guard<std::mutex> lk(mu);
-                    out = reqs[me.slot_req[b]].out;
+                    const Request& r = reqs[pool.slot_req[b]];
+                    out = r.out;
+                    me = &meshes[r.mesh];
                 }
                 launch_unpermute(a, 1, c->slot.outbuf, stream);
                 cudaMemcpyAsync(out, c->slot.outbuf, n * 3 * sizeof(double), cudaMemcpyDeviceToHost, stream);
                 cudaError_t e = cudaStreamSynchronize(stream);
                 std::lock_guard<std::mutex> lk(mu);
-                Request& r = reqs[me.slot_req[b]];
-                fill_stats(c, me.ph[b], &r.st);
-                r.status = e == cudaSuccess ? me.ph[b].status : MFEM_ECUDA;
+                Request& r = reqs[pool.slot_req[b]];
+                fill_stats(c, pool.ph[b], &r.st);
+                r.status = e == cudaSuccess ? pool.ph[b].status : MFEM_ECUDA;
                 c->warm_kind[b] = 1;   // a WARM-start mesh continues from this solution
                 const size_t H = c->plan.H;
                 cudaMemcpyAsync(c->slot.xf_prev + (size_t)b * H * 12, c->slot.xf + (size_t)b * H * 12,
                                 H * 12 * sizeof(double), cudaMemcpyDeviceToDevice, stream);
-                if (me.bank && me.ph[b].status == MFEM_OK) {   // the mesh's latest frame
-                    cudaMemcpyAsync(me.bank, c->slot.x + b * n * 3, n * 3 * sizeof(double), cudaMemcpyDeviceToDevice,
+                if (me->bank && pool.ph[b].status == MFEM_OK) {   // the mesh's latest frame
+                    cudaMemcpyAsync(me->bank, c->slot.x + b * n * 3, n * 3 * sizeof(double), cudaMemcpyDeviceToDevice,
                                     stream);
                     if (c->xpred_valid[b])
-                        cudaMemcpyAsync(me.bank + n * 3, c->slot.xpred + b * n * 3, n * 3 * sizeof(double),
+                        cudaMemcpyAsync(me->bank + n * 3, c->slot.xpred + b * n * 3, n * 3 * sizeof(double),
                                         cudaMemcpyDeviceToDevice, stream);
-                    cudaMemcpyAsync(me.bank + 2 * n * 3, c->slot.xf + (size_t)b * H * 12, H * 12 * sizeof(double),
+                    cudaMemcpyAsync(me->bank + 2 * n * 3, c->slot.xf + (size_t)b * H * 12, H * 12 * sizeof(double),
                                     cudaMemcpyDeviceToDevice, stream);
-                    me.bank_state = c->xpred_valid[b] ? 2 : 1;
+                    me->bank_state = c->xpred_valid[b] ? 2 : 1;
                 }
                 r.done = true;
                 r.t_done = now_s();
-                me.slot_req[b] = 0;
+                pool.slot_req[b] = 0;
+                pool.busy--;
+                if (!pool.busy) pool.idle_since = r.t_done;
                 in_use--;
                 completed++;
                 cv_done.notify_all();
@@ -229,20 +309,20 @@ mfem_status mfem_server_add(mfem_server* s, mfem_ctx* c, int32_t* mesh_id) {
     if (!s || !c || !mesh_id) return ctx_fail(nullptr, MFEM_EINVAL, "null argument");
     std::lock_guard<std::mutex> lk(s->mu);
     if (c->owned_by_server) return ctx_fail(c, MFEM_EINVAL, "context already belongs to a server");
+    // the mesh's first slot pool: its own context, kPoolSlots slots or what the budget holds
     const size_t per = slot_bytes_for(c, 1);
-    int cap = s->max_slots;
+    const size_t bank_bytes = c->opt.init == MFEM_INIT_WARM
+                                  ? sizeof(double) * ((size_t)c->plan.n * 6 + (size_t)c->plan.H * 12) : 0;
+    int cap = std::min(s->max_slots, kPoolSlots);
     if (s->budget) {
-        size_t left = s->budget > s->used ? s->budget - s->used : 0;
+        size_t left = s->budget > s->used + bank_bytes ? s->budget - s->used - bank_bytes : 0;
         cap = (int)std::min<size_t>((size_t)cap, left / per);
         if (cap < 1) return ctx_fail(c, MFEM_ENOMEM, "one request slot of this mesh exceeds the server budget");
     }
     MeshEntry me;
-    me.ctx = c;
-    me.cap = cap;
     // everything that can fail comes before the context is changed, so a
     // refused mesh is left as the caller handed it over
-    if (c->opt.init == MFEM_INIT_WARM &&
-        cudaMalloc((void**)&me.bank, sizeof(double) * ((size_t)c->plan.n * 6 + (size_t)c->plan.H * 12)) != cudaSuccess)
+    if (bank_bytes && cudaMalloc((void**)&me.bank, bank_bytes) != cudaSuccess)
         return ctx_fail(c, MFEM_ENOMEM, "warm-start bank");
     mfem_status st = ensure_slots(c, cap);
     if (st != MFEM_OK) {
@@ -252,11 +332,17 @@ mfem_status mfem_server_add(mfem_server* s, mfem_ctx* c, int32_t* mesh_id) {
     cudaStreamSynchronize(c->stream);
     c->stream = s->stream;
     if (c->tile_rows == 0) c->tile_rows = 256;   // one tile for every mesh in a shared launch
-    if (!s->meshes.empty()) c->tile_rows = s->meshes[0].ctx->tile_rows;
+    if (!s->meshes.empty()) c->tile_rows = s->meshes[0].owner()->tile_rows;
     c->owned_by_server = true;
-    me.ph.assign(cap, ProbHost());
-    me.slot_req.assign(cap, 0);
-    s->used += per * cap;
+    auto p = std::make_unique<Pool>();
+    p->ctx = c;
+    p->cap = cap;
+    p->bytes = per * cap + bank_bytes;
+    p->ph.assign(cap, ProbHost());
+    p->slot_req.assign(cap, 0);
+    p->idle_since = now_s();
+    me.pools.push_back(std::move(p));
+    s->used += per * cap + bank_bytes;
     s->meshes.push_back(std::move(me));
     *mesh_id = (int32_t)s->meshes.size() - 1;
     return MFEM_OK;
@@ -266,7 +352,7 @@ mfem_status mfem_server_submit(mfem_server* s, int32_t mesh_id, const double* xf
     if (!s || !xf || !out || !ticket) return ctx_fail(nullptr, MFEM_EINVAL, "null argument");
     std::lock_guard<std::mutex> lk(s->mu);
     if (mesh_id < 0 || mesh_id >= (int)s->meshes.size()) return ctx_fail(nullptr, MFEM_EINVAL, "bad mesh id");
-    mfem_ctx* c = s->meshes[mesh_id].ctx;
+    mfem_ctx* c = s->meshes[mesh_id].owner();
     const int H = c->plan.H;
     for (int i = 0; i < 12 * H; ++i)
         if (!std::isfinite(xf[i])) return ctx_fail(nullptr, MFEM_EINVAL, "non-finite handle transform");
@@ -313,13 +399,17 @@ mfem_status mfem_server_wait(mfem_server* s, uint64_t ticket, int32_t timeout_ms
 }
 
 mfem_status mfem_server_counters(mfem_server* s, int64_t* completed, int64_t* steps, int64_t* pcg_launches,
-                                 int32_t* peak_slots) {
+                                 int32_t* peak_slots, int64_t* pools_added, int64_t* pools_released,
+                                 int64_t* device_bytes) {
     if (!s) return ctx_fail(nullptr, MFEM_EINVAL, "null server");
     std::lock_guard<std::mutex> lk(s->mu);
     if (completed) *completed = s->completed;
     if (steps) *steps = s->steps;
     if (pcg_launches) *pcg_launches = s->pcg_launches;
     if (peak_slots) *peak_slots = s->peak;
+    if (pools_added) *pools_added = s->pools_added;
+    if (pools_released) *pools_released = s->pools_released;
+    if (device_bytes) *device_bytes = (int64_t)s->used;
     return MFEM_OK;
 }
 
@@ -334,9 +424,11 @@ void mfem_server_destroy(mfem_server* s) {
     if (s->worker.joinable()) s->worker.join();
     for (auto& me : s->meshes) {
         if (me.bank) cudaFree(me.bank);
-        me.ctx->owned_by_server = false;
-        me.ctx->stream = me.ctx->own_stream;
-        mfem_destroy(me.ctx);
+        for (size_t i = me.pools.size(); i-- > 1;) mfem_destroy(me.pools[i]->ctx);   // slot pools first
+        mfem_ctx* c = me.owner();
+        c->owned_by_server = false;
+        c->stream = c->own_stream;
+        mfem_destroy(c);
     }
     if (s->stream) cudaStreamDestroy(s->stream);
     delete s;

@@ -108,7 +108,8 @@ _SIGS = [
     ("mfem_server_wait", C.c_int32, [C.c_void_p, C.c_uint64, C.c_int32, C.POINTER(Stats),
                                      C.POINTER(C.c_double)]),
     ("mfem_server_counters", C.c_int32, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
-                                         C.POINTER(C.c_int64), _ip]),
+                                         C.POINTER(C.c_int64), _ip, C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                         C.POINTER(C.c_int64)]),
     ("mfem_server_destroy", None, [C.c_void_p]),
 ]
 
@@ -456,10 +457,12 @@ class Server:
         return out, st.as_dict(), lat.value
 
     def counters(self):
-        a, b, c = C.c_int64(), C.c_int64(), C.c_int64()
+        a, b, c, e, f, g = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64(), C.c_int64()
         d = C.c_int32()
-        _check(self._lib.mfem_server_counters(self._srv, C.byref(a), C.byref(b), C.byref(c), C.byref(d)))
-        return dict(completed=a.value, steps=b.value, pcg_launches=c.value, peak_slots=d.value)
+        _check(self._lib.mfem_server_counters(self._srv, C.byref(a), C.byref(b), C.byref(c), C.byref(d), C.byref(e),
+                                              C.byref(f), C.byref(g)))
+        return dict(completed=a.value, steps=b.value, pcg_launches=c.value, peak_slots=d.value,
+                    pools_added=e.value, pools_released=f.value, device_bytes=g.value)
 
     def close(self):
         if getattr(self, "_srv", None):

@@ -97,3 +97,37 @@ def test_served_animation_continues_from_the_latest_frame(mfem):
             cold_it.append(sc["newton_iters"])
     assert sum(warm_it) < sum(cold_it), (warm_it, cold_it)
     srv.close()
+
+
+def test_admission_by_device_memory_grows_and_releases_slot_pools(mfem):
+    """A mesh starts with one pool of 8 request slots; a burst of requests gets
+    further pools (sharing the mesh's device data) while the budget has room,
+    the rest wait in the queue; every result equals the pose solved alone; pools
+    idle for half a second are released and their memory returns to the budget."""
+    import time
+    cfg = dict(figure_config(3000, seeds=range(20)), model="snh")
+    opts = dict(precision="mixed", tile_rows=128)
+    alone = mfem.Context.from_config(cfg, **opts)
+    ref = [alone.solve_batch(cfg["xfs"][i:i + 1])[0][0] for i in range(20)]
+    probe = mfem.Server(max_slots=64)
+    probe.add(mfem.Context.from_config(cfg, **opts))
+    one_pool = probe.counters()["device_bytes"]           # the first pool: 8 slots
+    probe.close()
+    budget = int(2.6 * one_pool)                           # room for two more pools of 8 slots at most
+    srv = mfem.Server(device_mem_budget=budget, max_slots=64)
+    mid = srv.add(mfem.Context.from_config(cfg, **opts))
+    tickets = [srv.submit(mid, cfg["xfs"][i]) for i in range(20)]
+    for i, t in enumerate(tickets):
+        out, st, _ = srv.wait(t, timeout_ms=120000)
+        assert st["converged"] == 1
+        assert np.array_equal(out, ref[i]), i
+    c = srv.counters()
+    assert c["completed"] == 20 and c["pools_added"] >= 1
+    assert 8 < c["peak_slots"] <= 24 and c["device_bytes"] <= budget
+    time.sleep(0.7)
+    out, st, _ = srv.wait(srv.submit(mid, cfg["xfs"][3]), timeout_ms=120000)   # wakes the worker: idle pools go
+    assert np.array_equal(out, ref[3])
+    c2 = srv.counters()
+    assert c2["pools_released"] >= 1 and c2["device_bytes"] < c["device_bytes"]
+    srv.close()
+    alone.close()
