@@ -730,6 +730,27 @@ def run_serve(args, dist):
         for t in [submit(mi), submit(mi)]:
             srv.wait(t)
 
+    # per-mesh cost: each mesh alone, 24 consecutive frames with 8 in flight
+    # (requests of one mesh completed per second on the whole GPU); the mix's
+    # ceiling when a quarter of the requests go to each mesh is their harmonic
+    # mean
+    alone = []
+    for mi in range(len(specs)):
+        t0 = time.perf_counter()
+        pending = [submit(mi) for _ in range(8)]
+        done, lats, its = 0, [], []
+        while pending:
+            _, st, l_s = srv.wait(pending.pop(0))
+            lats.append(1e3 * l_s)
+            its.append(st["newton_iters"])
+            done += 1
+            if done + len(pending) < 24:
+                pending.append(submit(mi))
+        thr = done / (time.perf_counter() - t0)
+        alone.append(dict(sizes[mi], requests_per_s=thr, ms_per_request=1e3 / thr,
+                          newton_iters_mean=statistics.mean(its)))
+    ceiling = len(specs) / sum(1.0 / a["requests_per_s"] for a in alone)
+
     def phase(rate, seconds, seed):
         """Poisson arrivals at `rate` for `seconds`; returns per-request
         (mesh, latency s, newton iters, converged) and the window (s)."""
@@ -812,6 +833,7 @@ def run_serve(args, dist):
                            "note": "per request (submit to result in host memory) at 70% of the measured "
                                    "capacity; the offered-load phase is under `offered_load`"},
             "offered_load": s1, "at_70pct_capacity": s2,
+            "per_mesh_alone": alone, "mix_ceiling_per_s": ceiling,
             "server": {"scheduling_rounds": c1["steps"] - c0["steps"],
                        "pcg_launches": c1["pcg_launches"] - c0["pcg_launches"], "peak_slots": c1["peak_slots"],
                        "pools_added": c1["pools_added"], "pools_released": c1["pools_released"],
@@ -834,7 +856,13 @@ def run_large(args, dist):
     dev = torch.device("cuda", dist.local)
     nb = args.batch
     cfg = character_config(2_000_000, 40, seeds=range(dist.rank * nb, dist.rank * nb + nb))
+    t_plan = time.perf_counter()
+    mfem.plan(cfg["X"], cfg["T"], cfg["joints"], cfg["parent"], cluster_rule=cfg["cluster_rule"],
+              pin_radius=cfg.get("pin_radius", 0.0))
+    t_plan = time.perf_counter() - t_plan          # host clustering and pins (mfem_plan)
+    t_create = time.perf_counter()
     ctx = mfem.Context.from_config(cfg, precision="mixed", max_batch=nb, newton_tol=1e-6)
+    t_create = time.perf_counter() - t_create      # mfem_create: planning, layout, upload, coarse set-up
     stream = torch.cuda.Stream(dev)      # a created stream (CUDA graphs cannot capture the legacy one)
     torch.cuda.set_stream(stream)
     ctx.set_stream(stream.cuda_stream)
@@ -878,7 +906,8 @@ def run_large(args, dist):
             "config": {"workload": f"character{info['m']}-h40-snh-batch{nb}", "tets": info["m"],
                        "verts": info["n"], "handles": info["n_handles"], "pins": info["n_pins"],
                        "batch_poses": nb, "precision": "mixed", "newton_tol": 1e-6,
-                       "device_bytes": info["device_bytes"], "parallelism": f"replicas x{dist.world}"},
+                       "device_bytes": info["device_bytes"], "parallelism": f"replicas x{dist.world}",
+                       "host_plan_s": t_plan, "create_s": t_create},
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
                            "note": "per batch step"},
             "newton_iters_mean": statistics.mean(s["newton_iters"] for s in stats),

@@ -358,7 +358,7 @@ const char* mfem_last_error(const mfem_ctx* ctx);
  * request slots; a request that finds every slot of its mesh busy gets a new
  * pool of up to 8 slots (sharing the mesh's device data) when the budget has
  * room for it -- pools of other meshes idle at that moment are released to make
- * room -- and otherwise waits in the queue; pools idle for 0.5 s are
+ * room -- and otherwise waits in the queue; pools idle for 2 s are
  * released. */
 mfem_status mfem_server_create(size_t device_mem_budget, int32_t max_slots, mfem_server** out);
 

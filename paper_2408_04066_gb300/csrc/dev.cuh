@@ -29,13 +29,15 @@ __host__ __device__ __forceinline__ int ke_offset(int a, int b) {   // a <= b
 }
 
 // Per-problem PCG vector area, in elements of the PCG type, rows padded to 32:
-// two ping-pong records zp[n][8] = (z.xyz, 0, p.xyz, 0) so a neighbour's z and
-// previous p come from one 32-byte (FP32) record, then the row record
-// rec[n][12] = (dx.xyz, 0, r.xyz, 0, q.xyz, 0), three aligned 16-byte vectors.
+// the neighbour record nb[n][4] = (u.xyz, 0) -- the preconditioned residual,
+// the one vector the SpMV gathers from neighbours (16 bytes in FP32) -- then
+// the row record rec[n][24] = (dx, r, p, s, w, zb), six aligned 4-element
+// groups: the Newton increment, the residual, the search direction, s = K p,
+// w = K u, and the block-Jacobi part of u.
 constexpr int kVecStride = 28;                 // times npad32(n)
-constexpr int kOffZP0 = 0, kOffZP1 = 8, kOffRec = 16;
-constexpr int kRec = 12;
-constexpr int kRecDX = 0, kRecR = 4, kRecQ = 8;
+constexpr int kOffNB = 0, kOffRec = 4;
+constexpr int kRec = 24;
+constexpr int kRecDX = 0, kRecR = 4, kRecP = 8, kRecS = 12, kRecW = 16, kRecZB = 20;
 __host__ __device__ __forceinline__ size_t npad32(int n) { return ((size_t)n + 31) & ~(size_t)31; }
 
 // Problem states (PCG)
@@ -43,13 +45,13 @@ enum : int { kIdle = 0, kActive = 1, kConverged = 2, kMaxIter = 3 };
 
 // Per-problem scalars.  Tickets are reset to 0 by the tile that completes them.
 struct ProbScal {
-    double rho, alpha, beta, rr0, rr, tol2;
+    double rho, alpha, beta, rr0, rr, tol2;   // rho: the last (r, u); alpha, beta: the next step's
     double gnorm2, energy, slope, energy_trial;
     double alpha_ls, pad0;
     float alpha_f, beta_f;   // FP32 copies of alpha and beta for the FP32 kernels
     int iter, state, maxit, active;
     unsigned tk_a, tk_b, tk_g, tk_e, tk_s, tk_init, tk_c;
-    int cinit;   // two-level: the next correction is the first of this solve (beta = 0)
+    int first;   // the next reduction is the solve's first (beta = 0, alpha = (r,u) / (w,u))
 };
 
 // Two-level preconditioner constants: restriction partials are formed per unit
@@ -68,9 +70,8 @@ struct PcgDesc {
     const int* col;        // [slots] column block or -1
     const T* val;          // [slots/32][9][32]
     const T* dinv;         // [n][9] inverse diagonal blocks
-    T* zp0;                // [n][8] (z, p) records, read at even iterations
-    T* zp1;                // [n][8] read at odd iterations
-    T* rec;                // [n][12] (dx, r, q) records
+    T* nb;                 // [n][4] neighbour records (u)
+    T* rec;                // [n][24] row records (dx, r, p, s, w, zb)
     double* part;          // [tiles][4] tile partials
     ProbScal* sc;
     int n_rows, n_tiles, unit_begin;   // the SpMV's tiles (autotuned rows per block)

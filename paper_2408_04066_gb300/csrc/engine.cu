@@ -242,17 +242,18 @@ void end_profile(mfem_ctx* c) {
 namespace {
 
 // Algorithmic bytes of one PCG iteration of one problem (each datum crossing
-// HBM once, 3-vectors counted as 3 elements): matrix values and column ids;
-// k_pcg_spmv reads the row's z and p_old and writes p_new and q; k_pcg_update
-// reads p_new, q, dx, r and the 9-element D^-1 and writes dx, r, z.
-// With the two-level preconditioner the update also reads the aggregate offset
-// (16) and the correction reads r, z, the offset and writes z (per row); the
-// coarse product's A_c^{-1} is counted per launch in run_pcg.
+// HBM once, 3-vectors counted as 3 elements): k_pcg_spmv reads the matrix
+// values and column ids and the row's u and r, and writes w (the neighbours' u
+// are the same vector); k_pcg_update reads u, w, p, s, dx, r and the 9-element
+// D^-1 and writes p, s, dx, r and zb, and u under block Jacobi.  With the
+// two-level preconditioner the update reads the aggregate offset (16) for the
+// restriction and the correction reads zb and the offset and writes u (per
+// row); the coarse product's A_c^{-1} is counted per launch in run_pcg.
 double pcg_bytes_per_iter(const mfem_ctx* c, bool coarse) {
     const double kt = c->slot.prec == 1 ? 4.0 : 8.0;
     const double nnzb = (double)c->plan.nnz_blocks, n = c->plan.n;
-    double b = nnzb * (9.0 * kt + 4.0) + n * (4.0 * 3.0 * kt) + n * (4.0 * 3.0 * kt + 9.0 * kt + 3.0 * 3.0 * kt);
-    if (coarse) b += n * (16.0 + 3.0 * 3.0 * kt + 16.0);
+    double b = nnzb * (9.0 * kt + 4.0) + n * (3.0 * 3.0 * kt) + n * (6.0 * 3.0 * kt + 9.0 * kt + 5.0 * 3.0 * kt);
+    b += coarse ? n * (16.0 + 3.0 * kt + 16.0 + 3.0 * kt) : n * 3.0 * kt;
     return b;
 }
 
@@ -288,8 +289,7 @@ void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc
             d.dinv = (const T*)c->slot.dinv + (size_t)b * n * 9;
             const size_t np = npad32(n);
             T* v = (T*)c->slot.vec + (size_t)b * kVecStride * np;
-            d.zp0 = v + kOffZP0 * np;
-            d.zp1 = v + kOffZP1 * np;
+            d.nb = v + kOffNB * np;
             d.rec = v + kOffRec * np;
             d.part = c->slot.part + (size_t)b * c->slot.part_tiles * 4;
             d.sc = c->slot.sc + b;

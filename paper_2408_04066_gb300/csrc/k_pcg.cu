@@ -72,97 +72,7 @@ __device__ __forceinline__ void restrict_units(const float (&r)[3], bool valid, 
     }
 }
 
-// r = -g, z = D^{-1} r, dx = 0, p_old = 0; rho = r.z, rr0 = r.r per problem.
-// A problem with the coarse correction on (coarse_b[b]) leaves rho to the first
-// correction and writes the restriction of r instead.
-template <typename T>
-__global__ void k_pcg_init(ElemArgs A, double tol2, int maxit, const double* __restrict__ tol2_b,
-                           const int* __restrict__ coarse_b) {
-    const int b = blockIdx.y;
-    if (!A.slot.active[b]) return;
-    const int n = A.mesh.n;
-    const int row = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool coarse = coarse_b && coarse_b[b];
-    double v[2] = {0.0, 0.0};
-    float r32[3] = {0.f, 0.f, 0.f};
-    if (row < n) {
-        const double* g = A.slot.g + ((size_t)b * n + row) * 3;
-        const T* di = (const T*)A.slot.dinv + ((size_t)b * n + row) * 9;
-        T* rec = vecp<T>(A.slot, b, kOffRec, n) + kRec * (size_t)row;
-        T* zp = vecp<T>(A.slot, b, kOffZP0, n) + 8 * (size_t)row;
-        T rr[3] = {(T)(-g[0]), (T)(-g[1]), (T)(-g[2])};
-#pragma unroll
-        for (int i = 0; i < kRec; ++i) rec[i] = (T)0;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            T zi = di[3 * i] * rr[0] + di[3 * i + 1] * rr[1] + di[3 * i + 2] * rr[2];
-            rec[kRecR + i] = rr[i];
-            zp[i] = zi;
-            zp[4 + i] = (T)0;
-            v[0] += (double)rr[i] * (double)zi;
-            v[1] += (double)rr[i] * (double)rr[i];
-        }
-        zp[3] = (T)0;
-        zp[7] = (T)0;
-        r32[0] = (float)rr[0];
-        r32[1] = (float)rr[1];
-        r32[2] = (float)rr[2];
-    }
-    if (coarse) {
-        __shared__ float qs[4][9];
-        const int row0 = (int)(blockIdx.x * blockDim.x);
-        stage_rotations(qs, row0, A.mesh.agg_handle, A.slot.xf + (size_t)b * A.mesh.H * 12, A.mesh.agg_shift,
-                        A.mesh.n_agg);
-        restrict_units(r32, row < n, row, row0, A.mesh.crel, qs, A.mesh.agg_shift,
-                       A.slot.rcp + (size_t)b * A.slot.rcp_stride + 6 * ((size_t)row0 / kCoarseRows));
-    }
-    double tot[2];
-    double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
-    if (tile_commit<2>(v, part, blockIdx.x, gridDim.x, &A.slot.sc[b].tk_init, 1, tot) && threadIdx.x == 0) {
-        ProbScal* sc = &A.slot.sc[b];
-        sc->rho = coarse ? 0.0 : tot[0];
-        sc->cinit = coarse ? 1 : 0;
-        sc->rr0 = tot[1];
-        sc->rr = tot[1];
-        sc->beta = 0.0;
-        sc->alpha = 0.0;
-        sc->alpha_f = 0.f;
-        sc->beta_f = 0.f;
-        sc->iter = 0;
-        sc->tol2 = tol2_b ? tol2_b[b] : tol2;
-        sc->maxit = maxit;
-        sc->state = (tot[1] > 0.0 && (coarse || tot[0] > 0.0) && maxit > 0) ? kActive : kConverged;
-    }
-}
-
-// ---- PCG iteration kernels ----------------------------------------------------
-// One PCG iteration is two ordinary launches over every problem of the
-// descriptor table; a block is one (problem, tile of TILE rows) unit and returns
-// at once when its problem is not active.
-//   k_pcg_spmv:   p_new = z + beta p_old (also for neighbours, recomputed on the
-//                 fly from their (z, p_old) record), q = K p_new, tile partial of
-//                 p.q; the last tile of a problem sets alpha = rho / p.q.
-//   k_pcg_update: dx += alpha p, r -= alpha q, z = D^{-1} r, partials of r.z and
-//                 r.r; the last tile sets beta, rho, the iteration count and the
-//                 convergence state (|r| <= tol |r0| or the iteration cap).
-// Kernel boundaries order every write before the next iteration's reads, so no
-// block ever waits on another.  z and p of a vertex share one 32-byte record
-// (two ping-pong buffers by iteration parity); the matrix streams through with
-// evict-first loads.
-__device__ __forceinline__ void ld_zp(const float* zp, int c, float (&z)[3], float (&p)[3]) {
-    const float4 a = *reinterpret_cast<const float4*>(zp + 8 * (size_t)c);
-    const float4 b = *reinterpret_cast<const float4*>(zp + 8 * (size_t)c + 4);
-    z[0] = a.x; z[1] = a.y; z[2] = a.z;
-    p[0] = b.x; p[1] = b.y; p[2] = b.z;
-}
-
-__device__ __forceinline__ void ld_zp(const double* zp, int c, double (&z)[3], double (&p)[3]) {
-    const double2* r = reinterpret_cast<const double2*>(zp + 8 * (size_t)c);
-    const double2 a = r[0], b = r[1], e = r[2], f = r[3];
-    z[0] = a.x; z[1] = a.y; z[2] = b.x;
-    p[0] = e.x; p[1] = e.y; p[2] = f.x;
-}
-
+// ---- vector access ------------------------------------------------------------
 // 3-vectors stored as aligned 4-element groups (x, y, z, 0)
 __device__ __forceinline__ void ld4(const float* p, float (&v)[3]) {
     const float4 a = *reinterpret_cast<const float4*>(p);
@@ -234,6 +144,98 @@ __device__ __forceinline__ void coeffs(const ProbScal* sc, double& a, double& b)
     b = sc->beta;
 }
 
+// z_bj = D^{-1} r for one row (D^{-1} row-major 3x3)
+template <typename T>
+__device__ __forceinline__ void apply_dinv(const T* __restrict__ di, const T (&r)[3], T (&z)[3]) {
+#pragma unroll
+    for (int i = 0; i < 3; ++i) z[i] = di[3 * i] * r[0] + di[3 * i + 1] * r[1] + di[3 * i + 2] * r[2];
+}
+
+// ---- PCG in single-reduction form --------------------------------------------
+// Paper §3 Eq. 12: the Newton system K dx = -g is SPD and solved by
+// preconditioned conjugate gradients.  The recurrences are those of the
+// single-reduction form of PCG (Chronopoulos and Gear, "s-step iterative
+// methods for symmetric linear systems", J. Comput. Appl. Math. 1989): with
+// u = M^{-1} r and w = K u,
+//   gamma = (r, u), delta = (w, u);  beta = gamma / gamma_old,
+//   alpha = gamma / (delta - beta gamma / alpha_old)   (first: beta = 0,
+//   alpha = gamma / delta);  p = u + beta p, s = w + beta s,
+//   dx += alpha p, r -= alpha s,
+// so an iteration needs ONE global reduction (gamma, delta and |r|^2 together,
+// in the SpMV) where the textbook form needs two; the update and the coarse
+// correction are row-local.  M^{-1} = D^{-1} (3x3 block Jacobi), or
+// D^{-1} + P Ahat P^T with the coarse correction (two-level).
+//
+// Kernels of one iteration, over every problem of the descriptor table (a
+// block is one (problem, tile) unit and returns at once for an inactive problem):
+//   [coarse product e = Ahat r_c per mesh]
+//   k_pcg_correct: u = zb + P e                      (two-level problems only)
+//   k_pcg_spmv:    w = K u (neighbour u gathered), partials of (r,u), (w,u),
+//                  (r,r); the last tile of a problem tests convergence
+//                  (|r| <= tol |r0| or the iteration cap) and sets alpha, beta
+//   k_pcg_update:  p, s, dx, r as above; zb = D^{-1} r; u = zb (block Jacobi) or
+//                  the restriction partials of r (two-level)
+// Kernel boundaries order every write before the next kernel's reads, so no
+// block ever waits on another.
+
+// r = -g, dx = p = s = 0, zb = D^{-1} r; u = zb, or (two-level, coarse_b[b])
+// the restriction partials of r for the first coarse product; |r0|^2.
+template <typename T>
+__global__ void k_pcg_init(ElemArgs A, double tol2, int maxit, const double* __restrict__ tol2_b,
+                           const int* __restrict__ coarse_b) {
+    const int b = blockIdx.y;
+    if (!A.slot.active[b]) return;
+    const int n = A.mesh.n;
+    const int row = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool coarse = coarse_b && coarse_b[b];
+    double v[1] = {0.0};
+    float r32[3] = {0.f, 0.f, 0.f};
+    if (row < n) {
+        const double* g = A.slot.g + ((size_t)b * n + row) * 3;
+        const T* di = (const T*)A.slot.dinv + ((size_t)b * n + row) * 9;
+        T* rec = vecp<T>(A.slot, b, kOffRec, n) + kRec * (size_t)row;
+        const T r[3] = {(T)(-g[0]), (T)(-g[1]), (T)(-g[2])};
+        T z[3];
+        apply_dinv(di, r, z);
+        st4(rec + kRecDX, (T)0, (T)0, (T)0);
+        st4(rec + kRecR, r[0], r[1], r[2]);
+        st4(rec + kRecP, (T)0, (T)0, (T)0);
+        st4(rec + kRecS, (T)0, (T)0, (T)0);
+        st4(rec + kRecW, (T)0, (T)0, (T)0);
+        st4(rec + kRecZB, z[0], z[1], z[2]);
+        if (!coarse) st4(vecp<T>(A.slot, b, kOffNB, n) + 4 * (size_t)row, z[0], z[1], z[2]);
+        v[0] = (double)r[0] * (double)r[0] + (double)r[1] * (double)r[1] + (double)r[2] * (double)r[2];
+        r32[0] = (float)r[0];
+        r32[1] = (float)r[1];
+        r32[2] = (float)r[2];
+    }
+    if (coarse) {
+        __shared__ float qs[4][9];
+        const int row0 = (int)(blockIdx.x * blockDim.x);
+        stage_rotations(qs, row0, A.mesh.agg_handle, A.slot.xf + (size_t)b * A.mesh.H * 12, A.mesh.agg_shift,
+                        A.mesh.n_agg);
+        restrict_units(r32, row < n, row, row0, A.mesh.crel, qs, A.mesh.agg_shift,
+                       A.slot.rcp + (size_t)b * A.slot.rcp_stride + 6 * ((size_t)row0 / kCoarseRows));
+    }
+    double tot[1];
+    double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
+    if (tile_commit<1>(v, part, blockIdx.x, gridDim.x, &A.slot.sc[b].tk_init, 1, tot) && threadIdx.x == 0) {
+        ProbScal* sc = &A.slot.sc[b];
+        sc->rho = 0.0;
+        sc->first = 1;
+        sc->rr0 = tot[0];
+        sc->rr = tot[0];
+        sc->beta = 0.0;
+        sc->alpha = 0.0;
+        sc->alpha_f = 0.f;
+        sc->beta_f = 0.f;
+        sc->iter = 0;
+        sc->tol2 = tol2_b ? tol2_b[b] : tol2;
+        sc->maxit = maxit;
+        sc->state = (tot[0] > 0.0 && maxit > 0) ? kActive : kConverged;
+    }
+}
+
 // problem of unit u: last descriptor whose unit_begin (SpMV tiles) or
 // unit_begin_u (row-local kernels' tiles, ROWU) is <= u
 template <bool ROWU = false, typename T>
@@ -247,10 +249,13 @@ __device__ __forceinline__ int unit_problem(const PcgDesc<T>* __restrict__ D, in
     return lo;
 }
 
-// Full occupancy (2048 threads per SM) matters more than registers here: the
-// kernel is latency-bound on its dependent col -> gather loads.
+// Full occupancy (2048 threads per SM) matters more than registers in the FP32
+// kernel: it is latency-bound on its dependent col -> neighbour loads.  The
+// FP64 kernel is bound by the FP64 pipe and takes half that occupancy for the
+// registers its double accumulators need (no spills).
 template <typename T, int TILE>
-__global__ void __launch_bounds__(TILE, 2048 / TILE) k_pcg_spmv(const PcgDesc<T>* __restrict__ D, int n_probs) {
+__global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 2048 : 1024) / TILE)
+    k_pcg_spmv(const PcgDesc<T>* __restrict__ D, int n_probs) {
     // prologue on data no kernel of the iteration writes (the descriptor table
     // and the matrix structure), overlapping the previous kernel's drain
     const int u = blockIdx.x;
@@ -267,13 +272,7 @@ __global__ void __launch_bounds__(TILE, 2048 / TILE) k_pcg_spmv(const PcgDesc<T>
     pdl_wait();
     pdl_trigger();
     if (sc->state != kActive) return;
-    const int iter = sc->iter;
-    const T* zpo = (iter & 1) ? d.zp1 : d.zp0;
-    T* zpn = (iter & 1) ? d.zp0 : d.zp1;
-    T alpha_unused, beta;
-    coeffs(sc, alpha_unused, beta);
-    double v[1] = {0.0};
-    Partial<T> pq = Partial<T>::zero();
+    double v[3] = {0.0, 0.0, 0.0};
     if (row < d.n_rows) {
         const int lane = row & 31;
         T a0 = 0, a1 = 0, a2 = 0;
@@ -283,36 +282,59 @@ __global__ void __launch_bounds__(TILE, 2048 / TILE) k_pcg_spmv(const PcgDesc<T>
             const int c = __ldcs(d.col + g + lane);
             if (c >= 0) {
                 const T* vv = d.val + (size_t)g * 9 + lane;
-                T zc[3], pc[3];
-                ld_zp(zpo, c, zc, pc);
-                const T q0 = fma(beta, pc[0], zc[0]);
-                const T q1 = fma(beta, pc[1], zc[1]);
-                const T q2 = fma(beta, pc[2], zc[2]);
-                a0 += __ldcs(vv) * q0 + __ldcs(vv + 32) * q1 + __ldcs(vv + 64) * q2;
-                a1 += __ldcs(vv + 96) * q0 + __ldcs(vv + 128) * q1 + __ldcs(vv + 160) * q2;
-                a2 += __ldcs(vv + 192) * q0 + __ldcs(vv + 224) * q1 + __ldcs(vv + 256) * q2;
+                T q[3];
+                ld4(d.nb + 4 * (size_t)c, q);
+                a0 += __ldcs(vv) * q[0] + __ldcs(vv + 32) * q[1] + __ldcs(vv + 64) * q[2];
+                a1 += __ldcs(vv + 96) * q[0] + __ldcs(vv + 128) * q[1] + __ldcs(vv + 160) * q[2];
+                a2 += __ldcs(vv + 192) * q[0] + __ldcs(vv + 224) * q[1] + __ldcs(vv + 256) * q[2];
             }
         }
-        T zr[3], pr[3];
-        ld_zp(zpo, row, zr, pr);
-        const T pn0 = fma(beta, pr[0], zr[0]);
-        const T pn1 = fma(beta, pr[1], zr[1]);
-        const T pn2 = fma(beta, pr[2], zr[2]);
-        st4(zpn + 8 * (size_t)row + 4, pn0, pn1, pn2);
-        st4(d.rec + kRec * (size_t)row + kRecQ, a0, a1, a2);
-        pq = dot3_partial(pn0, pn1, pn2, a0, a1, a2);
+        // epilogue with short live ranges (the kernel runs at 32 registers):
+        // each partial is reduced over the warp as soon as it is formed
+        T ur[3];
+        ld4(d.nb + 4 * (size_t)row, ur);
+        T* rec = d.rec + kRec * (size_t)row;
+        st4(rec + kRecW, a0, a1, a2);
+        v[1] = warp_sum_partial(dot3_partial(a0, a1, a2, ur[0], ur[1], ur[2]));
+        T r[3];
+        ld4(rec + kRecR, r);
+        v[0] = warp_sum_partial(dot3_partial(r[0], r[1], r[2], ur[0], ur[1], ur[2]));
+        v[2] = warp_sum_partial(dot3_partial(r[0], r[1], r[2], r[0], r[1], r[2]));
+    } else {
+        // rows past the end still take part in the warp sums (all lanes shuffle)
+        const Partial<T> z = Partial<T>::zero();
+        v[1] = warp_sum_partial(z);
+        v[0] = warp_sum_partial(z);
+        v[2] = warp_sum_partial(z);
     }
-    v[0] = warp_sum_partial(pq);
-    double tot[1];
-    if (tile_commit<1>(v, d.part, tile, d.n_tiles, &sc->tk_a, 0, tot, true) && threadIdx.x == 0) {
-        const double pq = tot[0];
-        if (pq > 0.0 && isfinite(pq)) {
-            sc->alpha = sc->rho / pq;
-        } else {  // breakdown (p = 0 or K not SPD along p): stop with the current dx
-            sc->alpha = 0.0;
+    double tot[3];
+    if (tile_commit<3>(v, d.part, tile, d.n_tiles, &sc->tk_a, 0, tot, true) && threadIdx.x == 0) {
+        const double gamma = tot[0], delta = tot[1];
+        sc->rr = tot[2];
+        if (!(tot[2] > sc->tol2 * sc->rr0)) {   // |r| at target: dx is the solve's result
             sc->state = kConverged;
+        } else if (sc->iter >= sc->maxit) {
+            sc->state = kMaxIter;
+        } else {
+            double beta = 0.0, den = delta;
+            if (!sc->first) {
+                beta = gamma / sc->rho;
+                den = delta - beta * gamma / sc->alpha;
+            }
+            if (gamma > 0.0 && den > 0.0 && isfinite(gamma) && isfinite(den)) {
+                sc->alpha = gamma / den;
+                sc->beta = beta;
+                sc->rho = gamma;
+                sc->first = 0;
+                sc->iter = sc->iter + 1;
+            } else {   // breakdown (u orthogonal to r, or K / M lost definiteness along u): keep dx
+                sc->alpha = 0.0;
+                sc->beta = 0.0;
+                sc->state = kConverged;
+            }
+            sc->alpha_f = (float)sc->alpha;
+            sc->beta_f = (float)sc->beta;
         }
-        sc->alpha_f = (float)sc->alpha;
     }
 }
 
@@ -328,58 +350,40 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
     if (coarse) stage_rotations(qs, tile * TILE, d.agg_handle, d.xf, d.agg_shift, d.coarse_n / 6);
     pdl_wait();
     pdl_trigger();
-    if (sc->state != kActive) return;
-    const int iter = sc->iter;
-    T* zpn = (iter & 1) ? d.zp0 : d.zp1;
-    T alpha, beta_unused;
-    coeffs(sc, alpha, beta_unused);
-    double v[2] = {0.0, 0.0};
+    if (sc->state != kActive) return;   // block-uniform
+    T alpha, beta;
+    coeffs(sc, alpha, beta);
     float r32[3] = {0.f, 0.f, 0.f};
-    Partial<T> rz = Partial<T>::zero(), rr2 = Partial<T>::zero();
     if (row < d.n_rows) {
-        T* zrec = zpn + 8 * (size_t)row;
         T* rec = d.rec + kRec * (size_t)row;
-        const T* di = d.dinv + 9 * (size_t)row;
-        T pp[3], dxv[3], r0[3], qv[3], rr[3], zz[3];
-        ld4(zrec + 4, pp);
-        ld4(rec + kRecDX, dxv);
-        ld4(rec + kRecR, r0);
-        ld4(rec + kRecQ, qv);
+        T uu[3], ww[3], pp[3], ss[3], dx[3], r[3], z[3];
+        ld4(d.nb + 4 * (size_t)row, uu);
+        ld4(rec + kRecW, ww);
+        ld4(rec + kRecP, pp);
+        ld4(rec + kRecS, ss);
+        ld4(rec + kRecDX, dx);
+        ld4(rec + kRecR, r);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
-            dxv[i] = fma(alpha, pp[i], dxv[i]);
-            rr[i] = fma(-alpha, qv[i], r0[i]);
+            pp[i] = fma(beta, pp[i], uu[i]);
+            ss[i] = fma(beta, ss[i], ww[i]);
+            dx[i] = fma(alpha, pp[i], dx[i]);
+            r[i] = fma(-alpha, ss[i], r[i]);
         }
-        st4(rec + kRecDX, dxv[0], dxv[1], dxv[2]);
-        st4(rec + kRecR, rr[0], rr[1], rr[2]);
-#pragma unroll
-        for (int i = 0; i < 3; ++i) zz[i] = di[3 * i] * rr[0] + di[3 * i + 1] * rr[1] + di[3 * i + 2] * rr[2];
-        st4(zrec, zz[0], zz[1], zz[2]);
-        if (!coarse) rz = dot3_partial(rr[0], rr[1], rr[2], zz[0], zz[1], zz[2]);
-        rr2 = dot3_partial(rr[0], rr[1], rr[2], rr[0], rr[1], rr[2]);
-        r32[0] = (float)rr[0];
-        r32[1] = (float)rr[1];
-        r32[2] = (float)rr[2];
+        apply_dinv(d.dinv + 9 * (size_t)row, r, z);
+        st4(rec + kRecP, pp[0], pp[1], pp[2]);
+        st4(rec + kRecS, ss[0], ss[1], ss[2]);
+        st4(rec + kRecDX, dx[0], dx[1], dx[2]);
+        st4(rec + kRecR, r[0], r[1], r[2]);
+        st4(rec + kRecZB, z[0], z[1], z[2]);
+        if (!coarse) st4(d.nb + 4 * (size_t)row, z[0], z[1], z[2]);   // u = D^{-1} r
+        r32[0] = (float)r[0];
+        r32[1] = (float)r[1];
+        r32[2] = (float)r[2];
     }
-    if (coarse)   // z is finished by k_pcg_correct, which also forms r.z and beta
+    if (coarse)   // u is finished by k_pcg_correct after the coarse product
         restrict_units(r32, row < d.n_rows, row, tile * TILE, d.crel, qs, d.agg_shift,
                        d.rcp + 6 * ((size_t)tile * TILE / kCoarseRows));
-    v[0] = warp_sum_partial(rz);
-    v[1] = warp_sum_partial(rr2);
-    double tot[2];
-    if (tile_commit<2>(v, d.part, tile, d.n_tiles_u, &sc->tk_b, 1, tot, true) && threadIdx.x == 0) {
-        if (!coarse) {
-            const double rho_new = tot[0];
-            sc->beta = sc->rho != 0.0 ? rho_new / sc->rho : 0.0;
-            sc->beta_f = (float)sc->beta;
-            sc->rho = rho_new;
-        }
-        sc->rr = tot[1];
-        const int itn = sc->iter + 1;
-        sc->iter = itn;
-        if (!(tot[1] > sc->tol2 * sc->rr0)) sc->state = kConverged;
-        else if (itn >= sc->maxit) sc->state = kMaxIter;
-    }
 }
 
 // Coarse solve of the two-level preconditioner: e = A_c^{-1} r_c for the
@@ -510,11 +514,12 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(const float* __restrict__ A
     }
 }
 
-// z_i += Q_a P_i e_a (e_a = the six coarse values of row i's aggregate, e_t +
-// e_w x (X_i - c_a) turned by the pose rotation of the aggregate), then r.z and
-// beta = rho_new / rho (0 on the first correction of a solve).  The block first
-// gathers e and Q of its aggregates into shared memory.  Problems without the
-// coarse correction return at once.
+// u_i = zb_i + Q_a P_i e_a (e_a = the six coarse values of row i's aggregate,
+// e_t + e_w x (X_i - c_a) turned by the pose rotation of the aggregate), written
+// to the neighbour record the next k_pcg_spmv gathers.  The block first gathers
+// the slice partials of e of its aggregates (added in slice order) and their
+// rotations into shared memory.  Problems without the coarse correction return
+// at once (their u was written by the update).
 template <typename T, int TILE>
 __global__ void __launch_bounds__(TILE) k_pcg_correct(const PcgDesc<T>* __restrict__ D, int n_probs) {
     constexpr int kMaxAgg = TILE / kCoarseRows;   // aggregates a block can touch
@@ -541,17 +546,13 @@ __global__ void __launch_bounds__(TILE) k_pcg_correct(const PcgDesc<T>* __restri
     pdl_wait();
     pdl_trigger();
     if (sc->state != kActive) return;   // block-uniform: before any barrier
-    // the row's own loads go out first, so their latency overlaps the staging
-    T* zp = (sc->iter & 1) ? d.zp1 : d.zp0;   // the record the next k_pcg_spmv reads
-    T r[3] = {(T)0, (T)0, (T)0}, z[3] = {(T)0, (T)0, (T)0};
-    if (row < d.n_rows) {
-        ld4(d.rec + kRec * (size_t)row + kRecR, r);
-        ld4(zp + 8 * (size_t)row, z);
-    }
+    // the row's own load goes out first, so its latency overlaps the staging
+    T z[3] = {(T)0, (T)0, (T)0};
+    if (row < d.n_rows) ld4(d.rec + kRec * (size_t)row + kRecZB, z);
     // slice partials of e, one load per thread, then added in slice order
-    for (int idx = threadIdx.x; idx < kMaxAgg * 6 * n_ks; idx += TILE) {
+    for (int idx = threadIdx.x; idx < kMaxAgg * 6 * n_ks && idx < TILE; idx += TILE) {
         const int ks = idx / (kMaxAgg * 6), r = idx - ks * kMaxAgg * 6, a = a0 + r / 6;
-        if (idx < TILE) part_e[idx] = a < n_agg ? d.ec[(size_t)ks * d.coarse_n + 6 * a + r % 6] : 0.f;
+        part_e[idx] = a < n_agg ? d.ec[(size_t)ks * d.coarse_n + 6 * a + r % 6] : 0.f;
     }
     __syncthreads();
     if ((int)threadIdx.x < kMaxAgg * 6) {
@@ -565,7 +566,6 @@ __global__ void __launch_bounds__(TILE) k_pcg_correct(const PcgDesc<T>* __restri
         es[threadIdx.x / 6][threadIdx.x % 6] = v;
     }
     __syncthreads();
-    Partial<T> rz = Partial<T>::zero();
     if (row < d.n_rows) {
         if (off.w != 0.f) {
             const int ai = (row >> d.agg_shift) - a0;
@@ -576,23 +576,8 @@ __global__ void __launch_bounds__(TILE) k_pcg_correct(const PcgDesc<T>* __restri
             const float l2 = e[2] + (e[3] * off.y - e[4] * off.x);
 #pragma unroll
             for (int i = 0; i < 3; ++i) z[i] += (T)(Q[3 * i] * l0 + Q[3 * i + 1] * l1 + Q[3 * i + 2] * l2);
-            st4(zp + 8 * (size_t)row, z[0], z[1], z[2]);
         }
-        rz = dot3_partial(r[0], r[1], r[2], z[0], z[1], z[2]);
-    }
-    double v[1] = {warp_sum_partial(rz)};
-    double tot[1];
-    if (tile_commit<1>(v, d.part, tile, d.n_tiles_u, &sc->tk_c, 3, tot, true) && threadIdx.x == 0) {
-        const double rho_new = tot[0];
-        if (rho_new > 0.0 && isfinite(rho_new)) {
-            sc->beta = (sc->cinit || sc->rho == 0.0) ? 0.0 : rho_new / sc->rho;
-            sc->rho = rho_new;
-        } else {   // z orthogonal to r, or the preconditioner lost definiteness: stop here
-            sc->beta = 0.0;
-            sc->state = kConverged;
-        }
-        sc->cinit = 0;
-        sc->beta_f = (float)sc->beta;
+        st4(d.nb + 4 * (size_t)row, z[0], z[1], z[2]);
     }
 }
 

@@ -36,7 +36,28 @@ using namespace mfem;
 namespace {
 
 constexpr int kPoolSlots = 8;           // request slots per pool
-constexpr double kPoolIdleRelease = 0.5;   // seconds a pool other than the first stays idle before release
+constexpr double kPoolIdleRelease = 2.0;   // seconds a pool other than the first stays idle before release
+// A WARM request carries the latest solution's nonlinear correction only when
+// no handle has turned more than this from that solution's pose (a few frames
+// of an animation); further away it takes the co-rotational start alone, which
+// under a backlog -- many frames of a mesh admitted at once, all behind the
+// latest solution -- measured fewer Newton steps than a stale correction.
+constexpr double kWarmMaxTurn = 15.0 * 3.14159265358979323846 / 180.0;
+
+// Largest rotation angle between the handles of two poses ([H][12] each).
+double max_turn(const double* a, const double* b, int H) {
+    double worst = 0.0;
+    for (int h = 0; h < H; ++h) {
+        const double* A = a + 12 * h;
+        const double* B = b + 12 * h;
+        double tr = 0.0;   // trace(Q_a Q_b^T)
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) tr += A[4 * i + j] * B[4 * i + j];
+        const double c = std::min(1.0, std::max(-1.0, 0.5 * (tr - 1.0)));
+        worst = std::max(worst, std::acos(c));
+    }
+    return worst;
+}
 
 double now_s() {
     return std::chrono::duration<double>(std::chrono::steady_clock::now().time_since_epoch()).count();
@@ -69,6 +90,7 @@ struct MeshEntry {
     // request, so every request continues from the latest frame solved
     double* bank = nullptr;
     int bank_state = 0;   // 0 none, 1 x and pose, 2 also the predictor result
+    std::vector<double> bank_xf;   // host copy of the bank's pose
     mfem_ctx* owner() const { return pools[0]->ctx; }
 };
 
@@ -206,7 +228,8 @@ void mfem_server::run() {
                     cudaMemcpyAsync(c->slot.xf_prev + (size_t)slot * H * 12, me.bank + 2 * n3, H * 12 * sizeof(double),
                                     cudaMemcpyDeviceToDevice, stream);
                     c->warm_kind[slot] = 1;
-                    c->xpred_valid[slot] = me.bank_state == 2;
+                    c->xpred_valid[slot] = me.bank_state == 2 &&
+                                           max_turn(r.xf.data(), me.bank_xf.data(), (int)H) <= kWarmMaxTurn;
                 }
                 cudaMemcpyAsync(c->slot.xf + (size_t)slot * H * 12, r.xf.data(), H * 12 * sizeof(double),
                                 cudaMemcpyHostToDevice, stream);
@@ -272,6 +295,7 @@ void mfem_server::run() {
                     cudaMemcpyAsync(me->bank + 2 * n * 3, c->slot.xf + (size_t)b * H * 12, H * 12 * sizeof(double),
                                     cudaMemcpyDeviceToDevice, stream);
                     me->bank_state = c->xpred_valid[b] ? 2 : 1;
+                    me->bank_xf = r.xf;
                 }
                 r.done = true;
                 r.t_done = now_s();
