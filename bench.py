@@ -48,6 +48,10 @@ def parse():
                         "10k/50k/200k/800k meshes; large: one 2M-tet 40-handle character")
     p.add_argument("--rate", type=float, default=500.0, help="serve: mean Poisson arrival rate (requests/s)")
     p.add_argument("--duration", type=float, default=20.0, help="serve: seconds of arrivals per phase")
+    p.add_argument("--cg-tol", type=float, default=None, help="PCG target per Newton step (library default 3e-2)")
+    p.add_argument("--coarse-agg", type=int, default=0, help="vertices per coarse aggregate (0: library default)")
+    p.add_argument("--coarse-product", default="tc", choices=["tc", "fp32"], help="coarse solve on tensor cores or FP32")
+    p.add_argument("--precond", default="two_level", choices=["two_level", "block_jacobi"])
     p.add_argument("--ncu-case", action="store_true",
                    help="one small solve for profiler captures: 8 poses, 3 Newton steps, 256-row tiles")
     return p.parse_args()
@@ -335,10 +339,14 @@ def cpu_baseline(args):
                        f"(BLAS/OpenMP threads = 1); frame times {', '.join(f'{x:.2f}' for x in times)} s")}
 
 
-def workload_config(m, n, H, pins, nb, precision):
-    return {"workload": f"figure{m // 1000}k-snh-batch{nb}", "tets": m, "verts": n,
-            "handles": H, "pins": pins, "batch_poses": nb, "precision": precision, "newton_tol": 1e-6,
-            "l2": "256 MiB buffer written between timed steps; per-step working set > L2"}
+def workload_config(m, n, H, pins, nb, precision, args=None):
+    c = {"workload": f"figure{m // 1000}k-snh-batch{nb}", "tets": m, "verts": n,
+         "handles": H, "pins": pins, "batch_poses": nb, "precision": precision, "newton_tol": 1e-6,
+         "l2": "256 MiB buffer written between timed steps; per-step working set > L2"}
+    if args is not None:
+        c.update(cg_tol=args.cg_tol if args.cg_tol is not None else 3e-2, precond=args.precond,
+                 coarse_product=args.coarse_product, coarse_agg=args.coarse_agg or "default (64)")
+    return c
 
 
 def run_reference(args, dist):
@@ -386,7 +394,10 @@ def run_mfem(args, dist):
     dev = torch.device("cuda", dist.local)
     nb = args.batch
     cfg = figure_config(args.tets, model=args.model, seeds=range(dist.rank * nb, dist.rank * nb + nb))
-    opts = dict(precision=args.precision, max_batch=nb, newton_tol=1e-6)
+    opts = dict(precision=args.precision, max_batch=nb, newton_tol=1e-6, coarse_agg=args.coarse_agg,
+                coarse_product=args.coarse_product, precond=args.precond)
+    if args.cg_tol is not None:
+        opts["cg_tol"] = args.cg_tol
     ctx = mfem.Context.from_config(cfg, **opts)
     stream = torch.cuda.Stream(dev)      # a created stream (CUDA graphs cannot capture the legacy one)
     torch.cuda.set_stream(stream)
@@ -528,7 +539,7 @@ def run_mfem(args, dist):
                            "preconditioner's coarse solve (BF16 tensor cores, FP32 accumulation)"),
             "data": "synthetic",
             "config": dict(workload_config(info["m"], info["n"], info["n_handles"], info["n_pins"], nb,
-                                           args.precision), parallelism=f"replicas x{dist.world}"),
+                                           args.precision, args), parallelism=f"replicas x{dist.world}"),
             "latency_ms": dict(req, note=f"per request: one pose per request through the server, {nb} requests "
                                          f"kept in flight, submit to result in host memory"),
             "batch_step_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
