@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--coarse-agg", type=int, default=0, help="vertices per coarse aggregate (0: library default)")
     p.add_argument("--coarse-product", default="tc", choices=["tc", "fp32"], help="coarse solve on tensor cores or FP32")
     p.add_argument("--precond", default="two_level", choices=["two_level", "block_jacobi"])
+    p.add_argument("--tile-rows", type=int, default=0, help="SpMV rows per block (0: autotune)")
+    p.add_argument("--spmv-split", type=int, default=0, help="SpMV threads per row (0: autotune)")
     p.add_argument("--ncu-case", action="store_true",
                    help="one small solve for profiler captures: 8 poses, 3 Newton steps, 256-row tiles")
     return p.parse_args()
@@ -395,7 +397,8 @@ def run_mfem(args, dist):
     nb = args.batch
     cfg = figure_config(args.tets, model=args.model, seeds=range(dist.rank * nb, dist.rank * nb + nb))
     opts = dict(precision=args.precision, max_batch=nb, newton_tol=1e-6, coarse_agg=args.coarse_agg,
-                coarse_product=args.coarse_product, precond=args.precond)
+                coarse_product=args.coarse_product, precond=args.precond, tile_rows=args.tile_rows,
+                spmv_split=args.spmv_split)
     if args.cg_tol is not None:
         opts["cg_tol"] = args.cg_tol
     ctx = mfem.Context.from_config(cfg, **opts)
@@ -548,6 +551,9 @@ def run_mfem(args, dist):
             "newton_iters_mean": statistics.mean(newton), "pcg_iters_mean": statistics.mean(pcg_it),
             "all_converged": conv,
             "element_updates_per_s": element_rate(prof),
+            "autotuned": {"spmv_rows_per_block": prof[-1]["tile_rows"], "spmv_threads_per_row": prof[-1]["spmv_split"],
+                          "coarse_product": "tcgen05 BF16" if prof[-1]["coarse_tc"] else "FP32 CUDA cores",
+                          "coarse_dof": prof[-1]["coarse_dof"]},
             "roofline": roof, "cpu_baseline": cpu, "cpu_baseline_all_cores": cpu_all,
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(xfs_h.numel() * 8),
                     "d2h_bytes_per_step": int(out_h.numel() * 8)},

@@ -133,7 +133,7 @@ typedef struct {
                             linear solve from any start); a state set by
                             mfem_set_state is used as it is */
     int32_t max_batch;   /* poses per mfem_solve_batch call allocated for (16) */
-    int32_t tile_rows;   /* PCG rows per block: 64, 128 or 256; 0 = autotune (timed
+    int32_t tile_rows;   /* SpMV rows per block: 64, 128 or 256; 0 = autotune (timed
                             on the first assembled system) */
     int32_t diagnostics; /* 1: fill inverted/skew/angle fields of mfem_stats (0) */
     int32_t rotation;    /* MFEM_ROT_RIG (default): R_k is the rotation of the tet's
@@ -165,6 +165,8 @@ typedef struct {
                             the coarse space at most 6144 dof (6 per aggregate);
                             else a power of two >= 64, raised to that smallest size
                             if it is below it.  Other values: MFEM_EINVAL */
+    int32_t spmv_split;  /* SpMV threads per row: 1, 2 (two threads take a row's
+                            even and odd slots), 0 = autotune with tile_rows */
     int32_t coarse_product; /* the coarse solve e = A_c^{-1} r_c of the two-level
                             preconditioner: MFEM_COARSE_TC (default) -- A_c^{-1}
                             rounded to BF16 (a fixed symmetric matrix) times r_c
@@ -205,12 +207,13 @@ typedef struct {
     double assemble_ms;
     double linesearch_ms;
     double total_ms;          /* first to last library event of the call */
-    int32_t tile_rows;        /* PCG tile in use */
+    int32_t tile_rows;        /* SpMV rows per block in use */
     int32_t grid_blocks;      /* PCG blocks per launch (tiles of all problems) */
     int64_t element_updates;  /* per-tet local steps (a1) of the Newton element passes */
     int32_t coarse_dof;       /* dimension of the two-level coarse space (0: none) */
     int32_t coarse_launches;  /* coarse-solve and correction launches (two-level) */
     int32_t coarse_tc;        /* 1: the coarse solves ran on the tensor cores */
+    int32_t spmv_split;       /* SpMV threads per row in use */
 } mfem_profile;
 
 typedef struct mfem_ctx mfem_ctx;

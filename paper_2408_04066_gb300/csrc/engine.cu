@@ -221,6 +221,7 @@ void end_profile(mfem_ctx* c) {
     P.coarse_tc = c->mesh.coarse_n > 0 && c->mesh.coarse_tc ? 1 : 0;
     P.pcg_iters = c->prof.pcg_iters;
     P.tile_rows = c->tile_rows;
+    P.spmv_split = c->spmv_split;
     P.grid_blocks = c->grid_blocks;
     for (int i = 0; i < c->prof.used; ++i) {
         float ms = 0.f;
@@ -380,13 +381,13 @@ mfem_status read_scalars(mfem_ctx* c, int B) {
 // time these launch parameters occur (the descriptor table lives at a fixed
 // device address; only its contents change), else launched directly.
 template <typename T>
-mfem_status launch_chunk(mfem_ctx* c, const PcgDesc<T>* dst, int nd, int units, int units_u, int tile, int n_it,
-                         const std::vector<CoarseJob>& jobs) {
+mfem_status launch_chunk(mfem_ctx* c, const PcgDesc<T>* dst, int nd, int units, int units_u, int tile, int split,
+                         int n_it, const std::vector<CoarseJob>& jobs) {
     const int nj = (int)jobs.size();
     if (c->opt.launch == MFEM_LAUNCH_GRAPH && !c->graphs_off) {
         char buf[96];
-        snprintf(buf, sizeof buf, "%d %p %d %d %d %d %d", (int)sizeof(T), (const void*)dst, nd, units, units_u, tile,
-                 n_it);
+        snprintf(buf, sizeof buf, "%d %p %d %d %d %d %d %d", (int)sizeof(T), (const void*)dst, nd, units, units_u, tile,
+                 split, n_it);
         std::string key(buf);
         for (const auto& j : jobs) {
             snprintf(buf, sizeof buf, " %p %d %d %d %d %d", j.key, j.Abf ? 1 : 0, j.N, j.d0, j.nd, j.agg_units);
@@ -402,7 +403,7 @@ mfem_status launch_chunk(mfem_ctx* c, const PcgDesc<T>* dst, int nd, int units, 
             cudaGraphExec_t ex = nullptr;
             bool ok = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
             if (ok) {
-                const cudaError_t e1 = launch_pcg_iters<T>(dst, nd, units, units_u, tile, n_it, jobs.data(), nj, c->stream);
+                const cudaError_t e1 = launch_pcg_iters<T>(dst, nd, units, units_u, tile, split, n_it, jobs.data(), nj, c->stream);
                 const cudaError_t e2 = cudaStreamEndCapture(c->stream, &g);
                 ok = e1 == cudaSuccess && e2 == cudaSuccess && g && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess;
             }
@@ -410,7 +411,7 @@ mfem_status launch_chunk(mfem_ctx* c, const PcgDesc<T>* dst, int nd, int units, 
             if (!ok) {   // keep to direct launches from now on
                 cudaGetLastError();
                 c->graphs_off = true;
-                CK(launch_pcg_iters<T>(dst, nd, units, units_u, tile, n_it, jobs.data(), nj, c->stream));
+                CK(launch_pcg_iters<T>(dst, nd, units, units_u, tile, split, n_it, jobs.data(), nj, c->stream));
                 return MFEM_OK;
             }
             it = c->graphs.emplace(key, ex).first;
@@ -418,12 +419,12 @@ mfem_status launch_chunk(mfem_ctx* c, const PcgDesc<T>* dst, int nd, int units, 
         CK(cudaGraphLaunch(it->second, c->stream));
         return MFEM_OK;
     }
-    CK(launch_pcg_iters<T>(dst, nd, units, units_u, tile, n_it, jobs.data(), nj, c->stream));
+    CK(launch_pcg_iters<T>(dst, nd, units, units_u, tile, split, n_it, jobs.data(), nj, c->stream));
     return MFEM_OK;
 }
 
 template <typename T>
-mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, int max_iters, bool count,
+mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, int split, int max_iters, bool count,
                     bool one_chunk = false) {
     mfem_ctx* c = c0;
     std::vector<PcgDesc<T>> d;
@@ -452,7 +453,8 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
     CK(cudaMemcpyAsync((void*)dst, hst, bytes, cudaMemcpyHostToDevice, c->stream));
     c->grid_blocks = units;
     if (max_iters > 0) {
-        CK(launch_pcg_iters<T>(dst, (int)d.size(), units, units_u, tile, max_iters, jobs.data(), nj, c->stream));
+        CK(launch_pcg_iters<T>(dst, (int)d.size(), units, units_u, tile, split, max_iters, jobs.data(), nj,
+                               c->stream));
         return MFEM_OK;
     }
     int cap = 0;
@@ -462,7 +464,7 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
         const int n_it = std::min(kPcgChunk, cap - done);
         if (one_chunk && done > 0) break;
         int pe = count ? c->prof.begin(2, c->stream) : -1;
-        mfem_status lst = launch_chunk<T>(c, dst, (int)d.size(), units, units_u, tile, n_it, jobs);
+        mfem_status lst = launch_chunk<T>(c, dst, (int)d.size(), units, units_u, tile, split, n_it, jobs);
         if (lst != MFEM_OK) return lst;
         if (count) {
             c->prof.end(pe, c->stream);
@@ -493,59 +495,72 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
     return MFEM_OK;
 }
 
-// Pick the PCG tile by timing a fixed number of iterations of each candidate on
-// the first assembled system (results are discarded; PCG is re-initialised
-// afterwards).  MFEM_AUTOTUNE_CACHE names a file of earlier picks.
+// Pick the SpMV's shape -- rows per block (64, 128, 256) and threads per row
+// (1, 2) -- by timing a fixed number of PCG iterations of each candidate on the
+// first assembled system (results are discarded; PCG is re-initialised
+// afterwards).  A shape fixed by the options is not searched.
+// MFEM_AUTOTUNE_CACHE names a file of earlier picks ("key tile split" lines).
 mfem_status autotune_tile(mfem_ctx* c, std::vector<Group>& gs) {
     const char* cache = std::getenv("MFEM_AUTOTUNE_CACHE");
     char key[128];
     snprintf(key, sizeof key, "%d %d %lld %d %d", c->plan.n, c->plan.m, (long long)c->plan.nnz_blocks,
              c->slot.prec, gs[0].B);
+    std::vector<int> tiles, splits;
+    for (int t : kPcgTiles)
+        if (!c->opt.tile_rows || t == c->opt.tile_rows) tiles.push_back(t);
+    for (int sp = 1; sp <= 2; ++sp)
+        if (!c->opt.spmv_split || sp == c->opt.spmv_split) splits.push_back(sp);
     if (cache) {
         if (FILE* f = fopen(cache, "r")) {
             char line[256];
             while (fgets(line, sizeof line, f)) {
-                int tile = 0;
+                int tile = 0, sp = 1;
                 size_t kl = strlen(key);
-                if (strncmp(line, key, kl) == 0 && sscanf(line + kl, " %d", &tile) == 1 && pcg_tile_supported(tile))
+                if (strncmp(line, key, kl) == 0 && sscanf(line + kl, " %d %d", &tile, &sp) >= 1 &&
+                    std::find(tiles.begin(), tiles.end(), tile) != tiles.end() &&
+                    std::find(splits.begin(), splits.end(), sp) != splits.end()) {
                     c->tile_rows = tile;
+                    c->spmv_split = sp;
+                }
             }
             fclose(f);
-            if (c->tile_rows) return MFEM_OK;
+            if (c->tile_rows && c->spmv_split) return MFEM_OK;
         }
     }
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 1e30f;
-    int best_tile = 256;
+    int best_tile = tiles.back(), best_split = splits.front();
     for (auto& g : gs)
         for (int b = 0; b < g.B; ++b) g.ph[b].coarse = 0;   // timed with block Jacobi
     ElemArgs a = elem_args(c);
-    for (int tile : kPcgTiles) {
-        for (int rep = 0; rep < 2; ++rep) {
-            launch_pcg_init(a, gs[0].B, tile, 0.0, 1 << 30, nullptr, nullptr, c->stream);
-            CK(cudaEventRecord(e0, c->stream));
-            mfem_status st = c->slot.prec == 1 ? run_pcg<float>(c, gs, 1, tile, 20, false)
-                                               : run_pcg<double>(c, gs, 0, tile, 20, false);
-            if (st != MFEM_OK) return st;
-            CK(cudaEventRecord(e1, c->stream));
-            CK(cudaEventSynchronize(e1));
-            c->ring_pos = 0;
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (rep == 1 && ms < best) {
-                best = ms;
-                best_tile = tile;
+    for (int tile : tiles)
+        for (int sp : splits)
+            for (int rep = 0; rep < 2; ++rep) {
+                launch_pcg_init(a, gs[0].B, tile, 0.0, 1 << 30, nullptr, nullptr, c->stream);
+                CK(cudaEventRecord(e0, c->stream));
+                mfem_status st = c->slot.prec == 1 ? run_pcg<float>(c, gs, 1, tile, sp, 20, false)
+                                                   : run_pcg<double>(c, gs, 0, tile, sp, 20, false);
+                if (st != MFEM_OK) return st;
+                CK(cudaEventRecord(e1, c->stream));
+                CK(cudaEventSynchronize(e1));
+                c->ring_pos = 0;
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (rep == 1 && ms < best) {
+                    best = ms;
+                    best_tile = tile;
+                    best_split = sp;
+                }
             }
-        }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     c->tile_rows = best_tile;
+    c->spmv_split = best_split;
     if (cache) {
         if (FILE* f = fopen(cache, "a")) {
-            fprintf(f, "%s %d\n", key, best_tile);
+            fprintf(f, "%s %d %d\n", key, best_tile, best_split);
             fclose(f);
         }
     }
@@ -809,7 +824,7 @@ mfem_status advance(std::vector<Group>& gs) {
                 start[b] = 1;
             }
             if (!any_of(start)) continue;
-            if (c->tile_rows == 0) {   // first PCG of this context: time the tiles
+            if (c->tile_rows == 0 || c->spmv_split == 0) {   // first PCG of this context: time the shapes
                 std::vector<Group> one{Group{gc, g.B, g.ph}};
                 for (int b = 0; b < g.B; ++b) g.ph[b].in_pcg = start[b];
                 mfem_status st = upload_active(gc, g.B, start);
@@ -895,8 +910,8 @@ mfem_status advance(std::vector<Group>& gs) {
             if (g.ctx->slot.prec == prec)
                 for (int b = 0; b < g.B; ++b) any |= g.ph[b].active && g.ph[b].in_pcg;
         if (!any) continue;
-        mfem_status st = prec == 1 ? run_pcg<float>(c, gs, 1, c->tile_rows, 0, true, true)
-                                   : run_pcg<double>(c, gs, 0, c->tile_rows, 0, true, true);
+        mfem_status st = prec == 1 ? run_pcg<float>(c, gs, 1, c->tile_rows, c->spmv_split, 0, true, true)
+                                   : run_pcg<double>(c, gs, 0, c->tile_rows, c->spmv_split, 0, true, true);
         if (st != MFEM_OK) return st;
     }
     CK(cudaGetLastError());
@@ -1063,6 +1078,7 @@ mfem_ctx* ctx_slot_clone(mfem_ctx* src, int cap, cudaStream_t stream, mfem_statu
     c->mesh_shared = true;
     c->slot.prec = src->slot.prec;
     c->tile_rows = src->tile_rows;
+    c->spmv_split = src->spmv_split;
     c->owned_by_server = true;
     mfem_status s = MFEM_OK;
     if (cudaMallocHost((void**)&c->cerr_host, sizeof(unsigned)) != cudaSuccess) s = MFEM_ENOMEM;
@@ -1103,6 +1119,7 @@ void mfem_default_options(mfem_options* o) {
     o->init = MFEM_INIT_COROT;
     o->max_batch = 16;
     o->tile_rows = 0;
+    o->spmv_split = 0;
     o->diagnostics = 0;
     o->rotation = MFEM_ROT_RIG;
     o->precond = MFEM_PRECOND_TWO_LEVEL;
@@ -1256,6 +1273,7 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
     if (o.launch != MFEM_LAUNCH_GRAPH && o.launch != MFEM_LAUNCH_DIRECT) return fail(MFEM_EINVAL, "bad launch mode");
     if (o.tile_rows != 0 && !pcg_tile_supported(o.tile_rows))
         return fail(MFEM_EINVAL, "tile_rows must be 0, 64, 128 or 256");
+    if (o.spmv_split < 0 || o.spmv_split > 2) return fail(MFEM_EINVAL, "spmv_split must be 0, 1 or 2");
     if (o.coarse_agg != 0 && (o.coarse_agg < kCoarseUnit || (o.coarse_agg & (o.coarse_agg - 1)) != 0 ||
                               o.coarse_agg > (1 << 24)))
         return fail(MFEM_EINVAL, "coarse_agg must be 0 or a power of two >= 64");
@@ -1270,6 +1288,7 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
     c->model = mat->model;
     c->slot.prec = o.precision == MFEM_MIXED ? 1 : 0;
     c->tile_rows = o.tile_rows;
+    c->spmv_split = o.spmv_split;
     const Plan& P = c->plan;
     if (cudaGetDevice(&c->device) != cudaSuccess) return fail(MFEM_ECUDA, "no CUDA device");
     if (cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking) != cudaSuccess)

@@ -92,7 +92,8 @@ struct mfem_ctx {
     int fext_sets = 0;
     unsigned* diag_host = nullptr;
     unsigned* cerr_host = nullptr;   // pinned copy of mesh.coarse_err, read with the problem scalars
-    int tile_rows = 0;       // PCG rows per block
+    int tile_rows = 0;       // SpMV rows per block (0: autotune)
+    int spmv_split = 0;      // SpMV threads per row, 1 or 2 (0: autotune)
     int grid_blocks = 0;
     bool pose_set = false;
     // per slot: 0 = x holds no start, 1 = x is the solution of the pose in

@@ -253,8 +253,15 @@ __device__ __forceinline__ int unit_problem(const PcgDesc<T>* __restrict__ D, in
 // kernel: it is latency-bound on its dependent col -> neighbour loads.  The
 // FP64 kernel is bound by the FP64 pipe and takes half that occupancy for the
 // registers its double accumulators need (no spills).
-template <typename T, int TILE>
-__global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 2048 : 1024) / TILE)
+//
+// SPLIT = threads per row.  SPLIT = 1: lane l of a warp takes row l of its
+// 32-row slice and walks all the row's slots.  SPLIT = 2: a warp takes 16 rows
+// of a slice, lanes l and l + 16 the even and odd slots of row l (each warp
+// load still covers whole 32-byte sectors: 16 lanes read 64 consecutive
+// bytes), so each thread's dependent chain is half as long; the two halves
+// are added with one shuffle.  The autotuner picks the tile and SPLIT.
+template <typename T, int TILE, int SPLIT>
+__global__ void __launch_bounds__(TILE * SPLIT, (sizeof(T) == 4 ? 2048 : 1024) / (TILE * SPLIT))
     k_pcg_spmv(const PcgDesc<T>* __restrict__ D, int n_probs) {
     // prologue on data no kernel of the iteration writes (the descriptor table
     // and the matrix structure), overlapping the previous kernel's drain
@@ -262,9 +269,14 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 2048 : 1024) / TILE)
     const PcgDesc<T>& d = D[unit_problem(D, n_probs, u)];
     ProbScal* sc = d.sc;
     const int tile = u - d.unit_begin;
-    const int row = tile * TILE + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // row of this thread and its first slot (parity) within the row
+    const int half = SPLIT == 2 ? (lane >> 4) : 0;
+    const int rs = SPLIT == 2 ? ((warp & 1) << 4) + (lane & 15) : lane;   // row within the slice
+    const int row = tile * TILE + (SPLIT == 2 ? (warp >> 1) * 32 : warp * 32) + rs;
+    const bool valid = row < d.n_rows;
     int base = 0, w = 0;
-    if (row < d.n_rows) {
+    if (valid) {
         const int s = row >> 5;
         base = __ldg(d.slice_ptr + s);
         w = (__ldg(d.slice_ptr + s + 1) - base) >> 5;
@@ -272,41 +284,42 @@ __global__ void __launch_bounds__(TILE, (sizeof(T) == 4 ? 2048 : 1024) / TILE)
     pdl_wait();
     pdl_trigger();
     if (sc->state != kActive) return;
-    double v[3] = {0.0, 0.0, 0.0};
-    if (row < d.n_rows) {
-        const int lane = row & 31;
-        T a0 = 0, a1 = 0, a2 = 0;
+    T a0 = 0, a1 = 0, a2 = 0;
 #pragma unroll 4
-        for (int k = 0; k < w; ++k) {
-            const int g = base + (k << 5);
-            const int c = __ldcs(d.col + g + lane);
-            if (c >= 0) {
-                const T* vv = d.val + (size_t)g * 9 + lane;
-                T q[3];
-                ld4(d.nb + 4 * (size_t)c, q);
-                a0 += __ldcs(vv) * q[0] + __ldcs(vv + 32) * q[1] + __ldcs(vv + 64) * q[2];
-                a1 += __ldcs(vv + 96) * q[0] + __ldcs(vv + 128) * q[1] + __ldcs(vv + 160) * q[2];
-                a2 += __ldcs(vv + 192) * q[0] + __ldcs(vv + 224) * q[1] + __ldcs(vv + 256) * q[2];
-            }
+    for (int k = half; k < w; k += SPLIT) {
+        const int g = base + (k << 5);
+        const int c = __ldcs(d.col + g + rs);
+        if (c >= 0) {
+            const T* vv = d.val + (size_t)g * 9 + rs;
+            T q[3];
+            ld4(d.nb + 4 * (size_t)c, q);
+            a0 += __ldcs(vv) * q[0] + __ldcs(vv + 32) * q[1] + __ldcs(vv + 64) * q[2];
+            a1 += __ldcs(vv + 96) * q[0] + __ldcs(vv + 128) * q[1] + __ldcs(vv + 160) * q[2];
+            a2 += __ldcs(vv + 192) * q[0] + __ldcs(vv + 224) * q[1] + __ldcs(vv + 256) * q[2];
         }
-        // epilogue with short live ranges (the kernel runs at 32 registers):
-        // each partial is reduced over the warp as soon as it is formed
-        T ur[3];
-        ld4(d.nb + 4 * (size_t)row, ur);
-        T* rec = d.rec + kRec * (size_t)row;
-        st4(rec + kRecW, a0, a1, a2);
-        v[1] = warp_sum_partial(dot3_partial(a0, a1, a2, ur[0], ur[1], ur[2]));
-        T r[3];
-        ld4(rec + kRecR, r);
-        v[0] = warp_sum_partial(dot3_partial(r[0], r[1], r[2], ur[0], ur[1], ur[2]));
-        v[2] = warp_sum_partial(dot3_partial(r[0], r[1], r[2], r[0], r[1], r[2]));
-    } else {
-        // rows past the end still take part in the warp sums (all lanes shuffle)
-        const Partial<T> z = Partial<T>::zero();
-        v[1] = warp_sum_partial(z);
-        v[0] = warp_sum_partial(z);
-        v[2] = warp_sum_partial(z);
     }
+    if (SPLIT == 2) {   // the odd slots' half (lanes 16-31) into the even half
+        a0 += __shfl_xor_sync(0xffffffffu, a0, 16);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, 16);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, 16);
+    }
+    // epilogue at uniform control flow with short live ranges (the kernel runs
+    // at 32 registers): each partial is reduced over the warp as soon as it is
+    // formed; rows past the end and the second half of a split row add zeros
+    const bool owner = valid && half == 0;
+    if (!owner) a0 = a1 = a2 = 0;
+    T ur[3] = {0, 0, 0};
+    T* rec = d.rec + kRec * (size_t)row;
+    if (owner) {
+        ld4(d.nb + 4 * (size_t)row, ur);
+        st4(rec + kRecW, a0, a1, a2);
+    }
+    double v[3];
+    v[1] = warp_sum_partial(dot3_partial(a0, a1, a2, ur[0], ur[1], ur[2]));
+    T r[3] = {0, 0, 0};
+    if (owner) ld4(rec + kRecR, r);
+    v[0] = warp_sum_partial(dot3_partial(r[0], r[1], r[2], ur[0], ur[1], ur[2]));
+    v[2] = warp_sum_partial(dot3_partial(r[0], r[1], r[2], r[0], r[1], r[2]));
     double tot[3];
     if (tile_commit<3>(v, d.part, tile, d.n_tiles, &sc->tk_a, 0, tot, true) && threadIdx.x == 0) {
         const double gamma = tot[0], delta = tot[1];
@@ -583,7 +596,7 @@ __global__ void __launch_bounds__(TILE) k_pcg_correct(const PcgDesc<T>* __restri
 
 // Each launch may start while the previous kernel of the stream drains
 // (programmatic stream serialization); the kernels wait on it first thing.
-template <typename T, int TILE>
+template <typename T, int TILE, int SPLIT>
 cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units, int n_units_u, int iters,
                                const CoarseJob* jobs, int n_jobs, cudaStream_t s) {
     cudaLaunchAttribute attr[1];
@@ -599,6 +612,8 @@ cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units
     cudaLaunchConfig_t cfg_u = cfg;   // row-local kernels: their own fixed tile
     cfg_u.gridDim = dim3(n_units_u);
     cfg_u.blockDim = dim3(kRowTileU);
+    cudaLaunchConfig_t cfg_s = cfg;   // the SpMV: SPLIT threads per row
+    cfg_s.blockDim = dim3(TILE * SPLIT);
     for (int i = 0; i < iters; ++i) {
         cudaError_t e;
         if (n_jobs > 0) {   // two-level: finish z of the current residual first
@@ -631,7 +646,7 @@ cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units
             e = cudaLaunchKernelEx(&cfg_u, k_pcg_correct<T, kRowTileU>, descs, n_probs);
             if (e != cudaSuccess) return e;
         }
-        e = cudaLaunchKernelEx(&cfg, k_pcg_spmv<T, TILE>, descs, n_probs);
+        e = cudaLaunchKernelEx(&cfg_s, k_pcg_spmv<T, TILE, SPLIT>, descs, n_probs);
         if (e != cudaSuccess) return e;
         e = cudaLaunchKernelEx(&cfg_u, k_pcg_update<T, kRowTileU>, descs, n_probs);
         if (e != cudaSuccess) return e;
@@ -650,13 +665,18 @@ void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int m
 
 template <typename T>
 cudaError_t launch_pcg_iters(const PcgDesc<T>* descs, int n_probs, int n_units, int n_units_u, int tile_rows,
-                             int iters, const CoarseJob* jobs, int n_jobs, cudaStream_t s) {
-    switch (tile_rows) {
-        case 64: return launch_pcg_iters_t<T, 64>(descs, n_probs, n_units, n_units_u, iters, jobs, n_jobs, s);
-        case 128: return launch_pcg_iters_t<T, 128>(descs, n_probs, n_units, n_units_u, iters, jobs, n_jobs, s);
-        case 256: return launch_pcg_iters_t<T, 256>(descs, n_probs, n_units, n_units_u, iters, jobs, n_jobs, s);
-        default: return cudaErrorInvalidValue;
-    }
+                             int split, int iters, const CoarseJob* jobs, int n_jobs, cudaStream_t s) {
+#define MFEM_PCG_CASE(TR, SP)                                                                                  \
+    if (tile_rows == TR && split == SP)                                                                        \
+        return launch_pcg_iters_t<T, TR, SP>(descs, n_probs, n_units, n_units_u, iters, jobs, n_jobs, s);
+    MFEM_PCG_CASE(64, 1)
+    MFEM_PCG_CASE(128, 1)
+    MFEM_PCG_CASE(256, 1)
+    MFEM_PCG_CASE(64, 2)
+    MFEM_PCG_CASE(128, 2)
+    MFEM_PCG_CASE(256, 2)
+#undef MFEM_PCG_CASE
+    return cudaErrorInvalidValue;
 }
 
 bool pcg_tile_supported(int tile_rows) { return tile_rows == 64 || tile_rows == 128 || tile_rows == 256; }
@@ -677,9 +697,9 @@ cudaError_t launch_coarse_only(const PcgDesc<float>* descs, int n_probs, const C
                               job->nd);
 }
 
-template cudaError_t launch_pcg_iters<float>(const PcgDesc<float>*, int, int, int, int, int, const CoarseJob*,
+template cudaError_t launch_pcg_iters<float>(const PcgDesc<float>*, int, int, int, int, int, int, const CoarseJob*,
                                              int, cudaStream_t);
-template cudaError_t launch_pcg_iters<double>(const PcgDesc<double>*, int, int, int, int, int, const CoarseJob*,
-                                              int, cudaStream_t);
+template cudaError_t launch_pcg_iters<double>(const PcgDesc<double>*, int, int, int, int, int, int,
+                                              const CoarseJob*, int, cudaStream_t);
 
 }  // namespace mfem

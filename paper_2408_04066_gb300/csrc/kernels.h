@@ -139,10 +139,11 @@ struct CoarseJob {
     int N, d0, nd, agg_units;   // agg_units: 64-row units per aggregate
 };
 // n_units: SpMV tiles (tile_rows rows) over all problems; n_units_u: the
-// update and correction kernels' tiles (kRowTileU rows).
+// update and correction kernels' tiles (kRowTileU rows); split: SpMV threads
+// per row (1 or 2).
 template <typename T>
 cudaError_t launch_pcg_iters(const PcgDesc<T>* descs_dev, int n_probs, int n_units, int n_units_u, int tile_rows,
-                             int iters, const CoarseJob* jobs, int n_jobs, cudaStream_t s);
+                             int split, int iters, const CoarseJob* jobs, int n_jobs, cudaStream_t s);
 bool pcg_tile_supported(int tile_rows);
 
 // Coarse space set-up: A_c = P^T K P of the assembled matrix `val` (problem 0 of

@@ -355,8 +355,12 @@ mfem_status mfem_server_add(mfem_server* s, mfem_ctx* c, int32_t* mesh_id) {
     }
     cudaStreamSynchronize(c->stream);
     c->stream = s->stream;
-    if (c->tile_rows == 0) c->tile_rows = 256;   // one tile for every mesh in a shared launch
-    if (!s->meshes.empty()) c->tile_rows = s->meshes[0].owner()->tile_rows;
+    if (c->tile_rows == 0) c->tile_rows = 256;   // one SpMV shape for every mesh in a shared launch
+    if (c->spmv_split == 0) c->spmv_split = 1;
+    if (!s->meshes.empty()) {
+        c->tile_rows = s->meshes[0].owner()->tile_rows;
+        c->spmv_split = s->meshes[0].owner()->spmv_split;
+    }
     c->owned_by_server = true;
     auto p = std::make_unique<Pool>();
     p->ctx = c;

@@ -48,7 +48,7 @@ class Options(C.Structure):
                 ("cg_max", C.c_int32), ("init", C.c_int32), ("max_batch", C.c_int32),
                 ("tile_rows", C.c_int32), ("diagnostics", C.c_int32), ("rotation", C.c_int32),
                 ("precond", C.c_int32), ("launch", C.c_int32), ("coarse_agg", C.c_int32),
-                ("coarse_product", C.c_int32)]
+                ("spmv_split", C.c_int32), ("coarse_product", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -67,7 +67,7 @@ class Profile(C.Structure):
                 ("element_ms", C.c_double), ("element_bytes", C.c_double), ("assemble_ms", C.c_double),
                 ("linesearch_ms", C.c_double), ("total_ms", C.c_double), ("tile_rows", C.c_int32),
                 ("grid_blocks", C.c_int32), ("element_updates", C.c_int64), ("coarse_dof", C.c_int32),
-                ("coarse_launches", C.c_int32), ("coarse_tc", C.c_int32)]
+                ("coarse_launches", C.c_int32), ("coarse_tc", C.c_int32), ("spmv_split", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
