@@ -151,9 +151,7 @@ typedef struct {
                             aggregates of consecutive (Morton-ordered) vertices,
                             its matrix the rest-shape Hessian's, inverted once per
                             mesh and turned per pose with each aggregate's handle
-                            rotation; used from the second Newton step of a pose
-                            (the first step from the rigid guess, whose residual
-                            sits at the cluster boundaries, uses block Jacobi).
+                            rotation; used on every Newton step.
                             MFEM_PRECOND_BLOCK_JACOBI: block Jacobi only */
     int32_t launch;      /* MFEM_LAUNCH_GRAPH (default): each chunk of PCG iterations
                             is captured once per set of launch parameters as a CUDA

@@ -26,7 +26,6 @@ struct ProbHost {
     int converged = 0;
     int pred = 0;        // co-rotational predictor step pending (SNH, COROT or WARM init)
     int corr = 0;        // after the predictor, add the last solve's rotated correction (WARM)
-    int rigid_start = 0; // the first Newton step starts from the rigid guess (block Jacobi for it)
     int coarse = 0;      // the current PCG solve uses the two-level preconditioner
     int expect_conv = 0; // the current step was solved to just reach newton_tol: test the next
                          // iterate with forces only (no element Hessian, no matrix)
