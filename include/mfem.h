@@ -150,8 +150,11 @@ typedef struct {
                             additive coarse correction on the six rigid modes of
                             aggregates of consecutive (Morton-ordered) vertices,
                             its matrix the rest-shape Hessian's, inverted once per
-                            mesh and turned per pose with each aggregate's handle
-                            rotation; used on every Newton step.
+                            mesh; before every solve each aggregate's modes are
+                            turned by the rotation fitted to its vertices'
+                            current positions (polar factor of sum x_i (X_i -
+                            c)^T; its handle's rotation where that has none);
+                            used on every Newton step.
                             MFEM_PRECOND_BLOCK_JACOBI: block Jacobi only */
     int32_t launch;      /* MFEM_LAUNCH_GRAPH (default): each chunk of PCG iterations
                             is captured once per set of launch parameters as a CUDA

@@ -78,8 +78,7 @@ struct PcgDesc {
     int n_tiles_u;                     // the row-local kernels' tiles (kRowTileU rows per block)
     // two-level preconditioner (coarse = 0: block Jacobi only for this solve)
     const float4* crel;    // [n] rest offset from the aggregate centroid, w = 1 free / 0 pin
-    const int* agg_handle; // [n_agg]
-    const double* xf;      // [H][12] the problem's pose
+    const float* aggq;     // [n_agg][9] the problem's aggregate rotations (row-major)
     float* rcp;            // [ceil(n/64)][6] restriction partials per 64-row unit
     float* rcs;            // [coarse_n] per-aggregate sums of rcp (aggregates over 64 rows)
     const float* rc;       // the coarse residual read by the coarse product: rcp or rcs

@@ -88,7 +88,8 @@ mfem_status upload(mfem_ctx* c, U** dst, const U* src, size_t count) {
 
 void free_slots(mfem_ctx* c) {
     SlotDev& S = c->slot;
-    void* ptrs[] = {S.xf, S.xf_prev, S.xpred, S.dcorr, S.tol2, S.coarse_on, S.rcp, S.ec, S.rcs, S.x, S.xprev, S.xp,
+    void* ptrs[] = {S.xf, S.xf_prev, S.xpred, S.dcorr, S.tol2, S.coarse_on, S.rcp, S.ec, S.rcs, S.aggq, S.x, S.xprev,
+                    S.xp,
                     S.g, S.ge, S.Ke, S.val, S.dinv, S.vec, S.part, S.sc, S.active, S.alpha, S.outbuf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -113,7 +114,8 @@ size_t bytes_per_slot(const mfem_ctx* c) {
     return H * 12 * 8 + 4 * n * 3 * 8 + m * 12 * 8 + m * kKe * kt + slots * 9 * kt + n * 9 * kt +
            kVecStride * npad32((int)n) * kt + (size_t)part_tiles_for(c) * 4 * 8 + sizeof(ProbScal) + 4 + 8 + 8 +
            H * 12 * 8 + (c->opt.init == MFEM_INIT_WARM ? 2 * n * 3 * 8 : 0) + 4 + (line_search(c) ? n * 3 * 8 : 0) +
-           (c->mesh.coarse_n > 0 ? ((n + 255) / 256) * 24 * 4 + (coarse_ks(c) + 1) * c->mesh.coarse_n * 4 + 128 : 0);
+           (c->mesh.coarse_n > 0 ? ((n + 255) / 256) * 24 * 4 + (coarse_ks(c) + 1) * c->mesh.coarse_n * 4 + 128 +
+                                        (size_t)c->mesh.n_agg * 9 * 4 : 0);
 }
 
 mfem_status alloc_slots(mfem_ctx* c, int B) {
@@ -158,6 +160,7 @@ mfem_status alloc_slots(mfem_ctx* c, int B) {
         AL(S.ec, B * coarse_ks(c) * c->mesh.coarse_n * sizeof(float));
         S.rcs_stride = ((size_t)c->mesh.coarse_n + 31) & ~(size_t)31;
         AL(S.rcs, B * S.rcs_stride * sizeof(float));
+        AL(S.aggq, B * (size_t)c->mesh.n_agg * 9 * sizeof(float));
     }
 #undef AL
     CK(cudaMemset(S.sc, 0, B * sizeof(ProbScal)));
@@ -301,8 +304,7 @@ void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc
             d.unit_begin_u = units_u;
             d.coarse = g.ph[b].coarse && c->mesh.coarse_n > 0;
             d.crel = c->mesh.crel;
-            d.agg_handle = c->mesh.agg_handle;
-            d.xf = c->slot.xf + (size_t)b * c->plan.H * 12;
+            d.aggq = c->slot.aggq ? c->slot.aggq + (size_t)b * c->mesh.n_agg * 9 : nullptr;
             d.rcp = c->slot.rcp ? c->slot.rcp + (size_t)b * c->slot.rcp_stride : nullptr;
             d.ec = c->slot.ec ? c->slot.ec + (size_t)b * coarse_ks(c) * c->mesh.coarse_n : nullptr;
             d.rcs = c->slot.rcs ? c->slot.rcs + (size_t)b * c->slot.rcs_stride : nullptr;
@@ -892,6 +894,10 @@ mfem_status advance(std::vector<Group>& gs) {
             }
             st = upload_ints(gc, g.B, co.data(), gc->slot.coarse_on);
             if (st != MFEM_OK) return st;
+            if (any_of(co)) {   // the coarse modes' rotations for these iterates (active = start)
+                launch_agg_rotations(elem_args(gc), g.B, s);
+                gc->prof.launches++;
+            }
             launch_pcg_init(elem_args(gc), g.B, c->tile_rows, 0.0, gc->opt.cg_max, gc->slot.tol2,
                             gc->slot.coarse_on, s);
             gc->prof.launches++;

@@ -11,10 +11,10 @@
 // FP64 by Gauss-Jordan elimination without pivoting (A_c is SPD); a mode whose
 // pivot falls below 1e-10 of its own diagonal (an aggregate with too few free
 // vertices to carry it) is dropped, its row and column zero in the inverse.
-// The inverse is kept in FP32, symmetrised.  During a solve the aggregate's
-// modes are turned with the rotation of its handle (the coarse matrix of a
-// rigidly turned region is the rest one in turned coordinates), so the rest
-// inverse serves every pose.
+// The inverse is kept in FP32, symmetrised.  During a solve each aggregate's
+// modes are turned with a rotation fitted to the aggregate's current motion
+// (k_agg_rotations; the coarse matrix of a rigidly turned region is the rest
+// one in turned coordinates), so the rest inverse serves every pose.
 #include <cuda_runtime.h>
 
 #include "kernels.h"
@@ -135,7 +135,104 @@ __global__ void k_sym_f32(const double* __restrict__ A, int N, int ld, float* __
     out[(size_t)i * ld + j] = j < N ? (float)(0.5 * (A[(size_t)i * N + j] + A[(size_t)j * N + i])) : 0.f;
 }
 
+// Orthogonal polar factor of M by Higham's scaled Newton iteration
+// X <- (gamma X + X^{-T} / gamma) / 2 (N. J. Higham, "Computing the polar
+// decomposition -- with applications", SIAM J. Sci. Stat. Comput. 1986), in
+// FP32 (the rotation turns a preconditioner's coarse modes; it needs no more).
+// Returns false if M is singular or not of positive determinant (no rotation).
+__device__ bool polar_rotation_pos(const float (&M)[3][3], float (&R)[3][3]) {
+    float X[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) X[i][j] = M[i][j];
+    for (int it = 0; it < 12; ++it) {
+        const float c00 = X[1][1] * X[2][2] - X[1][2] * X[2][1], c01 = X[1][2] * X[2][0] - X[1][0] * X[2][2],
+                    c02 = X[1][0] * X[2][1] - X[1][1] * X[2][0];
+        const float c10 = X[0][2] * X[2][1] - X[0][1] * X[2][2], c11 = X[0][0] * X[2][2] - X[0][2] * X[2][0],
+                    c12 = X[0][1] * X[2][0] - X[0][0] * X[2][1];
+        const float c20 = X[0][1] * X[1][2] - X[0][2] * X[1][1], c21 = X[0][2] * X[1][0] - X[0][0] * X[1][2],
+                    c22 = X[0][0] * X[1][1] - X[0][1] * X[1][0];
+        const float det = X[0][0] * c00 + X[0][1] * c01 + X[0][2] * c02;
+        if (!(det > 0.f)) return false;
+        const float id = 1.f / det;
+        const float IT[3][3] = {{c00 * id, c01 * id, c02 * id}, {c10 * id, c11 * id, c12 * id},
+                                {c20 * id, c21 * id, c22 * id}};   // X^{-T}
+        float nx = 0.f, ni = 0.f;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                nx += X[i][j] * X[i][j];
+                ni += IT[i][j] * IT[i][j];
+            }
+        const float gam = sqrtf(sqrtf(ni / nx));
+        float diff = 0.f;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) {
+                const float y = 0.5f * (gam * X[i][j] + IT[i][j] / gam);
+                diff += (y - X[i][j]) * (y - X[i][j]);
+                X[i][j] = y;
+            }
+        if (diff <= 1e-12f) break;
+    }
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) R[i][j] = X[i][j];
+    return true;
+}
+
+// One warp per (aggregate, problem): R_a = the rotation of the polar
+// decomposition of M = sum_i x_i (X_i - c_a)^T over the aggregate's free
+// vertices (shape matching: for x_i = R (X_i - c_a) + t, M = R S with S
+// symmetric positive definite, so the fit is R exactly; sum_i (X_i - c_a) = 0
+// makes the translation drop out).  M is summed in FP64 (x carries the
+// aggregate's absolute position), the polar factor taken in FP32.  When M has
+// no rotation factor (an aggregate without enough free vertices, or inverted),
+// R_a is the rotation of the aggregate's majority handle.  The coarse modes of
+// the two-level preconditioner are turned by R_a, so they follow each
+// aggregate's own motion -- also at cluster boundaries, where the handle's
+// rotation does not.
+__global__ void __launch_bounds__(32) k_agg_rotations(ElemArgs A) {
+    const int a = blockIdx.x, b = blockIdx.y, lane = threadIdx.x;
+    if (!A.slot.active[b]) return;   // warp-uniform
+    const MeshDev& M = A.mesh;
+    const int size = 1 << M.agg_shift;
+    const int i0 = a * size, i1 = min(M.n, i0 + size);
+    const double* x = A.slot.x + (size_t)b * M.n * 3;
+    double m[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) m[e] = 0.0;
+    for (int i = i0 + lane; i < i1; i += 32) {
+        const float4 r = M.crel[i];
+        if (r.w == 0.f) continue;
+        const double xi[3] = {x[3 * (size_t)i], x[3 * (size_t)i + 1], x[3 * (size_t)i + 2]};
+        const double ri[3] = {r.x, r.y, r.z};
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) m[3 * p + q] = fma(xi[p], ri[q], m[3 * p + q]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int e = 0; e < 9; ++e) m[e] += __shfl_xor_sync(0xffffffffu, m[e], o);
+    if (lane == 0) {
+        const float Mm[3][3] = {{(float)m[0], (float)m[1], (float)m[2]},
+                                {(float)m[3], (float)m[4], (float)m[5]},
+                                {(float)m[6], (float)m[7], (float)m[8]}};
+        float R[3][3];
+        float* out = A.slot.aggq + ((size_t)b * M.n_agg + a) * 9;
+        if (polar_rotation_pos(Mm, R)) {
+            for (int e = 0; e < 9; ++e) out[e] = R[e / 3][e % 3];
+        } else {
+            const double* T = A.slot.xf + (size_t)b * M.H * 12 + 12 * (size_t)M.agg_handle[a];
+            for (int e = 0; e < 9; ++e) out[e] = (float)T[4 * (e / 3) + e % 3];
+        }
+    }
+}
+
 }  // namespace
+
+void launch_agg_rotations(const ElemArgs& a, int B, cudaStream_t s) {
+    if (a.mesh.n_agg <= 0) return;
+    k_agg_rotations<<<dim3(a.mesh.n_agg, B), 32, 0, s>>>(a);
+}
 
 cudaError_t build_coarse_inverse(const MeshDev& M, const void* val, int prec, const int* cnb_ptr, const int* cnb,
                                  int cnb_max, int agg_size, float* Ainv, cudaStream_t s) {

@@ -16,20 +16,20 @@ namespace mfem {
 
 namespace {
 
-// Pose rotations of the aggregates a block of rows from row0 touches (blocks
-// hold <= 256 rows, so <= 4 aggregates) into qs; threads 0..35 load, the caller
+// Rotations of the aggregates a block of rows from row0 touches (blocks hold
+// <= 256 rows, so <= 4 aggregates) into qs; threads 0..35 load, the caller
 // synchronises (restrict_units does).
-__device__ __forceinline__ void stage_rotations(float (*qs)[9], int row0, const int* __restrict__ agg_handle,
-                                                const double* __restrict__ xf, int agg_shift, int n_agg) {
+__device__ __forceinline__ void stage_rotations(float (*qs)[9], int row0, const float* __restrict__ aggq,
+                                                int agg_shift, int n_agg) {
     const int a0 = row0 >> agg_shift;
     if (threadIdx.x < 36) {
         const int ai = threadIdx.x / 9, e = threadIdx.x % 9, a = a0 + ai;
-        qs[ai][e] = a < n_agg ? (float)xf[12 * agg_handle[a] + 4 * (e / 3) + e % 3] : 0.f;
+        qs[ai][e] = a < n_agg ? aggq[9 * a + e] : 0.f;
     }
 }
 
 // Coarse residual of the rows of one block: y_i = Q_a^T r_i (the aggregate's
-// pose rotation undone, Q staged by stage_rotations), contribution
+// rotation undone, Q staged by stage_rotations), contribution
 // P_i^T y_i = (y_i, (X_i - c_a) x y_i) of a free row, summed per 64-row unit
 // (two warps: shuffle sums, then the pair in fixed order) and written to
 // rcp_block[6 u + c].  Every thread of the block calls it; rows past the end
@@ -212,8 +212,7 @@ __global__ void k_pcg_init(ElemArgs A, double tol2, int maxit, const double* __r
     if (coarse) {
         __shared__ float qs[4][9];
         const int row0 = (int)(blockIdx.x * blockDim.x);
-        stage_rotations(qs, row0, A.mesh.agg_handle, A.slot.xf + (size_t)b * A.mesh.H * 12, A.mesh.agg_shift,
-                        A.mesh.n_agg);
+        stage_rotations(qs, row0, A.slot.aggq + (size_t)b * A.mesh.n_agg * 9, A.mesh.agg_shift, A.mesh.n_agg);
         restrict_units(r32, row < n, row, row0, A.mesh.crel, qs, A.mesh.agg_shift,
                        A.slot.rcp + (size_t)b * A.slot.rcp_stride + 6 * ((size_t)row0 / kCoarseRows));
     }
@@ -354,13 +353,13 @@ __global__ void __launch_bounds__(TILE * SPLIT, (sizeof(T) == 4 ? 2048 : 1024) /
 template <typename T, int TILE>
 __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restrict__ D, int n_probs) {
     __shared__ float qs[4][9];
-    const int u = blockIdx.x;   // prologue: descriptor and pose rotations (fixed during the solve)
+    const int u = blockIdx.x;   // prologue: descriptor and aggregate rotations (fixed during the solve)
     const PcgDesc<T>& d = D[unit_problem<true>(D, n_probs, u)];
     ProbScal* sc = d.sc;
     const int tile = u - d.unit_begin_u;
     const int row = tile * TILE + threadIdx.x;
     const bool coarse = d.coarse != 0;
-    if (coarse) stage_rotations(qs, tile * TILE, d.agg_handle, d.xf, d.agg_shift, d.coarse_n / 6);
+    if (coarse) stage_rotations(qs, tile * TILE, d.aggq, d.agg_shift, d.coarse_n / 6);
     pdl_wait();
     pdl_trigger();
     if (sc->state != kActive) return;   // block-uniform
@@ -528,7 +527,7 @@ __global__ void __launch_bounds__(256) k_coarse_gemm(const float* __restrict__ A
 }
 
 // u_i = zb_i + Q_a P_i e_a (e_a = the six coarse values of row i's aggregate,
-// e_t + e_w x (X_i - c_a) turned by the pose rotation of the aggregate), written
+// e_t + e_w x (X_i - c_a) turned by the aggregate's rotation), written
 // to the neighbour record the next k_pcg_spmv gathers.  The block first gathers
 // the slice partials of e of its aggregates (added in slice order) and their
 // rotations into shared memory.  Problems without the coarse correction return
@@ -554,7 +553,7 @@ __global__ void __launch_bounds__(TILE) k_pcg_correct(const PcgDesc<T>* __restri
     if (row < d.n_rows) off = d.crel[row];
     if ((int)threadIdx.x < kMaxAgg * 9) {
         const int ai = threadIdx.x / 9, q = threadIdx.x % 9, a = a0 + ai;
-        qs[ai][q] = a < n_agg ? (float)d.xf[12 * d.agg_handle[a] + 4 * (q / 3) + q % 3] : 0.f;
+        qs[ai][q] = a < n_agg ? d.aggq[9 * a + q] : 0.f;
     }
     pdl_wait();
     pdl_trigger();

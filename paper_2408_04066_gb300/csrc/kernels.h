@@ -68,6 +68,7 @@ struct SlotDev {
     float* rcp = nullptr;    // [B][rcp_stride] restriction partials (6 floats per 64-row unit)
     float* ec = nullptr;     // [B][ceil(coarse_n / kCoarseKC)][coarse_n] partial coarse corrections
     float* rcs = nullptr;    // [B][rcs_stride] per-aggregate coarse residual (aggregates over 64 rows)
+    float* aggq = nullptr;   // [B][n_agg][9] rotation of each aggregate's coarse modes for the current solve
     size_t rcs_stride = 0;
     size_t rcp_stride = 0;
     double* outbuf = nullptr;  // [B][n][3] caller-order staging
@@ -119,6 +120,10 @@ void launch_unpermute(const ElemArgs& a, int B, double* out, cudaStream_t s);
 void launch_permute_in(const ElemArgs& a, int b, const double* xin, cudaStream_t s);
 // element outputs (s, lambda) in caller tet order for problem b
 void launch_elem_out(const ElemArgs& a, int b, double* s_out, double* lam_out, cudaStream_t s);
+// two-level preconditioner: the rotation of each aggregate's coarse modes for
+// the problems' current iterates (shape matching; the handle's rotation when
+// the aggregate's deformation has no rotation factor)
+void launch_agg_rotations(const ElemArgs& a, int B, cudaStream_t s);
 // diagnostics: inverted count, max rel skew, max angle for problem b
 void launch_diag(const ElemArgs& a, int b, unsigned* out3, cudaStream_t s);
 
