@@ -185,6 +185,23 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
+def pcg_traffic(tr, pose_iters, coarse_launches, pairs):
+    """DRAM bytes per PCG launch pair from the ncu record: the row kernels'
+    bytes per pose-iteration times the pose-iterations, plus the coarse
+    product's bytes per launch (one launch serves every pose of a mesh) times
+    its launches, over the launch pairs."""
+    if not tr:
+        return None
+    return (tr["row_dram_bytes_per_pose_iteration"] * pose_iters
+            + tr["coarse_dram_bytes_per_launch"] * coarse_launches) / pairs
+
+
+TRAFFIC_NOTE = ("ncu dram__bytes_read+write of one two-level iteration (k_coarse_tc, k_pcg_correct, k_pcg_spmv, "
+                "k_pcg_update) on the profiling case (8 poses of this mesh): the row kernels' bytes per "
+                "pose-iteration and the coarse product's per launch, scaled by this run's pose-iterations and "
+                "coarse launches per launch pair")
+
+
 def pcg_traffic_record(mesh=None):
     """DRAM bytes per pose-iteration of the PCG kernels from the committed ncu
     summary (profiles/pcg_traffic.json), if it was taken on the current kernel
@@ -457,10 +474,8 @@ def run_mfem(args, dist):
     roof = {"kernel": PCG_KERNELS, "bound": "hbm", "achieved": achieved,
             "peak": peak, "peak_source": f"{peak_kind} hbm_gbs (copy, burst)", "unit": "GB/s",
             "frac": achieved / peak,
-            "traffic": (tr["dram_bytes_per_pose_iteration"] * pcg_pose_iters / pairs if tr else None),
-            "traffic_note": ("ncu dram__bytes_read+write of one k_pcg_spmv and one k_pcg_update launch on the "
-                             "profiling case, per pose-iteration, times pose-iterations per launch pair here"
-                             if tr else "no ncu record for the current kernel source"),
+            "traffic": pcg_traffic(tr, pcg_pose_iters, sum(p["coarse_launches"] for p in prof), pairs),
+            "traffic_note": TRAFFIC_NOTE if tr else "no ncu record for the current kernel source",
             "algorithmic_bytes_per_launch_pair": pcg_bytes / pairs,
             "avg_launch_pair_ms": pcg_ms / pairs, "launch_pairs": pairs,
             "pose_iterations_per_pair": pcg_pose_iters / pairs,
@@ -609,7 +624,7 @@ def _roofline(profs, total_ms, mesh):
     return {"kernel": PCG_KERNELS, "bound": "hbm", "achieved": achieved,
             "peak": peak, "peak_source": f"{peak_kind} hbm_gbs (copy, burst)", "unit": "GB/s",
             "frac": achieved / peak,
-            "traffic": tr["dram_bytes_per_pose_iteration"] * iters / pairs if tr else None,
+            "traffic": pcg_traffic(tr, iters, sum(p["coarse_launches"] for p in profs), pairs),
             "algorithmic_bytes_per_launch_pair": pcg_bytes / pairs, "avg_launch_pair_ms": pcg_ms / pairs,
             "launch_pairs": pairs, "pose_iterations_per_pair": iters / pairs,
             "share_of_step": pcg_ms / total_ms if total_ms else None}

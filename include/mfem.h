@@ -194,8 +194,9 @@ typedef struct {
 
 /* Device-side profile of the last solve call, timed with CUDA events on the
  * context's stream.  The dominant work is the PCG iteration: an SpMV+dot
- * kernel and an update kernel per iteration, plus the coarse product and
- * correction kernels on two-level iterations, enqueued in chunks. */
+ * kernel and an update kernel per iteration, plus on two-level iterations one
+ * kernel per mesh for the coarse product and correction (tensor cores), or the
+ * product and a correction kernel (CUDA cores), enqueued in chunks. */
 typedef struct {
     int32_t kernel_launches;  /* all library kernels launched in the call */
     int32_t pcg_launches;     /* SpMV and update launches (two per iteration) */
@@ -316,8 +317,9 @@ mfem_status mfem_get_elem_static(mfem_ctx* ctx, double* s, double* lam);
  * for inspection and tests (not part of the paper's method, §5: the reduced
  * space is the preconditioner's).  rc: host [B][N] FP32 coarse residuals in the
  * coarse basis of mfem_get_info's mesh (N = profile.coarse_dof), e: host
- * [B][N] results e_b = A_c^{-1} rc_b as the solve computes them (slice
- * partials added in slice order).  product: MFEM_COARSE_TC or
+ * [B][N] results e_b = A_c^{-1} rc_b as the solve computes them (on the
+ * tensor cores: the full K range accumulated in tensor memory; on the CUDA
+ * cores: slice partials added in slice order).  product: MFEM_COARSE_TC or
  * MFEM_COARSE_FP32.  Allocates and frees device memory during the call.
  * MFEM_EINVAL if the context has no coarse space or B < 1. */
 mfem_status mfem_coarse_apply(mfem_ctx* ctx, const float* rc, int32_t B, float* e, int32_t product);

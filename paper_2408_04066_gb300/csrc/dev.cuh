@@ -8,6 +8,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace mfem {
@@ -63,6 +64,35 @@ constexpr int kCoarseRowPasses = 1;   // 32-row passes per block of the coarse p
 // row stride of the stored A_c^{-1} (rows padded with zeros to 32 floats)
 __host__ __device__ __forceinline__ int coarse_ld(int N) { return (N + 31) & ~31; }
 
+// B operand of the tensor-core coarse product, per group of kCoarseGroupSlots
+// request slots of a context: each slot's coarse residual r_c split exactly
+// into three BF16 parts (r = hi + mid + lo, 3 x 8 significand bits) that are
+// rows p, 16 + p, 32 + p (p = slot mod 16) of an N = 48 operand, stored per
+// chunk of kTcKC columns in the MMA's no-swizzle K-major core-matrix layout
+// (K step of 16 columns: 1536 bytes; 8-row group: 256 bytes; K-adjacent core
+// matrices 128 bytes apart; row: 16 bytes), so that one 1-D bulk copy lands
+// a whole chunk.  Columns past N stay zero.
+constexpr int kTcKC = 128;
+constexpr int kCoarseGroupSlots = 16;
+constexpr int kCoarseBRows = 3 * kCoarseGroupSlots;            // 48
+constexpr int kCoarseBChunk = kCoarseBRows * kTcKC;            // elements per chunk
+__host__ __device__ __forceinline__ int coarse_chunks(int N) { return (N + kTcKC - 1) / kTcKC; }
+__host__ __device__ __forceinline__ size_t coarse_b_offset(int row, int k) {
+    const int ch = k / kTcKC, kk = k % kTcKC;
+    const int s = kk >> 4, j2 = (kk >> 3) & 1, c = kk & 7, g = row >> 3, r = row & 7;
+    return (size_t)ch * kCoarseBChunk + s * (kCoarseBRows * 16) + g * 128 + j2 * 64 + r * 8 + c;
+}
+// Store component k of slot p's coarse residual into its group's B operand.
+__device__ __forceinline__ void coarse_b_store(uint16_t* __restrict__ grp, int p, int k, float v) {
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const float r1 = v - __bfloat162float(h);
+    const __nv_bfloat16 m = __float2bfloat16_rn(r1);
+    const __nv_bfloat16 l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+    grp[coarse_b_offset(p, k)] = __bfloat16_as_ushort(h);
+    grp[coarse_b_offset(kCoarseGroupSlots + p, k)] = __bfloat16_as_ushort(m);
+    grp[coarse_b_offset(2 * kCoarseGroupSlots + p, k)] = __bfloat16_as_ushort(l);
+}
+
 // One PCG problem (a pose of a mesh) in a descriptor table.
 template <typename T>
 struct PcgDesc {
@@ -83,6 +113,13 @@ struct PcgDesc {
     float* rcs;            // [coarse_n] per-aggregate sums of rcp (aggregates over 64 rows)
     const float* rc;       // the coarse residual read by the coarse product: rcp or rcs
     float* ec;             // [ceil(coarse_n / kCoarseKC)][coarse_n] partial coarse corrections
+    // tensor-core path: the slot's group of the B operand (null on the CUDA-core
+    // path); the restriction writes it where an aggregate is one 64-row unit
+    // (bunit), else the per-aggregate sum does (bagg)
+    uint16_t* bunit;
+    uint16_t* bagg;
+    int bslot;             // the problem's request slot in its context
+    int ctc;               // 1: coarse product and correction by the fused tensor-core kernel
     int coarse, agg_shift, coarse_n;
     int unit_begin_u;
 };

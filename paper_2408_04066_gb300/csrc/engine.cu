@@ -88,8 +88,8 @@ mfem_status upload(mfem_ctx* c, U** dst, const U* src, size_t count) {
 
 void free_slots(mfem_ctx* c) {
     SlotDev& S = c->slot;
-    void* ptrs[] = {S.xf, S.xf_prev, S.xpred, S.dcorr, S.tol2, S.coarse_on, S.rcp, S.ec, S.rcs, S.aggq, S.x, S.xprev,
-                    S.xp,
+    void* ptrs[] = {S.xf, S.xf_prev, S.xpred, S.dcorr, S.tol2, S.coarse_on, S.rcp, S.ec, S.rcs, S.aggq, S.bsplit,
+                    S.x, S.xprev, S.xp,
                     S.g, S.ge, S.Ke, S.val, S.dinv, S.vec, S.part, S.sc, S.active, S.alpha, S.outbuf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -115,7 +115,9 @@ size_t bytes_per_slot(const mfem_ctx* c) {
            kVecStride * npad32((int)n) * kt + (size_t)part_tiles_for(c) * 4 * 8 + sizeof(ProbScal) + 4 + 8 + 8 +
            H * 12 * 8 + (c->opt.init == MFEM_INIT_WARM ? 2 * n * 3 * 8 : 0) + 4 + (line_search(c) ? n * 3 * 8 : 0) +
            (c->mesh.coarse_n > 0 ? ((n + 255) / 256) * 24 * 4 + (coarse_ks(c) + 1) * c->mesh.coarse_n * 4 + 128 +
-                                        (size_t)c->mesh.n_agg * 9 * 4 : 0);
+                                        (size_t)c->mesh.n_agg * 9 * 4 +
+                                        coarse_b_bytes(c->mesh.coarse_n, kCoarseGroupSlots) / kCoarseGroupSlots
+                                  : 0);
 }
 
 mfem_status alloc_slots(mfem_ctx* c, int B) {
@@ -161,6 +163,8 @@ mfem_status alloc_slots(mfem_ctx* c, int B) {
         S.rcs_stride = ((size_t)c->mesh.coarse_n + 31) & ~(size_t)31;
         AL(S.rcs, B * S.rcs_stride * sizeof(float));
         AL(S.aggq, B * (size_t)c->mesh.n_agg * 9 * sizeof(float));
+        AL(S.bsplit, coarse_b_bytes(c->mesh.coarse_n, B));
+        CK(cudaMemset(S.bsplit, 0, coarse_b_bytes(c->mesh.coarse_n, B)));   // columns past N stay zero
     }
 #undef AL
     CK(cudaMemset(S.sc, 0, B * sizeof(ProbScal)));
@@ -279,9 +283,10 @@ void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc
         const int first = (int)out.size();
         bool any_coarse = false;
         for (int b = 0; b < g.B; ++b) any_coarse |= g.ph[b].active && g.ph[b].in_pcg && g.ph[b].coarse;
+        const bool tc = c->mesh.coarse_tc && c->mesh.Abf && c->slot.bsplit;
         if (jobs && any_coarse && c->mesh.coarse_n > 0)
-            jobs->push_back(CoarseJob{c->mesh.Ainv, c->mesh.coarse_tc ? c->mesh.Abf : nullptr, c->mesh.coarse_err, c,
-                                      c->mesh.coarse_n, first, 0, c->plan.agg_size / kCoarseRows});
+            jobs->push_back(CoarseJob{c->mesh.Ainv, tc ? c->mesh.Abf : nullptr, c->slot.bsplit, c->mesh.coarse_err, c,
+                                      c->mesh.coarse_n, first, 0, c->plan.agg_size / kCoarseRows, c->slot.cap});
         const int n = c->plan.n;
         const size_t slots = (size_t)c->plan.slice_ptr.back();
         for (int b = 0; b < g.B; ++b) {
@@ -309,6 +314,13 @@ void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc
             d.ec = c->slot.ec ? c->slot.ec + (size_t)b * coarse_ks(c) * c->mesh.coarse_n : nullptr;
             d.rcs = c->slot.rcs ? c->slot.rcs + (size_t)b * c->slot.rcs_stride : nullptr;
             d.rc = c->plan.agg_size == kCoarseRows ? d.rcp : d.rcs;
+            d.ctc = d.coarse && tc;
+            uint16_t* bg = c->slot.bsplit ? c->slot.bsplit + (size_t)(b / kCoarseGroupSlots) *
+                                                                 coarse_chunks(c->mesh.coarse_n) * kCoarseBChunk
+                                          : nullptr;
+            d.bunit = d.ctc && c->plan.agg_size == kCoarseRows ? bg : nullptr;
+            d.bagg = d.ctc && c->plan.agg_size != kCoarseRows ? bg : nullptr;
+            d.bslot = b;
             d.agg_shift = c->mesh.agg_shift;
             d.coarse_n = c->mesh.coarse_n;
             units += d.n_tiles;
@@ -470,8 +482,13 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
         if (lst != MFEM_OK) return lst;
         if (count) {
             c->prof.end(pe, c->stream);
-            int cl = nj > 0 ? nj + 1 : 0;
-            for (const auto& j : jobs) cl += j.agg_units > 1;
+            int cl = nj;   // coarse kernels: per job the product (fused with the correction on the tensor cores) ...
+            bool cuda_core = false;
+            for (const auto& j : jobs) {
+                cl += j.agg_units > 1;   // ... the per-aggregate sums of larger aggregates ...
+                cuda_core |= j.Abf == nullptr;
+            }
+            cl += cuda_core ? 1 : 0;   // ... and the correction after CUDA-core products
             c->prof.launches += (2 + cl) * n_it;
             c->prof.pcg_launches += 2 * n_it;
             c->prof.coarse_launches += cl * n_it;
@@ -1671,23 +1688,30 @@ mfem_status mfem_coarse_apply(mfem_ctx* c, const float* rc, int32_t B, float* e,
     if (c->mesh.coarse_n <= 0) return ctx_fail(c, MFEM_EINVAL, "the context has no coarse space");
     if (B < 1) return ctx_fail(c, MFEM_EINVAL, "B must be >= 1");
     if (product != MFEM_COARSE_TC && product != MFEM_COARSE_FP32) return ctx_fail(c, MFEM_EINVAL, "bad product");
+    const bool tc = product == MFEM_COARSE_TC;
     const int N = c->mesh.coarse_n;
     const size_t nks = coarse_ks(c);
-    // per problem: r_c, the slice partials, and scalars marking it active
+    // per problem: r_c, scalars marking it active, and the product's output --
+    // slice partials (CUDA cores) or, on the tensor cores, the B operand and e
+    const size_t n_out = tc ? (((size_t)B + kCoarseGroupSlots - 1) / kCoarseGroupSlots) * kCoarseGroupSlots * N
+                            : (size_t)B * nks * N;
     float* rc_d = nullptr;
-    float* ec_d = nullptr;
+    float* out_d = nullptr;
+    void* bs_d = nullptr;
     ProbScal* sc_d = nullptr;
     PcgDesc<float>* d_d = nullptr;
     auto cleanup = [&]() {
         cudaFree(rc_d);
-        cudaFree(ec_d);
+        cudaFree(out_d);
+        cudaFree(bs_d);
         cudaFree(sc_d);
         cudaFree(d_d);
     };
     // r_c rows padded to the 16-byte-aligned stride the kernels' vector loads need
     const size_t ldr = coarse_ld(N);
     cudaError_t err = cudaMalloc((void**)&rc_d, sizeof(float) * (size_t)B * ldr);
-    if (err == cudaSuccess) err = cudaMalloc((void**)&ec_d, sizeof(float) * (size_t)B * nks * N);
+    if (err == cudaSuccess) err = cudaMalloc((void**)&out_d, sizeof(float) * n_out);
+    if (err == cudaSuccess && tc) err = cudaMalloc(&bs_d, coarse_b_bytes(N, B));
     if (err == cudaSuccess) err = cudaMalloc((void**)&sc_d, sizeof(ProbScal) * (size_t)B);
     if (err == cudaSuccess) err = cudaMalloc((void**)&d_d, sizeof(PcgDesc<float>) * (size_t)B);
     std::vector<ProbScal> sc(B);
@@ -1697,10 +1721,12 @@ mfem_status mfem_coarse_apply(mfem_ctx* c, const float* rc, int32_t B, float* e,
         sc[b].state = kActive;
         std::memset(&d[b], 0, sizeof(PcgDesc<float>));
         d[b].coarse = 1;
+        d[b].ctc = tc ? 1 : 0;
+        d[b].bslot = b;
         d[b].coarse_n = N;
         d[b].sc = sc_d + b;
         d[b].rc = rc_d + (size_t)b * ldr;
-        d[b].ec = ec_d + (size_t)b * nks * N;
+        if (!tc) d[b].ec = out_d + (size_t)b * nks * N;
     }
     if (err == cudaSuccess)
         err = cudaMemcpy2DAsync(rc_d, sizeof(float) * ldr, rc, sizeof(float) * N, sizeof(float) * N, B,
@@ -1709,27 +1735,32 @@ mfem_status mfem_coarse_apply(mfem_ctx* c, const float* rc, int32_t B, float* e,
         err = cudaMemcpyAsync(sc_d, sc.data(), sizeof(ProbScal) * B, cudaMemcpyHostToDevice, c->stream);
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(d_d, d.data(), sizeof(PcgDesc<float>) * B, cudaMemcpyHostToDevice, c->stream);
-    if (err == cudaSuccess) err = cudaMemsetAsync(ec_d, 0, sizeof(float) * (size_t)B * nks * N, c->stream);
+    if (err == cudaSuccess) err = cudaMemsetAsync(out_d, 0, sizeof(float) * n_out, c->stream);
+    if (err == cudaSuccess && tc) err = cudaMemsetAsync(bs_d, 0, coarse_b_bytes(N, B), c->stream);
+    if (err == cudaSuccess && tc) err = coarse_split(rc_d, N, (int)ldr, B, bs_d, c->stream);
     if (err == cudaSuccess) err = cudaMemsetAsync(c->mesh.coarse_err, 0, sizeof(unsigned), c->stream);
     if (err == cudaSuccess) {
-        CoarseJob j{c->mesh.Ainv, product == MFEM_COARSE_TC ? c->mesh.Abf : nullptr, c->mesh.coarse_err, c, N, 0, B,
-                    1};
-        err = launch_coarse_only(d_d, B, &j, c->stream);
+        CoarseJob j{c->mesh.Ainv, tc ? c->mesh.Abf : nullptr, bs_d, c->mesh.coarse_err, c, N, 0, B, 1, B};
+        err = launch_coarse_only(d_d, B, &j, tc ? out_d : nullptr, c->stream);
     }
-    std::vector<float> ec((size_t)B * nks * N);
+    std::vector<float> out(n_out);
     unsigned werr = 0;
     if (err == cudaSuccess)
-        err = cudaMemcpyAsync(ec.data(), ec_d, sizeof(float) * ec.size(), cudaMemcpyDeviceToHost, c->stream);
+        err = cudaMemcpyAsync(out.data(), out_d, sizeof(float) * n_out, cudaMemcpyDeviceToHost, c->stream);
     if (err == cudaSuccess)
         err = cudaMemcpyAsync(&werr, c->mesh.coarse_err, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream);
     if (err == cudaSuccess) err = cudaStreamSynchronize(c->stream);
     cleanup();
     if (err != cudaSuccess) return cuda_check(c, err, "coarse apply");
     if (werr) return ctx_fail(c, MFEM_ECUDA, "coarse product: a bounded wait in the tensor-core kernel ran out");
+    if (tc) {   // e of every slot, complete
+        std::memcpy(e, out.data(), sizeof(float) * (size_t)B * N);
+        return MFEM_OK;
+    }
     for (int b = 0; b < B; ++b)   // slices added in slice order, as the correction kernel does
         for (int i = 0; i < N; ++i) {
             float v = 0.f;
-            for (size_t k = 0; k < nks; ++k) v += ec[((size_t)b * nks + k) * N + i];
+            for (size_t k = 0; k < nks; ++k) v += out[((size_t)b * nks + k) * N + i];
             e[(size_t)b * N + i] = v;
         }
     return MFEM_OK;

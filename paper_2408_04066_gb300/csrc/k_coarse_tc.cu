@@ -1,37 +1,37 @@
-// Coarse solve of the two-level preconditioner on the tensor cores.
+// Coarse solve and correction of the two-level preconditioner on the tensor
+// cores, fused into one kernel per mesh and PCG iteration.
 //
-// e = A_c^{-1} r_c for every problem of one mesh inside a PCG iteration: a dense
-// product of the per-mesh inverse coarse matrix (N x N, N = 6 rigid modes per
-// aggregate) with up to 16 coarse residuals per CTA group.  It is the one dense
-// contraction of the solve (the preconditioner's reduced space; the method
-// itself has none, paper §5), and it is bound by streaming A_c^{-1}: the FP32
-// CUDA-core version read 4 bytes of A_c^{-1} per 16 FMAs and was limited by
-// instruction issue.  Here A_c^{-1} is stored once per mesh in BF16 (half the
-// bytes) and multiplied by tcgen05 MMAs with FP32 accumulation in tensor
-// memory:
+// u = zb + P e,  e = A_c^{-1} r_c  for every two-level problem of one mesh: the
+// product is the one dense contraction of the solve (the preconditioner's
+// reduced space; the method itself has none, paper §5) and it is bound by
+// streaming A_c^{-1}, stored once per mesh in BF16.
 //
-//   * A_c^{-1} is pre-tiled at set-up into tiles of 128 rows x kCoarseKC
-//     columns, each tile contiguous and already in the MMA's no-swizzle
-//     K-major layout (8-row x 16-byte core matrices; per K = 16 step the
-//     128 x 16 sub-tile is 4 KB, core matrices K-adjacent 128 B apart and
-//     8-row groups 256 B apart).  One CTA takes one tile: four 16 KB 1-D bulk
-//     copies (the TMA engine, one mbarrier each) land it in shared memory, so
-//     the MMAs on the first quarter start while the rest arrives.
-//   * r_c of each problem is split exactly into three BF16 parts
-//     (r = hi + mid + lo: 3 x 8 significand bits hold the FP32 value), the B
-//     operand has N = 48 columns (16 problems x 3 parts), and the epilogue adds
-//     the three FP32 partial products.  The preconditioner therefore stays the
-//     fixed linear map block-Jacobi + P Ahat P^T with Ahat = bf16(A_c^{-1})
-//     (symmetric: rounding is entrywise), which keeps PCG's theory intact at
-//     any tolerance.
-//   * One thread issues the 16 MMAs (M = 128, N = 48, K = 16) of the tile and
-//     commits them to an mbarrier; each warp then reads its 32 TMEM lanes
-//     (rows) with tcgen05.ld and writes the slice partials ec[slice][row] that
-//     the correction kernel adds in slice order, so results are deterministic.
+//   * A cluster of kFuSplit CTAs owns a row block of kFuAggsBlk aggregates
+//     (their 6 kFuAggsBlk rows of A_c^{-1}, padded to the MMA's M = 128); CTA q
+//     of the cluster streams the q-th part of the K range: per chunk of kTcKC
+//     columns one 32 KB block of A (packed at set-up in the MMA's no-swizzle
+//     K-major core-matrix layout) and the matching 12 KB chunk of the B
+//     operand, by 1-D bulk copies (the TMA engine) into a ring of kFuStages
+//     shared-memory stages; one thread issues the MMAs (M = 128, N = 48,
+//     K = 16), FP32 accumulation in tensor memory.
+//   * The cluster adds its kFuSplit partial products through distributed
+//     shared memory in rank order (deterministic), CTA q keeping the rows of
+//     its kFuAggsCta aggregates; then every thread of the CTA applies the
+//     correction to those aggregates' vertex rows: u_i = zb_i + Q_a (e_t +
+//     e_w x (X_i - c_a)), written to the neighbour record the next SpMV
+//     gathers.  No slice partials, no separate correction kernel.
+//   * B: each problem's r_c split exactly into three BF16 parts (r = hi + mid +
+//     lo: 3 x 8 significand bits hold the FP32 value), N = 48 columns for 16
+//     request slots; the restriction writes it in the operand layout (see
+//     coarse_b_store).  The epilogue adds the three FP32 partial products, so
+//     the preconditioner stays the fixed linear map block-Jacobi + P Ahat P^T
+//     with Ahat = bf16(A_c^{-1}) (symmetric: rounding is entrywise), which
+//     keeps PCG's theory intact at any tolerance.
 //
-// Every wait is bounded by the global timer; a wait that runs out sets a bit
-// of the mesh's error word (read by the host after the solve), waits (bounded)
-// for the copies it issued, frees its tensor memory and returns.
+// Every wait on a copy or an MMA is bounded by the global timer; a wait that
+// runs out sets a bit of the mesh's error word (read by the host after the
+// solve), waits (bounded) for the copies it issued and frees its tensor memory.
+// The cluster barriers are reached by every CTA of a cluster on every path.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -43,25 +43,29 @@ namespace mfem {
 
 namespace {
 
-constexpr int kTcM = 128;                       // rows of A_c^{-1} per tile (MMA M)
-constexpr int kTcKS = kCoarseKC;                // columns per tile (K slice)
-constexpr int kTcProbs = 16;                    // problems per CTA group
-constexpr int kTcN = 3 * kTcProbs;              // MMA N: three BF16 parts per problem
-constexpr int kTcSteps = kTcKS / 16;            // MMAs per tile (K = 16 each)
-constexpr int kTcChunks = 4;                    // bulk copies per tile
-constexpr int kTcStepA = kTcM * 16 * 2;         // bytes of A per K step (4 KB)
-constexpr int kTcStepB = kTcN * 16 * 2;         // bytes of B per K step (1.5 KB)
-constexpr int kTcABytes = kTcStepA * kTcSteps;  // 64 KB
-constexpr int kTcBBytes = kTcStepB * kTcSteps;  // 24 KB
-constexpr int kTcChunkBytes = kTcABytes / kTcChunks;
-constexpr int kTcTmemCols = 64;                 // >= kTcN, a power of two >= 32
-constexpr int kTcSmem = kTcABytes + kTcBBytes + 64;
+constexpr int kFuSplit = 4;                       // CTAs per cluster: parts of the K range
+constexpr int kFuAggsCta = 5;                     // aggregates each CTA corrects
+constexpr int kFuAggsBlk = kFuSplit * kFuAggsCta; // aggregates per cluster (row block)
+constexpr int kFuStages = 4;                      // shared-memory ring of A + B chunks
+constexpr int kFuThreads = 320;                   // 10 warps: one per 32 vertex rows of 5 x 64
+constexpr int kTcM = 128;                         // MMA M: rows of A_c^{-1} per row block (6 x 20, padded)
+constexpr int kTcProbs = kCoarseGroupSlots;       // request slots per CTA group
+constexpr int kTcN = kCoarseBRows;                // MMA N: three BF16 parts per slot
+constexpr int kTcSteps = kTcKC / 16;              // MMAs per chunk (K = 16 each)
+constexpr int kFuStepA = kTcM * 16 * 2;           // bytes of A per K step (4 KB)
+constexpr int kFuStepB = kTcN * 16 * 2;           // bytes of B per K step (1.5 KB)
+constexpr int kFuChunkA = kFuStepA * kTcSteps;    // 32 KB
+constexpr int kFuChunkB = kFuStepB * kTcSteps;    // 12 KB
+constexpr int kFuStage = kFuChunkA + kFuChunkB;   // 44 KB
+constexpr int kFuSmem = kFuStages * kFuStage + 128;
+constexpr int kTcTmemCols = 64;                   // >= kTcN, a power of two >= 32
 constexpr uint64_t kTcWaitNs = 200ull * 1000ull * 1000ull;   // 0.2 s per bounded wait
 
-static_assert(kTcKS % (16 * kTcChunks) == 0, "K slice must split into whole MMA steps per chunk");
-static_assert(kTcChunkBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
-static_assert((kTcProbs & (kTcProbs - 1)) == 0 && (kTcProbs * kTcKS / 8) % 128 == 0,
-              "B build: whole work items per thread, problem index in the low bits");
+static_assert(6 * kFuAggsBlk <= kTcM, "a row block's coarse rows fit the MMA's M");
+static_assert(kFuChunkB == kCoarseBChunk * 2, "B chunk layout shared with the restriction");
+static_assert(kTcM * kTcN * 4 <= kFuStage, "the partial product fits one stage for the cluster sum");
+static_assert(kFuChunkA % 16 == 0 && kFuChunkB % 16 == 0 && kFuStage % 1024 == 0, "bulk copies: 16-byte units");
+static_assert(kFuThreads >= 128, "warps 0-3 read the 128 TMEM lanes");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -161,70 +165,151 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Element (row, k) of a 128 x kTcKS tile in its K-major core-matrix layout
-// (bf16 elements): K step s, K-core j2, 8-row group g, row r in the group.
-__host__ __device__ __forceinline__ size_t tile_offset(int row, int kk) {
+// Element (row, k) of a row block's chunk (bf16 elements): K step s, K-core j2,
+// 8-row group g, row r in the group.
+__host__ __device__ __forceinline__ size_t a_offset(int row, int kk) {
     const int s = kk >> 4, j2 = (kk >> 3) & 1, c = kk & 7, g = row >> 3, r = row & 7;
     return (size_t)s * (kTcM * 16) + (size_t)(g * 2 + j2) * 64 + r * 8 + c;
 }
 
-// Set-up: FP32 A_c^{-1} (rows of ld floats) -> tiles of BF16.
-__global__ void k_coarse_pack_bf16(const float* __restrict__ Ainv, int N, int ld, int nks,
+// Set-up: FP32 A_c^{-1} (rows of ld floats) -> per row block and chunk, BF16.
+__global__ void k_coarse_pack_bf16(const float* __restrict__ Ainv, int N, int ld, int nkc,
                                    __nv_bfloat16* __restrict__ out) {
-    const int kk = blockIdx.x * blockDim.x + threadIdx.x;   // column within the slice
-    const int row = blockIdx.y;                              // global row
-    const int ks = blockIdx.z;
-    if (kk >= kTcKS) return;
-    const int mt = row / kTcM, r = row % kTcM, k = ks * kTcKS + kk;
-    const float v = (row < N && k < N) ? Ainv[(size_t)row * ld + k] : 0.f;
-    out[((size_t)mt * nks + ks) * (kTcM * kTcKS) + tile_offset(r, kk)] = __float2bfloat16_rn(v);
+    const int kk = threadIdx.x;                        // column within the chunk
+    const int r = blockIdx.y % kTcM, rb = blockIdx.y / kTcM;
+    const int ch = blockIdx.z;
+    const int row = rb * 6 * kFuAggsBlk + r, k = ch * kTcKC + kk;
+    const float v = (r < 6 * kFuAggsBlk && row < N && k < N) ? Ainv[(size_t)row * ld + k] : 0.f;
+    out[((size_t)rb * nkc + ch) * (kFuChunkA / 2) + a_offset(r, kk)] = __float2bfloat16_rn(v);
 }
 
+// mfem_coarse_apply: r_c of B problems (rows of ldr floats) -> their B operand.
+__global__ void k_coarse_split(const float* __restrict__ rc, int N, int ldr, int nkc, uint16_t* __restrict__ bs) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x, b = blockIdx.y;
+    if (k >= N) return;
+    coarse_b_store(bs + (size_t)(b / kCoarseGroupSlots) * nkc * kCoarseBChunk, b % kCoarseGroupSlots, k,
+                   rc[(size_t)b * ldr + k]);
+}
+
+__device__ __forceinline__ void ldv(const float* p, float (&v)[3]) {
+    const float4 a = *reinterpret_cast<const float4*>(p);
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = a.z;
+}
+__device__ __forceinline__ void ldv(const double* p, double (&v)[3]) {
+    const double2 a = reinterpret_cast<const double2*>(p)[0], b = reinterpret_cast<const double2*>(p)[1];
+    v[0] = a.x;
+    v[1] = a.y;
+    v[2] = b.x;
+}
+__device__ __forceinline__ void stv(float* p, const float (&v)[3]) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], 0.f);
+}
+__device__ __forceinline__ void stv(double* p, const double (&v)[3]) {
+    reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+    reinterpret_cast<double2*>(p)[1] = make_double2(v[2], 0.0);
+}
+
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// FP32 at the same shared-memory offset in CTA `rank` of the cluster
+__device__ __forceinline__ float ld_cluster_f32(const float* local, uint32_t rank) {
+    uint32_t remote;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(local)), "r"(rank));
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(remote) : "memory");
+    return v;
+}
+
+// Cluster (rb, pg): row block rb (aggregates kFuAggsBlk rb ..), request slots
+// 16 pg .. 16 pg + 15 of the context; CTA q = cluster rank takes chunks
+// [q c_per, (q + 1) c_per) of the K range and corrects aggregates
+// kFuAggsBlk rb + kFuAggsCta q ...  The problems are found in the descriptor
+// table d0 .. d0+nd-1 by slot; a slot without a two-level problem inside PCG
+// contributes nothing (its B columns give outputs never read).
+// e_out (mfem_coarse_apply): write e[slot][row] instead of the correction.
 template <typename T>
-__global__ void __launch_bounds__(128) k_coarse_tc(const __nv_bfloat16* __restrict__ Abf, int N, int nks,
-                                                   const PcgDesc<T>* __restrict__ D, int d0, int nd,
-                                                   unsigned* __restrict__ err) {
+__global__ void __launch_bounds__(kFuThreads, 1)
+    k_coarse_fused(const __nv_bfloat16* __restrict__ Abf, int N, int nkc, const uint16_t* __restrict__ Bs,
+                   const PcgDesc<T>* __restrict__ D, int d0, int nd, unsigned* __restrict__ err,
+                   float* __restrict__ e_out) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    unsigned char* sA = smem;
-    unsigned char* sB = smem + kTcABytes;
-    uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kTcABytes + kTcBBytes);   // chunks, then MMA done
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + kTcChunks + 1);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + kFuStages * kFuStage);   // chunk landed
+    uint64_t* empty = full + kFuStages;                                           // its MMAs done
+    uint64_t* done = empty + kFuStages;                                           // every MMA done
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(done + 1);
+    float* red = reinterpret_cast<float*>(smem);   // after the K loop: the partial product [kTcN][kTcM]
     __shared__ const PcgDesc<T>* dp[kTcProbs];
-    __shared__ const float* rcs[kTcProbs];
+    __shared__ float es[6 * kFuAggsCta][kTcProbs + 1];
+    __shared__ float qs[kFuAggsCta][kTcProbs][9];
     __shared__ int any, s_ok;
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int mt = blockIdx.x, ks = blockIdx.y, pg = blockIdx.z;
+    const uint32_t q = cluster_rank();
+    const int rb = blockIdx.x / kFuSplit, pg = blockIdx.y;
+    const int c_per = (nkc + kFuSplit - 1) / kFuSplit;
+    const int c_lo = min(nkc, (int)q * c_per), nch = min(nkc, c_lo + c_per) - c_lo;   // this CTA's chunks
+    const int nst = nch < kFuStages ? nch : kFuStages;
+    const unsigned char* gA =
+        reinterpret_cast<const unsigned char*>(Abf) + ((size_t)rb * nkc + c_lo) * kFuChunkA;
+    const unsigned char* gB =
+        reinterpret_cast<const unsigned char*>(Bs) + ((size_t)pg * nkc + c_lo) * kFuChunkB;
+    const int a_cta = kFuAggsBlk * rb + kFuAggsCta * (int)q;   // first aggregate this CTA corrects
     // prologue on data fixed during the solve, overlapping the previous kernel:
-    // the descriptors, and the tile of A_c^{-1} itself (four bulk copies, one
-    // barrier each) -- it does not depend on the previous kernel
-    const PcgDesc<T>* mine = nullptr;
-    if (t < kTcProbs && pg * kTcProbs + t < nd && D[d0 + pg * kTcProbs + t].coarse) mine = &D[d0 + pg * kTcProbs + t];
+    // the slots' descriptors and aggregate rotations, and the first chunks of
+    // A_c^{-1} (their barriers also expect the B chunk, copied after the wait)
+    if (t < kTcProbs) {
+        const int slot = pg * kTcProbs + t;
+        const PcgDesc<T>* mine = nullptr;
+#pragma unroll 8
+        for (int i = 0; i < nd; ++i) {   // independent loads: no early exit
+            const bool hit = D[d0 + i].bslot == slot && D[d0 + i].coarse;
+            if (hit && !mine) mine = &D[d0 + i];
+        }
+        dp[t] = mine;
+    }
     if (t == 0) {
         any = 0;
         s_ok = 1;
-        for (int c = 0; c <= kTcChunks; ++c) mbar_init(&bars[c], 1);
+        for (int c = 0; c < 2 * kFuStages + 1; ++c) mbar_init(&full[c], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        const unsigned char* gA =
-            reinterpret_cast<const unsigned char*>(Abf + ((size_t)mt * nks + ks) * (size_t)(kTcM * kTcKS));
-        for (int c = 0; c < kTcChunks; ++c) {
-            mbar_expect_tx(&bars[c], kTcChunkBytes);
-            bulk_g2s(sA + c * kTcChunkBytes, gA + (size_t)c * kTcChunkBytes, kTcChunkBytes, &bars[c]);
+        for (int c = 0; c < nst; ++c) {
+            mbar_expect_tx(&full[c], kFuStage);
+            bulk_g2s(smem + c * kFuStage, gA + (size_t)c * kFuChunkA, kFuChunkA, &full[c]);
         }
+    }
+    __syncthreads();
+    for (int i = t; i < kFuAggsCta * kTcProbs * 9; i += kFuThreads) {
+        const int ai = i / (kTcProbs * 9), p = (i / 9) % kTcProbs, e = i % 9;
+        const PcgDesc<T>* d = dp[p];
+        const int a = a_cta + ai;
+        qs[ai][p][e] = (d && d->aggq && a < N / 6) ? d->aggq[9 * a + e] : 0.f;
     }
     pdl_wait();
     pdl_trigger();
+    if (t == 0)   // B chunks of the first stages: written by the previous kernel
+        for (int c = 0; c < nst; ++c)
+            bulk_g2s(smem + c * kFuStage + kFuChunkA, gB + (size_t)c * kFuChunkB, kFuChunkB, &full[c]);
     __syncthreads();
     if (t < kTcProbs) {
-        const PcgDesc<T>* p = (mine && mine->sc->state == kActive) ? mine : nullptr;
-        dp[t] = p;
-        rcs[t] = p ? p->rc : nullptr;
-        if (p) atomicOr(&any, 1);
+        const PcgDesc<T>* d = dp[t];
+        if (d && d->sc->state != kActive) d = nullptr;
+        dp[t] = d;
+        if (d) atomicOr(&any, 1);
     }
     __syncthreads();
-    if (!any) {   // block-uniform: nothing to compute; let the prefetch land before the memory is released
+    // the same for every CTA of the cluster (same slots, states final after the wait)
+    if (!any) {   // nothing to compute; let the copies land before the memory is released
         if (t == 0)
-            for (int c = 0; c < kTcChunks; ++c) mbar_wait(&bars[c], 0);
+            for (int c = 0; c < nst; ++c)
+                if (!mbar_wait(&full[c], 0)) atomicOr(err, 4u);
         return;
     }
     if (warp == 0) {   // tensor memory for the 128 x 48 FP32 accumulator
@@ -234,134 +319,189 @@ __global__ void __launch_bounds__(128) k_coarse_tc(const __nv_bfloat16* __restri
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
-    // B operand: each problem's r_c slice as three BF16 parts (rows p, 16 + p,
-    // 32 + p of the N = 48 operand), zero for absent problems and past N.  A
-    // work item is 8 consecutive columns of one problem: two 16-byte loads, and
-    // each part is one 16-byte row of a core matrix; the problem index varies
-    // fastest over the threads, so a warp's stores fill consecutive rows.
-    const int k0 = ks * kTcKS;
-#pragma unroll
-    for (int it = 0; it < (kTcProbs * kTcKS / 8) / 128; ++it) {
-        const int item = t + 128 * it;
-        const int p = item & (kTcProbs - 1), kk0 = 8 * (item / kTcProbs), k = k0 + kk0;
-        const float* src = rcs[p];
-        float v[8];
-        if (src && k + 7 < N) {
-            const float4 a = *reinterpret_cast<const float4*>(src + k);
-            const float4 c = *reinterpret_cast<const float4*>(src + k + 4);
-            v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = c.x; v[5] = c.y; v[6] = c.z; v[7] = c.w;
-        } else {
-#pragma unroll
-            for (int e = 0; e < 8; ++e) v[e] = (src && k + e < N) ? src[k + e] : 0.f;
-        }
-        uint32_t hi[4], mid[4], lo[4];
-#pragma unroll
-        for (int e = 0; e < 8; e += 2) {
-            __nv_bfloat16 h[2], m[2], l[2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                const float r = v[e + q];
-                h[q] = __float2bfloat16_rn(r);
-                const float r1 = r - __bfloat162float(h[q]);
-                m[q] = __float2bfloat16_rn(r1);
-                l[q] = __float2bfloat16_rn(r1 - __bfloat162float(m[q]));
-            }
-            hi[e / 2] = (uint32_t)__bfloat16_as_ushort(h[0]) | ((uint32_t)__bfloat16_as_ushort(h[1]) << 16);
-            mid[e / 2] = (uint32_t)__bfloat16_as_ushort(m[0]) | ((uint32_t)__bfloat16_as_ushort(m[1]) << 16);
-            lo[e / 2] = (uint32_t)__bfloat16_as_ushort(l[0]) | ((uint32_t)__bfloat16_as_ushort(l[1]) << 16);
-        }
-        unsigned char* step = sB + (kk0 >> 4) * kTcStepB + ((kk0 >> 3) & 1) * 128;
-        const int n0 = p, n1 = kTcProbs + p, n2 = 2 * kTcProbs + p;
-        *reinterpret_cast<uint4*>(step + (n0 >> 3) * 256 + (n0 & 7) * 16) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-        *reinterpret_cast<uint4*>(step + (n1 >> 3) * 256 + (n1 & 7) * 16) = make_uint4(mid[0], mid[1], mid[2], mid[3]);
-        *reinterpret_cast<uint4*>(step + (n2 >> 3) * 256 + (n2 & 7) * 16) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
-    }
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // B visible to the tensor cores
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
 
-    if (t == 0) {   // one thread issues every MMA of the tile
+    if (t == 0) {   // one thread issues every MMA and keeps the ring full
         constexpr uint32_t idesc = umma_idesc_bf16(kTcM, kTcN);
-        const uint32_t a0 = smem_u32(sA), b0 = smem_u32(sB);
+        const uint32_t base = smem_u32(smem);
         bool ok = true;
-        for (int c = 0; c < kTcChunks && ok; ++c) {
-            ok = mbar_wait(&bars[c], 0);
+        int issued = nst;   // chunks whose copies were issued
+        for (int c = 0; c < nch && ok; ++c) {
+            const int s = c % kFuStages;
+            ok = mbar_wait(&full[s], (uint32_t)(c / kFuStages) & 1u);
             if (!ok) break;
             tc_fence_after();
-            for (int s = c * (kTcSteps / kTcChunks); s < (c + 1) * (kTcSteps / kTcChunks); ++s)
-                umma_bf16(tmem, umma_desc(a0 + s * kTcStepA, 128, 256), umma_desc(b0 + s * kTcStepB, 128, 256),
-                          idesc, s > 0 ? 1u : 0u);
+            const uint32_t a0 = base + s * kFuStage, b0 = a0 + kFuChunkA;
+            for (int k = 0; k < kTcSteps; ++k)
+                umma_bf16(tmem, umma_desc(a0 + k * kFuStepA, 128, 256), umma_desc(b0 + k * kFuStepB, 128, 256), idesc,
+                          (c > 0 || k > 0) ? 1u : 0u);
+            umma_commit(&empty[s]);
+            // refill the stage of the previous chunk (its MMAs were issued one
+            // chunk ago) with the chunk kFuStages after it
+            const int cp = c - 1, cn = cp + kFuStages;
+            if (cp >= 0 && cn < nch) {
+                const int sp = cp % kFuStages;
+                ok = mbar_wait(&empty[sp], (uint32_t)(cp / kFuStages) & 1u);
+                if (!ok) break;
+                mbar_expect_tx(&full[sp], kFuStage);
+                bulk_g2s(smem + sp * kFuStage, gA + (size_t)cn * kFuChunkA, kFuChunkA, &full[sp]);
+                bulk_g2s(smem + sp * kFuStage + kFuChunkA, gB + (size_t)cn * kFuChunkB, kFuChunkB, &full[sp]);
+                issued = cn + 1;
+            }
         }
         // arrives once every MMA issued above has completed (at once if none was)
-        umma_commit(&bars[kTcChunks]);
+        umma_commit(done);
         if (!ok) {
             s_ok = 0;
             atomicOr(err, 1u);
-            for (int c = 0; c < kTcChunks; ++c) mbar_wait(&bars[c], 0);   // our copies in flight, bounded
+            // the copies in flight: the last use of each stage that was issued, bounded
+            for (int c = issued - nst; c < issued; ++c)
+                if (c >= 0) mbar_wait(&full[c % kFuStages], (uint32_t)(c / kFuStages) & 1u);
         }
     }
-    const bool done = mbar_wait(&bars[kTcChunks], 0);
+    const bool fin = mbar_wait(done, 0);
     tc_fence_after();
-    const int all_done = __syncthreads_and(done ? 1 : 0);
-    if (all_done && s_ok) {
-        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
-        float hi[16], mid[16], lo[16];
-        tmem_ld16(lane_addr, hi);
-        tmem_ld16(lane_addr + kTcProbs, mid);
-        tmem_ld16(lane_addr + 2 * kTcProbs, lo);
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        const int row = mt * kTcM + warp * 32 + lane;
-        if (row < N) {
+    const int all_done = __syncthreads_and(fin ? 1 : 0);
+    if (!all_done && t == 0) {
+        atomicOr(err, 2u);
+        mbar_wait(done, 0);   // once more, bounded, before the memory is reused
+    }
+    // this CTA's partial product -> shared memory, column-major [kTcN][kTcM]
+    // (no MMA ran for a CTA without chunks: its part is zero)
+    if (warp < kTcM / 32) {
+        const int row = warp * 32 + lane;
+        if (nch > 0 && all_done && s_ok) {
+            const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+            float v[16];
 #pragma unroll
-            for (int p = 0; p < kTcProbs; ++p)
-                if (dp[p]) dp[p]->ec[(size_t)ks * N + row] = (hi[p] + mid[p]) + lo[p];
+            for (int part = 0; part < 3; ++part) {
+                tmem_ld16(lane_addr + part * kTcProbs, v);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int p = 0; p < kTcProbs; ++p) red[(part * kTcProbs + p) * kTcM + row] = v[p];
+            }
+        } else {
+#pragma unroll
+            for (int c = 0; c < kTcN; ++c) red[c * kTcM + row] = 0.f;
         }
-    } else if (!all_done) {
-        if (t == 0) atomicOr(err, 2u);
-        mbar_wait(&bars[kTcChunks], 0);   // once more, bounded, before the memory is released
     }
     tc_fence_before();
-    __syncthreads();
+    cluster_sync();   // every CTA's part visible to the cluster
+    // the rows of this CTA's aggregates: the cluster's parts added in rank order
+    for (int i = t; i < 6 * kFuAggsCta * kTcProbs; i += kFuThreads) {
+        const int r = i % (6 * kFuAggsCta), p = i / (6 * kFuAggsCta);
+        const int row = 6 * kFuAggsCta * (int)q + r;
+        float e = 0.f;
+#pragma unroll
+        for (uint32_t j = 0; j < (uint32_t)kFuSplit; ++j) {
+            const float hi = ld_cluster_f32(red + p * kTcM + row, j);
+            const float mid = ld_cluster_f32(red + (kTcProbs + p) * kTcM + row, j);
+            const float lo = ld_cluster_f32(red + (2 * kTcProbs + p) * kTcM + row, j);
+            e += (hi + mid) + lo;
+        }
+        es[r][p] = e;
+    }
+    cluster_sync();   // no CTA leaves or reuses its part while another reads it
     if (warp == 0)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols)
                      : "memory");
+    if (e_out) {   // the product alone
+        for (int i = t; i < 6 * kFuAggsCta * kTcProbs; i += kFuThreads) {
+            const int r = i % (6 * kFuAggsCta), p = i / (6 * kFuAggsCta), row = 6 * a_cta + r;
+            if (dp[p] && row < N) e_out[(size_t)(pg * kTcProbs + p) * N + row] = es[r][p];
+        }
+        return;
+    }
+    // correction of the aggregates' vertex rows for every problem of the group
+    const PcgDesc<T>* d0p = nullptr;
+    for (int p = 0; p < kTcProbs && !d0p; ++p) d0p = dp[p];
+    const int shift = d0p->agg_shift, n = d0p->n_rows, n_agg = N / 6;
+    const int row0 = a_cta << shift;
+    const int row1 = min(n, min(n_agg, a_cta + kFuAggsCta) << shift);
+    const float4* crel = d0p->crel;
+    for (int row = row0 + t; row < row1; row += kFuThreads) {
+        const float4 off = crel[row];
+        const int ai = (row >> shift) - a_cta;
+        T z[kTcProbs][3];
+#pragma unroll
+        for (int p = 0; p < kTcProbs; ++p)
+            if (dp[p]) ldv(dp[p]->rec + kRec * (size_t)row + kRecZB, z[p]);
+#pragma unroll
+        for (int p = 0; p < kTcProbs; ++p) {
+            const PcgDesc<T>* d = dp[p];
+            if (!d) continue;
+            if (off.w != 0.f) {
+                const float e0 = es[6 * ai][p], e1 = es[6 * ai + 1][p], e2 = es[6 * ai + 2][p];
+                const float e3 = es[6 * ai + 3][p], e4 = es[6 * ai + 4][p], e5 = es[6 * ai + 5][p];
+                const float l0 = e0 + (e4 * off.z - e5 * off.y);
+                const float l1 = e1 + (e5 * off.x - e3 * off.z);
+                const float l2 = e2 + (e3 * off.y - e4 * off.x);
+                const float* Q = qs[ai][p];
+#pragma unroll
+                for (int i = 0; i < 3; ++i) z[p][i] += (T)(Q[3 * i] * l0 + Q[3 * i + 1] * l1 + Q[3 * i + 2] * l2);
+            }
+            stv(d->nb + 4 * (size_t)row, z[p]);
+        }
+    }
 }
+
+// Row blocks of an N x N inverse (clusters along the mesh's aggregates)
+__host__ __device__ __forceinline__ int row_blocks(int N) { return (N / 6 + kFuAggsBlk - 1) / kFuAggsBlk; }
 
 }  // namespace
 
-size_t coarse_tc_bytes(int N) {
-    const size_t mt = ((size_t)N + kTcM - 1) / kTcM, nks = ((size_t)N + kTcKS - 1) / kTcKS;
-    return mt * nks * (size_t)kTcM * kTcKS * sizeof(__nv_bfloat16);
+size_t coarse_tc_bytes(int N) { return (size_t)row_blocks(N) * coarse_chunks(N) * (size_t)kFuChunkA; }
+
+size_t coarse_b_bytes(int N, int slots) {
+    const size_t groups = ((size_t)slots + kCoarseGroupSlots - 1) / kCoarseGroupSlots;
+    return groups * coarse_chunks(N) * (size_t)kFuChunkB;
 }
 
 cudaError_t coarse_tc_pack(const float* Ainv, int N, void* Abf, cudaStream_t s) {
-    const int mt = (N + kTcM - 1) / kTcM, nks = (N + kTcKS - 1) / kTcKS;
-    k_coarse_pack_bf16<<<dim3((kTcKS + 127) / 128, mt * kTcM, nks), 128, 0, s>>>(
-        Ainv, N, coarse_ld(N), nks, static_cast<__nv_bfloat16*>(Abf));
+    k_coarse_pack_bf16<<<dim3(1, row_blocks(N) * kTcM, coarse_chunks(N)), kTcKC, 0, s>>>(
+        Ainv, N, coarse_ld(N), coarse_chunks(N), static_cast<__nv_bfloat16*>(Abf));
+    return cudaGetLastError();
+}
+
+cudaError_t coarse_split(const float* rc, int N, int ldr, int B, void* Bs, cudaStream_t s) {
+    k_coarse_split<<<dim3((N + 255) / 256, B), 256, 0, s>>>(rc, N, ldr, coarse_chunks(N), static_cast<uint16_t*>(Bs));
     return cudaGetLastError();
 }
 
 cudaError_t coarse_tc_init() {
-    cudaError_t e = cudaFuncSetAttribute(k_coarse_tc<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_coarse_fused<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFuSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_coarse_tc<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+        e = cudaFuncSetAttribute(k_coarse_fused<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, kFuSmem);
     return e;
 }
 
 template <typename T>
-cudaError_t launch_coarse_tc(const cudaLaunchConfig_t& base, const CoarseJob& j, const PcgDesc<T>* descs) {
+cudaError_t launch_coarse_fused(const cudaLaunchConfig_t& base, const CoarseJob& j, const PcgDesc<T>* descs,
+                                float* e_out) {
     cudaLaunchConfig_t cfg = base;
-    const int mt = (j.N + kTcM - 1) / kTcM, nks = (j.N + kTcKS - 1) / kTcKS;
-    cfg.gridDim = dim3(mt, nks, (j.nd + kTcProbs - 1) / kTcProbs);
-    cfg.blockDim = dim3(128);
-    cfg.dynamicSmemBytes = kTcSmem;
-    return cudaLaunchKernelEx(&cfg, k_coarse_tc<T>, static_cast<const __nv_bfloat16*>(j.Abf), j.N, nks, descs,
-                              j.d0, j.nd, j.err);
+    cudaLaunchAttribute attr[2];
+    int na = 0;
+    for (unsigned i = 0; i < base.numAttrs && na < 1; ++i) attr[na++] = base.attrs[i];   // programmatic launch
+    attr[na].id = cudaLaunchAttributeClusterDimension;
+    attr[na].val.clusterDim.x = kFuSplit;
+    attr[na].val.clusterDim.y = 1;
+    attr[na].val.clusterDim.z = 1;
+    ++na;
+    cfg.attrs = attr;
+    cfg.numAttrs = na;
+    cfg.gridDim = dim3(kFuSplit * row_blocks(j.N), (j.slots + kCoarseGroupSlots - 1) / kCoarseGroupSlots);
+    cfg.blockDim = dim3(kFuThreads);
+    cfg.dynamicSmemBytes = kFuSmem;
+    return cudaLaunchKernelEx(&cfg, k_coarse_fused<T>, static_cast<const __nv_bfloat16*>(j.Abf), j.N,
+                              coarse_chunks(j.N), static_cast<const uint16_t*>(j.Bs), descs, j.d0, j.nd, j.err, e_out);
 }
 
-template cudaError_t launch_coarse_tc<float>(const cudaLaunchConfig_t&, const CoarseJob&, const PcgDesc<float>*);
-template cudaError_t launch_coarse_tc<double>(const cudaLaunchConfig_t&, const CoarseJob&, const PcgDesc<double>*);
+template cudaError_t launch_coarse_fused<float>(const cudaLaunchConfig_t&, const CoarseJob&, const PcgDesc<float>*,
+                                                float*);
+template cudaError_t launch_coarse_fused<double>(const cudaLaunchConfig_t&, const CoarseJob&, const PcgDesc<double>*,
+                                                 float*);
 
 }  // namespace mfem

@@ -36,7 +36,8 @@ __device__ __forceinline__ void stage_rotations(float (*qs)[9], int row0, const 
 // pass valid = false.
 __device__ __forceinline__ void restrict_units(const float (&r)[3], bool valid, int row, int row0,
                                                const float4* __restrict__ crel, const float (*qs)[9], int agg_shift,
-                                               float* __restrict__ rcp_block) {
+                                               float* __restrict__ rcp_block, uint16_t* __restrict__ bgrp = nullptr,
+                                               int bslot = 0, int coarse_n = 0) {
     __shared__ float ws[8][6];
     const int a0 = row0 >> agg_shift;   // row0: the block's first row
     __syncthreads();
@@ -68,7 +69,12 @@ __device__ __forceinline__ void restrict_units(const float (&r)[3], bool valid, 
     const int units = blockDim.x / kCoarseRows;
     if ((int)threadIdx.x < 6 * units) {
         const int u = threadIdx.x / 6, c = threadIdx.x % 6;
-        rcp_block[6 * u + c] = ws[2 * u][c] + ws[2 * u + 1][c];
+        const float v = ws[2 * u][c] + ws[2 * u + 1][c];
+        rcp_block[6 * u + c] = v;
+        // an aggregate is one unit: this is r_c, also written as the
+        // tensor-core product's B operand (all its units lie in this block)
+        const int k = 6 * (row0 / kCoarseRows + u) + c;   // units past the last aggregate write nothing
+        if (bgrp && k < coarse_n) coarse_b_store(bgrp, bslot % kCoarseGroupSlots, k, v);
     }
 }
 
@@ -213,8 +219,12 @@ __global__ void k_pcg_init(ElemArgs A, double tol2, int maxit, const double* __r
         __shared__ float qs[4][9];
         const int row0 = (int)(blockIdx.x * blockDim.x);
         stage_rotations(qs, row0, A.slot.aggq + (size_t)b * A.mesh.n_agg * 9, A.mesh.agg_shift, A.mesh.n_agg);
+        uint16_t* bg = nullptr;
+        if (A.slot.bsplit && A.mesh.agg_shift == 6)
+            bg = A.slot.bsplit + (size_t)(b / kCoarseGroupSlots) * coarse_chunks(A.mesh.coarse_n) * kCoarseBChunk;
         restrict_units(r32, row < n, row, row0, A.mesh.crel, qs, A.mesh.agg_shift,
-                       A.slot.rcp + (size_t)b * A.slot.rcp_stride + 6 * ((size_t)row0 / kCoarseRows));
+                       A.slot.rcp + (size_t)b * A.slot.rcp_stride + 6 * ((size_t)row0 / kCoarseRows), bg, b,
+                       A.mesh.coarse_n);
     }
     double tot[1];
     double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
@@ -395,7 +405,7 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
     }
     if (coarse)   // u is finished by k_pcg_correct after the coarse product
         restrict_units(r32, row < d.n_rows, row, tile * TILE, d.crel, qs, d.agg_shift,
-                       d.rcp + 6 * ((size_t)tile * TILE / kCoarseRows));
+                       d.rcp + 6 * ((size_t)tile * TILE / kCoarseRows), d.bunit, d.bslot, d.coarse_n);
 }
 
 // Coarse solve of the two-level preconditioner: e = A_c^{-1} r_c for the
@@ -426,6 +436,7 @@ __global__ void k_coarse_rc(const PcgDesc<T>* __restrict__ D, int d0, int nd) {
     float v = 0.f;
     for (int u = a << ush; u < u1; ++u) v += q.rcp[6 * (size_t)u + comp];
     q.rcs[k] = v;
+    if (q.bagg) coarse_b_store(q.bagg, q.bslot % kCoarseGroupSlots, k, v);
 }
 
 template <typename T, int NP>
@@ -542,7 +553,7 @@ __global__ void __launch_bounds__(TILE) k_pcg_correct(const PcgDesc<T>* __restri
     // rotations), overlapping the previous kernel's drain
     const int u = blockIdx.x;
     const PcgDesc<T>& d = D[unit_problem<true>(D, n_probs, u)];
-    if (!d.coarse) return;
+    if (!d.coarse || d.ctc) return;   // block Jacobi, or corrected by the fused tensor-core kernel
     ProbScal* sc = d.sc;
     const int tile = u - d.unit_begin_u;
     const int row = tile * TILE + threadIdx.x;
@@ -615,7 +626,8 @@ cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units
     cfg_s.blockDim = dim3(TILE * SPLIT);
     for (int i = 0; i < iters; ++i) {
         cudaError_t e;
-        if (n_jobs > 0) {   // two-level: finish z of the current residual first
+        if (n_jobs > 0) {   // two-level: finish u of the current residual first
+            bool any_cuda_core = false;
             for (int j = 0; j < n_jobs; ++j) {
                 if (jobs[j].agg_units > 1) {   // per-aggregate sums of the unit partials
                     cudaLaunchConfig_t rc = cfg;
@@ -624,11 +636,12 @@ cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units
                     e = cudaLaunchKernelEx(&rc, k_coarse_rc<T>, descs, jobs[j].d0, jobs[j].nd);
                     if (e != cudaSuccess) return e;
                 }
-                if (jobs[j].Abf) {   // tensor cores, BF16 A_c^{-1}
-                    e = launch_coarse_tc<T>(cfg, jobs[j], descs);
+                if (jobs[j].Abf) {   // tensor cores, BF16 A_c^{-1}: product and correction in one kernel
+                    e = launch_coarse_fused<T>(cfg, jobs[j], descs, nullptr);
                     if (e != cudaSuccess) return e;
                     continue;
                 }
+                any_cuda_core = true;
                 cudaLaunchConfig_t gc = cfg;
                 const int np = jobs[j].nd <= 8 ? 8 : 16;
                 gc.gridDim = dim3((jobs[j].N + 32 * kCoarseRowPasses - 1) / (32 * kCoarseRowPasses),
@@ -642,8 +655,10 @@ cudaError_t launch_pcg_iters_t(const PcgDesc<T>* descs, int n_probs, int n_units
                                            descs, jobs[j].d0, jobs[j].nd);
                 if (e != cudaSuccess) return e;
             }
-            e = cudaLaunchKernelEx(&cfg_u, k_pcg_correct<T, kRowTileU>, descs, n_probs);
-            if (e != cudaSuccess) return e;
+            if (any_cuda_core) {
+                e = cudaLaunchKernelEx(&cfg_u, k_pcg_correct<T, kRowTileU>, descs, n_probs);
+                if (e != cudaSuccess) return e;
+            }
         }
         e = cudaLaunchKernelEx(&cfg_s, k_pcg_spmv<T, TILE, SPLIT>, descs, n_probs);
         if (e != cudaSuccess) return e;
@@ -680,10 +695,11 @@ cudaError_t launch_pcg_iters(const PcgDesc<T>* descs, int n_probs, int n_units, 
 
 bool pcg_tile_supported(int tile_rows) { return tile_rows == 64 || tile_rows == 128 || tile_rows == 256; }
 
-cudaError_t launch_coarse_only(const PcgDesc<float>* descs, int n_probs, const CoarseJob* job, cudaStream_t s) {
+cudaError_t launch_coarse_only(const PcgDesc<float>* descs, int n_probs, const CoarseJob* job, float* e_out,
+                               cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.stream = s;
-    if (job->Abf) return launch_coarse_tc<float>(cfg, *job, descs);
+    if (job->Abf) return launch_coarse_fused<float>(cfg, *job, descs, e_out);
     const int np = job->nd <= 8 ? 8 : 16;
     cfg.gridDim = dim3((job->N + 32 * kCoarseRowPasses - 1) / (32 * kCoarseRowPasses),
                        (job->N + kCoarseKC - 1) / kCoarseKC, (job->nd + np - 1) / np);

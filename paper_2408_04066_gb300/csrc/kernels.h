@@ -69,6 +69,7 @@ struct SlotDev {
     float* ec = nullptr;     // [B][ceil(coarse_n / kCoarseKC)][coarse_n] partial coarse corrections
     float* rcs = nullptr;    // [B][rcs_stride] per-aggregate coarse residual (aggregates over 64 rows)
     float* aggq = nullptr;   // [B][n_agg][9] rotation of each aggregate's coarse modes for the current solve
+    uint16_t* bsplit = nullptr;  // tensor-core coarse product: B operand, [ceil(B/16)][chunks][48 x 256] BF16
     size_t rcs_stride = 0;
     size_t rcp_stride = 0;
     double* outbuf = nullptr;  // [B][n][3] caller-order staging
@@ -138,10 +139,12 @@ void launch_pcg_init(const ElemArgs& a, int B, int tile_rows, double tol2, int m
 // One mesh's coarse solve inside the PCG iterations: descriptors d0 .. d0+nd-1.
 struct CoarseJob {
     const float* Ainv;          // FP32 inverse (CUDA-core product) ...
-    const void* Abf;            // ... or its BF16 tiles (tensor-core product), when not null
+    const void* Abf;            // ... or its packed BF16 rows (fused tensor-core kernel), when not null
+    const void* Bs;             // tensor cores: the context's B operand (groups of 16 slots)
     unsigned* err;              // the mesh's coarse-product error word
     const void* key;            // the mesh (context) the job belongs to
     int N, d0, nd, agg_units;   // agg_units: 64-row units per aggregate
+    int slots;                  // tensor cores: request slots of the context (B groups = ceil(slots / 16))
 };
 // n_units: SpMV tiles (tile_rows rows) over all problems; n_units_u: the
 // update and correction kernels' tiles (kRowTileU rows); split: SpMV threads
@@ -157,15 +160,24 @@ bool pcg_tile_supported(int tile_rows);
 cudaError_t build_coarse_inverse(const MeshDev& M, const void* val, int prec, const int* cnb_ptr, const int* cnb,
                                  int cnb_max, int agg_size, float* Ainv, cudaStream_t s);
 
-// Tensor-core coarse product (k_coarse_tc.cu): bytes of the BF16 tiles of an
-// N x N inverse, their packing from the FP32 inverse, the one-time kernel
-// attribute set-up (before any capture), and the launch for one job.
-// The coarse product alone for one job (mfem_coarse_apply).
-cudaError_t launch_coarse_only(const PcgDesc<float>* descs, int n_probs, const CoarseJob* job, cudaStream_t s);
+// The coarse product alone for one job (mfem_coarse_apply): the CUDA-core
+// product writes slice partials to each descriptor's ec; the tensor-core
+// product writes e[slot][N] to e_out.
+cudaError_t launch_coarse_only(const PcgDesc<float>* descs, int n_probs, const CoarseJob* job, float* e_out,
+                               cudaStream_t s);
+// Fused tensor-core coarse product and correction (k_coarse_tc.cu): bytes of
+// the packed BF16 rows of an N x N inverse and of the B operand for `slots`
+// request slots, the packing from the FP32 inverse, the split of FP32 coarse
+// residuals (rows of ldr floats) into the B operand, the one-time kernel
+// attribute set-up (before any capture), and the launch for one job (e_out
+// null: correction of the problems' u; else the product alone into e_out).
 size_t coarse_tc_bytes(int N);
+size_t coarse_b_bytes(int N, int slots);
 cudaError_t coarse_tc_pack(const float* Ainv, int N, void* Abf, cudaStream_t s);
+cudaError_t coarse_split(const float* rc, int N, int ldr, int B, void* Bs, cudaStream_t s);
 cudaError_t coarse_tc_init();
 template <typename T>
-cudaError_t launch_coarse_tc(const cudaLaunchConfig_t& base, const CoarseJob& j, const PcgDesc<T>* descs);
+cudaError_t launch_coarse_fused(const cudaLaunchConfig_t& base, const CoarseJob& j, const PcgDesc<T>* descs,
+                                float* e_out);
 
 }  // namespace mfem

@@ -111,12 +111,13 @@ def test_single_thread_baseline_times_five_frames():
 
 def test_roofline_arithmetic():
     """`roofline` of the JSON line: achieved = algorithmic bytes / PCG time,
-    frac = achieved / peak, traffic = the ncu record's bytes per
-    pose-iteration x pose-iterations per launch pair (or None without a record
-    for the current kernel source)."""
+    frac = achieved / peak, traffic = (the ncu record's row-kernel bytes per
+    pose-iteration x pose-iterations + its coarse-product bytes per launch x
+    coarse launches) per launch pair (or None without a record for the current
+    kernel source)."""
     import bench
-    profs = [dict(pcg_ms=2.0, pcg_bytes=8e9, pcg_launches=40, pcg_iters=100),
-             dict(pcg_ms=3.0, pcg_bytes=12e9, pcg_launches=60, pcg_iters=140)]
+    profs = [dict(pcg_ms=2.0, pcg_bytes=8e9, pcg_launches=40, pcg_iters=100, coarse_launches=15),
+             dict(pcg_ms=3.0, pcg_bytes=12e9, pcg_launches=60, pcg_iters=140, coarse_launches=25)]
     r = bench._roofline(profs, total_ms=10.0, mesh=(198474, 40103))
     peak, kind = bench.hbm_peak()
     assert r["bound"] == "hbm" and r["unit"] == "GB/s" and r["peak"] == peak
@@ -129,4 +130,8 @@ def test_roofline_arithmetic():
     if rec is None:
         assert r["traffic"] is None
     else:
-        assert r["traffic"] == pytest.approx(rec["dram_bytes_per_pose_iteration"] * 240 / 50)
+        assert r["traffic"] == pytest.approx((rec["row_dram_bytes_per_pose_iteration"] * 240
+                                              + rec["coarse_dram_bytes_per_launch"] * 40) / 50)
+    fake = {"row_dram_bytes_per_pose_iteration": 3.0, "coarse_dram_bytes_per_launch": 100.0}
+    assert bench.pcg_traffic(fake, 10, 2, 4) == pytest.approx((30 + 200) / 4)
+    assert bench.pcg_traffic(None, 10, 2, 4) is None

@@ -1,6 +1,9 @@
 """The coarse solve of the two-level preconditioner on the tensor cores
 (tcgen05, BF16 operands, FP32 accumulation), through the C ABI
 (mfem_coarse_apply), against the FP32 CUDA-core product of the same context.
+Inside a solve the same kernel also applies the correction u = zb + P e; the
+solve-level tests compare it with the CUDA-core product and its separate
+correction kernel.
 
 The tensor-core product stores A_c^{-1} rounded to BF16 (Ahat) and splits each
 coarse residual exactly into three BF16 parts, so it must equal Ahat r up to
@@ -51,7 +54,7 @@ def _bf16_rn(a):
 def test_columns_are_the_bf16_inverse(ctx):
     c, _ = ctx
     N = c.profile()["coarse_dof"]
-    assert N > 256          # more than one 128-row tile and one 256-column slice
+    assert N > 256          # several 30-row groups and more than one 256-column chunk
     eye = np.eye(N, dtype=np.float32)
     e32 = c.coarse_apply(eye, "fp32")          # row b = A_c^{-1} e_b (a column of the inverse)
     etc = c.coarse_apply(eye, "tc")
@@ -111,5 +114,25 @@ def test_solves_agree_across_products(mfem, precision):
         out[prod] = (x, [s["pcg_iters"] for s in st])
     err = np.abs(out["tc"][0] - out["fp32"][0]).max() / bbox
     assert err <= (1e-9 if precision == "fp64" else 1e-5), err
+    for a, b in zip(out["tc"][1], out["fp32"][1]):
+        assert abs(a - b) <= max(3, 0.05 * b), (out["tc"][1], out["fp32"][1])
+
+
+def test_solves_agree_with_two_slot_groups(mfem):
+    """20 poses in one batch: request slots 16..19 form a second group of the
+    tensor-core kernel's B operand (and a second CTA row of its grid)."""
+    cfg = figure_config(10000, seeds=range(20), model="snh")
+    X = cfg["X"]
+    bbox = float(np.linalg.norm(X.max(0) - X.min(0)))
+    out = {}
+    for prod in ("tc", "fp32"):
+        c = mfem.Context.from_config(cfg, precision="mixed", max_batch=20, newton_max=80, coarse_product=prod,
+                                     newton_tol=1e-9, cg_tol=1e-3)
+        x, st = c.solve_batch(cfg["xfs"])
+        c.close()
+        assert all(s["converged"] for s in st)
+        out[prod] = (x, [s["pcg_iters"] for s in st])
+    err = np.abs(out["tc"][0] - out["fp32"][0]).max() / bbox
+    assert err <= 1e-5, err
     for a, b in zip(out["tc"][1], out["fp32"][1]):
         assert abs(a - b) <= max(3, 0.05 * b), (out["tc"][1], out["fp32"][1])
