@@ -955,14 +955,17 @@ def run_large(args, dist):
 
 def run_ncu_case(args):
     """Small, fixed case for ncu captures (a few GB on the device, short kernels):
-    the 200k-tet figure, 8 poses, 3 Newton steps, PCG tiles of 256 rows."""
+    the 200k-tet figure, 8 poses, 3 Newton steps, PCG tiles of 256 rows, one
+    SpMV thread per row."""
     import torch
     from paper_2408_04066_gb300 import build as B
     B.build()
     from paper_2408_04066_gb300 import mfem
     from synth import figure_config
     cfg = figure_config(args.tets, model=args.model, seeds=range(8))
-    ctx = mfem.Context.from_config(cfg, precision=args.precision, max_batch=8, newton_max=3, tile_rows=256)
+    # the headline's SpMV shape, fixed: under ncu's serialised launches the autotuner's timings mislead
+    ctx = mfem.Context.from_config(cfg, precision=args.precision, max_batch=8, newton_max=3, tile_rows=256,
+                                   spmv_split=1)
     ctx.solve_batch(torch.tensor(cfg["xfs"], dtype=torch.float64, device="cuda"))
     torch.cuda.synchronize()
     print(json.dumps({"ncu_case": ctx.profile()}), flush=True)
