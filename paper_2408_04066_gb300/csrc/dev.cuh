@@ -22,11 +22,15 @@ constexpr int kRowTileU = 256;       // rows per block of the PCG update and cor
 // symmetric 12x12 element matrix in the order (0,0) (0,1) (0,2) (0,3) (1,1)
 // (1,2) (1,3) (2,2) (2,3) (3,3); a diagonal block is symmetric and keeps its six
 // upper entries (xx, yy, zz, yz, xz, xy), an off-diagonal block its nine
-// (row-major): 78 values per tet.
-constexpr int kKe = 78;
+// (row-major) and one unused value, so that every block starts on an even
+// element (8-byte loads in FP32, 16-byte in FP64): 84 values per tet.  The
+// element-block array carries kKePad values past its last record (a reader
+// may load ten values from the last diagonal block).
+constexpr int kKe = 84;
+constexpr int kKePad = 4;
 __host__ __device__ __forceinline__ int ke_offset(int a, int b) {   // a <= b
     const int p = a * 4 - (a * (a - 1)) / 2 + (b - a);              // block index
-    return 9 * p - 3 * (a + (b > a ? 1 : 0));                        // minus the diagonal blocks' 3 saved
+    return 10 * p - 4 * (a + (b > a ? 1 : 0));                       // minus the diagonal blocks' 4 saved
 }
 
 // Per-problem PCG vector area, in elements of the PCG type, rows padded to 32:

@@ -146,7 +146,7 @@ mfem_status alloc_slots(mfem_ctx* c, int B) {
     AL(S.g, B * n * 3 * 8);
     AL(S.outbuf, B * n * 3 * 8);
     AL(S.ge, B * m * 12 * 8);
-    AL(S.Ke, B * m * kKe * kt);
+    AL(S.Ke, (B * m * kKe + kKePad) * kt);
     AL(S.val, B * slots * 9 * kt);
     AL(S.dinv, B * n * 9 * kt);
     AL(S.vec, B * kVecStride * npad32((int)n) * kt);

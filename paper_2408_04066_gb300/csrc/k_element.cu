@@ -250,7 +250,7 @@ __device__ __forceinline__ void Ecol(const KT (&g)[3], const KT (&u)[3], KT (&e)
 }
 
 // Element blocks K_ab = W E_a^T C E_b for a <= b, generic 6x6 C, in the
-// 78-value layout (diagonal blocks: upper entries only).
+// element-block layout (diagonal blocks: upper entries only).
 template <typename KT>
 __device__ __forceinline__ void blocks_generic(const KT (&C)[6][6], const KT (&G)[4][3], const KT (&Q)[3][3],
                                                KT W, KT* __restrict__ out) {
@@ -303,7 +303,7 @@ __device__ __forceinline__ void blocks_generic(const KT (&C)[6][6], const KT (&G
 
 // ARAP / co-rotational blocks in closed form:
 // K_ab = W [mu (G_a.G_b) I + mu h_b h_a^T + lam h_a h_b^T], h_a = Q G_a,
-// in the 78-value layout.
+// in the element-block layout.
 template <typename KT>
 __device__ __forceinline__ void blocks_quadratic(const KT (&G)[4][3], const KT (&Q)[3][3], KT wm, KT wl,
                                                  KT* __restrict__ out) {
@@ -520,7 +520,8 @@ __device__ __forceinline__ double vertex_energy(const ElemArgs& A, int b, int v,
 // shared-memory area and the warp then copies the area out with consecutive
 // lanes on consecutive words; forces first, then the blocks in the same area.
 // FP64 Hessians (KT = double) are written directly.
-constexpr int kStageWords = 2560;   // floats per warp: 32 x 78 blocks, or 32 x 12 doubles of forces
+constexpr int kStageWords = 32 * kKe;   // floats per warp: 32 records of blocks (or 32 x 12 doubles of forces)
+static_assert(kStageWords >= 32 * 12 * 2, "the force stage fits");
 
 template <typename KT, int MODEL, bool HESS>
 __global__ void __launch_bounds__(kTetTile, 4) k_element(ElemArgs A) {

@@ -57,6 +57,51 @@ __device__ __forceinline__ double row_gradient(const ElemArgs& A, int b, int row
     return g0 * g0 + g1 * g1 + g2 * g2;
 }
 
+// The ten values from the start of contribution `code`'s stored block (tet
+// code >> 4, local vertices ((code >> 2) & 3, code & 3), either order): five
+// aligned pairs
+__device__ __forceinline__ void load_block(const float* __restrict__ Ke, int code, float (&v)[10]) {
+    const int t = code >> 4, ea = (code >> 2) & 3, eb = code & 3;
+    const float2* q = reinterpret_cast<const float2*>(Ke + (size_t)t * kKe + ke_offset(min(ea, eb), max(ea, eb)));
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const float2 p = __ldg(q + i);
+        v[2 * i] = p.x;
+        v[2 * i + 1] = p.y;
+    }
+}
+__device__ __forceinline__ void load_block(const double* __restrict__ Ke, int code, double (&v)[10]) {
+    const int t = code >> 4, ea = (code >> 2) & 3, eb = code & 3;
+    const double2* q = reinterpret_cast<const double2*>(Ke + (size_t)t * kKe + ke_offset(min(ea, eb), max(ea, eb)));
+#pragma unroll
+    for (int i = 0; i < 5; ++i) {
+        const double2 p = __ldg(q + i);
+        v[2 * i] = p.x;
+        v[2 * i + 1] = p.y;
+    }
+}
+
+// Add the block in the slot's orientation: a diagonal block from its six
+// upper entries (xx, yy, zz, yz, xz, xy), an upper block as stored, a lower
+// block transposed.
+template <typename KT>
+__device__ __forceinline__ void add_block(KT (&acc)[9], int code, const KT (&v)[10]) {
+    const int ea = (code >> 2) & 3, eb = code & 3;
+    if (ea == eb) {
+        acc[0] += v[0]; acc[1] += v[5]; acc[2] += v[4];
+        acc[3] += v[5]; acc[4] += v[1]; acc[5] += v[3];
+        acc[6] += v[4]; acc[7] += v[3]; acc[8] += v[2];
+    } else if (ea < eb) {
+#pragma unroll
+        for (int e = 0; e < 9; ++e) acc[e] += v[e];
+    } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) acc[3 * i + j] += v[3 * j + i];
+    }
+}
+
 // One thread per slot of the sliced pattern: the slot's 3x3 block summed from
 // the element blocks of every tet holding both vertices (the contributions of
 // a slot are sorted by tet, so the order -- and every bit of the result -- is
@@ -81,26 +126,24 @@ __global__ void __launch_bounds__(kRowTile) k_assemble_slots(ElemArgs A) {
 #pragma unroll
     for (int e = 0; e < 9; ++e) acc[e] = (KT)0;
     const int c0 = __ldg(M.contrib_ptr + gs), c1 = __ldg(M.contrib_ptr + gs + 1);
-    for (int ci = c0; ci < c1; ++ci) {
+    // contributions four at a time, every load of the four issued first: ten
+    // values (five pairs) from each block's start, whatever its kind
+    int ci = c0;
+    for (; ci + 3 < c1; ci += 4) {
+        int code[4];
+        KT v[4][10];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) code[q] = __ldg(M.contrib + ci + q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) load_block(Ke, code[q], v[q]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) add_block(acc, code[q], v[q]);
+    }
+    for (; ci < c1; ++ci) {
         const int code = __ldg(M.contrib + ci);
-        const int t = code >> 4, ea = (code >> 2) & 3, eb = code & 3;
-        if (ea == eb) {   // symmetric diagonal block: six stored entries
-            const KT* blk = Ke + (size_t)t * kKe + ke_offset(ea, ea);
-            const KT xx = blk[0], yy = blk[1], zz = blk[2], yz = blk[3], xz = blk[4], xy = blk[5];
-            acc[0] += xx; acc[1] += xy; acc[2] += xz;
-            acc[3] += xy; acc[4] += yy; acc[5] += yz;
-            acc[6] += xz; acc[7] += yz; acc[8] += zz;
-        } else if (ea < eb) {
-            const KT* blk = Ke + (size_t)t * kKe + ke_offset(ea, eb);
-#pragma unroll
-            for (int e = 0; e < 9; ++e) acc[e] += blk[e];
-        } else {
-            const KT* blk = Ke + (size_t)t * kKe + ke_offset(eb, ea);
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-                for (int j = 0; j < 3; ++j) acc[3 * i + j] += blk[3 * j + i];
-        }
+        KT v[10];
+        load_block(Ke, code, v);
+        add_block(acc, code, v);
     }
     const bool diag = (c == row);
     const bool pin_r = M.pin_handle_v[row] >= 0;
