@@ -549,8 +549,10 @@ def run_mfem(args, dist):
             "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.precision == "mixed" else "f64",
-            "dtype_note": ("mixed: FP32 element Hessians, matrix, SpMV and PCG vectors; FP64 positions, element "
-                           "forces (the Newton residual), stop test and line-search energies; PCG inner products "
+            "dtype_note": ("mixed: FP32 element Hessians, matrix, SpMV and PCG vectors; FP64 positions, "
+                           "deformation gradients, stretches, stresses, the gradient sum (the Newton residual), "
+                           "stop test and line-search energies; element forces formed in FP32 from the FP64 stress "
+                           "(newton_tol >= 1e-7; tighter tests keep them in FP64); PCG inner products "
                            "as float-float (Dekker/Knuth error-free FP32 pairs, ~48 bits) per row and warp, "
                            "then FP64; coarse solve BF16 x 3-part BF16 split on the tensor cores, FP32 "
                            "accumulation" if args.precision == "mixed" else "FP64 throughout except the "

@@ -67,6 +67,7 @@ ElemArgs elem_args(const mfem_ctx* c) {
     a.fext = c->fext_dev;
     a.fext_stride = c->fext_sets > 1 ? 3 * (int64_t)c->plan.n : 0;
     a.rot_polar = c->opt.rotation == MFEM_ROT_POLAR ? 1 : 0;
+    a.f32_forces = c->slot.prec == 1 && c->opt.newton_tol >= kF32ForcesTol ? 1 : 0;
     return a;
 }
 

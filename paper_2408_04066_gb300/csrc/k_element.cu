@@ -551,28 +551,68 @@ __global__ void __launch_bounds__(kTetTile, 4) k_element(ElemArgs A) {
         mu = M.mu[k];
         lam = M.lam[k];
         w = M.vol[k];
-        en[0] = w * psi_sigma<MODEL>(S, mu, lam, sig);
-        // forces f_a = W Lambda G_a, Lambda = Q sigma (a = 1..3), f_0 = -(f_1 + f_2 + f_3)
-        const double sw[3][3] = {{w * sig[0], w * sig[5], w * sig[4]},
-                                 {w * sig[5], w * sig[1], w * sig[3]},
-                                 {w * sig[4], w * sig[3], w * sig[2]}};
-        double P[3][3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int j = 0; j < 3; ++j) P[i][j] = Q[i][0] * sw[0][j] + Q[i][1] * sw[1][j] + Q[i][2] * sw[2][j];
-        double f0[3] = {0.0, 0.0, 0.0};
         double* gl = gs + 12 * lane;
+        if (sizeof(KT) == 4 && A.f32_forces) {
+            // mixed path: F, S, the energy and the stress in FP64 (positions and
+            // rotations cancel in F and S, the stress terms of order mu cancel
+            // near the rest state); the stress rounded to FP32 keeps its own
+            // relative precision, and the forces W Q sigma G_a are formed from
+            // it in FP32
+            en[0] = w * psi_sigma<MODEL>(S, mu, lam, sig);
+            float sg[6];
 #pragma unroll
-        for (int a = 1; a < 4; ++a)
+            for (int i = 0; i < 6; ++i) sg[i] = (float)sig[i];
+            const float wf = (float)w;
+            const float sw[3][3] = {{wf * sg[0], wf * sg[5], wf * sg[4]},
+                                    {wf * sg[5], wf * sg[1], wf * sg[3]},
+                                    {wf * sg[4], wf * sg[3], wf * sg[2]}};
+            float Qf[3][3], Gf[3][3], P[3][3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i) {
-                const double f = P[i][0] * G[a][0] + P[i][1] * G[a][1] + P[i][2] * G[a][2];
-                gl[3 * a + i] = f;
-                f0[i] -= f;
-            }
+            for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int i = 0; i < 3; ++i) gl[i] = f0[i];
+                for (int j = 0; j < 3; ++j) {
+                    Qf[i][j] = (float)Q[i][j];
+                    Gf[i][j] = M.Dminv32[(size_t)(3 * i + j) * m + k];
+                }
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j)
+                    P[i][j] = Qf[i][0] * sw[0][j] + Qf[i][1] * sw[1][j] + Qf[i][2] * sw[2][j];
+            float f0[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const float f = P[i][0] * Gf[a][0] + P[i][1] * Gf[a][1] + P[i][2] * Gf[a][2];
+                    gl[3 * (a + 1) + i] = (double)f;
+                    f0[i] -= f;
+                }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) gl[i] = (double)f0[i];
+        } else {
+            en[0] = w * psi_sigma<MODEL>(S, mu, lam, sig);
+            // forces f_a = W Lambda G_a, Lambda = Q sigma (a = 1..3), f_0 = -(f_1 + f_2 + f_3)
+            const double sw[3][3] = {{w * sig[0], w * sig[5], w * sig[4]},
+                                     {w * sig[5], w * sig[1], w * sig[3]},
+                                     {w * sig[4], w * sig[3], w * sig[2]}};
+            double P[3][3];
+#pragma unroll
+            for (int i = 0; i < 3; ++i)
+#pragma unroll
+                for (int j = 0; j < 3; ++j) P[i][j] = Q[i][0] * sw[0][j] + Q[i][1] * sw[1][j] + Q[i][2] * sw[2][j];
+            double f0[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int a = 1; a < 4; ++a)
+#pragma unroll
+                for (int i = 0; i < 3; ++i) {
+                    const double f = P[i][0] * G[a][0] + P[i][1] * G[a][1] + P[i][2] * G[a][2];
+                    gl[3 * a + i] = f;
+                    f0[i] -= f;
+                }
+#pragma unroll
+            for (int i = 0; i < 3; ++i) gl[i] = f0[i];
+        }
     }
     __syncwarp();
     {   // forces out: the warp's 32 contiguous 96-byte records

@@ -84,7 +84,13 @@ struct ElemArgs {
     const double* fext = nullptr;  // external vertex forces [sets][n][3] (internal order) or null
     int64_t fext_stride = 0;       // doubles between problems' force fields (0: one shared field)
     int rot_polar = 0;             // 1: R_k = rotation factor of F_k (co-rotational FEM), else the rig's
+    int f32_forces = 0;            // mixed path: element forces formed in FP32 from the FP64 stress
 };
+// The mixed path forms element forces in FP32 when the Newton stop test is at
+// least this loose: the FP32 forces leave a residual floor near 1e-8 of the
+// initial gradient (measured: the 10k-tet figure converges to 1e-8 and stalls
+// at 6e-9; the 200k figure reaches 1e-9), so tighter tests keep FP64 forces.
+constexpr double kF32ForcesTol = 1.0e-7;
 
 #ifdef __CUDACC__
 // Vector `off` of problem b in the interleaved PCG vector block of a slot.

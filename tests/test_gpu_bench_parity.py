@@ -206,3 +206,22 @@ def test_cfg4_served_requests(mfem, record_property):
     record_property("parity", json.dumps({"config": "cfg4 served 10k/50k/200k/800k", **res}))
     assert res["10k_corot_err"] <= TOL_MIXED and res["50k_snh_err"] <= TOL_MIXED, res
     assert res["200k_corot_rel_grad"] <= 1.5e-6 and res["800k_snh_rel_grad"] <= 1.5e-6, res
+
+
+def test_fp32_forces_at_their_threshold(mfem, record_property):
+    """The mixed path forms element forces in FP32 when newton_tol >= 1e-7
+    (the loosest tolerance that still keeps a 10x margin over the residual
+    floor those forces leave, ~1e-8 on this mesh): at exactly that tolerance
+    every pose converges and matches the oracle."""
+    cfg = figure_config(10000, seeds=range(12), model="snh")
+    so = S.Setup.from_config(cfg)
+    ctx = mfem.Context.from_config(cfg, precision="mixed", max_batch=12, newton_max=80, newton_tol=1e-7, cg_tol=1e-3)
+    x, st = ctx.solve_batch(cfg["xfs"])
+    ctx.close()
+    assert all(s["converged"] for s in st)
+    assert max(s["rel_grad"] for s in st) <= 1e-7
+    ref = solve_many(cfg, list(cfg["xfs"]), "snh", newton_tol=1e-12, newton_max=80)
+    errs = [_err(x[b], ref[b][0], so.bbox_diag) for b in range(12)]
+    record_property("parity", json.dumps({"config": "10k figure x12 poses, FP32 forces at newton_tol 1e-7",
+                                          "max_err": max(errs)}))
+    assert max(errs) <= TOL_MIXED, errs
