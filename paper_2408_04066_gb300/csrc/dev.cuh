@@ -33,17 +33,22 @@ __host__ __device__ __forceinline__ int ke_offset(int a, int b) {   // a <= b
     return 10 * p - 4 * (a + (b > a ? 1 : 0));                       // minus the diagonal blocks' 4 saved
 }
 
-// Per-problem PCG vector area, in elements of the PCG type, rows padded to 32:
-// the neighbour record nb[n][4] = (u.xyz, 0) -- the preconditioned residual,
-// the one vector the SpMV gathers from neighbours (16 bytes in FP32) -- then
-// the row record rec[n][24] = (dx, r, p, s, w, zb), six aligned 4-element
-// groups: the Newton increment, the residual, the search direction, s = K p,
-// w = K u, and the block-Jacobi part of u.
+// Per-problem PCG vector area, in elements of the PCG type, rows padded to 32
+// (np = npad32(n)): the neighbour record nb[np][4] = (u.xyz, 0) -- the
+// preconditioned residual, the one vector the SpMV gathers from neighbours (16
+// bytes in FP32) -- then six row fields of [np][4] each, field-major (a warp's
+// access to one field of 32 consecutive rows is one contiguous run): the Newton
+// increment dx, the residual r, the search direction p, s = K p, w = K u, and
+// the block-Jacobi part zb of u.  Field f (kRecDX .. kRecZB) of row i is at
+// rec + f * np + 4 i (rec_field).
 constexpr int kVecStride = 28;                 // times npad32(n)
 constexpr int kOffNB = 0, kOffRec = 4;
-constexpr int kRec = 24;
 constexpr int kRecDX = 0, kRecR = 4, kRecP = 8, kRecS = 12, kRecW = 16, kRecZB = 20;
 __host__ __device__ __forceinline__ size_t npad32(int n) { return ((size_t)n + 31) & ~(size_t)31; }
+template <typename T>
+__host__ __device__ __forceinline__ T* rec_field(T* rec, size_t np, int f, size_t row) {
+    return rec + (size_t)f * np + 4 * row;
+}
 
 // Problem states (PCG)
 enum : int { kIdle = 0, kActive = 1, kConverged = 2, kMaxIter = 3 };
@@ -103,9 +108,9 @@ struct PcgDesc {
     const int* slice_ptr;  // [n_slices+1] first slot of each slice
     const int* col;        // [slots] column block or -1
     const T* val;          // [slots/32][9][32]
-    const T* dinv;         // [n][9] inverse diagonal blocks
+    const T* dinv;         // [9][npad32(n)] inverse diagonal blocks, entry-major
     T* nb;                 // [n][4] neighbour records (u)
-    T* rec;                // [n][24] row records (dx, r, p, s, w, zb)
+    T* rec;                // the six row fields (dx, r, p, s, w, zb), field-major (rec_field)
     double* part;          // [tiles][4] tile partials
     ProbScal* sc;
     int n_rows, n_tiles, unit_begin;   // the SpMV's tiles (autotuned rows per block)

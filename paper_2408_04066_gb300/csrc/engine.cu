@@ -112,7 +112,7 @@ size_t bytes_per_slot(const mfem_ctx* c) {
     const size_t n = c->plan.n, m = c->plan.m, H = c->plan.H;
     const size_t kt = c->slot.prec == 1 ? 4 : 8;
     const size_t slots = (size_t)c->plan.slice_ptr.back();
-    return H * 12 * 8 + 4 * n * 3 * 8 + m * 12 * 8 + m * kKe * kt + slots * 9 * kt + n * 9 * kt +
+    return H * 12 * 8 + 4 * n * 3 * 8 + m * 12 * 8 + m * kKe * kt + slots * 9 * kt + 9 * npad32((int)n) * kt +
            kVecStride * npad32((int)n) * kt + (size_t)part_tiles_for(c) * 4 * 8 + sizeof(ProbScal) + 4 + 8 + 8 +
            H * 12 * 8 + (c->opt.init == MFEM_INIT_WARM ? 2 * n * 3 * 8 : 0) + 4 + (line_search(c) ? n * 3 * 8 : 0) +
            (c->mesh.coarse_n > 0 ? ((n + 255) / 256) * 24 * 4 + (coarse_ks(c) + 1) * c->mesh.coarse_n * 4 + 128 +
@@ -149,7 +149,7 @@ mfem_status alloc_slots(mfem_ctx* c, int B) {
     AL(S.ge, B * m * 12 * 8);
     AL(S.Ke, (B * m * kKe + kKePad) * kt);
     AL(S.val, B * slots * 9 * kt);
-    AL(S.dinv, B * n * 9 * kt);
+    AL(S.dinv, B * 9 * npad32((int)n) * kt);
     AL(S.vec, B * kVecStride * npad32((int)n) * kt);
     AL(S.part, B * (size_t)S.part_tiles * 4 * 8);
     AL(S.sc, B * sizeof(ProbScal));
@@ -296,7 +296,7 @@ void build_descs(std::vector<Group>& gs, int tile, int prec, std::vector<PcgDesc
             d.slice_ptr = c->mesh.slice_ptr;
             d.col = c->mesh.col;
             d.val = (const T*)c->slot.val + (size_t)b * slots * 9;
-            d.dinv = (const T*)c->slot.dinv + (size_t)b * n * 9;
+            d.dinv = (const T*)c->slot.dinv + (size_t)b * 9 * npad32(n);
             const size_t np = npad32(n);
             T* v = (T*)c->slot.vec + (size_t)b * kVecStride * np;
             d.nb = v + kOffNB * np;
@@ -440,7 +440,7 @@ mfem_status launch_chunk(mfem_ctx* c, const PcgDesc<T>* dst, int nd, int units, 
 
 template <typename T>
 mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, int split, int max_iters, bool count,
-                    bool one_chunk = false) {
+                    bool one_chunk = false, bool slopes = false) {
     mfem_ctx* c = c0;
     std::vector<PcgDesc<T>> d;
     std::vector<CoarseJob> jobs;
@@ -495,6 +495,27 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
             c->prof.coarse_launches += cl * n_it;
             c->prof.pcg_bytes += coarse_bytes * n_it;
         }
+        // slopes g.dx of every problem inside PCG, read back with the PCG
+        // states: a problem whose PCG ended in this chunk has its line-search
+        // slope without another round trip (the others' are not used)
+        if (slopes)
+            for (auto& g : gs) {
+                mfem_ctx* gc = g.ctx;
+                if (gc->slot.prec != prec || !line_search(gc)) continue;
+                std::vector<int> m(g.B, 0);
+                bool any_ls = false;
+                for (int b = 0; b < g.B; ++b) {
+                    m[b] = g.ph[b].active && g.ph[b].in_pcg && !g.ph[b].pred;
+                    any_ls |= m[b] != 0;
+                }
+                if (!any_ls) continue;
+                mfem_status st = upload_active(gc, g.B, m);
+                if (st != MFEM_OK) return st;
+                int pl = gc->prof.begin(3, c->stream);
+                launch_slope(elem_args(gc), g.B, c->stream);
+                gc->prof.end(pl, c->stream);
+                gc->prof.launches++;
+            }
         bool any = false;
         for (auto& g : gs)
             if (g.ctx->slot.prec == prec) {
@@ -934,8 +955,8 @@ mfem_status advance(std::vector<Group>& gs) {
             if (g.ctx->slot.prec == prec)
                 for (int b = 0; b < g.B; ++b) any |= g.ph[b].active && g.ph[b].in_pcg;
         if (!any) continue;
-        mfem_status st = prec == 1 ? run_pcg<float>(c, gs, 1, c->tile_rows, c->spmv_split, 0, true, true)
-                                   : run_pcg<double>(c, gs, 0, c->tile_rows, c->spmv_split, 0, true, true);
+        mfem_status st = prec == 1 ? run_pcg<float>(c, gs, 1, c->tile_rows, c->spmv_split, 0, true, true, true)
+                                   : run_pcg<double>(c, gs, 0, c->tile_rows, c->spmv_split, 0, true, true, true);
         if (st != MFEM_OK) return st;
     }
     CK(cudaGetLastError());
@@ -958,30 +979,15 @@ mfem_status advance(std::vector<Group>& gs) {
         }
     }
     if (!any_fin) return MFEM_OK;
-    // slope g.dx for the line search (SNH, or any model whose rotations follow
-    // F; the predictor step is taken whole)
-    bool any_ls = false;
+    // line-searched steps (SNH, or any model whose rotations follow F; the
+    // predictor step is taken whole): their slopes g.dx came back with the
+    // PCG states of the chunk that ended them
     std::vector<std::vector<int>> ls(gs.size());
     for (size_t gi = 0; gi < gs.size(); ++gi) {
         Group& g = gs[gi];
         ls[gi].assign(g.B, 0);
         if (!line_search(g.ctx)) continue;
         for (int b = 0; b < g.B; ++b) ls[gi][b] = fin[gi][b] && !g.ph[b].pred;
-        if (!any_of(ls[gi])) continue;
-        any_ls = true;
-        mfem_ctx* gc = g.ctx;
-        mfem_status st = upload_active(gc, g.B, ls[gi]);
-        if (st != MFEM_OK) return st;
-        int pl = gc->prof.begin(3, s);
-        launch_slope(elem_args(gc), g.B, s);
-        gc->prof.end(pl, s);
-        gc->prof.launches++;
-        st = read_scalars(gc, g.B);
-        if (st != MFEM_OK) return st;
-    }
-    if (any_ls) {
-        CK(cudaStreamSynchronize(s));
-        synced(gs);
     }
     // backtracking line search on E (SNH, polar rotations): attempt 0 (the full
     // step) is taken speculatively -- x_prev is kept, x moves to x_prev + dx, and

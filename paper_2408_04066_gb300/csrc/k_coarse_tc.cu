@@ -428,7 +428,7 @@ __global__ void __launch_bounds__(kFuThreads, 1)
         T z[kTcProbs][3];
 #pragma unroll
         for (int p = 0; p < kTcProbs; ++p)
-            if (dp[p]) ldv(dp[p]->rec + kRec * (size_t)row + kRecZB, z[p]);
+            if (dp[p]) ldv(rec_field(dp[p]->rec, npad32(n), kRecZB, row), z[p]);
 #pragma unroll
         for (int p = 0; p < kTcProbs; ++p) {
             const PcgDesc<T>* d = dp[p];

@@ -693,9 +693,11 @@ __global__ void __launch_bounds__(kTetTile) k_energy_trial(ElemArgs A) {
     double en[1] = {0.0};
     if (k < m) {
         const double* x = A.slot.x + (size_t)b * n * 3;
-        const T* dx = (const T*)A.slot.vec + (size_t)b * kVecStride * npad32(n) + kOffRec * npad32(n) + kRecDX;
+        // the dx field: 4 elements per vertex
+        const T* dx = rec_field((const T*)A.slot.vec + (size_t)b * kVecStride * npad32(n) + kOffRec * npad32(n),
+                                npad32(n), kRecDX, 0);
         double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6], sig[6];
-        gather_x<T>(x, dx, A.slot.alpha[b], M.tet[k], xa, kRec);
+        gather_x<T>(x, dx, A.slot.alpha[b], M.tet[k], xa, 4);
         load_G(M.Dminv64, m, k, G);
         tet_rotation(A, xf, qs, k, xa, G, Q);
         stretch(xa, G, Q, F, S);
@@ -703,8 +705,8 @@ __global__ void __launch_bounds__(kTetTile) k_energy_trial(ElemArgs A) {
     }
     if (k < n) {
         const double* xv = A.slot.x + ((size_t)b * n + k) * 3;
-        const T* dv = (const T*)A.slot.vec + (size_t)b * kVecStride * npad32(n) + kOffRec * npad32(n) +
-                      kRec * (size_t)k + kRecDX;
+        const T* dv = rec_field((const T*)A.slot.vec + (size_t)b * kVecStride * npad32(n) + kOffRec * npad32(n),
+                                npad32(n), kRecDX, k);
         const double al = A.slot.alpha[b];
         const double y[3] = {fma(al, (double)dv[0], xv[0]), fma(al, (double)dv[1], xv[1]),
                              fma(al, (double)dv[2], xv[2])};

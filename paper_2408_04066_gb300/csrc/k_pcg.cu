@@ -150,11 +150,16 @@ __device__ __forceinline__ void coeffs(const ProbScal* sc, double& a, double& b)
     b = sc->beta;
 }
 
-// z_bj = D^{-1} r for one row (D^{-1} row-major 3x3)
+// z_bj = D^{-1} r for one row: D^{-1} row-major 3x3, its entry e of every row
+// stored contiguously (entry e of row `row` at di[e * np + row], np = npad32(n)),
+// so a warp's load of one entry is one contiguous 32-row run
 template <typename T>
-__device__ __forceinline__ void apply_dinv(const T* __restrict__ di, const T (&r)[3], T (&z)[3]) {
+__device__ __forceinline__ void apply_dinv(const T* __restrict__ di, size_t np, int row, const T (&r)[3], T (&z)[3]) {
+    T m[9];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) z[i] = di[3 * i] * r[0] + di[3 * i + 1] * r[1] + di[3 * i + 2] * r[2];
+    for (int e = 0; e < 9; ++e) m[e] = di[e * np + row];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) z[i] = m[3 * i] * r[0] + m[3 * i + 1] * r[1] + m[3 * i + 2] * r[2];
 }
 
 // ---- PCG in single-reduction form --------------------------------------------
@@ -198,17 +203,18 @@ __global__ void k_pcg_init(ElemArgs A, double tol2, int maxit, const double* __r
     float r32[3] = {0.f, 0.f, 0.f};
     if (row < n) {
         const double* g = A.slot.g + ((size_t)b * n + row) * 3;
-        const T* di = (const T*)A.slot.dinv + ((size_t)b * n + row) * 9;
-        T* rec = vecp<T>(A.slot, b, kOffRec, n) + kRec * (size_t)row;
+        const T* di = (const T*)A.slot.dinv + (size_t)b * 9 * npad32(n);
+        T* rec = vecp<T>(A.slot, b, kOffRec, n);
+        const size_t np = npad32(n);
         const T r[3] = {(T)(-g[0]), (T)(-g[1]), (T)(-g[2])};
         T z[3];
-        apply_dinv(di, r, z);
-        st4(rec + kRecDX, (T)0, (T)0, (T)0);
-        st4(rec + kRecR, r[0], r[1], r[2]);
-        st4(rec + kRecP, (T)0, (T)0, (T)0);
-        st4(rec + kRecS, (T)0, (T)0, (T)0);
-        st4(rec + kRecW, (T)0, (T)0, (T)0);
-        st4(rec + kRecZB, z[0], z[1], z[2]);
+        apply_dinv(di, np, row, r, z);
+        st4(rec_field(rec, np, kRecDX, row), (T)0, (T)0, (T)0);
+        st4(rec_field(rec, np, kRecR, row), r[0], r[1], r[2]);
+        st4(rec_field(rec, np, kRecP, row), (T)0, (T)0, (T)0);
+        st4(rec_field(rec, np, kRecS, row), (T)0, (T)0, (T)0);
+        st4(rec_field(rec, np, kRecW, row), (T)0, (T)0, (T)0);
+        st4(rec_field(rec, np, kRecZB, row), z[0], z[1], z[2]);
         if (!coarse) st4(vecp<T>(A.slot, b, kOffNB, n) + 4 * (size_t)row, z[0], z[1], z[2]);
         v[0] = (double)r[0] * (double)r[0] + (double)r[1] * (double)r[1] + (double)r[2] * (double)r[2];
         r32[0] = (float)r[0];
@@ -318,15 +324,15 @@ __global__ void __launch_bounds__(TILE * SPLIT, (sizeof(T) == 4 ? 2048 : 1024) /
     const bool owner = valid && half == 0;
     if (!owner) a0 = a1 = a2 = 0;
     T ur[3] = {0, 0, 0};
-    T* rec = d.rec + kRec * (size_t)row;
+    const size_t np = npad32(d.n_rows);
     if (owner) {
         ld4(d.nb + 4 * (size_t)row, ur);
-        st4(rec + kRecW, a0, a1, a2);
+        st4(rec_field(d.rec, np, kRecW, row), a0, a1, a2);
     }
     double v[3];
     v[1] = warp_sum_partial(dot3_partial(a0, a1, a2, ur[0], ur[1], ur[2]));
     T r[3] = {0, 0, 0};
-    if (owner) ld4(rec + kRecR, r);
+    if (owner) ld4(rec_field(d.rec, np, kRecR, row), r);
     v[0] = warp_sum_partial(dot3_partial(r[0], r[1], r[2], ur[0], ur[1], ur[2]));
     v[2] = warp_sum_partial(dot3_partial(r[0], r[1], r[2], r[0], r[1], r[2]));
     double tot[3];
@@ -377,14 +383,14 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
     coeffs(sc, alpha, beta);
     float r32[3] = {0.f, 0.f, 0.f};
     if (row < d.n_rows) {
-        T* rec = d.rec + kRec * (size_t)row;
+        const size_t np = npad32(d.n_rows);
         T uu[3], ww[3], pp[3], ss[3], dx[3], r[3], z[3];
         ld4(d.nb + 4 * (size_t)row, uu);
-        ld4(rec + kRecW, ww);
-        ld4(rec + kRecP, pp);
-        ld4(rec + kRecS, ss);
-        ld4(rec + kRecDX, dx);
-        ld4(rec + kRecR, r);
+        ld4(rec_field(d.rec, np, kRecW, row), ww);
+        ld4(rec_field(d.rec, np, kRecP, row), pp);
+        ld4(rec_field(d.rec, np, kRecS, row), ss);
+        ld4(rec_field(d.rec, np, kRecDX, row), dx);
+        ld4(rec_field(d.rec, np, kRecR, row), r);
 #pragma unroll
         for (int i = 0; i < 3; ++i) {
             pp[i] = fma(beta, pp[i], uu[i]);
@@ -392,12 +398,12 @@ __global__ void __launch_bounds__(TILE) k_pcg_update(const PcgDesc<T>* __restric
             dx[i] = fma(alpha, pp[i], dx[i]);
             r[i] = fma(-alpha, ss[i], r[i]);
         }
-        apply_dinv(d.dinv + 9 * (size_t)row, r, z);
-        st4(rec + kRecP, pp[0], pp[1], pp[2]);
-        st4(rec + kRecS, ss[0], ss[1], ss[2]);
-        st4(rec + kRecDX, dx[0], dx[1], dx[2]);
-        st4(rec + kRecR, r[0], r[1], r[2]);
-        st4(rec + kRecZB, z[0], z[1], z[2]);
+        apply_dinv(d.dinv, np, row, r, z);
+        st4(rec_field(d.rec, np, kRecP, row), pp[0], pp[1], pp[2]);
+        st4(rec_field(d.rec, np, kRecS, row), ss[0], ss[1], ss[2]);
+        st4(rec_field(d.rec, np, kRecDX, row), dx[0], dx[1], dx[2]);
+        st4(rec_field(d.rec, np, kRecR, row), r[0], r[1], r[2]);
+        st4(rec_field(d.rec, np, kRecZB, row), z[0], z[1], z[2]);
         if (!coarse) st4(d.nb + 4 * (size_t)row, z[0], z[1], z[2]);   // u = D^{-1} r
         r32[0] = (float)r[0];
         r32[1] = (float)r[1];
@@ -571,7 +577,7 @@ __global__ void __launch_bounds__(TILE) k_pcg_correct(const PcgDesc<T>* __restri
     if (sc->state != kActive) return;   // block-uniform: before any barrier
     // the row's own load goes out first, so its latency overlaps the staging
     T z[3] = {(T)0, (T)0, (T)0};
-    if (row < d.n_rows) ld4(d.rec + kRec * (size_t)row + kRecZB, z);
+    if (row < d.n_rows) ld4(rec_field(d.rec, npad32(d.n_rows), kRecZB, row), z);
     // slice partials of e, one load per thread, then added in slice order
     for (int idx = threadIdx.x; idx < kMaxAgg * 6 * n_ks && idx < TILE; idx += TILE) {
         const int ks = idx / (kMaxAgg * 6), r = idx - ks * kMaxAgg * 6, a = a0 + r / 6;

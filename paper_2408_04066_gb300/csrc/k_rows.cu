@@ -167,16 +167,18 @@ __global__ void __launch_bounds__(kRowTile) k_assemble_slots(ElemArgs A) {
         const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
         const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
         const double id = det != 0.0 ? 1.0 / det : 0.0;
-        KT* di = (KT*)A.slot.dinv + ((size_t)b * M.n + row) * 9;
-        di[0] = (KT)(c00 * id);
-        di[1] = (KT)((a[2] * a[7] - a[1] * a[8]) * id);
-        di[2] = (KT)((a[1] * a[5] - a[2] * a[4]) * id);
-        di[3] = (KT)(c01 * id);
-        di[4] = (KT)((a[0] * a[8] - a[2] * a[6]) * id);
-        di[5] = (KT)((a[2] * a[3] - a[0] * a[5]) * id);
-        di[6] = (KT)(c02 * id);
-        di[7] = (KT)((a[1] * a[6] - a[0] * a[7]) * id);
-        di[8] = (KT)((a[0] * a[4] - a[1] * a[3]) * id);
+        // entry e of the row's inverse at e * npad32(n) + row (one run per entry)
+        KT* di = (KT*)A.slot.dinv + (size_t)b * 9 * npad32(M.n) + row;
+        const size_t np = npad32(M.n);
+        di[0 * np] = (KT)(c00 * id);
+        di[1 * np] = (KT)((a[2] * a[7] - a[1] * a[8]) * id);
+        di[2 * np] = (KT)((a[1] * a[5] - a[2] * a[4]) * id);
+        di[3 * np] = (KT)(c01 * id);
+        di[4 * np] = (KT)((a[0] * a[8] - a[2] * a[6]) * id);
+        di[5 * np] = (KT)((a[2] * a[3] - a[0] * a[5]) * id);
+        di[6 * np] = (KT)(c02 * id);
+        di[7 * np] = (KT)((a[1] * a[6] - a[0] * a[7]) * id);
+        di[8 * np] = (KT)((a[0] * a[4] - a[1] * a[3]) * id);
     }
 }
 
@@ -202,7 +204,7 @@ __global__ void __launch_bounds__(kRowTile) k_slope(ElemArgs A) {
     double v[1] = {0.0};
     if (row < n) {
         const double* g = A.slot.g + ((size_t)b * n + row) * 3;
-        const T* dx = vecp<T>(A.slot, b, kOffRec, n) + kRec * (size_t)row + kRecDX;
+        const T* dx = rec_field(vecp<T>(A.slot, b, kOffRec, n), npad32(n), kRecDX, row);
         v[0] = g[0] * (double)dx[0] + g[1] * (double)dx[1] + g[2] * (double)dx[2];
     }
     double tot[1];
@@ -220,7 +222,7 @@ __global__ void k_update(ElemArgs A) {
     if (i >= 3 * n) return;
     const T* rec = vecp<T>(A.slot, b, kOffRec, n);
     double* x = A.slot.x + (size_t)b * n * 3;
-    x[i] = fma(A.slot.alpha[b], (double)rec[kRec * (size_t)(i / 3) + kRecDX + i % 3], x[i]);
+    x[i] = fma(A.slot.alpha[b], (double)rec_field(rec, npad32(n), kRecDX, i / 3)[i % 3], x[i]);
 }
 
 __global__ void k_unpermute(ElemArgs A, double* __restrict__ out) {

@@ -56,7 +56,7 @@ struct SlotDev {
     double* ge = nullptr;    // [B][m][12] element forces
     void* Ke = nullptr;      // [B][m][90]  (float or double)
     void* val = nullptr;     // [B][slots*9]
-    void* dinv = nullptr;    // [B][n][9]
+    void* dinv = nullptr;    // [B][9][npad32(n)] block-Jacobi inverses, entry-major
     void* vec = nullptr;     // [B][6][n][3]: dx r z p0 p1 q
     double* part = nullptr;  // [B][tiles][4]
     int part_tiles = 0;
