@@ -1196,7 +1196,8 @@ void mfem_destroy(mfem_ctx* c) {
     if (c->mesh_shared) c->mesh = MeshDev();   // the owner frees the mesh data
     MeshDev& M = c->mesh;
     void* ptrs[] = {M.tet, M.Dminv64, M.Dminv32, M.vol, M.cluster, M.mu, M.lam, M.X, M.vhandle, M.pin_handle_v,
-                    M.vperm, M.tperm, M.slice_ptr, M.col, M.slot_row, M.contrib_ptr, M.contrib, M.vinc_ptr, M.vinc,
+                    M.vperm, M.tperm, M.slice_ptr, M.col, M.slot_row, M.up_slot, M.up_mirror, M.contrib_ptr,
+                    M.contrib, M.vinc_ptr, M.vinc,
                     M.crel, M.agg_handle, M.Ainv, M.Abf, M.coarse_err, c->descs_dev, c->diag_dev, c->fext_dev};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -1362,6 +1363,9 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
     UP(M.slice_ptr, sp.data(), sp.size());
     UP(M.col, P.sell_col.data(), P.sell_col.size());
     UP(M.slot_row, P.slot_row.data(), P.slot_row.size());
+    UP(M.up_slot, P.up_slot.data(), P.up_slot.size());
+    UP(M.up_mirror, P.up_mirror.data(), P.up_mirror.size());
+    M.n_up = (int64_t)P.up_slot.size();
     UP(M.contrib_ptr, P.contrib_ptr.data(), P.contrib_ptr.size());
     UP(M.contrib, P.contrib.data(), P.contrib.size());
     UP(M.vinc_ptr, P.vinc_ptr.data(), P.vinc_ptr.size());

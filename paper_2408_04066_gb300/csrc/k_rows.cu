@@ -102,23 +102,26 @@ __device__ __forceinline__ void add_block(KT (&acc)[9], int code, const KT (&v)[
     }
 }
 
-// One thread per slot of the sliced pattern: the slot's 3x3 block summed from
-// the element blocks of every tet holding both vertices (the contributions of
-// a slot are sorted by tet, so the order -- and every bit of the result -- is
-// the same as a row-by-row gather), pin elimination or the penalty term, and,
-// on the diagonal slot, the row's block-Jacobi inverse.  Consecutive threads
-// take consecutive slots, so the block writes are coalesced; a slot's gather is
-// a handful of loads, so there are ~15x more independent threads than rows to
-// hide their latency.  The gradient gather runs in k_gradient.
+// One thread per diagonal or upper slot of the sliced pattern: the slot's 3x3
+// block summed from the element blocks of every tet holding both vertices (the
+// contributions of a slot are sorted by tet, so the order -- and every bit of
+// the result -- is the same as a row-by-row gather), pin elimination or the
+// penalty term, written to the slot and, transposed, to its mirror slot (the
+// lower block sums the transposes of the same blocks in the same order: the
+// same bits as gathering it), and, on the diagonal, the row's block-Jacobi
+// inverse.  Consecutive threads take consecutive upper slots, so the own
+// writes are nearly coalesced; the mirror writes are scattered.  The gradient
+// gather runs in k_gradient.
 template <typename KT>
 __global__ void __launch_bounds__(kRowTile) k_assemble_slots(ElemArgs A) {
     const int b = blockIdx.y;
     if (!A.slot.active[b]) return;
     const MeshDev& M = A.mesh;
-    const int64_t gs = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (gs >= M.slots) return;
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= M.n_up) return;
+    const int64_t gs = __ldg(M.up_slot + t);
+    const int ms = __ldg(M.up_mirror + t);
     const int c = __ldg(M.col + gs);
-    if (c < 0) return;   // padding: stays zero
     const int row = __ldg(M.slot_row + gs);
     const int lane = row & 31;
     const KT* Ke = (const KT*)A.slot.Ke + (size_t)b * M.m * kKe;
@@ -157,9 +160,17 @@ __global__ void __launch_bounds__(kRowTile) k_assemble_slots(ElemArgs A) {
         acc[4] += (KT)A.ks;
         acc[8] += (KT)A.ks;
     }
-    KT* out = (KT*)A.slot.val + (size_t)b * M.slots * 9 + (size_t)(gs - lane) * 9 + lane;
+    KT* val = (KT*)A.slot.val + (size_t)b * M.slots * 9;
+    KT* out = val + (size_t)(gs - lane) * 9 + lane;
 #pragma unroll
     for (int e = 0; e < 9; ++e) out[32 * e] = acc[e];
+    if (ms >= 0) {   // the transposed block in the mirror slot (lane = its row's)
+        KT* mout = val + (size_t)(ms - (c & 31)) * 9 + (c & 31);
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) mout[32 * (3 * i + j)] = acc[3 * j + i];
+    }
     if (diag) {  // block-Jacobi: inverse of the diagonal block, formed in FP64
         double a[9];
 #pragma unroll
@@ -252,7 +263,7 @@ __global__ void k_permute_in(ElemArgs A, int b, const double* __restrict__ xin) 
 }  // namespace
 
 void launch_assemble(const ElemArgs& a, int B, cudaStream_t s) {
-    const dim3 grid((unsigned)((a.mesh.slots + kRowTile - 1) / kRowTile), B);
+    const dim3 grid((unsigned)((a.mesh.n_up + kRowTile - 1) / kRowTile), B);
     if (a.slot.prec == 1) k_assemble_slots<float><<<grid, kRowTile, 0, s>>>(a);
     else k_assemble_slots<double><<<grid, kRowTile, 0, s>>>(a);
     launch_gradient(a, B, s);

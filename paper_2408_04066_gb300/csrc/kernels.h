@@ -27,6 +27,9 @@ struct MeshDev {
     int* slice_ptr = nullptr;     // [n_slices+1]
     int* col = nullptr;           // [slots]
     int* slot_row = nullptr;      // [slots] block row of each slot
+    int64_t n_up = 0;
+    int* up_slot = nullptr;       // [n_up] diagonal and upper slots
+    int* up_mirror = nullptr;     // [n_up] slot of each one's transposed block, -1 on the diagonal
     int* contrib_ptr = nullptr;   // [slots+1]
     int* contrib = nullptr;       // [16m]
     int* vinc_ptr = nullptr;      // [n+1]

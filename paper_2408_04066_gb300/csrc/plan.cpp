@@ -384,6 +384,23 @@ mfem_status plan_layout(const mfem_material* mat, const double* rest_verts, cons
     std::vector<int32_t> fill(p.contrib_ptr.begin(), p.contrib_ptr.end() - 1);
     for (int k = 0; k < m; ++k)  // tet-major, so each list is sorted by tet
         for (int c = 0; c < 16; ++c) p.contrib[fill[cslot[16 * (size_t)k + c]]++] = 16 * k + c;
+    // diagonal and upper slots with their mirror slots (the lower block (j, i)
+    // sums the transposes of the same element blocks as (i, j), in the same
+    // tet order)
+    {
+        std::vector<std::pair<int64_t, int64_t>> up;
+        up.reserve((size_t)(p.nnz_blocks / 2 + n));
+        for (int i = 0; i < n; ++i)
+            for (int j : nb[i])
+                if (j >= i) up.emplace_back(slot_of(i, j), j > i ? slot_of(j, i) : -1);
+        std::sort(up.begin(), up.end());
+        p.up_slot.resize(up.size());
+        p.up_mirror.resize(up.size());
+        for (size_t t = 0; t < up.size(); ++t) {
+            p.up_slot[t] = (int32_t)up[t].first;
+            p.up_mirror[t] = (int32_t)up[t].second;
+        }
+    }
     // vertex incidence for the gradient gather
     p.vinc_ptr.assign(n + 1, 0);
     for (int k = 0; k < m; ++k)

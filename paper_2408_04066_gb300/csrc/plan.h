@@ -48,6 +48,10 @@ struct Plan {
     // element-block -> matrix-block gather lists
     std::vector<int32_t> contrib_ptr;  // [slots+1]
     std::vector<int32_t> contrib;      // [16 m] code: tet*16 + a*4 + b
+    // assembly of the symmetric pattern: the diagonal and upper slots (column
+    // >= row), by slot, each with the slot of its transposed block (-1 on the
+    // diagonal)
+    std::vector<int32_t> up_slot, up_mirror;
     std::vector<int32_t> vinc_ptr;     // [n+1]
     std::vector<int32_t> vinc;         // [4 m] code: tet*4 + a
     double bbox_diag = 0.0;
