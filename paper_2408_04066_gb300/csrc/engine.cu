@@ -19,7 +19,9 @@ constexpr double kLsC = 1.0e-4;      // Armijo constant
 constexpr int kLsMax = 20;           // halvings
 constexpr double kLsNoise = 1.0e-10; // predicted decrease below this * |E|: take the step
 constexpr int kPcgTiles[3] = {64, 128, 256};   // PCG rows per block the autotuner times
-constexpr int kPcgChunk = 16;                   // PCG iterations enqueued between convergence checks
+constexpr int kPcgChunk = 16;                   // PCG iterations enqueued between convergence checks (no history)
+constexpr int kPcgChunkMin = 8, kPcgChunkMax = 64;   // bounds of a predicted chunk (multiples of 8)
+constexpr int kPcgHistSteps = 16;               // Newton steps remembered per slot
 constexpr double kPredTol = 3e-3;   // PCG target of the co-rotational predictor step (at most cg_tol)
 constexpr double kEwGamma = 0.9;    // forcing rule where the Newton model is trusted (see advance)
 constexpr double kEwMin = 1e-4;     // tightest PCG target that rule sets (well above FP32 PCG's floor)
@@ -177,6 +179,7 @@ mfem_status alloc_slots(mfem_ctx* c, int B) {
         CK(cudaMemcpy(S.x + (size_t)b * n * 3, c->mesh.X, n * 3 * 8, cudaMemcpyDeviceToDevice));
     c->warm_kind.assign(B, 0);
     c->xpred_valid.assign(B, 0);
+    c->pcg_hist.assign((size_t)B * kPcgHistSteps, 0);
     // pinned host staging
     if (c->sc_host) cudaFreeHost(c->sc_host);
     if (c->active_host) cudaFreeHost(c->active_host);
@@ -475,9 +478,37 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
     int cap = 0;
     for (auto& g : gs)
         if (g.ctx->slot.prec == prec) cap = std::max(cap, g.ctx->opt.cg_max);
-    for (int done = 0; done < cap; done += kPcgChunk) {
-        const int n_it = std::min(kPcgChunk, cap - done);
+    // one chunk per scheduling round: as many iterations as the last problem of
+    // the table is expected to need -- each slot's last solve of the same
+    // Newton step, less what this solve has run (kPcgChunk without history),
+    // at most kPcgChunkMax -- so that a round usually ends with every solve of
+    // the table done.  A round costs a host round trip (~160 us measured on
+    // the 200k figure); ending rounds at the first expected finish instead
+    // took more rounds than the idle iterations it saved (456 against 489
+    // frames/s; fixed chunks of 16 / 24 / 32 / 48 / 64: 471 / 480 / 449 / 490
+    // / 463)
+    int chunk = kPcgChunk;
+    if (one_chunk) {
+        int best = 0;
+        for (auto& g : gs) {
+            if (g.ctx->slot.prec != prec) continue;
+            for (int b = 0; b < g.B; ++b) {
+                const ProbHost& p = g.ph[b];
+                if (!p.active || !p.in_pcg) continue;
+                const int h = g.ctx->pcg_hist[(size_t)b * kPcgHistSteps + std::min(p.it, kPcgHistSteps - 1)];
+                best = std::max(best, h > 0 ? h - p.pcg_launched : kPcgChunk);
+            }
+        }
+        chunk = std::min(kPcgChunkMax, std::max(kPcgChunkMin, (best + 7) / 8 * 8));
+    }
+    for (int done = 0; done < cap; done += chunk) {
+        const int n_it = std::min(chunk, cap - done);
         if (one_chunk && done > 0) break;
+        if (one_chunk)
+            for (auto& g : gs)
+                if (g.ctx->slot.prec == prec)
+                    for (int b = 0; b < g.B; ++b)
+                        if (g.ph[b].active && g.ph[b].in_pcg) g.ph[b].pcg_launched += n_it;
         int pe = count ? c->prof.begin(2, c->stream) : -1;
         mfem_status lst = launch_chunk<T>(c, dst, (int)d.size(), units, units_u, tile, split, n_it, jobs);
         if (lst != MFEM_OK) return lst;
@@ -941,7 +972,10 @@ mfem_status advance(std::vector<Group>& gs) {
                             gc->slot.coarse_on, s);
             gc->prof.launches++;
             for (int b = 0; b < g.B; ++b)
-                if (start[b]) g.ph[b].in_pcg = 1;
+                if (start[b]) {
+                    g.ph[b].in_pcg = 1;
+                    g.ph[b].pcg_launched = 0;
+                }
         }
     }
     // ---- a5: one chunk of PCG iterations over every problem inside PCG
@@ -972,6 +1006,8 @@ mfem_status advance(std::vector<Group>& gs) {
                 fin[gi][b] = 1;
                 any_fin = true;
                 p.pcg_iters += g.ctx->sc_host[b].iter;
+                g.ctx->pcg_hist[(size_t)b * kPcgHistSteps + std::min(p.it, kPcgHistSteps - 1)] =
+                    std::max(1, g.ctx->sc_host[b].iter);
                 g.ctx->prof.pcg_iters += g.ctx->sc_host[b].iter;
                 g.ctx->prof.pcg_bytes += g.ctx->sc_host[b].iter * pcg_bytes_per_iter(g.ctx, p.coarse);
                 g.ctx->alpha_host[b] = 1.0;

@@ -38,6 +38,7 @@ struct ProbHost {
     // E(x_prev + dx) anyway, decides Armijo's test at alpha = 1
     int spec = 0;
     double spec_e0 = 0.0, spec_slope = 0.0;
+    int pcg_launched = 0;   // PCG iterations launched in the current solve
 };
 
 // Profile accumulator with a pool of CUDA events on the context stream.
@@ -100,6 +101,9 @@ struct mfem_ctx {
     // 2 = x was set by the caller (a warm start uses it as it is)
     std::vector<int> warm_kind;
     std::vector<int> xpred_valid;   // per slot: slot.xpred holds the last solve's predictor result
+    // per slot and Newton step: PCG iterations that step's last solve took
+    // (0 = none yet), from which the length of the next PCG chunk is predicted
+    std::vector<int> pcg_hist;
     mfem::Profiler prof;
     // PCG chunks captured as CUDA graphs, keyed by the launch parameters
     std::map<std::string, cudaGraphExec_t> graphs;
