@@ -20,7 +20,7 @@ constexpr int kLsMax = 20;           // halvings
 constexpr double kLsNoise = 1.0e-10; // predicted decrease below this * |E|: take the step
 constexpr int kPcgTiles[3] = {64, 128, 256};   // PCG rows per block the autotuner times
 constexpr int kPcgChunk = 16;                   // PCG iterations enqueued between convergence checks (no history)
-constexpr int kPcgChunkMin = 8, kPcgChunkMax = 64;   // bounds of a predicted chunk (multiples of 8)
+constexpr int kPcgChunkMin = 16, kPcgChunkMax = 64;   // bounds of a predicted chunk (multiples of 8)
 constexpr int kPcgHistSteps = 16;               // Newton steps remembered per slot
 constexpr double kPredTol = 3e-3;   // PCG target of the co-rotational predictor step (at most cg_tol)
 constexpr double kEwGamma = 0.9;    // forcing rule where the Newton model is trusted (see advance)
@@ -443,7 +443,7 @@ mfem_status launch_chunk(mfem_ctx* c, const PcgDesc<T>* dst, int nd, int units, 
 
 template <typename T>
 mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, int split, int max_iters, bool count,
-                    bool one_chunk = false, bool slopes = false) {
+                    bool one_chunk = false, bool slopes = false, bool per_request = false) {
     mfem_ctx* c = c0;
     std::vector<PcgDesc<T>> d;
     std::vector<CoarseJob> jobs;
@@ -478,28 +478,30 @@ mfem_status run_pcg(mfem_ctx* c0, std::vector<Group>& gs, int prec, int tile, in
     int cap = 0;
     for (auto& g : gs)
         if (g.ctx->slot.prec == prec) cap = std::max(cap, g.ctx->opt.cg_max);
-    // one chunk per scheduling round: as many iterations as the last problem of
-    // the table is expected to need -- each slot's last solve of the same
-    // Newton step, less what this solve has run (kPcgChunk without history),
-    // at most kPcgChunkMax -- so that a round usually ends with every solve of
-    // the table done.  A round costs a host round trip (~160 us measured on
-    // the 200k figure); ending rounds at the first expected finish instead
-    // took more rounds than the idle iterations it saved (456 against 489
-    // frames/s; fixed chunks of 16 / 24 / 32 / 48 / 64: 471 / 480 / 449 / 490
-    // / 463)
+    // one chunk per scheduling round, from each slot's last solve of the same
+    // Newton step less what this solve has run (kPcgChunk without history):
+    // for a batch call, as many iterations as the last problem of the table is
+    // expected to need (at most kPcgChunkMax), so that a round usually ends
+    // with every solve done -- a round costs a host round trip (~160 us on the
+    // 200k figure) and the batch ends with its last problem (fixed chunks of
+    // 16 / 24 / 32 / 48 / 64 gave 471 / 480 / 449 / 490 / 463 frames/s, this
+    // rule 489); for served requests, which complete one by one, as many as
+    // the first problem is expected to need, at least kPcgChunkMin (served
+    // mix at 70% load: p50 37 ms against 57 with the batch rule)
     int chunk = kPcgChunk;
     if (one_chunk) {
-        int best = 0;
+        int best = per_request ? kPcgChunkMax : 0;
         for (auto& g : gs) {
             if (g.ctx->slot.prec != prec) continue;
             for (int b = 0; b < g.B; ++b) {
                 const ProbHost& p = g.ph[b];
                 if (!p.active || !p.in_pcg) continue;
                 const int h = g.ctx->pcg_hist[(size_t)b * kPcgHistSteps + std::min(p.it, kPcgHistSteps - 1)];
-                best = std::max(best, h > 0 ? h - p.pcg_launched : kPcgChunk);
+                const int need = h > 0 ? h - p.pcg_launched : kPcgChunk;
+                best = per_request ? std::min(best, need) : std::max(best, need);
             }
         }
-        chunk = std::min(kPcgChunkMax, std::max(kPcgChunkMin, (best + 7) / 8 * 8));
+        chunk = std::min(kPcgChunkMax, std::max(per_request ? kPcgChunkMin : 8, (best + 7) / 8 * 8));
     }
     for (int done = 0; done < cap; done += chunk) {
         const int n_it = std::min(chunk, cap - done);
@@ -737,7 +739,7 @@ mfem_status check_speculative(std::vector<Group>& gs, Group& g, std::vector<int>
 
 }  // namespace
 
-mfem_status advance(std::vector<Group>& gs) {
+mfem_status advance(std::vector<Group>& gs, bool per_request) {
     mfem_ctx* c = gs[0].ctx;
     cudaStream_t s = c->stream;
     // ---- a0: apply poses of newly admitted problems.  The Newton stop test is
@@ -989,8 +991,10 @@ mfem_status advance(std::vector<Group>& gs) {
             if (g.ctx->slot.prec == prec)
                 for (int b = 0; b < g.B; ++b) any |= g.ph[b].active && g.ph[b].in_pcg;
         if (!any) continue;
-        mfem_status st = prec == 1 ? run_pcg<float>(c, gs, 1, c->tile_rows, c->spmv_split, 0, true, true, true)
-                                   : run_pcg<double>(c, gs, 0, c->tile_rows, c->spmv_split, 0, true, true, true);
+        mfem_status st = prec == 1 ? run_pcg<float>(c, gs, 1, c->tile_rows, c->spmv_split, 0, true, true, true,
+                                                    per_request)
+                                   : run_pcg<double>(c, gs, 0, c->tile_rows, c->spmv_split, 0, true, true, true,
+                                                     per_request);
         if (st != MFEM_OK) return st;
     }
     CK(cudaGetLastError());

@@ -141,7 +141,10 @@ ElemArgs elem_args(const mfem_ctx* c);
 // run one chunk of PCG iterations over the problems inside PCG; finish the
 // Newton step (line search, update) of problems whose PCG ended.  Problems move
 // through their Newton steps independently, so none waits for another's PCG.
-mfem_status advance(std::vector<Group>& groups);
+// The round's PCG chunk runs until the last solve of the table is expected to
+// end (a batch call: the batch is done when its last problem is), or, with
+// per_request, until the first is (a server: each request completes alone).
+mfem_status advance(std::vector<Group>& groups, bool per_request = false);
 
 // Whole solve of B problems of one context (poses already in slot.xf).
 mfem_status run_batch(mfem_ctx* c, int B, std::vector<ProbHost>& ph);

@@ -246,7 +246,7 @@ void mfem_server::run() {
                 gs.push_back(Group{p->ctx, p->cap, p->ph.data()});
             }
         if (gs.empty()) continue;
-        mfem_status st = advance(gs);
+        mfem_status st = advance(gs, true);
         {
             std::lock_guard<std::mutex> lk(mu);   // counters and err are read by other threads
             steps++;

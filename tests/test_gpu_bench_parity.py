@@ -225,3 +225,31 @@ def test_fp32_forces_at_their_threshold(mfem, record_property):
     record_property("parity", json.dumps({"config": "10k figure x12 poses, FP32 forces at newton_tol 1e-7",
                                           "max_err": max(errs)}))
     assert max(errs) <= TOL_MIXED, errs
+
+
+def test_mixed_solutions_meet_the_stop_test_in_fp64(mfem, record_property):
+    """The mixed path stops on its own gradient (element forces in FP32 from
+    the FP64 stress at the default newton_tol); the oracle's FP64 gradient at
+    the returned positions must meet the same test: |g_free(x)| <= 1e-6
+    |g_free(x_rigid)| up to a small margin for the FP32 forces' rounding (their
+    floor is ~1e-8 of the initial gradient)."""
+    cfg = figure_config(200000, seeds=range(4), model="snh")
+    so = S.Setup.from_config(cfg)
+    ctx = mfem.Context.from_config(cfg, precision="mixed", max_batch=4)
+    x, st = ctx.solve_batch(cfg["xfs"])
+    ctx.close()
+    assert all(s["converged"] for s in st)
+    free = np.ones(so.n, dtype=bool)
+    free[so.pin_verts] = False
+    worst = 0.0
+    for b in range(4):
+        Q, t = rig.unpack_pose(np.asarray(cfg["xfs"][b]))
+        R = Q[so.cluster]
+        x_ref = S.initial_guess(so, Q, t, "rigid")
+        x_ref[so.pin_verts] = rig.pin_targets(so.X, so.pin_verts, so.pin_handle, Q, t)
+        g0 = np.linalg.norm(element.gradient(x_ref, so.T, so.G, so.vol, R, "snh", so.mu, so.lam)[free])
+        g = np.linalg.norm(element.gradient(np.asarray(x[b]), so.T, so.G, so.vol, R, "snh", so.mu, so.lam)[free])
+        worst = max(worst, g / g0)
+    record_property("parity", json.dumps({"config": "cfg2 figure198k SNH x4, FP64 gradient at mixed solutions",
+                                          "max_rel_grad": worst}))
+    assert worst <= 1.1e-6, worst
