@@ -70,6 +70,7 @@ ElemArgs elem_args(const mfem_ctx* c) {
     a.fext_stride = c->fext_sets > 1 ? 3 * (int64_t)c->plan.n : 0;
     a.rot_polar = c->opt.rotation == MFEM_ROT_POLAR ? 1 : 0;
     a.f32_forces = c->slot.prec == 1 && c->opt.newton_tol >= kF32ForcesTol ? 1 : 0;
+    a.ff_elem = a.f32_forces && !a.rot_polar && c->slot.xff && c->mesh.Dminv_lo && c->mesh.mulam_ff ? 1 : 0;
     return a;
 }
 
@@ -92,7 +93,7 @@ mfem_status upload(mfem_ctx* c, U** dst, const U* src, size_t count) {
 void free_slots(mfem_ctx* c) {
     SlotDev& S = c->slot;
     void* ptrs[] = {S.xf, S.xf_prev, S.xpred, S.dcorr, S.tol2, S.coarse_on, S.rcp, S.ec, S.rcs, S.aggq, S.bsplit,
-                    S.x, S.xprev, S.xp,
+                    S.x, S.xff, S.xprev, S.xp,
                     S.g, S.ge, S.Ke, S.val, S.dinv, S.vec, S.part, S.sc, S.active, S.alpha, S.outbuf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -114,7 +115,8 @@ size_t bytes_per_slot(const mfem_ctx* c) {
     const size_t n = c->plan.n, m = c->plan.m, H = c->plan.H;
     const size_t kt = c->slot.prec == 1 ? 4 : 8;
     const size_t slots = (size_t)c->plan.slice_ptr.back();
-    return H * 12 * 8 + 4 * n * 3 * 8 + m * 12 * 8 + m * kKe * kt + slots * 9 * kt + 9 * npad32((int)n) * kt +
+    return H * 12 * 8 + 4 * n * 3 * 8 + (kt == 4 ? n * 3 * 8 : 0) + m * 12 * 8 + m * kKe * kt + slots * 9 * kt +
+           9 * npad32((int)n) * kt +
            kVecStride * npad32((int)n) * kt + (size_t)part_tiles_for(c) * 4 * 8 + sizeof(ProbScal) + 4 + 8 + 8 +
            H * 12 * 8 + (c->opt.init == MFEM_INIT_WARM ? 2 * n * 3 * 8 : 0) + 4 + (line_search(c) ? n * 3 * 8 : 0) +
            (c->mesh.coarse_n > 0 ? ((n + 255) / 256) * 24 * 4 + (coarse_ks(c) + 1) * c->mesh.coarse_n * 4 + 128 +
@@ -144,6 +146,7 @@ mfem_status alloc_slots(mfem_ctx* c, int B) {
         AL(S.dcorr, B * n * 3 * 8);
     }
     AL(S.x, B * n * 3 * 8);
+    if (S.prec == 1) AL(S.xff, B * n * 3 * sizeof(float2));
     if (line_search(c)) AL(S.xprev, B * n * 3 * 8);
     AL(S.xp, B * n * 3 * 8);
     AL(S.g, B * n * 3 * 8);
@@ -1235,7 +1238,7 @@ void mfem_destroy(mfem_ctx* c) {
     free_slots(c);
     if (c->mesh_shared) c->mesh = MeshDev();   // the owner frees the mesh data
     MeshDev& M = c->mesh;
-    void* ptrs[] = {M.tet, M.Dminv64, M.Dminv32, M.vol, M.cluster, M.mu, M.lam, M.X, M.vhandle, M.pin_handle_v,
+    void* ptrs[] = {M.tet, M.Dminv64, M.Dminv32, M.Dminv_lo, M.mulam_ff, M.vol, M.cluster, M.mu, M.lam, M.X, M.vhandle, M.pin_handle_v,
                     M.vperm, M.tperm, M.slice_ptr, M.col, M.slot_row, M.up_slot, M.up_mirror, M.contrib_ptr,
                     M.contrib, M.vinc_ptr, M.vinc,
                     M.crel, M.agg_handle, M.Ainv, M.Abf, M.coarse_err, c->descs_dev, c->diag_dev, c->fext_dev};
@@ -1374,12 +1377,22 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
     M.n_pins = (int)P.pin_vert.size();
     M.slots = P.slice_ptr.back();
     std::vector<double> Dm64((size_t)9 * P.m);
-    std::vector<float> Dm32((size_t)9 * P.m);
+    std::vector<float> Dm32((size_t)9 * P.m), DmLo((size_t)9 * P.m);
     for (int k = 0; k < P.m; ++k)
         for (int e = 0; e < 9; ++e) {
-            Dm64[(size_t)e * P.m + k] = P.Dminv[9 * (size_t)k + e];
-            Dm32[(size_t)e * P.m + k] = (float)P.Dminv[9 * (size_t)k + e];
+            const double v = P.Dminv[9 * (size_t)k + e];
+            Dm64[(size_t)e * P.m + k] = v;
+            Dm32[(size_t)e * P.m + k] = (float)v;
+            DmLo[(size_t)e * P.m + k] = (float)(v - (double)(float)v);
         }
+    std::vector<float> mulam((size_t)4 * P.m);   // (mu, lam) as float pairs
+    for (int k = 0; k < P.m; ++k) {
+        const double mu = P.mu[k], lam = P.lam[k];
+        mulam[4 * (size_t)k] = (float)mu;
+        mulam[4 * (size_t)k + 1] = (float)(mu - (double)(float)mu);
+        mulam[4 * (size_t)k + 2] = (float)lam;
+        mulam[4 * (size_t)k + 3] = (float)(lam - (double)(float)lam);
+    }
     std::vector<int32_t> pin_h(P.n, -1);
     for (size_t i = 0; i < P.pin_vert.size(); ++i) pin_h[P.pin_vert[i]] = P.pin_handle[i];
     std::vector<int32_t> sp(P.slice_ptr.begin(), P.slice_ptr.end());
@@ -1391,6 +1404,8 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
     UP(M.tet, (const int4*)P.tet.data(), (size_t)P.m);
     UP(M.Dminv64, Dm64.data(), Dm64.size());
     UP(M.Dminv32, Dm32.data(), Dm32.size());
+    UP(M.Dminv_lo, DmLo.data(), DmLo.size());
+    UP(M.mulam_ff, (const float4*)mulam.data(), (size_t)P.m);
     UP(M.vol, P.vol.data(), P.vol.size());
     UP(M.cluster, P.cluster.data(), P.cluster.size());
     UP(M.mu, P.mu.data(), P.mu.size());

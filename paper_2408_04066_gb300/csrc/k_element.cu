@@ -122,6 +122,147 @@ __device__ __forceinline__ double psi_sigma(const double (&S)[6], double mu, dou
     }
 }
 
+// ---- float-float element path (mixed precision) -----------------------------
+// F, S, the energy density and the stress in float-float arithmetic (value =
+// hi + lo, ~48 significant bits: Dekker's product by fused multiply-add,
+// Knuth's two-sum) from positions, shape gradients and rotations held as float
+// pairs, so that the element pass needs almost no FP64 instructions (GB300
+// issues FP64 at a small fraction of its FP32 rate).  Only the energy's
+// weighting and sum stay FP64.
+__device__ __forceinline__ FF ff_from(float hi, float lo) { return FF{hi, lo}; }
+__device__ __forceinline__ FF ff_split(double v) {
+    const float h = (float)v;
+    return FF{h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ FF ff_neg(FF a) { return FF{-a.hi, -a.lo}; }
+__device__ __forceinline__ FF ff_sub(FF a, FF b) { return ff_add(a, ff_neg(b)); }
+__device__ __forceinline__ FF ff_mul(FF a, FF b) {
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float h = __fadd_rn(p, e);
+    return FF{h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+__device__ __forceinline__ FF ff_scale2(FF a, float s) { return FF{a.hi * s, a.lo * s}; }   // s a power of two
+__device__ __forceinline__ FF ff_addf(FF a, float b) { return ff_add(a, FF{b, 0.f}); }
+
+// S = sym(Q^T F), F = sum_a (x_a - x_0) G_a^T (a = 1..3), all as float pairs;
+// G[r] = row r of D_m^{-1} (G_{r+1}).
+__device__ __forceinline__ void stretch_ff(const FF (&xa)[4][3], const FF (&G)[3][3], const FF (&Q)[3][3],
+                                           FF (&S)[6]) {
+    FF d[3][3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) d[a][i] = ff_sub(xa[a + 1][i], xa[0][i]);
+    FF F[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            F[i][j] = ff_add(ff_add(ff_mul(d[0][i], G[0][j]), ff_mul(d[1][i], G[1][j])), ff_mul(d[2][i], G[2][j]));
+    FF Am[3][3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+            Am[i][j] = ff_add(ff_add(ff_mul(Q[0][i], F[0][j]), ff_mul(Q[1][i], F[1][j])), ff_mul(Q[2][i], F[2][j]));
+    S[0] = Am[0][0];
+    S[1] = Am[1][1];
+    S[2] = Am[2][2];
+    S[3] = ff_scale2(ff_add(Am[1][2], Am[2][1]), 0.5f);
+    S[4] = ff_scale2(ff_add(Am[0][2], Am[2][0]), 0.5f);
+    S[5] = ff_scale2(ff_add(Am[0][1], Am[1][0]), 0.5f);
+}
+
+// psi_sigma in float-float: returns Psi, writes sigma rounded to FP32
+template <int MODEL>
+__device__ __forceinline__ FF psi_sigma_ff(const FF (&S)[6], FF mu, FF lam, float (&sig)[6]) {
+    const FF d0 = ff_addf(S[0], -1.f), d1 = ff_addf(S[1], -1.f), d2 = ff_addf(S[2], -1.f);
+    if (MODEL == 0 || MODEL == 1) {
+        const FF off = ff_add(ff_add(ff_mul(S[3], S[3]), ff_mul(S[4], S[4])), ff_mul(S[5], S[5]));
+        const FF sq = ff_add(ff_add(ff_mul(d0, d0), ff_mul(d1, d1)), ff_mul(d2, d2));
+        FF psi = ff_mul(mu, ff_add(sq, ff_scale2(off, 2.f)));
+        const float m2 = 2.f * mu.hi;
+        sig[0] = m2 * d0.hi;
+        sig[1] = m2 * d1.hi;
+        sig[2] = m2 * d2.hi;
+        sig[3] = m2 * S[3].hi;
+        sig[4] = m2 * S[4].hi;
+        sig[5] = m2 * S[5].hi;
+        if (MODEL == 1) {
+            const FF tr = ff_add(ff_add(d0, d1), d2);
+            psi = ff_add(psi, ff_scale2(ff_mul(lam, ff_mul(tr, tr)), 0.5f));
+            const float lt = lam.hi * tr.hi;
+            sig[0] += lt;
+            sig[1] += lt;
+            sig[2] += lt;
+        }
+        return psi;
+    }
+    const FF a = S[0], b = S[1], c = S[2], s12 = S[3], s02 = S[4], s01 = S[5];
+    const FF c00 = ff_sub(ff_mul(b, c), ff_mul(s12, s12)), c11 = ff_sub(ff_mul(a, c), ff_mul(s02, s02));
+    const FF c22 = ff_sub(ff_mul(a, b), ff_mul(s01, s01));
+    const FF c12 = ff_sub(ff_mul(s01, s02), ff_mul(a, s12)), c02 = ff_sub(ff_mul(s01, s12), ff_mul(b, s02));
+    const FF c01 = ff_sub(ff_mul(s02, s12), ff_mul(c, s01));
+    // the energy in D = S - I, where its terms of first order in the strain
+    // cancel exactly: |S|^2 - 3 = 2 tr D + |D|^2 and J - 1 = tr D + I2(D) + det D,
+    // so Psi = mu/2 |D|^2 - mu (I2(D) + det D) + (lam + mu)/2 (J - 1)^2 is formed
+    // to the precision of Psi itself rather than of mu
+    const FF off2 = ff_add(ff_add(ff_mul(s12, s12), ff_mul(s02, s02)), ff_mul(s01, s01));
+    const FF nD2 = ff_add(ff_add(ff_add(ff_mul(d0, d0), ff_mul(d1, d1)), ff_mul(d2, d2)), ff_scale2(off2, 2.f));
+    const FF I2 = ff_sub(ff_add(ff_add(ff_mul(d0, d1), ff_mul(d0, d2)), ff_mul(d1, d2)), off2);
+    const FF I3 = ff_add(ff_add(ff_mul(d0, ff_sub(ff_mul(d1, d2), ff_mul(s12, s12))),
+                                ff_mul(s01, ff_sub(ff_mul(s12, s02), ff_mul(s01, d2)))),
+                         ff_mul(s02, ff_sub(ff_mul(s01, s12), ff_mul(d1, s02))));
+    const FF J1 = ff_add(ff_add(ff_add(ff_add(d0, d1), d2), I2), I3);   // J - 1
+    const FF ls = ff_add(lam, mu);
+    const FF psi = ff_add(ff_sub(ff_scale2(ff_mul(mu, nD2), 0.5f), ff_mul(mu, ff_add(I2, I3))),
+                          ff_scale2(ff_mul(ls, ff_mul(J1, J1)), 0.5f));
+    const FF kk = ff_sub(ff_mul(ls, J1), mu);
+    const FF sg[6] = {ff_add(ff_mul(mu, a), ff_mul(kk, c00)),   ff_add(ff_mul(mu, b), ff_mul(kk, c11)),
+                      ff_add(ff_mul(mu, c), ff_mul(kk, c22)),   ff_add(ff_mul(mu, s12), ff_mul(kk, c12)),
+                      ff_add(ff_mul(mu, s02), ff_mul(kk, c02)), ff_add(ff_mul(mu, s01), ff_mul(kk, c01))};
+#pragma unroll
+    for (int i = 0; i < 6; ++i) sig[i] = sg[i].hi + sg[i].lo;
+    return psi;
+}
+
+// SNH Hessian from an FP32 stretch (the float-float path's; same formulas as
+// snh_hessian below with every operand in FP32)
+__device__ void snh_hessian_f(const float (&S)[6], float mu, float lam, float (&C)[6][6]) {
+    const float a = S[0], b = S[1], c = S[2];
+    const float sq2 = (float)1.4142135623730951, is2 = (float)0.7071067811865476;
+    const float d = sq2 * S[3], e = sq2 * S[4], f = sq2 * S[5];
+    const float ls = lam + mu;
+    const float J = a * b * c + d * e * f * is2 - 0.5f * (a * d * d + b * e * e + c * f * f);
+    const float j[6] = {b * c - 0.5f * d * d, a * c - 0.5f * e * e, a * b - 0.5f * f * f,
+                        e * f * is2 - a * d,   d * f * is2 - b * e,   d * e * is2 - c * f};
+    float HJ[6][6];
+#pragma unroll
+    for (int p = 0; p < 6; ++p)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) HJ[p][q] = 0.f;
+    HJ[0][1] = HJ[1][0] = c;
+    HJ[0][2] = HJ[2][0] = b;
+    HJ[1][2] = HJ[2][1] = a;
+    HJ[0][3] = HJ[3][0] = -d;
+    HJ[1][4] = HJ[4][1] = -e;
+    HJ[2][5] = HJ[5][2] = -f;
+    HJ[3][3] = -a;
+    HJ[4][4] = -b;
+    HJ[5][5] = -c;
+    HJ[3][4] = HJ[4][3] = f * is2;
+    HJ[3][5] = HJ[5][3] = e * is2;
+    HJ[4][5] = HJ[5][4] = d * is2;
+    const float k = ls * (J - 1.f) - mu;
+#pragma unroll
+    for (int p = 0; p < 6; ++p)
+#pragma unroll
+        for (int q = 0; q < 6; ++q) C[p][q] = k * HJ[p][q] + ls * j[p] * j[q] + (p == q ? mu : 0.f);
+}
+
 // ---- SNH Hessian in Mandel coordinates, SPD filtering ----------------------
 // s = (a, b, c, d, e, f) = (S00, S11, S22, sqrt2 S12, sqrt2 S02, sqrt2 S01).
 template <typename RT>
@@ -494,6 +635,18 @@ __device__ __forceinline__ const double (*stage_pose(double (*qs)[9], const doub
     return qs;
 }
 
+// The same as float pairs, in the same shared memory (8 bytes per entry).
+__device__ __forceinline__ const float2 (*stage_pose_ff(float2 (*qs)[9], const double* __restrict__ xf, int H))[9] {
+    if (H > kMaxStagedHandles) return nullptr;
+    for (int i = threadIdx.x; i < 9 * H; i += blockDim.x) {
+        const int h = i / 9, e = i - 9 * h;
+        const FF v = ff_split(xf[12 * h + 4 * (e / 3) + e % 3]);
+        qs[h][e] = make_float2(v.hi, v.lo);
+    }
+    __syncthreads();
+    return qs;
+}
+
 // Energy terms that live on vertex v at position y: -f_v . y for an external
 // force (§4, "Collision response") and k_s/2 |y - x_p|^2 for a pin under the
 // penalty form of Eq. 6.
@@ -523,6 +676,17 @@ __device__ __forceinline__ double vertex_energy(const ElemArgs& A, int b, int v,
 constexpr int kStageWords = 32 * kKe;   // floats per warp: 32 records of blocks (or 32 x 12 doubles of forces)
 static_assert(kStageWords >= 32 * 12 * 2, "the force stage fits");
 
+// Positions of the active problems as float pairs (hi = x rounded to FP32,
+// lo = x - hi rounded), read by the float-float element path.
+__global__ void k_x_split(ElemArgs A) {
+    const int b = blockIdx.y;
+    if (!A.slot.active[b]) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 3 * A.mesh.n) return;
+    const FF v = ff_split(A.slot.x[(size_t)b * A.mesh.n * 3 + i]);
+    A.slot.xff[(size_t)b * A.mesh.n * 3 + i] = make_float2(v.hi, v.lo);
+}
+
 template <typename KT, int MODEL, bool HESS>
 __global__ void __launch_bounds__(kTetTile, 4) k_element(ElemArgs A) {
     __shared__ double qsh[kMaxStagedHandles][9];
@@ -536,12 +700,77 @@ __global__ void __launch_bounds__(kTetTile, 4) k_element(ElemArgs A) {
     const int k0 = k - lane;                         // the warp's first tet
     const int nvalid = max(0, min(32, m - k0));      // tets of this warp
     const double* xf = A.slot.xf + (size_t)b * M.H * 12;
-    const double(*qs)[9] = stage_pose(qsh, xf, M.H);
+    // mixed path at newton_tol >= kF32ForcesTol with rig rotations: F, S,
+    // stress and energy in float-float from the positions' float pairs
+    const bool ffp = sizeof(KT) == 4 && A.ff_elem;   // uniform
+    const double(*qs)[9] = ffp ? nullptr : stage_pose(qsh, xf, M.H);
+    const float2(*qsf)[9] = ffp ? stage_pose_ff(reinterpret_cast<float2(*)[9]>(qsh), xf, M.H) : nullptr;
     double en[1] = {0.0};
     double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6], sig[6];
     double mu = 0.0, lam = 0.0, w = 0.0;
+    FF Sff[6], Qff[3][3], muf{0.f, 0.f}, lamf{0.f, 0.f};
     double* gs = reinterpret_cast<double*>(stage[warp]);   // [32][12] forces
-    if (k < m) {
+    if (ffp && k < m) {
+        const float2* xp = A.slot.xff + (size_t)b * n * 3;
+        const int4 tv = M.tet[k];
+        const int id[4] = {tv.x, tv.y, tv.z, tv.w};
+        FF xa4[4][3], Gff[3][3];
+#pragma unroll
+        for (int a = 0; a < 4; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float2 v = xp[3 * (size_t)id[a] + i];
+                xa4[a][i] = FF{v.x, v.y};
+            }
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                Gff[r][c] = FF{M.Dminv32[(size_t)(3 * r + c) * m + k], M.Dminv_lo[(size_t)(3 * r + c) * m + k]};
+        const int h = M.cluster[k];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (qsf) {
+                    const float2 v = qsf[h][3 * i + j];
+                    Qff[i][j] = FF{v.x, v.y};
+                } else {
+                    Qff[i][j] = ff_split(xf[12 * h + 4 * i + j]);
+                }
+            }
+        stretch_ff(xa4, Gff, Qff, Sff);
+        const float4 ml = M.mulam_ff[k];
+        muf = FF{ml.x, ml.y};
+        lamf = FF{ml.z, ml.w};
+        w = M.vol[k];
+        float sg[6];
+        const FF psi = psi_sigma_ff<MODEL>(Sff, muf, lamf, sg);
+        en[0] = w * ((double)psi.hi + (double)psi.lo);
+        // forces f_a = W Q sigma G_a in FP32 from the stress (as on the FP32-force path)
+        const float wf = (float)w;
+        const float sw[3][3] = {{wf * sg[0], wf * sg[5], wf * sg[4]},
+                                {wf * sg[5], wf * sg[1], wf * sg[3]},
+                                {wf * sg[4], wf * sg[3], wf * sg[2]}};
+        float P[3][3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int j = 0; j < 3; ++j)
+                P[i][j] = Qff[i][0].hi * sw[0][j] + Qff[i][1].hi * sw[1][j] + Qff[i][2].hi * sw[2][j];
+        double* gl = gs + 12 * lane;
+        float f0[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                const float f = P[i][0] * Gff[a][0].hi + P[i][1] * Gff[a][1].hi + P[i][2] * Gff[a][2].hi;
+                gl[3 * (a + 1) + i] = (double)f;
+                f0[i] -= f;
+            }
+#pragma unroll
+        for (int i = 0; i < 3; ++i) gl[i] = (double)f0[i];
+    } else if (k < m) {
         const double* x = A.slot.x + (size_t)b * n * 3;
         const int4 tv = M.tet[k];
         gather_x<float>(x, nullptr, 0.0, tv, xa);
@@ -630,15 +859,17 @@ __global__ void __launch_bounds__(kTetTile, 4) k_element(ElemArgs A) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 Gk[r + 1][c] = sizeof(KT) == 4 ? (KT)M.Dminv32[(size_t)(3 * r + c) * m + k] : (KT)G[r + 1][c];
-                Qk[r][c] = (KT)Q[r][c];
+                Qk[r][c] = ffp ? (KT)Qff[r][c].hi : (KT)Q[r][c];
             }
 #pragma unroll
         for (int c = 0; c < 3; ++c) Gk[0][c] = -(Gk[1][c] + Gk[2][c] + Gk[3][c]);
         if (MODEL == 2) {
             bool fp64 = sizeof(KT) == 8;
+            float sf[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) sf[i] = ffp ? Sff[i].hi : (float)S[i];
             if (!fp64) {  // near-degenerate or inverted stretch: FP64 Hessian
-                const float s0 = (float)S[0], s1 = (float)S[1], s2 = (float)S[2];
-                const float s3 = (float)S[3], s4 = (float)S[4], s5 = (float)S[5];
+                const float s0 = sf[0], s1 = sf[1], s2 = sf[2], s3 = sf[3], s4 = sf[4], s5 = sf[5];
                 const float J = s0 * (s1 * s2 - s3 * s3) + s5 * (s4 * s3 - s2 * s5) + s4 * (s5 * s3 - s1 * s4);
                 fp64 = J < (float)kFallbackJ;
             }
@@ -647,17 +878,25 @@ __global__ void __launch_bounds__(kTetTile, 4) k_element(ElemArgs A) {
                 // the Hessian of a strongly strained tet in FP64 (its terms cancel);
                 // the SPD filter of the result in the kernel's precision (GB300 runs
                 // FP64 at a small fraction of FP32, and the filter needs no more)
-                double Cd[6][6];
-                snh_hessian<double>(S, mu, lam, Cd);
+                double Cd[6][6], Sd[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) Sd[i] = ffp ? (double)Sff[i].hi + (double)Sff[i].lo : S[i];
+                snh_hessian<double>(Sd, ffp ? M.mu[k] : mu, ffp ? M.lam[k] : lam, Cd);
 #pragma unroll
                 for (int p = 0; p < 6; ++p)
 #pragma unroll
                     for (int q = 0; q < 6; ++q) C[p][q] = (KT)Cd[p][q];
+            } else if (ffp) {
+                snh_hessian_f(sf, muf.hi, lamf.hi, reinterpret_cast<float(&)[6][6]>(C));
             } else {
                 snh_hessian<KT>(S, mu, lam, C);
             }
-            if (!chol_shifted_ok<KT>(C, (KT)(kSpdEps * mu))) filter_spd<KT>(C, (KT)(kSpdEps * mu));
+            const KT floor = ffp ? (KT)((float)kSpdEps * muf.hi) : (KT)(kSpdEps * mu);
+            if (!chol_shifted_ok<KT>(C, floor)) filter_spd<KT>(C, floor);
             blocks_generic<KT>(C, Gk, Qk, (KT)w, ke);
+        } else if (ffp) {
+            const float wf = (float)w;
+            blocks_quadratic<KT>(Gk, Qk, (KT)(wf * muf.hi), (KT)(MODEL == 1 ? wf * lamf.hi : 0.f), ke);
         } else {
             blocks_quadratic<KT>(Gk, Qk, (KT)(w * mu), (KT)(w * (MODEL == 1 ? lam : 0.0)), ke);
         }
@@ -908,8 +1147,12 @@ void launch_warm_step(const ElemArgs& a, int B, int apply, cudaStream_t s) {
 }
 
 void launch_element(const ElemArgs& a, int B, cudaStream_t s, bool hess) {
-    if (a.slot.prec == 1) launch_element_t<float>(a, B, hess, s);
-    else launch_element_t<double>(a, B, hess, s);
+    if (a.slot.prec == 1) {
+        if (a.ff_elem) k_x_split<<<dim3((3 * a.mesh.n + 255) / 256, B), 256, 0, s>>>(a);
+        launch_element_t<float>(a, B, hess, s);
+    } else {
+        launch_element_t<double>(a, B, hess, s);
+    }
 }
 
 void launch_energy_trial(const ElemArgs& a, int B, cudaStream_t s) {

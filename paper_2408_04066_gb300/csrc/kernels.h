@@ -15,6 +15,8 @@ struct MeshDev {
     int4* tet = nullptr;          // [m]
     double* Dminv64 = nullptr;    // [9][m]
     float* Dminv32 = nullptr;     // [9][m]
+    float* Dminv_lo = nullptr;    // [9][m] D_m^{-1} - Dminv32 (the float pair's low part)
+    float4* mulam_ff = nullptr;   // [m] (mu, lam) as float pairs: (mu_hi, mu_lo, lam_hi, lam_lo)
     double* vol = nullptr;        // [m]
     int* cluster = nullptr;       // [m]
     double* mu = nullptr;         // [m]
@@ -53,6 +55,7 @@ struct SlotDev {
     double* xpred = nullptr;    // [B][n][3] x after the predictor step of the last solve (WARM only)
     double* dcorr = nullptr;    // [B][n][3] last solve's solution minus xpred (WARM only)
     double* x = nullptr;     // [B][n][3]
+    float2* xff = nullptr;   // [B][n][3] x as float pairs (hi, lo), refreshed before each mixed element pass
     double* xprev = nullptr; // [B][n][3] x before a speculative full Newton step (line-searched models)
     double* xp = nullptr;    // [B][n][3] pin targets (pinned rows only)
     double* g = nullptr;     // [B][n][3] masked gradient
@@ -88,6 +91,7 @@ struct ElemArgs {
     int64_t fext_stride = 0;       // doubles between problems' force fields (0: one shared field)
     int rot_polar = 0;             // 1: R_k = rotation factor of F_k (co-rotational FEM), else the rig's
     int f32_forces = 0;            // mixed path: element forces formed in FP32 from the FP64 stress
+    int ff_elem = 0;               // mixed path: F, S, stress and energy in float-float arithmetic (xff)
 };
 // The mixed path forms element forces in FP32 when the Newton stop test is at
 // least this loose: the FP32 forces leave a residual floor near 1e-8 of the
