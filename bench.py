@@ -550,9 +550,11 @@ def run_mfem(args, dist):
             "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.precision == "mixed" else "f64",
             "dtype_note": ("mixed: FP32 element Hessians, matrix, SpMV and PCG vectors; FP64 positions, "
-                           "deformation gradients, stretches, stresses, the gradient sum (the Newton residual), "
-                           "stop test and line-search energies; element forces formed in FP32 from the FP64 stress "
-                           "(newton_tol >= 1e-7; tighter tests keep them in FP64); PCG inner products "
+                           "the gradient sum (the Newton residual), stop test and line-search trial energies; "
+                           "deformation gradients, stretches, stresses and element energies in float-float "
+                           "(FP32 pairs, ~48 bits) from float pairs of the FP64 positions, element forces in FP32 "
+                           "from that stress (newton_tol >= 1e-7; tighter tests keep all of these in FP64); "
+                           "PCG inner products "
                            "as float-float (Dekker/Knuth error-free FP32 pairs, ~48 bits) per row and warp, "
                            "then FP64; coarse solve BF16 x 3-part BF16 split on the tensor cores, FP32 "
                            "accumulation" if args.precision == "mixed" else "FP64 throughout except the "

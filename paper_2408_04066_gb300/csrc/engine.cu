@@ -70,7 +70,9 @@ ElemArgs elem_args(const mfem_ctx* c) {
     a.fext_stride = c->fext_sets > 1 ? 3 * (int64_t)c->plan.n : 0;
     a.rot_polar = c->opt.rotation == MFEM_ROT_POLAR ? 1 : 0;
     a.f32_forces = c->slot.prec == 1 && c->opt.newton_tol >= kF32ForcesTol ? 1 : 0;
-    a.ff_elem = a.f32_forces && !a.rot_polar && c->slot.xff && c->mesh.Dminv_lo && c->mesh.mulam_ff ? 1 : 0;
+    a.ff_elem = a.f32_forces && !a.rot_polar && c->slot.xff && c->slot.qff && c->mesh.Dminv_lo && c->mesh.mulam_ff
+                    ? 1
+                    : 0;
     return a;
 }
 
@@ -93,7 +95,7 @@ mfem_status upload(mfem_ctx* c, U** dst, const U* src, size_t count) {
 void free_slots(mfem_ctx* c) {
     SlotDev& S = c->slot;
     void* ptrs[] = {S.xf, S.xf_prev, S.xpred, S.dcorr, S.tol2, S.coarse_on, S.rcp, S.ec, S.rcs, S.aggq, S.bsplit,
-                    S.x, S.xff, S.xprev, S.xp,
+                    S.x, S.xff, S.qff, S.xprev, S.xp,
                     S.g, S.ge, S.Ke, S.val, S.dinv, S.vec, S.part, S.sc, S.active, S.alpha, S.outbuf};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -115,7 +117,7 @@ size_t bytes_per_slot(const mfem_ctx* c) {
     const size_t n = c->plan.n, m = c->plan.m, H = c->plan.H;
     const size_t kt = c->slot.prec == 1 ? 4 : 8;
     const size_t slots = (size_t)c->plan.slice_ptr.back();
-    return H * 12 * 8 + 4 * n * 3 * 8 + (kt == 4 ? n * 3 * 8 : 0) + m * 12 * 8 + m * kKe * kt + slots * 9 * kt +
+    return H * 12 * 8 + 4 * n * 3 * 8 + (kt == 4 ? n * 3 * 8 + H * 9 * 8 : 0) + m * 12 * 8 + m * kKe * kt + slots * 9 * kt +
            9 * npad32((int)n) * kt +
            kVecStride * npad32((int)n) * kt + (size_t)part_tiles_for(c) * 4 * 8 + sizeof(ProbScal) + 4 + 8 + 8 +
            H * 12 * 8 + (c->opt.init == MFEM_INIT_WARM ? 2 * n * 3 * 8 : 0) + 4 + (line_search(c) ? n * 3 * 8 : 0) +
@@ -146,7 +148,10 @@ mfem_status alloc_slots(mfem_ctx* c, int B) {
         AL(S.dcorr, B * n * 3 * 8);
     }
     AL(S.x, B * n * 3 * 8);
-    if (S.prec == 1) AL(S.xff, B * n * 3 * sizeof(float2));
+    if (S.prec == 1) {
+        AL(S.xff, B * n * 3 * sizeof(float2));
+        AL(S.qff, B * H * 9 * sizeof(float2));
+    }
     if (line_search(c)) AL(S.xprev, B * n * 3 * 8);
     AL(S.xp, B * n * 3 * 8);
     AL(S.g, B * n * 3 * 8);
@@ -1385,9 +1390,9 @@ mfem_status mfem_create(const double* rest_verts, int32_t n, const int32_t* tets
             Dm32[(size_t)e * P.m + k] = (float)v;
             DmLo[(size_t)e * P.m + k] = (float)(v - (double)(float)v);
         }
-    std::vector<float> mulam((size_t)4 * P.m);   // (mu, lam) as float pairs
+    std::vector<float> mulam((size_t)4 * P.m);   // (W mu, W lam) as float pairs
     for (int k = 0; k < P.m; ++k) {
-        const double mu = P.mu[k], lam = P.lam[k];
+        const double mu = P.vol[k] * P.mu[k], lam = P.vol[k] * P.lam[k];
         mulam[4 * (size_t)k] = (float)mu;
         mulam[4 * (size_t)k + 1] = (float)(mu - (double)(float)mu);
         mulam[4 * (size_t)k + 2] = (float)lam;

@@ -129,7 +129,6 @@ __device__ __forceinline__ double psi_sigma(const double (&S)[6], double mu, dou
 // pairs, so that the element pass needs almost no FP64 instructions (GB300
 // issues FP64 at a small fraction of its FP32 rate).  Only the energy's
 // weighting and sum stay FP64.
-__device__ __forceinline__ FF ff_from(float hi, float lo) { return FF{hi, lo}; }
 __device__ __forceinline__ FF ff_split(double v) {
     const float h = (float)v;
     return FF{h, (float)(v - (double)h)};
@@ -146,6 +145,19 @@ __device__ __forceinline__ FF ff_mul(FF a, FF b) {
 }
 __device__ __forceinline__ FF ff_scale2(FF a, float s) { return FF{a.hi * s, a.lo * s}; }   // s a power of two
 __device__ __forceinline__ FF ff_addf(FF a, float b) { return ff_add(a, FF{b, 0.f}); }
+
+// float -> double by the IEEE 754 bit layouts (binary32: 1 + 8 + 23 bits,
+// binary64: 1 + 11 + 52; the exponent bias grows by 1023 - 127 = 896 and the
+// fraction moves up 29 bits) on the integer pipe: the conversion instruction
+// runs on GB300's narrow FP64 pipe.  Zero, subnormals, infinities and NaN take
+// the ordinary conversion.
+__device__ __forceinline__ double f2d_exact(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
+    return __hiloint2double((int)hi, (int)(u << 29));
+}
 
 // S = sym(Q^T F), F = sum_a (x_a - x_0) G_a^T (a = 1..3), all as float pairs;
 // G[r] = row r of D_m^{-1} (G_{r+1}).
@@ -635,14 +647,11 @@ __device__ __forceinline__ const double (*stage_pose(double (*qs)[9], const doub
     return qs;
 }
 
-// The same as float pairs, in the same shared memory (8 bytes per entry).
-__device__ __forceinline__ const float2 (*stage_pose_ff(float2 (*qs)[9], const double* __restrict__ xf, int H))[9] {
-    if (H > kMaxStagedHandles) return nullptr;
-    for (int i = threadIdx.x; i < 9 * H; i += blockDim.x) {
-        const int h = i / 9, e = i - 9 * h;
-        const FF v = ff_split(xf[12 * h + 4 * (e / 3) + e % 3]);
-        qs[h][e] = make_float2(v.hi, v.lo);
-    }
+// The float pairs of the rotations (split once per problem by k_x_split), in
+// the same shared memory (8 bytes per entry); global memory past the limit.
+__device__ __forceinline__ const float2 (*stage_pose_ff(float2 (*qs)[9], const float2* __restrict__ qff, int H))[9] {
+    if (H > kMaxStagedHandles) return reinterpret_cast<const float2(*)[9]>(qff);
+    for (int i = threadIdx.x; i < 9 * H; i += blockDim.x) qs[i / 9][i % 9] = qff[i];
     __syncthreads();
     return qs;
 }
@@ -676,15 +685,23 @@ __device__ __forceinline__ double vertex_energy(const ElemArgs& A, int b, int v,
 constexpr int kStageWords = 32 * kKe;   // floats per warp: 32 records of blocks (or 32 x 12 doubles of forces)
 static_assert(kStageWords >= 32 * 12 * 2, "the force stage fits");
 
-// Positions of the active problems as float pairs (hi = x rounded to FP32,
-// lo = x - hi rounded), read by the float-float element path.
+// Positions and handle rotations of the active problems as float pairs (hi =
+// the value rounded to FP32, lo = the remainder rounded), read by the
+// float-float element path.
 __global__ void k_x_split(ElemArgs A) {
     const int b = blockIdx.y;
     if (!A.slot.active[b]) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= 3 * A.mesh.n) return;
-    const FF v = ff_split(A.slot.x[(size_t)b * A.mesh.n * 3 + i]);
-    A.slot.xff[(size_t)b * A.mesh.n * 3 + i] = make_float2(v.hi, v.lo);
+    if (i < 3 * A.mesh.n) {
+        const FF v = ff_split(A.slot.x[(size_t)b * A.mesh.n * 3 + i]);
+        A.slot.xff[(size_t)b * A.mesh.n * 3 + i] = make_float2(v.hi, v.lo);
+    }
+    const int H = A.mesh.H;
+    if (i < 9 * H) {
+        const int h = i / 9, e = i - 9 * h;
+        const FF v = ff_split(A.slot.xf[((size_t)b * H + h) * 12 + 4 * (e / 3) + e % 3]);
+        A.slot.qff[(size_t)b * H * 9 + i] = make_float2(v.hi, v.lo);
+    }
 }
 
 template <typename KT, int MODEL, bool HESS>
@@ -704,8 +721,10 @@ __global__ void __launch_bounds__(kTetTile, 4) k_element(ElemArgs A) {
     // stress and energy in float-float from the positions' float pairs
     const bool ffp = sizeof(KT) == 4 && A.ff_elem;   // uniform
     const double(*qs)[9] = ffp ? nullptr : stage_pose(qsh, xf, M.H);
-    const float2(*qsf)[9] = ffp ? stage_pose_ff(reinterpret_cast<float2(*)[9]>(qsh), xf, M.H) : nullptr;
+    const float2(*qsf)[9] =
+        ffp ? stage_pose_ff(reinterpret_cast<float2(*)[9]>(qsh), A.slot.qff + (size_t)b * M.H * 9, M.H) : nullptr;
     double en[1] = {0.0};
+    FF enf{0.f, 0.f};   // the float-float path's energy
     double xa[4][3], G[4][3], Q[3][3], F[3][3], S[6], sig[6];
     double mu = 0.0, lam = 0.0, w = 0.0;
     FF Sff[6], Qff[3][3], muf{0.f, 0.f}, lamf{0.f, 0.f};
@@ -732,26 +751,18 @@ __global__ void __launch_bounds__(kTetTile, 4) k_element(ElemArgs A) {
         for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
-                if (qsf) {
-                    const float2 v = qsf[h][3 * i + j];
-                    Qff[i][j] = FF{v.x, v.y};
-                } else {
-                    Qff[i][j] = ff_split(xf[12 * h + 4 * i + j]);
-                }
+                const float2 v = qsf[h][3 * i + j];
+                Qff[i][j] = FF{v.x, v.y};
             }
         stretch_ff(xa4, Gff, Qff, Sff);
+        // (W mu, W lam): Psi, sigma and the Hessian below come out weighted by W
         const float4 ml = M.mulam_ff[k];
         muf = FF{ml.x, ml.y};
         lamf = FF{ml.z, ml.w};
-        w = M.vol[k];
         float sg[6];
-        const FF psi = psi_sigma_ff<MODEL>(Sff, muf, lamf, sg);
-        en[0] = w * ((double)psi.hi + (double)psi.lo);
+        enf = psi_sigma_ff<MODEL>(Sff, muf, lamf, sg);
         // forces f_a = W Q sigma G_a in FP32 from the stress (as on the FP32-force path)
-        const float wf = (float)w;
-        const float sw[3][3] = {{wf * sg[0], wf * sg[5], wf * sg[4]},
-                                {wf * sg[5], wf * sg[1], wf * sg[3]},
-                                {wf * sg[4], wf * sg[3], wf * sg[2]}};
+        const float sw[3][3] = {{sg[0], sg[5], sg[4]}, {sg[5], sg[1], sg[3]}, {sg[4], sg[3], sg[2]}};
         float P[3][3];
 #pragma unroll
         for (int i = 0; i < 3; ++i)
@@ -765,11 +776,11 @@ __global__ void __launch_bounds__(kTetTile, 4) k_element(ElemArgs A) {
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
                 const float f = P[i][0] * Gff[a][0].hi + P[i][1] * Gff[a][1].hi + P[i][2] * Gff[a][2].hi;
-                gl[3 * (a + 1) + i] = (double)f;
+                gl[3 * (a + 1) + i] = f2d_exact(f);
                 f0[i] -= f;
             }
 #pragma unroll
-        for (int i = 0; i < 3; ++i) gl[i] = (double)f0[i];
+        for (int i = 0; i < 3; ++i) gl[i] = f2d_exact(f0[i]);
     } else if (k < m) {
         const double* x = A.slot.x + (size_t)b * n * 3;
         const int4 tv = M.tet[k];
@@ -881,7 +892,11 @@ __global__ void __launch_bounds__(kTetTile, 4) k_element(ElemArgs A) {
                 double Cd[6][6], Sd[6];
 #pragma unroll
                 for (int i = 0; i < 6; ++i) Sd[i] = ffp ? (double)Sff[i].hi + (double)Sff[i].lo : S[i];
-                snh_hessian<double>(Sd, ffp ? M.mu[k] : mu, ffp ? M.lam[k] : lam, Cd);
+                if (ffp) {   // weighted by W, as the float-float path's Hessian
+                    mu = (double)muf.hi + (double)muf.lo;
+                    lam = (double)lamf.hi + (double)lamf.lo;
+                }
+                snh_hessian<double>(Sd, mu, lam, Cd);
 #pragma unroll
                 for (int p = 0; p < 6; ++p)
 #pragma unroll
@@ -893,10 +908,9 @@ __global__ void __launch_bounds__(kTetTile, 4) k_element(ElemArgs A) {
             }
             const KT floor = ffp ? (KT)((float)kSpdEps * muf.hi) : (KT)(kSpdEps * mu);
             if (!chol_shifted_ok<KT>(C, floor)) filter_spd<KT>(C, floor);
-            blocks_generic<KT>(C, Gk, Qk, (KT)w, ke);
+            blocks_generic<KT>(C, Gk, Qk, ffp ? (KT)1 : (KT)w, ke);
         } else if (ffp) {
-            const float wf = (float)w;
-            blocks_quadratic<KT>(Gk, Qk, (KT)(wf * muf.hi), (KT)(MODEL == 1 ? wf * lamf.hi : 0.f), ke);
+            blocks_quadratic<KT>(Gk, Qk, (KT)muf.hi, (KT)(MODEL == 1 ? lamf.hi : 0.f), ke);
         } else {
             blocks_quadratic<KT>(Gk, Qk, (KT)(w * mu), (KT)(w * (MODEL == 1 ? lam : 0.0)), ke);
         }
@@ -907,14 +921,20 @@ __global__ void __launch_bounds__(kTetTile, 4) k_element(ElemArgs A) {
         float2* dst = reinterpret_cast<float2*>((float*)A.slot.Ke + ((size_t)b * m + k0) * kKe);
         for (int i = lane; i < (kKe / 2) * nvalid; i += 32) dst[i] = src[i];
     }
-    if (k < n) {
+    const bool vterms = A.fext || A.constraint == 1;   // uniform
+    if (k < n && (vterms || !ffp)) {
         const double* xv = A.slot.x + ((size_t)b * n + k) * 3;
         const double y[3] = {xv[0], xv[1], xv[2]};
-        en[0] += vertex_energy(A, b, k, y);
+        const double ev = vertex_energy(A, b, k, y);
+        if (ffp) enf = ff_add(enf, ff_split(ev));
+        else en[0] += ev;
     }
+    // the float-float path sums its warp's energies in float-float and enters
+    // the block sum with the warp's total (FP64 from there on)
+    if (ffp) en[0] = ff_warp_sum(enf);
     double tot[1];
     double* part = A.slot.part + (size_t)b * A.slot.part_tiles * 4;
-    if (tile_commit<1>(en, part, blockIdx.x, gridDim.x, &A.slot.sc[b].tk_e, 0, tot) && threadIdx.x == 0)
+    if (tile_commit<1>(en, part, blockIdx.x, gridDim.x, &A.slot.sc[b].tk_e, 0, tot, ffp) && threadIdx.x == 0)
         A.slot.sc[b].energy = tot[0];
 }
 
@@ -1148,7 +1168,7 @@ void launch_warm_step(const ElemArgs& a, int B, int apply, cudaStream_t s) {
 
 void launch_element(const ElemArgs& a, int B, cudaStream_t s, bool hess) {
     if (a.slot.prec == 1) {
-        if (a.ff_elem) k_x_split<<<dim3((3 * a.mesh.n + 255) / 256, B), 256, 0, s>>>(a);
+        if (a.ff_elem) k_x_split<<<dim3((max(3 * a.mesh.n, 9 * a.mesh.H) + 255) / 256, B), 256, 0, s>>>(a);
         launch_element_t<float>(a, B, hess, s);
     } else {
         launch_element_t<double>(a, B, hess, s);

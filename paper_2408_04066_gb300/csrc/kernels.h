@@ -16,7 +16,8 @@ struct MeshDev {
     double* Dminv64 = nullptr;    // [9][m]
     float* Dminv32 = nullptr;     // [9][m]
     float* Dminv_lo = nullptr;    // [9][m] D_m^{-1} - Dminv32 (the float pair's low part)
-    float4* mulam_ff = nullptr;   // [m] (mu, lam) as float pairs: (mu_hi, mu_lo, lam_hi, lam_lo)
+    float4* mulam_ff = nullptr;   // [m] (W mu, W lam) as float pairs: (hi, lo, hi, lo); Psi, sigma and
+                                  // the Hessian are linear in (mu, lam), so they come out weighted by W
     double* vol = nullptr;        // [m]
     int* cluster = nullptr;       // [m]
     double* mu = nullptr;         // [m]
@@ -56,6 +57,7 @@ struct SlotDev {
     double* dcorr = nullptr;    // [B][n][3] last solve's solution minus xpred (WARM only)
     double* x = nullptr;     // [B][n][3]
     float2* xff = nullptr;   // [B][n][3] x as float pairs (hi, lo), refreshed before each mixed element pass
+    float2* qff = nullptr;   // [B][H][9] handle rotations as float pairs, refreshed with xff
     double* xprev = nullptr; // [B][n][3] x before a speculative full Newton step (line-searched models)
     double* xp = nullptr;    // [B][n][3] pin targets (pinned rows only)
     double* g = nullptr;     // [B][n][3] masked gradient
