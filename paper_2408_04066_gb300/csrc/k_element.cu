@@ -147,16 +147,32 @@ __device__ __forceinline__ FF ff_scale2(FF a, float s) { return FF{a.hi * s, a.l
 __device__ __forceinline__ FF ff_addf(FF a, float b) { return ff_add(a, FF{b, 0.f}); }
 
 // float -> double by the IEEE 754 bit layouts (binary32: 1 + 8 + 23 bits,
-// binary64: 1 + 11 + 52; the exponent bias grows by 1023 - 127 = 896 and the
-// fraction moves up 29 bits) on the integer pipe: the conversion instruction
-// runs on GB300's narrow FP64 pipe.  Zero, subnormals, infinities and NaN take
-// the ordinary conversion.
+// binary64: 1 + 11 + 52) in integer instructions only: the conversion
+// instruction runs on GB300's narrow FP64 pipe, and a conversion kept for the
+// rare cases would be if-converted and paid by every lane.  Normal numbers:
+// the exponent bias grows by 1023 - 127 = 896 and the fraction moves up 29
+// bits; a subnormal m 2^-149 with its leading bit at position p - 1 becomes
+// 1.f 2^(p - 150); zeros keep their sign; infinities and NaN keep their
+// fraction bits (a signalling NaN stays signalling).
 __device__ __forceinline__ double f2d_exact(float f) {
     const unsigned u = __float_as_uint(f);
-    const unsigned e = (u >> 23) & 0xffu;
-    if (e == 0u || e == 0xffu) return (double)f;
-    const unsigned hi = (u & 0x80000000u) | ((e + 896u) << 20) | ((u >> 3) & 0xfffffu);
-    return __hiloint2double((int)hi, (int)(u << 29));
+    const unsigned e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+    unsigned long long ed, frac;
+    if (e == 0xffu) {
+        ed = 0x7ffull;
+        frac = (unsigned long long)m << 29;
+    } else if (e != 0u) {
+        ed = e + 896u;
+        frac = (unsigned long long)m << 29;
+    } else if (m == 0u) {
+        ed = 0ull;
+        frac = 0ull;
+    } else {
+        const int p = 32 - __clz((int)m);
+        ed = (unsigned long long)(p + 873);
+        frac = ((unsigned long long)m << (53 - p)) & 0xfffffffffffffull;
+    }
+    return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) | (ed << 52) | frac));
 }
 
 // S = sym(Q^T F), F = sum_a (x_a - x_0) G_a^T (a = 1..3), all as float pairs;

@@ -1,10 +1,10 @@
 """The element kernel widens its FP32 forces to FP64 with integer operations on
 the IEEE 754 bit layouts (`f2d_exact` in k_element.cu) instead of the
 conversion instruction.  The function's own source text is compiled for the
-host here, with the two CUDA bit-cast intrinsics defined by memcpy, and
+host here, with the CUDA bit-cast and leading-zero intrinsics defined in C, and
 compared bit for bit with C's float -> double conversion over a stride of all
 2^32 bit patterns plus the edge cases (signed zeros, subnormals, the largest
-and smallest normals, infinities, NaN)."""
+and smallest normals, infinities, NaN) and every subnormal."""
 import os
 import re
 import shutil
@@ -22,9 +22,8 @@ HARNESS = r"""
 #define __device__
 #define __forceinline__ static inline
 static inline unsigned __float_as_uint(float f) { unsigned u; memcpy(&u, &f, 4); return u; }
-static inline double __hiloint2double(int hi, int lo) {
-    uint64_t b = ((uint64_t)(uint32_t)hi << 32) | (uint32_t)lo; double d; memcpy(&d, &b, 8); return d;
-}
+static inline int __clz(int x) { return x ? __builtin_clz((unsigned)x) : 32; }
+static inline double __longlong_as_double(long long v) { double d; memcpy(&d, &v, 8); return d; }
 %s
 static int same(float f) {
     double a = f2d_exact(f), b = (double)f;
@@ -40,6 +39,11 @@ int main(void) {
     }
     for (uint64_t u = 0; u < (1ull << 32); u += 97) {
         uint32_t v = (uint32_t)u; float f; memcpy(&f, &v, 4); bad += !same(f); ++n;
+    }
+    for (uint32_t v = 0; v < (1u << 23); ++v) {   /* every subnormal, both signs */
+        float f; uint32_t w = v | 0x80000000u;
+        memcpy(&f, &v, 4); bad += !same(f); ++n;
+        memcpy(&f, &w, 4); bad += !same(f); ++n;
     }
     printf("%%lu %%lu\n", n, bad);
     return 0;
@@ -60,5 +64,5 @@ def test_f2d_exact_matches_the_conversion(tmp_path):
     subprocess.run([gcc, "-O2", "-std=c11", str(c), "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
     n, bad = int(out[0]), int(out[1])
-    assert n > 44_000_000
+    assert n > 60_000_000
     assert bad == 0
