@@ -112,6 +112,51 @@ __device__ __forceinline__ void add_block(KT (&acc)[9], int code, const KT (&v)[
 // inverse.  Consecutive threads take consecutive upper slots, so the own
 // writes are nearly coalesced; the mirror writes are scattered.  The gradient
 // gather runs in k_gradient.
+// Block Jacobi: the inverse of a 3x3 diagonal block by its cofactors, entry e
+// written at di[e * np] (one run per entry).  The FP64 path forms it in FP64.
+// The mixed path forms it in FP32 from the block scaled by a power of two
+// (the largest entry into [0.5, 1): no overflow or underflow of the
+// determinant, and the scaling is exact).  It is only the preconditioner, and
+// its matrix is FP32; GB300's FP64 pipe is narrow.
+__device__ __forceinline__ void block_jacobi(const double (&a)[9], double* di, size_t np) {
+    const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+    const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    const double id = det != 0.0 ? 1.0 / det : 0.0;
+    di[0 * np] = c00 * id;
+    di[1 * np] = (a[2] * a[7] - a[1] * a[8]) * id;
+    di[2 * np] = (a[1] * a[5] - a[2] * a[4]) * id;
+    di[3 * np] = c01 * id;
+    di[4 * np] = (a[0] * a[8] - a[2] * a[6]) * id;
+    di[5 * np] = (a[2] * a[3] - a[0] * a[5]) * id;
+    di[6 * np] = c02 * id;
+    di[7 * np] = (a[1] * a[6] - a[0] * a[7]) * id;
+    di[8 * np] = (a[0] * a[4] - a[1] * a[3]) * id;
+}
+__device__ __forceinline__ void block_jacobi(const float (&acc)[9], float* di, size_t np) {
+    float mx = 0.f;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) mx = fmaxf(mx, fabsf(acc[e]));
+    int ex = 0;
+    frexpf(mx, &ex);                       // mx = f 2^ex, f in [0.5, 1)
+    const float sc = ldexpf(1.f, -ex);     // exact power of two
+    float a[9];
+#pragma unroll
+    for (int e = 0; e < 9; ++e) a[e] = acc[e] * sc;
+    const float c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
+    const float det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    // inv(acc) = sc inv(a)
+    const float id = det != 0.f ? sc / det : 0.f;
+    di[0 * np] = c00 * id;
+    di[1 * np] = (a[2] * a[7] - a[1] * a[8]) * id;
+    di[2 * np] = (a[1] * a[5] - a[2] * a[4]) * id;
+    di[3 * np] = c01 * id;
+    di[4 * np] = (a[0] * a[8] - a[2] * a[6]) * id;
+    di[5 * np] = (a[2] * a[3] - a[0] * a[5]) * id;
+    di[6 * np] = c02 * id;
+    di[7 * np] = (a[1] * a[6] - a[0] * a[7]) * id;
+    di[8 * np] = (a[0] * a[4] - a[1] * a[3]) * id;
+}
+
 template <typename KT>
 __global__ void __launch_bounds__(kRowTile) k_assemble_slots(ElemArgs A) {
     const int b = blockIdx.y;
@@ -171,26 +216,7 @@ __global__ void __launch_bounds__(kRowTile) k_assemble_slots(ElemArgs A) {
 #pragma unroll
             for (int j = 0; j < 3; ++j) mout[32 * (3 * i + j)] = acc[3 * j + i];
     }
-    if (diag) {  // block-Jacobi: inverse of the diagonal block, formed in FP64
-        double a[9];
-#pragma unroll
-        for (int e = 0; e < 9; ++e) a[e] = (double)acc[e];
-        const double c00 = a[4] * a[8] - a[5] * a[7], c01 = a[5] * a[6] - a[3] * a[8], c02 = a[3] * a[7] - a[4] * a[6];
-        const double det = a[0] * c00 + a[1] * c01 + a[2] * c02;
-        const double id = det != 0.0 ? 1.0 / det : 0.0;
-        // entry e of the row's inverse at e * npad32(n) + row (one run per entry)
-        KT* di = (KT*)A.slot.dinv + (size_t)b * 9 * npad32(M.n) + row;
-        const size_t np = npad32(M.n);
-        di[0 * np] = (KT)(c00 * id);
-        di[1 * np] = (KT)((a[2] * a[7] - a[1] * a[8]) * id);
-        di[2 * np] = (KT)((a[1] * a[5] - a[2] * a[4]) * id);
-        di[3 * np] = (KT)(c01 * id);
-        di[4 * np] = (KT)((a[0] * a[8] - a[2] * a[6]) * id);
-        di[5 * np] = (KT)((a[2] * a[3] - a[0] * a[5]) * id);
-        di[6 * np] = (KT)(c02 * id);
-        di[7 * np] = (KT)((a[1] * a[6] - a[0] * a[7]) * id);
-        di[8 * np] = (KT)((a[0] * a[4] - a[1] * a[3]) * id);
-    }
+    if (diag) block_jacobi(acc, (KT*)A.slot.dinv + (size_t)b * 9 * npad32(M.n) + row, npad32(M.n));
 }
 
 // Gradient only (a convergence test that needs no matrix): |g_free|^2 per problem.
