@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from oracle import solve as S, diag
-from synth import bar_twist_config, figure_config, identity_pose, rigid_pose, rodrigues, bar_mesh
+from synth import bar_twist_config, character_config, figure_config, identity_pose, rigid_pose, rodrigues, bar_mesh
 
 pytestmark = pytest.mark.gpu
 
@@ -266,3 +266,36 @@ def test_full_size_figure_property_check(mfem):
         # pins sit exactly on their targets
         xp = rig.pin_targets(so.X, so.pin_verts, so.pin_handle, Q, t)
         assert np.abs(xb[b][so.pin_verts] - xp).max() <= 1e-12 * so.bbox_diag
+
+
+def test_rig_above_the_staged_handle_limit(mfem):
+    """Rigs above the element kernels' staged-handle limit (64) read the pose
+    rotations from global memory: an 80-handle character on the 10k-tet
+    capsule mesh, FP64 solved tightly against the oracle, and mixed (the
+    float-float element pass) at the default tolerance by the oracle's FP64
+    gradient and energy at its solutions."""
+    from oracle import element, rig
+    cfg = character_config(10000, n_handles=80, seeds=range(2), max_angle_deg=15.0)
+    assert len(cfg["joints"]) == 80
+    so = S.Setup.from_config(cfg)
+    ctx = mfem.Context.from_config(cfg, precision="fp64", newton_tol=1e-11, cg_tol=1e-9, newton_max=80)
+    ctx.set_pose(cfg["xfs"][0])
+    x, st = ctx.solve()
+    xo, info = S.solve(so, cfg["xfs"][0], "snh", newton_tol=1e-12, newton_max=80)
+    assert st["converged"] == 1, st
+    assert _err(x, xo, so) <= TOL_FP64
+    ctx = mfem.Context.from_config(cfg, precision="mixed", max_batch=2)
+    xb, stb = ctx.solve_batch(cfg["xfs"])
+    for b in range(2):
+        assert stb[b]["converged"] == 1
+        Q, t = rig.unpack_pose(cfg["xfs"][b])
+        args = (so.T, so.G, so.vol, Q[so.cluster], "snh", so.mu, so.lam)
+        g = element.gradient(xb[b], *args)
+        g[so.pin_verts] = 0.0
+        x0 = S.initial_guess(so, Q, t, "rigid")
+        x0[so.pin_verts] = rig.pin_targets(so.X, so.pin_verts, so.pin_handle, Q, t)
+        g0 = element.gradient(x0, *args)
+        g0[so.pin_verts] = 0.0
+        assert np.linalg.norm(g) / np.linalg.norm(g0) <= 1.5e-6
+        en = float(np.sum(element.element_energy(xb[b], *args)))
+        assert abs(stb[b]["energy"] - en) <= 1e-10 * abs(en)
