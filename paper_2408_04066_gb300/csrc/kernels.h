@@ -62,10 +62,10 @@ struct SlotDev {
     double* xp = nullptr;    // [B][n][3] pin targets (pinned rows only)
     double* g = nullptr;     // [B][n][3] masked gradient
     double* ge = nullptr;    // [B][m][12] element forces
-    void* Ke = nullptr;      // [B][m][90]  (float or double)
+    void* Ke = nullptr;      // [B][m][kKe] + kKePad element blocks (float or double)
     void* val = nullptr;     // [B][slots*9]
     void* dinv = nullptr;    // [B][9][npad32(n)] block-Jacobi inverses, entry-major
-    void* vec = nullptr;     // [B][6][n][3]: dx r z p0 p1 q
+    void* vec = nullptr;     // [B][kVecStride][npad32(n)]: the neighbour record nb and the six row fields
     double* part = nullptr;  // [B][tiles][4]
     int part_tiles = 0;
     ProbScal* sc = nullptr;  // [B]
