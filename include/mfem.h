@@ -186,7 +186,9 @@ typedef struct {
     int32_t converged;       /* 1 if |g_free| <= newton_tol |g_free(x_0)| */
     double grad0;            /* |g_free(x_0)|, FP64 */
     double rel_grad;         /* final |g_free| / grad0, FP64 */
-    double energy;           /* final E(x), FP64 */
+    double energy;           /* final E(x): FP64 sum of the element energies (formed in
+                                float-float on the mixed path at newton_tol >= 1e-7,
+                                in FP64 otherwise) */
     int32_t inverted;        /* tets with det F <= 0 (diagnostics=1) */
     double max_rel_skew;     /* max |skew(R^T F)| / |F| (diagnostics=1) */
     double max_angle;        /* max angle (rad) between R_k and polar(F_k) (diagnostics=1) */
